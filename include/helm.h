@@ -1,0 +1,170 @@
+/*
+ * helm.h -- C ABI of libhelm, a single-GPU (sm_103a) matrix-free solver for the 3D
+ * heterogeneous Helmholtz equation, preconditioned by the Complex Shifted Laplace
+ * Preconditioner (CSLP) and one geometric-multigrid V-cycle.
+ *
+ * Method: Chen, Dwarka & Vuik, "A matrix-free parallel solution method for the
+ * three-dimensional heterogeneous Helmholtz equation" (arXiv 2308.06085).
+ *
+ * Problem (Sec. 2): -Lap u - k(x)^2 u = b on a box of n1 x n2 x n3 intervals of equal
+ * spacing h, with either homogeneous Dirichlet values or the first-order Sommerfeld
+ * condition du/dn - i k u = 0 on every face.
+ *
+ * Grid and vector layout (shared by every entry point):
+ *   - Unknowns per direction: N_d = n_d - 1 (Dirichlet, interior nodes 1..n_d-1) or
+ *     N_d = n_d + 1 (Sommerfeld, all nodes 0..n_d; the boundary nodes are unknowns
+ *     after ghost-point elimination, Sec. 2.4 Eq. elimination).
+ *   - A grid vector holds N1*N2*N3 values, x fastest: index (i3*N2 + i2)*N1 + i1.
+ *   - Complex values are interleaved (re, im): HELM_C128 = 2 doubles (16 bytes),
+ *     HELM_C64 = 2 floats (8 bytes).
+ *   - Vector pointers are DEVICE pointers owned by the caller unless an entry point says
+ *     otherwise.  They must be 16-byte (c128) / 8-byte (c64) aligned and may not alias
+ *     each other unless stated.
+ *
+ * Streams: every call is ordered on the CUDA stream passed as `stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  Calls return once the work is enqueued, except where
+ * stated (helm_solve and helm_solve_batched wait for the solve to finish).
+ *
+ * Errors: every entry point returns a helm_status; no C++ exception crosses the ABI.
+ * helm_last_error() gives a message for the last failing call on a context.  A context is
+ * not thread-safe: use one context per host thread.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define HELM_API __attribute__((visibility("default")))
+#else
+#define HELM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct helm_ctx helm_ctx;
+
+typedef enum {
+  HELM_OK = 0,
+  HELM_EINVAL = 1,   /* bad argument: sizes, pointers, enum values, unsupported option */
+  HELM_ENOMEM = 2,   /* device or host allocation failed */
+  HELM_ECUDA = 3,    /* a CUDA runtime call failed (message in helm_last_error) */
+  HELM_ENOCONV = 4,  /* max_iter reached before tol; x holds the last iterate */
+  HELM_ETIMEOUT = 5, /* reserved: a bounded device wait gave up */
+  HELM_ENUMERIC = 6  /* NaN/Inf residual or Krylov breakdown; x holds the last finite iterate */
+} helm_status;
+
+typedef enum { HELM_BC_DIRICHLET = 0, HELM_BC_SOMMERFELD = 1 } helm_bc;
+typedef enum { HELM_C128 = 0, HELM_C64 = 1 } helm_dtype;
+typedef enum { HELM_OP_A = 0, HELM_OP_M = 1 } helm_op;
+typedef enum { HELM_GMRES = 0, HELM_FGMRES = 1 } helm_krylov;
+typedef enum { HELM_PREC_FP64 = 0, HELM_PREC_MIXED = 1 } helm_precision;
+
+/* Solver parameters (Sec. 3.3-3.4 and Sec. 5).  helm_default_params fills the paper's
+ * values: beta1 = 1, beta2 = -0.5 (M = -Lap - (beta1 - beta2 i) k^2, Sec. 3.3 Eq.
+ * preconditioner), omega = 0.8 (Sec. 3.4.1), one pre- and one post-smoothing sweep
+ * (Sec. 3.4.5), coarsest_n = 4, GMRES(30), tol = 1e-6 on the true relative residual,
+ * max_iter = 2000, FP64 precision. */
+typedef struct {
+  double beta1;     /* real part of the CSLP shift multiplier */
+  double beta2;     /* CSLP complex shift; the shift is (beta1 - beta2 i) */
+  double omega;     /* damped-Jacobi relaxation, 0 < omega < 2 */
+  int nu1, nu2;     /* pre/post smoothing sweeps; this build supports nu1 = nu2 = 1 */
+  int coarsest_n;   /* >= 2; coarsen while every n_d is even and n_d/2 >= coarsest_n;
+                       the coarsest grid may hold at most 4096 unknowns */
+  int krylov;       /* helm_krylov: right-preconditioned GMRES(m) or flexible GMRES(m) */
+  int restart;      /* m, Krylov vectors per restart cycle, 1..256 */
+  double tol;       /* stop when ||b - A x|| / ||b|| <= tol */
+  int max_iter;     /* cap on products with A in the Arnoldi process (#Matvec) */
+  int precision;    /* helm_precision: HELM_PREC_MIXED runs the V-cycle in complex64
+                       under an FP64 flexible outer Krylov (forces HELM_FGMRES) */
+} helm_params;
+
+/* Per-solve report (host struct). */
+typedef struct {
+  int iterations;      /* products with A in the Arnoldi process (#Matvec, Sec. 5) */
+  int restarts;        /* restart cycles run */
+  int status;          /* helm_status of the solve */
+  double rel_residual; /* explicit ||b - A x|| / ||b|| at return */
+  double ms_total;     /* wall time of the call, host clock */
+} helm_solve_info;
+
+/* Fill *p with the defaults listed above. */
+HELM_API void helm_default_params(helm_params* p);
+
+/* Create a context: the multigrid hierarchy (Sec. 4.2; coarse grids re-discretise M with
+ * H = 2h, k^2 by injection, Sec. 3.4.4), the exact FP64 inverse of the coarsest M (the
+ * paper solves it by GMRES to 1e-11, Sec. 5), and Krylov workspaces.
+ *   n1, n2, n3 : intervals per direction, each >= 2
+ *   h          : grid spacing, > 0
+ *   k2         : k(x)^2 at the N1*N2*N3 unknown nodes (layout above), FP64, > 0 and
+ *                finite; a device or host pointer, copied (the caller keeps ownership)
+ *   bc         : boundary condition on all faces
+ *   p          : parameters, NULL for defaults; copied
+ *   stream     : stream for the set-up work; the call waits for it to finish
+ *   out        : receives the context; *out is NULL on failure
+ * Errors: HELM_EINVAL (sizes, h, k2 values, parameters), HELM_ENOMEM, HELM_ECUDA. */
+HELM_API helm_status helm_create(int n1, int n2, int n3, double h, const double* k2, helm_bc bc,
+                        const helm_params* p, void* stream, helm_ctx** out);
+
+/* Release every device and host resource of the context (NULL is accepted). */
+HELM_API helm_status helm_destroy(helm_ctx* ctx);
+
+/* Number of multigrid levels, and the interval counts and unknown counts of one level
+ * (level 0 = finest).  dims6 receives n1, n2, n3, N1, N2, N3; h_out the level's spacing. */
+HELM_API helm_status helm_levels(const helm_ctx* ctx, int* nlevels);
+HELM_API helm_status helm_level_dims(const helm_ctx* ctx, int level, int* dims6, double* h_out);
+
+/* Matrix-free operator product on the finest grid (Sec. 3.5, Algorithm 2):
+ *   HELM_OP_A : v = A_h u = (-Lap_h - k^2) u
+ *   HELM_OP_M : v = M_h u = (-Lap_h - (beta1 - beta2 i) k^2) u
+ * with the Sommerfeld ghost value u_ghost = u_opposite + 2 h i k u_p substituted on every
+ * boundary face a node lies on.  u and v are device vectors of type dt; u != v. */
+HELM_API helm_status helm_apply(helm_ctx* ctx, helm_op op, helm_dtype dt, const void* u, void* v,
+                       void* stream);
+
+/* One multigrid V-cycle z ~= M_h^{-1} r (Algorithm 1 applied recursively, Sec. 3.4.5):
+ * zero initial guess on each level, one damped-Jacobi sweep before and after each coarse
+ * correction, full-weighting restriction (Sec. 3.4.2), trilinear interpolation
+ * (Sec. 3.4.3), exact FP64 solve on the coarsest level.  dt = HELM_C128 runs every level
+ * in FP64; HELM_C64 runs them in FP32 (the coarsest solve stays FP64).  r, z: device. */
+HELM_API helm_status cslp_vcycle(helm_ctx* ctx, helm_dtype dt, const void* r, void* z, void* stream);
+
+/* One stage of the V-cycle on level `level`, for stage-by-stage checks:
+ *   stage 0 (down): out = R_l (b - M_l u1), u1 = omega D_l^{-1} b; out is on level l+1
+ *   stage 1 (up)  : out = S_l(u1 + P_l e), u1 as above, e on level l+1, out on level l
+ *   stage 2 (coarsest): out = M_L^{-1} b on the last level (level must be nlevels-1)
+ * b, e, out: device vectors of type dt on the levels stated. */
+HELM_API helm_status helm_vcycle_stage(helm_ctx* ctx, int level, int stage, helm_dtype dt,
+                              const void* b, const void* e, void* out, void* stream);
+
+/* Right-hand side of point sources (Sec. 2.4, discrete Dirac): b = 0, then 1/h^3 added at
+ * each source node.  nodes: HOST array of 3*nsrc ints, node coordinates (i1, i2, i3) with
+ * 0 <= i_d <= n_d; a node that is not an unknown (Dirichlet boundary) is skipped.
+ * b: device c128 vector. */
+HELM_API helm_status helm_rhs_point(helm_ctx* ctx, int nsrc, const int* nodes, void* b, void* stream);
+
+/* Solve A_h x = b to ||b - A x|| / ||b|| <= tol by right-preconditioned GMRES(m)
+ * (or FGMRES(m)) with one CSLP V-cycle as the preconditioner (Sec. 3.1-3.3).
+ *   b    : c128 right-hand side
+ *   x    : c128; on entry the initial guess, on exit the solution (a warm start resumes
+ *          an earlier solve)
+ *   b and x may both be device pointers, or both host pointers (pageable or pinned); host
+ *   buffers are copied through the context's device buffers on `stream`.
+ *   info : optional host struct, filled on return
+ * Waits for the solve.  Returns HELM_OK, HELM_ENOCONV (max_iter hit; x is the last
+ * iterate) or HELM_ENUMERIC (breakdown to NaN/Inf). */
+HELM_API helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_info* info,
+                       void* stream);
+
+/* Message for the last failing call on ctx (or for the last failing helm_create when
+ * ctx is NULL).  The string is owned by the library. */
+HELM_API const char* helm_last_error(const helm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELM_H */

@@ -1,0 +1,136 @@
+// common.cuh -- shared device types for libhelm: complex values, grid descriptors and the
+// pointwise pieces of the 7-point Helmholtz / CSLP operator (Sec. 2.4, Sec. 3.5).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+// Interleaved complex value; alignment makes a load one 16-byte (double) or 8-byte
+// (float) vector access.
+template <typename R>
+struct alignas(2 * sizeof(R)) cx {
+  R re, im;
+};
+using z128 = cx<double>;
+using z64 = cx<float>;
+
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> mkc(R a, R b) {
+  cx<R> z;
+  z.re = a;
+  z.im = b;
+  return z;
+}
+template <typename To, typename From>
+__device__ __forceinline__ cx<To> cvt(cx<From> a) {
+  return mkc<To>((To)a.re, (To)a.im);
+}
+template <typename R>
+__device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) { return mkc<R>(a.re + b.re, a.im + b.im); }
+template <typename R>
+__device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) { return mkc<R>(a.re - b.re, a.im - b.im); }
+template <typename R>
+__device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+  return mkc<R>(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
+}
+// a + b*c
+template <typename R>
+__device__ __forceinline__ cx<R> cfma(cx<R> b, cx<R> c, cx<R> a) {
+  R re = fma(b.re, c.re, a.re);
+  re = fma(-b.im, c.im, re);
+  R im = fma(b.re, c.im, a.im);
+  im = fma(b.im, c.re, im);
+  return mkc<R>(re, im);
+}
+// conj(a) * b accumulated into acc
+template <typename R>
+__device__ __forceinline__ void cdot_acc(cx<R> a, cx<R> b, R& re, R& im) {
+  re = fma(a.re, b.re, re);
+  re = fma(a.im, b.im, re);
+  im = fma(a.re, b.im, im);
+  im = fma(-a.im, b.re, im);
+}
+
+// Read-only (non-coherent L1) vector load of one complex value.
+__device__ __forceinline__ cx<double> ldg(const cx<double>* p) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return mkc<double>(v.x, v.y);
+}
+__device__ __forceinline__ cx<float> ldg(const cx<float>* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return mkc<float>(v.x, v.y);
+}
+
+// Grid of unknowns: N_d per direction, x fastest; bc 0 = Dirichlet, 1 = Sommerfeld.
+struct Grid {
+  int N1, N2, N3;
+  int bc;
+  double h;
+  __host__ __device__ size_t npts() const { return (size_t)N1 * N2 * N3; }
+};
+
+__host__ __device__ __forceinline__ size_t gidx(int i, int j, int k, int N1, int N2) {
+  return ((size_t)k * N2 + j) * N1 + i;
+}
+
+// Coefficients of (-Lap_h - s k^2) in working precision R.  s = s_re + i s_im:
+// s = 1 for A_h, s = beta1 - beta2 i for M_h (Sec. 3.5).
+template <typename R>
+struct OpCoef {
+  R ih2;      // 1 / h^2
+  R six_ih2;  // 6 / h^2
+  R s_re, s_im;
+  R two_over_h;  // 2 / h : a Sommerfeld face adds -i (2/h) k to the diagonal
+  R omega;       // damped-Jacobi relaxation (used by smoothing kernels)
+};
+
+// Diagonal of the operator at a node lying on `nf` Sommerfeld faces:
+// 6/h^2 - s k^2 - i (2 k / h) nf.  The face term comes from eliminating the ghost value
+// u_ghost = u_opposite + 2 h i k u_p (Sec. 2.4 Eq. elimination): its -1/h^2 coefficient
+// moves 2 h i k u_p onto the diagonal.
+template <typename R>
+__device__ __forceinline__ cx<R> op_diag(const OpCoef<R>& c, R k2p, int nf) {
+  R dre = fma(-c.s_re, k2p, c.six_ih2);
+  R dim = -c.s_im * k2p;
+  if (nf) dim = fma(-(R)nf * c.two_over_h, sqrt(k2p), dim);
+  return mkc<R>(dre, dim);
+}
+
+// v = d u_c - (1/h^2) (sum of the six neighbour values), neighbours already replaced by
+// the opposite value (Sommerfeld) or 0 (Dirichlet) where they fall outside the grid.
+template <typename R>
+__device__ __forceinline__ cx<R> op_combine(cx<R> d, cx<R> uc, R ih2, cx<R> a, cx<R> b, cx<R> c,
+                                            cx<R> e, cx<R> f, cx<R> g) {
+  R re = d.re * uc.re;
+  R im = d.re * uc.im;
+  re = fma(-d.im, uc.im, re);
+  im = fma(d.im, uc.re, im);
+  re = fma(-ih2, a.re, re); im = fma(-ih2, a.im, im);
+  re = fma(-ih2, b.re, re); im = fma(-ih2, b.im, im);
+  re = fma(-ih2, c.re, re); im = fma(-ih2, c.im, im);
+  re = fma(-ih2, e.re, re); im = fma(-ih2, e.im, im);
+  re = fma(-ih2, f.re, re); im = fma(-ih2, f.im, im);
+  re = fma(-ih2, g.re, re); im = fma(-ih2, g.im, im);
+  return mkc<R>(re, im);
+}
+
+// omega / d, computed (FP32 path) as omega conj(d) / |d|^2.
+template <typename R>
+__device__ __forceinline__ cx<R> omega_over(cx<R> d, R omega) {
+  R inv = omega / fma(d.re, d.re, d.im * d.im);
+  return mkc<R>(d.re * inv, -d.im * inv);
+}
+
+// Device control block for the Krylov loop: kernels of an Arnoldi step return at once
+// when `active` is 0, so the host can enqueue ahead without waiting.
+struct KrylovCtl {
+  int active;  // 1 while the current restart cycle continues
+  int jend;    // last Arnoldi column completed in this cycle
+  int flag;    // 1 = estimate reached tol, 2 = breakdown (zero or non-finite norm)
+  int iter0;   // #Matvec before this cycle
+  double bnorm;
+  double beta;
+  double est;
+};

@@ -1,0 +1,679 @@
+// helm_api.cu -- the C ABI of libhelm (include/helm.h): context and multigrid hierarchy
+// set-up, the V-cycle driver, and the host side of right-preconditioned GMRES(m) /
+// FGMRES(m).  All grid arithmetic runs in the kernels of stencil.cu and krylov.cu; the host
+// only orders launches, except at set-up, where it inverts the small coarsest-grid matrix.
+#include <chrono>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/helm.h"
+#include "internal.cuh"
+
+using namespace helm;
+
+namespace {
+
+constexpr int MAX_LEVELS = 32;
+constexpr int MAX_COARSE = 4096;  // unknowns of the dense coarsest solve
+constexpr int FLAG_LAG = 2;       // Arnoldi steps enqueued ahead of the host's flag check
+
+std::string g_create_error;
+
+struct Level {
+  int n1, n2, n3;
+  Grid g;
+  double* k2 = nullptr;    // FP64 k^2
+  float* k2f = nullptr;    // FP32 copy
+  z128* dinv = nullptr;    // omega / diag(M), FP64 path
+  // V-cycle work vectors: B = right-hand side (levels >= 1), U1 = pre-smoothed iterate,
+  // T = residual / corrected iterate, E = result (levels >= 1)
+  z128 *B64 = nullptr, *U164 = nullptr, *T64 = nullptr, *E64 = nullptr;
+  z64 *B32 = nullptr, *U132 = nullptr, *T32 = nullptr, *E32 = nullptr;
+};
+
+template <typename R> struct LevelBufs;
+template <> struct LevelBufs<double> {
+  static z128* B(Level& L) { return L.B64; }
+  static z128* U1(Level& L) { return L.U164; }
+  static z128* T(Level& L) { return L.T64; }
+  static z128* E(Level& L) { return L.E64; }
+  static const double* k2(Level& L) { return L.k2; }
+  static const z128* dinv(Level& L) { return L.dinv; }
+};
+template <> struct LevelBufs<float> {
+  static z64* B(Level& L) { return L.B32; }
+  static z64* U1(Level& L) { return L.U132; }
+  static z64* T(Level& L) { return L.T32; }
+  static z64* E(Level& L) { return L.E32; }
+  static const float* k2(Level& L) { return L.k2f; }
+  static const z64* dinv(Level&) { return nullptr; }
+};
+
+}  // namespace
+
+struct helm_ctx {
+  helm_params p;
+  int bc = 0;
+  int nlev = 0;
+  Level L[MAX_LEVELS];
+  int nc = 0;
+  z128* Minv = nullptr;
+  // Krylov workspace
+  int m = 0;
+  size_t n0 = 0;
+  z128* V = nullptr;      // (m+1) x n0
+  z128* Z64 = nullptr;    // m x n0, FGMRES in FP64
+  z64* Z32 = nullptr;     // m x n0, mixed precision
+  z128* zs = nullptr;     // n0 scratch (V-cycle output, GMRES)
+  z128* r = nullptr;      // n0 residual
+  z128* xs = nullptr;     // staging for host x
+  z128* bs = nullptr;     // staging for host b
+  z128* part = nullptr;   // (m+1) x RED_BLOCKS partial dots
+  double* partr = nullptr;
+  z128 *hpass = nullptr, *hacc = nullptr;
+  z128* H = nullptr;
+  double* cs = nullptr;
+  z128* sn = nullptr;
+  z128* gv = nullptr;
+  z128* y = nullptr;
+  double* hnorm = nullptr;
+  double* hist = nullptr;
+  int hist_len = 0;
+  KrylovCtl* ctl = nullptr;
+  int* one = nullptr;
+  int* rhs_idx = nullptr;
+  int rhs_cap = 0;
+  int* hflags = nullptr;  // pinned
+  KrylovCtl* hctl = nullptr;  // pinned
+  cudaEvent_t ev[FLAG_LAG + 2];
+  int nev = 0;
+  std::vector<void*> allocs;
+  std::string err;
+  double s_re = 1.0, s_im = 0.0;  // CSLP shift beta1 - beta2 i
+};
+
+namespace {
+
+helm_status fail(helm_ctx* c, helm_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_create_error = buf;
+  return st;
+}
+
+#define CU(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(c, HELM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+helm_status dalloc(helm_ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return HELM_OK;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, HELM_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", count * sizeof(T), cudaGetErrorString(e));
+  }
+  c->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return HELM_OK;
+}
+
+#define TRY(x)                          \
+  do {                                  \
+    helm_status s_ = (x);               \
+    if (s_ != HELM_OK) return s_;       \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int unknowns(int n, int bc) { return bc == HELM_BC_DIRICHLET ? n - 1 : n + 1; }
+
+helm_status check_launch(helm_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, HELM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  return HELM_OK;
+}
+
+// Dense coarsest operator M_L (row-major), entries as in the grid kernels: diagonal
+// 6/h^2 - s k^2 - i (2 k / h) per Sommerfeld face, -1/h^2 per in-grid neighbour, and a
+// neighbour beyond a Sommerfeld face folded onto the opposite node (ghost elimination).
+void assemble_coarse(const Level& L, int bc, std::complex<double> s, const std::vector<double>& k2,
+                     std::vector<std::complex<double>>& A) {
+  const int N1 = L.g.N1, N2 = L.g.N2, N3 = L.g.N3;
+  const int n = N1 * N2 * N3;
+  const double h = L.g.h, ih2 = 1.0 / (h * h);
+  A.assign((size_t)n * n, 0.0);
+  for (int k = 0; k < N3; ++k)
+    for (int j = 0; j < N2; ++j)
+      for (int i = 0; i < N1; ++i) {
+        const int p = (k * N2 + j) * N1 + i;
+        int nf = 0;
+        auto add = [&](int ii, int jj, int kk, int oi, int oj, int ok) {
+          if (ii >= 0 && ii < N1 && jj >= 0 && jj < N2 && kk >= 0 && kk < N3) {
+            A[(size_t)p * n + (kk * N2 + jj) * N1 + ii] += -ih2;
+          } else if (bc == HELM_BC_SOMMERFELD) {
+            ++nf;
+            A[(size_t)p * n + (ok * N2 + oj) * N1 + oi] += -ih2;
+          }
+        };
+        add(i - 1, j, k, i + 1, j, k);
+        add(i + 1, j, k, i - 1, j, k);
+        add(i, j - 1, k, i, j + 1, k);
+        add(i, j + 1, k, i, j - 1, k);
+        add(i, j, k - 1, i, j, k + 1);
+        add(i, j, k + 1, i, j, k - 1);
+        std::complex<double> d = 6.0 * ih2 - s * k2[p];
+        if (nf) d += std::complex<double>(0.0, -2.0 * std::sqrt(k2[p]) / h * nf);
+        A[(size_t)p * n + p] += d;
+      }
+}
+
+// In-place inverse by Gauss-Jordan elimination with partial pivoting.  Returns false on a
+// zero pivot.
+bool invert_dense(int n, std::vector<std::complex<double>>& A) {
+  std::vector<std::complex<double>> I((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    double best = std::abs(A[(size_t)col * n + col]);
+    for (int r = col + 1; r < n; ++r) {
+      const double v = std::abs(A[(size_t)r * n + col]);
+      if (v > best) { best = v; piv = r; }
+    }
+    if (best == 0.0) return false;
+    if (piv != col)
+      for (int q = 0; q < n; ++q) {
+        std::swap(A[(size_t)col * n + q], A[(size_t)piv * n + q]);
+        std::swap(I[(size_t)col * n + q], I[(size_t)piv * n + q]);
+      }
+    const std::complex<double> inv = 1.0 / A[(size_t)col * n + col];
+    for (int q = 0; q < n; ++q) {
+      A[(size_t)col * n + q] *= inv;
+      I[(size_t)col * n + q] *= inv;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const std::complex<double> f = A[(size_t)r * n + col];
+      if (f == 0.0) continue;
+      for (int q = 0; q < n; ++q) {
+        A[(size_t)r * n + q] -= f * A[(size_t)col * n + q];
+        I[(size_t)r * n + q] -= f * I[(size_t)col * n + q];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+// One V-cycle z ~= M^{-1} r in working precision R (input type TI, output type TO).
+template <typename R, typename TI, typename TO>
+void run_vcycle(helm_ctx* c, const cx<TI>* rin, cx<TO>* zout, cudaStream_t st, const int* active) {
+  using B = LevelBufs<R>;
+  const double sr = c->s_re, si = c->s_im, om = c->p.omega;
+  const int L = c->nlev;
+  if (L == 1) {
+    launch_coarse<TI, TO>(c->nc, c->Minv, rin, zout, st, active);
+    return;
+  }
+  // down: pre-smooth from zero, residual, restriction
+  for (int l = 0; l < L - 1; ++l) {
+    Level& F = c->L[l];
+    Level& C = c->L[l + 1];
+    if (l == 0) {
+      launch_smooth0<R, TI>(F.g, sr, si, om, B::k2(F), B::dinv(F), rin, B::U1(F), st, active);
+      launch_resid<R, R, TI, R>(F.g, sr, si, B::k2(F), B::U1(F), rin, B::T(F), st, active);
+    } else {
+      launch_smooth0<R, R>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::B(F), B::U1(F), st, active);
+      launch_resid<R, R, R, R>(F.g, sr, si, B::k2(F), B::U1(F), B::B(F), B::T(F), st, active);
+    }
+    launch_restrict<R>(F.g, C.g, B::T(F), B::B(C), st, active);
+  }
+  // coarsest: exact FP64 solve
+  launch_coarse<R, R>(c->nc, c->Minv, B::B(c->L[L - 1]), B::E(c->L[L - 1]), st, active);
+  // up: prolongation + correction, post-smoothing
+  for (int l = L - 2; l >= 0; --l) {
+    Level& F = c->L[l];
+    Level& C = c->L[l + 1];
+    launch_prolong_add<R>(F.g, C.g, B::U1(F), B::E(C), B::T(F), st, active);
+    if (l == 0)
+      launch_jacobi<R, TI, TO>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::T(F), rin, zout, st, active);
+    else
+      launch_jacobi<R, R, R>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::T(F), B::B(F), B::E(F), st, active);
+  }
+}
+
+void norm_into(helm_ctx* c, const z128* x, double* out, cudaStream_t st, const int* active) {
+  launch_norm2_part(x, c->n0, c->partr, st, active);
+  launch_reduce_norm(c->partr, out, st, active);
+}
+
+// GMRES(m) / FGMRES(m) on device-resident b and x.
+helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* info, cudaStream_t st) {
+  const Level& F = c->L[0];
+  const size_t n = c->n0;
+  const int m = c->m;
+  const bool mixed = c->p.precision == HELM_PREC_MIXED;
+  const bool flexible = mixed || c->p.krylov == HELM_FGMRES;
+  const double tol = c->p.tol;
+  KrylovCtl* ctl = c->ctl;
+  const int* act = &ctl->active;
+
+  norm_into(c, b, &ctl->bnorm, st, c->one);
+  launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, c->r, st, c->one);
+  norm_into(c, c->r, &ctl->beta, st, c->one);
+  CU(cudaMemcpyAsync(c->hctl, ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  double bnorm = c->hctl->bnorm;
+  int iters = 0, restarts = 0;
+  helm_status status = HELM_OK;
+  if (bnorm == 0.0) {
+    // b = 0: the solution is x = 0
+    CU(cudaMemsetAsync(x, 0, n * sizeof(z128), st));
+    CU(cudaStreamSynchronize(st));
+    if (info) { info->iterations = 0; info->restarts = 0; info->rel_residual = 0.0; }
+    return HELM_OK;
+  }
+  double relres = c->hctl->beta / bnorm;
+  for (;;) {
+    if (!(relres == relres) || relres == HUGE_VAL) { status = HELM_ENUMERIC; break; }
+    if (relres <= tol) { status = HELM_OK; break; }
+    if (iters >= c->p.max_iter) { status = HELM_ENOCONV; break; }
+    const int jmax = std::min(m, c->p.max_iter - iters);
+    launch_cycle_init(ctl, c->gv, m, iters, st);
+    launch_scale_inv(c->r, &ctl->beta, c->V, n, st, act);
+    for (int j = 0; j < jmax; ++j) {
+      z128* vj = c->V + (size_t)j * n;
+      z128* w = c->V + (size_t)(j + 1) * n;
+      if (mixed) {
+        z64* zj = c->Z32 + (size_t)j * n;
+        run_vcycle<float, double, float>(c, vj, zj, st, act);
+        launch_apply<double, float, double>(F.g, 1.0, 0.0, F.k2, zj, w, st, act);
+      } else {
+        z128* zj = flexible ? c->Z64 + (size_t)j * n : c->zs;
+        run_vcycle<double, double, double>(c, vj, zj, st, act);
+        launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, zj, w, st, act);
+      }
+      // classical Gram-Schmidt, two passes
+      launch_mdot(c->V, n, j + 1, w, n, c->part, st, act);
+      launch_reduce_dots(c->part, j + 1, c->hpass, c->hacc, 0, st, act);
+      launch_gs_update(c->V, n, j + 1, c->hpass, w, n, st, act);
+      launch_mdot(c->V, n, j + 1, w, n, c->part, st, act);
+      launch_reduce_dots(c->part, j + 1, c->hpass, c->hacc, 1, st, act);
+      launch_gs_update(c->V, n, j + 1, c->hpass, w, n, st, act);
+      norm_into(c, w, c->hnorm, st, act);
+      launch_givens(ctl, c->H, m, j, jmax, c->hacc, c->hnorm, c->cs, c->sn, c->gv, tol, c->hist, c->hist_len, st);
+      launch_scale_inv(w, c->hnorm, w, n, st, act);
+      TRY(check_launch(c, "Arnoldi step"));
+      CU(cudaMemcpyAsync(c->hflags + j, act, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CU(cudaEventRecord(c->ev[j % c->nev], st));
+      if (j >= FLAG_LAG) {
+        CU(cudaEventSynchronize(c->ev[(j - FLAG_LAG) % c->nev]));
+        if (c->hflags[j - FLAG_LAG] == 0) break;
+      }
+    }
+    CU(cudaMemcpyAsync(c->hctl, ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    const int jend = c->hctl->jend;
+    iters += jend + 1;
+    ++restarts;
+    if (jend >= 0) {
+      launch_trisolve(ctl, c->H, m, c->gv, c->y, st);
+      if (mixed) {
+        launch_xupdate<float>(ctl, c->Z32, n, c->y, x, n, st);
+      } else if (flexible) {
+        launch_xupdate<double>(ctl, c->Z64, n, c->y, x, n, st);
+      } else {
+        launch_combine(ctl, c->V, n, c->y, c->r, n, st);
+        run_vcycle<double, double, double>(c, c->r, c->zs, st, c->one);
+        launch_axpy1(c->zs, x, n, st);
+      }
+    }
+    launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, c->r, st, c->one);
+    norm_into(c, c->r, &ctl->beta, st, c->one);
+    TRY(check_launch(c, "solution update"));
+    CU(cudaMemcpyAsync(c->hctl, ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    relres = c->hctl->beta / bnorm;
+    if (c->hctl->flag == 2 && !(relres <= tol)) { status = HELM_ENUMERIC; break; }
+    if (jend < 0) { status = HELM_ENUMERIC; break; }
+  }
+  if (info) {
+    info->iterations = iters;
+    info->restarts = restarts;
+    info->rel_residual = relres;
+  }
+  return status;
+}
+
+template <typename R>
+void stage_impl(helm_ctx* c, int l, int stage, const cx<R>* b, const cx<R>* e, cx<R>* out, cudaStream_t st) {
+  using B = LevelBufs<R>;
+  const double sr = c->s_re, si = c->s_im, om = c->p.omega;
+  Level& F = c->L[l];
+  if (stage == 2) {
+    launch_coarse<R, R>(c->nc, c->Minv, b, out, st, nullptr);
+    return;
+  }
+  Level& C = c->L[l + 1];
+  launch_smooth0<R, R>(F.g, sr, si, om, B::k2(F), B::dinv(F), b, B::U1(F), st, nullptr);
+  if (stage == 0) {
+    launch_resid<R, R, R, R>(F.g, sr, si, B::k2(F), B::U1(F), b, B::T(F), st, nullptr);
+    launch_restrict<R>(F.g, C.g, B::T(F), out, st, nullptr);
+  } else {
+    launch_prolong_add<R>(F.g, C.g, B::U1(F), e, B::T(F), st, nullptr);
+    launch_jacobi<R, R, R>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::T(F), b, out, st, nullptr);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void helm_default_params(helm_params* p) {
+  if (!p) return;
+  p->beta1 = 1.0;
+  p->beta2 = -0.5;
+  p->omega = 0.8;
+  p->nu1 = 1;
+  p->nu2 = 1;
+  p->coarsest_n = 4;
+  p->krylov = HELM_GMRES;
+  p->restart = 30;
+  p->tol = 1e-6;
+  p->max_iter = 2000;
+  p->precision = HELM_PREC_FP64;
+}
+
+const char* helm_last_error(const helm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+helm_status helm_destroy(helm_ctx* ctx) {
+  if (!ctx) return HELM_OK;
+  for (void* q : ctx->allocs) cudaFree(q);
+  if (ctx->hflags) cudaFreeHost(ctx->hflags);
+  if (ctx->hctl) cudaFreeHost(ctx->hctl);
+  for (int i = 0; i < ctx->nev; ++i) cudaEventDestroy(ctx->ev[i]);
+  delete ctx;
+  return HELM_OK;
+}
+
+static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, const double* k2, int bc,
+                               cudaStream_t st) {
+  const helm_params& P = c->p;
+  c->bc = bc;
+  c->s_re = P.beta1;
+  c->s_im = -P.beta2;
+  // hierarchy (Sec. 4.2): halve while every n_d is even and n_d / 2 >= coarsest_n
+  int a = n1, b = n2, d = n3;
+  double hl = h;
+  int nl = 0;
+  for (;;) {
+    Level& L = c->L[nl];
+    L.n1 = a; L.n2 = b; L.n3 = d;
+    L.g.N1 = unknowns(a, bc); L.g.N2 = unknowns(b, bc); L.g.N3 = unknowns(d, bc);
+    L.g.bc = bc;
+    L.g.h = hl;
+    ++nl;
+    const bool can = a % 2 == 0 && b % 2 == 0 && d % 2 == 0 && a / 2 >= P.coarsest_n && b / 2 >= P.coarsest_n &&
+                     d / 2 >= P.coarsest_n && nl < MAX_LEVELS;
+    if (!can) break;
+    a /= 2; b /= 2; d /= 2;
+    hl *= 2;
+  }
+  c->nlev = nl;
+  const Level& Lc = c->L[nl - 1];
+  c->nc = Lc.g.N1 * Lc.g.N2 * Lc.g.N3;
+  if ((size_t)Lc.g.N1 * Lc.g.N2 * Lc.g.N3 > (size_t)MAX_COARSE)
+    return fail(c, HELM_EINVAL, "coarsest grid has %zu unknowns (limit %d): use interval counts divisible by a "
+                "larger power of two or a smaller coarsest_n", (size_t)Lc.g.N1 * Lc.g.N2 * Lc.g.N3, MAX_COARSE);
+  for (int l = 0; l < nl; ++l) {
+    Level& L = c->L[l];
+    const size_t np = L.g.npts();
+    TRY(dalloc(c, &L.k2, np));
+    TRY(dalloc(c, &L.k2f, np));
+    TRY(dalloc(c, &L.dinv, np));
+    TRY(dalloc(c, &L.U164, np));
+    TRY(dalloc(c, &L.T64, np));
+    TRY(dalloc(c, &L.U132, np));
+    TRY(dalloc(c, &L.T32, np));
+    if (l > 0) {
+      TRY(dalloc(c, &L.B64, np));
+      TRY(dalloc(c, &L.E64, np));
+      TRY(dalloc(c, &L.B32, np));
+      TRY(dalloc(c, &L.E32, np));
+    }
+  }
+  Level& L0 = c->L[0];
+  const size_t n0 = L0.g.npts();
+  c->n0 = n0;
+  CU(cudaMemcpyAsync(L0.k2, k2, n0 * sizeof(double), cudaMemcpyDefault, st));
+  int* bad = nullptr;
+  TRY(dalloc(c, &bad, 1));
+  CU(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  launch_check_k2(L0.k2, n0, bad, st);
+  int hbad = 0;
+  CU(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (hbad) return fail(c, HELM_EINVAL, "k2 has %d non-finite or non-positive entries", hbad);
+  for (int l = 1; l < nl; ++l) launch_inject(c->L[l - 1].g, c->L[l].g, c->L[l - 1].k2, c->L[l].k2, st);
+  for (int l = 0; l < nl; ++l) {
+    Level& L = c->L[l];
+    launch_to_float(L.k2, L.k2f, L.g.npts(), st);
+    launch_dinv(L.g, c->s_re, c->s_im, P.omega, L.k2, L.dinv, st);
+  }
+  TRY(check_launch(c, "set-up kernels"));
+  // coarsest: assemble M_L on the host and invert it once
+  std::vector<double> k2c(c->nc);
+  CU(cudaMemcpyAsync(k2c.data(), c->L[nl - 1].k2, c->nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  std::vector<std::complex<double>> A;
+  assemble_coarse(c->L[nl - 1], bc, std::complex<double>(c->s_re, c->s_im), k2c, A);
+  if (!invert_dense(c->nc, A)) return fail(c, HELM_ENUMERIC, "coarsest-grid operator is singular");
+  TRY(dalloc(c, &c->Minv, (size_t)c->nc * c->nc));
+  CU(cudaMemcpy(c->Minv, A.data(), A.size() * sizeof(z128), cudaMemcpyHostToDevice));
+  // Krylov workspace
+  const int m = P.restart;
+  c->m = m;
+  TRY(dalloc(c, &c->V, (size_t)(m + 1) * n0));
+  if (P.precision == HELM_PREC_MIXED) TRY(dalloc(c, &c->Z32, (size_t)m * n0));
+  else if (P.krylov == HELM_FGMRES) TRY(dalloc(c, &c->Z64, (size_t)m * n0));
+  TRY(dalloc(c, &c->zs, n0));
+  TRY(dalloc(c, &c->r, n0));
+  TRY(dalloc(c, &c->xs, n0));
+  TRY(dalloc(c, &c->bs, n0));
+  TRY(dalloc(c, &c->part, (size_t)(m + 1) * RED_BLOCKS));
+  TRY(dalloc(c, &c->partr, RED_BLOCKS));
+  TRY(dalloc(c, &c->hpass, MAX_BASIS));
+  TRY(dalloc(c, &c->hacc, MAX_BASIS));
+  TRY(dalloc(c, &c->H, (size_t)(m + 1) * m));
+  TRY(dalloc(c, &c->cs, m));
+  TRY(dalloc(c, &c->sn, m));
+  TRY(dalloc(c, &c->gv, m + 1));
+  TRY(dalloc(c, &c->y, m));
+  TRY(dalloc(c, &c->hnorm, 1));
+  c->hist_len = P.max_iter;
+  TRY(dalloc(c, &c->hist, c->hist_len));
+  TRY(dalloc(c, &c->ctl, 1));
+  TRY(dalloc(c, &c->one, 1));
+  const int one = 1;
+  CU(cudaMemcpy(c->one, &one, sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemset(c->ctl, 0, sizeof(KrylovCtl)));
+  CU(cudaHostAlloc((void**)&c->hflags, sizeof(int) * (m + FLAG_LAG + 1), cudaHostAllocDefault));
+  CU(cudaHostAlloc((void**)&c->hctl, sizeof(KrylovCtl), cudaHostAllocDefault));
+  c->nev = FLAG_LAG + 2;
+  for (int i = 0; i < c->nev; ++i) CU(cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming));
+  CU(cudaStreamSynchronize(st));
+  return HELM_OK;
+}
+
+helm_status helm_create(int n1, int n2, int n3, double h, const double* k2, helm_bc bc, const helm_params* p,
+                        void* stream, helm_ctx** out) {
+  if (!out) return fail(nullptr, HELM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n1 < 2 || n2 < 2 || n3 < 2) return fail(nullptr, HELM_EINVAL, "interval counts must be >= 2 (got %d %d %d)", n1, n2, n3);
+  if (!(h > 0.0) || !std::isfinite(h)) return fail(nullptr, HELM_EINVAL, "h must be positive and finite");
+  if (bc != HELM_BC_DIRICHLET && bc != HELM_BC_SOMMERFELD) return fail(nullptr, HELM_EINVAL, "unknown boundary condition %d", (int)bc);
+  if (!k2) return fail(nullptr, HELM_EINVAL, "k2 is NULL");
+  helm_params P;
+  if (p) P = *p;
+  else helm_default_params(&P);
+  if (!(P.omega > 0.0 && P.omega < 2.0)) return fail(nullptr, HELM_EINVAL, "omega must lie in (0, 2)");
+  if (P.nu1 != 1 || P.nu2 != 1) return fail(nullptr, HELM_EINVAL, "only nu1 = nu2 = 1 is supported");
+  if (P.coarsest_n < 2) return fail(nullptr, HELM_EINVAL, "coarsest_n must be >= 2");
+  if (P.restart < 1 || P.restart > MAX_BASIS - 1) return fail(nullptr, HELM_EINVAL, "restart must lie in 1..%d", MAX_BASIS - 1);
+  if (!(P.tol > 0.0)) return fail(nullptr, HELM_EINVAL, "tol must be positive");
+  if (P.max_iter < 1) return fail(nullptr, HELM_EINVAL, "max_iter must be >= 1");
+  if (P.krylov != HELM_GMRES && P.krylov != HELM_FGMRES) return fail(nullptr, HELM_EINVAL, "unknown krylov %d", P.krylov);
+  if (P.precision != HELM_PREC_FP64 && P.precision != HELM_PREC_MIXED) return fail(nullptr, HELM_EINVAL, "unknown precision %d", P.precision);
+  if (!std::isfinite(P.beta1) || !std::isfinite(P.beta2)) return fail(nullptr, HELM_EINVAL, "beta1, beta2 must be finite");
+  if (P.precision == HELM_PREC_MIXED) P.krylov = HELM_FGMRES;
+  helm_ctx* c = new (std::nothrow) helm_ctx();
+  if (!c) return fail(nullptr, HELM_ENOMEM, "host allocation failed");
+  c->p = P;
+  helm_status s = create_impl(c, n1, n2, n3, h, k2, (int)bc, (cudaStream_t)stream);
+  if (s != HELM_OK) {
+    g_create_error = c->err;
+    helm_destroy(c);
+    return s;
+  }
+  *out = c;
+  return HELM_OK;
+}
+
+helm_status helm_levels(const helm_ctx* ctx, int* nlevels) {
+  if (!ctx || !nlevels) return HELM_EINVAL;
+  *nlevels = ctx->nlev;
+  return HELM_OK;
+}
+
+helm_status helm_level_dims(const helm_ctx* ctx, int level, int* dims6, double* h_out) {
+  if (!ctx || !dims6 || level < 0 || level >= ctx->nlev) return HELM_EINVAL;
+  const Level& L = ctx->L[level];
+  dims6[0] = L.n1; dims6[1] = L.n2; dims6[2] = L.n3;
+  dims6[3] = L.g.N1; dims6[4] = L.g.N2; dims6[5] = L.g.N3;
+  if (h_out) *h_out = L.g.h;
+  return HELM_OK;
+}
+
+helm_status helm_apply(helm_ctx* c, helm_op op, helm_dtype dt, const void* u, void* v, void* stream) {
+  if (!c) return HELM_EINVAL;
+  if (!u || !v || u == v) return fail(c, HELM_EINVAL, "u and v must be distinct non-NULL device pointers");
+  if (op != HELM_OP_A && op != HELM_OP_M) return fail(c, HELM_EINVAL, "unknown operator %d", (int)op);
+  const double sr = op == HELM_OP_A ? 1.0 : c->s_re, si = op == HELM_OP_A ? 0.0 : c->s_im;
+  cudaStream_t st = (cudaStream_t)stream;
+  Level& L = c->L[0];
+  if (dt == HELM_C128)
+    launch_apply<double, double, double>(L.g, sr, si, L.k2, (const z128*)u, (z128*)v, st, nullptr);
+  else if (dt == HELM_C64)
+    launch_apply<float, float, float>(L.g, sr, si, L.k2f, (const z64*)u, (z64*)v, st, nullptr);
+  else
+    return fail(c, HELM_EINVAL, "unknown dtype %d", (int)dt);
+  return check_launch(c, "helm_apply");
+}
+
+helm_status cslp_vcycle(helm_ctx* c, helm_dtype dt, const void* r, void* z, void* stream) {
+  if (!c) return HELM_EINVAL;
+  if (!r || !z || r == z) return fail(c, HELM_EINVAL, "r and z must be distinct non-NULL device pointers");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dt == HELM_C128)
+    run_vcycle<double, double, double>(c, (const z128*)r, (z128*)z, st, nullptr);
+  else if (dt == HELM_C64)
+    run_vcycle<float, float, float>(c, (const z64*)r, (z64*)z, st, nullptr);
+  else
+    return fail(c, HELM_EINVAL, "unknown dtype %d", (int)dt);
+  return check_launch(c, "cslp_vcycle");
+}
+
+helm_status helm_vcycle_stage(helm_ctx* c, int level, int stage, helm_dtype dt, const void* b, const void* e,
+                              void* out, void* stream) {
+  if (!c) return HELM_EINVAL;
+  if (stage < 0 || stage > 2) return fail(c, HELM_EINVAL, "stage must be 0, 1 or 2");
+  if (stage == 2 && level != c->nlev - 1) return fail(c, HELM_EINVAL, "stage 2 runs on the last level only");
+  if (stage < 2 && (level < 0 || level >= c->nlev - 1)) return fail(c, HELM_EINVAL, "level out of range");
+  if (!b || !out || (stage == 1 && !e)) return fail(c, HELM_EINVAL, "NULL vector");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dt == HELM_C128)
+    stage_impl<double>(c, level, stage, (const z128*)b, (const z128*)e, (z128*)out, st);
+  else if (dt == HELM_C64)
+    stage_impl<float>(c, level, stage, (const z64*)b, (const z64*)e, (z64*)out, st);
+  else
+    return fail(c, HELM_EINVAL, "unknown dtype %d", (int)dt);
+  return check_launch(c, "helm_vcycle_stage");
+}
+
+helm_status helm_rhs_point(helm_ctx* c, int nsrc, const int* nodes, void* b, void* stream) {
+  if (!c) return HELM_EINVAL;
+  if (nsrc < 0 || (nsrc > 0 && !nodes) || !b) return fail(c, HELM_EINVAL, "bad source list or b");
+  cudaStream_t st = (cudaStream_t)stream;
+  const Level& L = c->L[0];
+  const int off = c->bc == HELM_BC_DIRICHLET ? 1 : 0;
+  std::vector<int> idx(nsrc > 0 ? nsrc : 1, -1);
+  for (int s = 0; s < nsrc; ++s) {
+    const int i = nodes[3 * s] - off, j = nodes[3 * s + 1] - off, k = nodes[3 * s + 2] - off;
+    if (nodes[3 * s] < 0 || nodes[3 * s] > L.n1 || nodes[3 * s + 1] < 0 || nodes[3 * s + 1] > L.n2 ||
+        nodes[3 * s + 2] < 0 || nodes[3 * s + 2] > L.n3)
+      return fail(c, HELM_EINVAL, "source %d outside the grid", s);
+    if (i < 0 || i >= L.g.N1 || j < 0 || j >= L.g.N2 || k < 0 || k >= L.g.N3) continue;
+    idx[s] = (int)gidx(i, j, k, L.g.N1, L.g.N2);
+  }
+  CU(cudaStreamSynchronize(st));
+  if (nsrc > c->rhs_cap) {
+    TRY(dalloc(c, &c->rhs_idx, nsrc));
+    c->rhs_cap = nsrc;
+  }
+  if (nsrc > 0) CU(cudaMemcpy(c->rhs_idx, idx.data(), nsrc * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemsetAsync(b, 0, c->n0 * sizeof(z128), st));
+  if (nsrc > 0) launch_rhs_point(L.g, nsrc, c->rhs_idx, 1.0 / (L.g.h * L.g.h * L.g.h), (z128*)b, st);
+  return check_launch(c, "helm_rhs_point");
+}
+
+helm_status helm_solve(helm_ctx* c, const void* b, void* x, helm_solve_info* info, void* stream) {
+  if (!c) return HELM_EINVAL;
+  if (!b || !x || b == x) return fail(c, HELM_EINVAL, "b and x must be distinct non-NULL pointers");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+  if (bdev != xdev) return fail(c, HELM_EINVAL, "b and x must both be device or both be host pointers");
+  const size_t bytes = c->n0 * sizeof(z128);
+  const z128* bd = (const z128*)b;
+  z128* xd = (z128*)x;
+  if (!bdev) {
+    CU(cudaMemcpyAsync(c->bs, b, bytes, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(c->xs, x, bytes, cudaMemcpyHostToDevice, st));
+    bd = c->bs;
+    xd = c->xs;
+  }
+  helm_solve_info tmp;
+  helm_solve_info* inf = info ? info : &tmp;
+  helm_status s = gmres_device(c, bd, xd, inf, st);
+  if (!bdev && (s == HELM_OK || s == HELM_ENOCONV || s == HELM_ENUMERIC)) {
+    CU(cudaMemcpyAsync(x, c->xs, bytes, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+  }
+  inf->status = (int)s;
+  inf->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (s == HELM_ENOCONV) fail(c, s, "max_iter (%d) reached at relative residual %.3e", c->p.max_iter, inf->rel_residual);
+  if (s == HELM_ENUMERIC) fail(c, s, "non-finite residual or Krylov breakdown");
+  return s;
+}
+
+}  // extern "C"

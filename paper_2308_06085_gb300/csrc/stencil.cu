@@ -1,0 +1,409 @@
+// stencil.cu -- matrix-free grid kernels of libhelm: the 7-point Helmholtz / CSLP operator
+// (Sec. 2.4, Sec. 3.5 Algorithm 2), damped Jacobi (Sec. 3.4.1), full-weighting restriction
+// (Sec. 3.4.2), trilinear interpolation (Sec. 3.4.3), k^2 injection for the DCG coarse
+// operators (Sec. 3.4.4) and the exact coarsest-grid solve.
+//
+// Every grid kernel maps a 32 x 8 tile of (x, y) columns to a 256-thread block and streams
+// along z: the z-1 / z / z+1 values of a thread's own column stay in registers (2.5D
+// streaming), the in-plane neighbours come through the read-only L1 path.
+#include "internal.cuh"
+
+namespace helm {
+
+namespace {
+
+constexpr int TX = 32, TY = 8;
+
+template <typename T>
+__device__ __forceinline__ cx<T> zero_c() {
+  return mkc<T>((T)0, (T)0);
+}
+
+// One stencil kernel for three uses (MODE):
+//   APPLY  : out = Op u
+//   RESID  : out = b - Op u
+//   JACOBI : out = u + (omega / d) (b - Op u)
+// with Op = -Lap_h - s k^2 (s in OpCoef).  DINV: read omega/d from a precomputed array
+// (FP64 path, where a complex division costs more than the 16-byte read) instead of
+// computing it.
+template <typename R, int MODE, bool DINV, typename TU, typename TB, typename TO>
+__global__ void __launch_bounds__(TX* TY)
+    k_stencil(Grid g, OpCoef<R> c, const R* __restrict__ k2, const cx<R>* __restrict__ dinv,
+              const cx<TU>* __restrict__ u, const cx<TB>* __restrict__ b, cx<TO>* __restrict__ out,
+              int zchunk, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const int i = blockIdx.x * TX + threadIdx.x;
+  const int j = blockIdx.y * TY + threadIdx.y;
+  if (i >= g.N1 || j >= g.N2) return;
+  const int k0 = blockIdx.z * zchunk;
+  if (k0 >= g.N3) return;
+  const int k1 = min(k0 + zchunk, g.N3);
+  const bool som = g.bc == 1;
+  const size_t S = (size_t)g.N1 * g.N2;
+  const long N1 = g.N1;
+  const bool hxm = i > 0, hxp = i < g.N1 - 1, hym = j > 0, hyp = j < g.N2 - 1;
+  const int nfxy = som ? (!hxm) + (!hxp) + (!hym) + (!hyp) : 0;
+  auto ld = [&](size_t q) { return cvt<R>(ldg(u + q)); };
+  size_t p = gidx(i, j, k0, g.N1, g.N2);
+  cx<R> uc = ld(p);
+  cx<R> um = (k0 > 0) ? ld(p - S) : zero_c<R>();
+  for (int k = k0; k < k1; ++k, p += S) {
+    const bool hzp = k + 1 < g.N3;
+    cx<R> up = hzp ? ld(p + S) : zero_c<R>();
+    int nf = nfxy;
+    cx<R> zm, zp;
+    if (k > 0) zm = um;
+    else if (som) { zm = up; ++nf; }
+    else zm = zero_c<R>();
+    if (hzp) zp = up;
+    else if (som) { zp = um; ++nf; }
+    else zp = zero_c<R>();
+    cx<R> xm = hxm ? ld(p - 1) : (som ? ld(p + 1) : zero_c<R>());
+    cx<R> xp = hxp ? ld(p + 1) : (som ? ld(p - 1) : zero_c<R>());
+    cx<R> ym = hym ? ld(p - N1) : (som ? ld(p + N1) : zero_c<R>());
+    cx<R> yp = hyp ? ld(p + N1) : (som ? ld(p - N1) : zero_c<R>());
+    const R kk = __ldg(k2 + p);
+    const cx<R> d = op_diag(c, kk, nf);
+    const cx<R> v = op_combine(d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
+    if (MODE == 0) {
+      out[p] = cvt<TO>(v);
+    } else {
+      const cx<R> r = csub(cvt<R>(ldg(b + p)), v);
+      if (MODE == 1) {
+        out[p] = cvt<TO>(r);
+      } else {
+        const cx<R> w = DINV ? ldg(dinv + p) : omega_over(d, c.omega);
+        out[p] = cvt<TO>(cfma(w, r, uc));
+      }
+    }
+    um = uc;
+    uc = up;
+  }
+}
+
+// Pre-smoothing from a zero initial guess: one damped-Jacobi sweep gives u1 = (omega/d) b.
+template <typename R, bool DINV, typename TB>
+__global__ void __launch_bounds__(TX* TY)
+    k_smooth0(Grid g, OpCoef<R> c, const R* __restrict__ k2, const cx<R>* __restrict__ dinv,
+              const cx<TB>* __restrict__ b, cx<R>* __restrict__ out, int zchunk,
+              const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const int i = blockIdx.x * TX + threadIdx.x;
+  const int j = blockIdx.y * TY + threadIdx.y;
+  if (i >= g.N1 || j >= g.N2) return;
+  const int k0 = blockIdx.z * zchunk;
+  const int k1 = min(k0 + zchunk, g.N3);
+  const bool som = g.bc == 1;
+  const int nfxy = som ? (i == 0) + (i == g.N1 - 1) + (j == 0) + (j == g.N2 - 1) : 0;
+  const size_t S = (size_t)g.N1 * g.N2;
+  size_t p = gidx(i, j, k0, g.N1, g.N2);
+  for (int k = k0; k < k1; ++k, p += S) {
+    cx<R> w;
+    if (DINV) {
+      w = ldg(dinv + p);
+    } else {
+      const int nf = nfxy + (som ? (k == 0) + (k == g.N3 - 1) : 0);
+      w = omega_over(op_diag(c, __ldg(k2 + p), nf), c.omega);
+    }
+    out[p] = cmul(w, cvt<R>(ldg(b + p)));
+  }
+}
+
+// omega / diag(M) at every node (FP64 path; computed once per level at set-up).
+__global__ void k_dinv(Grid g, OpCoef<double> c, const double* __restrict__ k2, z128* __restrict__ out) {
+  const size_t n = g.npts();
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(p % g.N1);
+    const int j = (int)((p / g.N1) % g.N2);
+    const int k = (int)(p / ((size_t)g.N1 * g.N2));
+    const int nf = g.bc == 1 ? (i == 0) + (i == g.N1 - 1) + (j == 0) + (j == g.N2 - 1) + (k == 0) + (k == g.N3 - 1) : 0;
+    const z128 d = op_diag(c, k2[p], nf);
+    // omega / d as omega conj(d) / |d|^2 in FP64 (set-up only)
+    const double m2 = d.re * d.re + d.im * d.im;
+    out[p] = mkc<double>(c.omega * d.re / m2, -c.omega * d.im / m2);
+  }
+}
+
+// Full weighting (Sec. 3.4.2): b_H(I) = (1/64) sum over the 27 fine neighbours of the fine
+// node 2I of weight 8 / 4 / 2 / 1 (centre / face / edge / corner) times r_h; fine values
+// outside the unknown set count as 0.
+template <typename R>
+__global__ void __launch_bounds__(TX* TY)
+    k_restrict(Grid gf, Grid gc, const cx<R>* __restrict__ r, cx<R>* __restrict__ out, int zchunk,
+               const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const int I = blockIdx.x * TX + threadIdx.x;
+  const int J = blockIdx.y * TY + threadIdx.y;
+  if (I >= gc.N1 || J >= gc.N2) return;
+  const int K0 = blockIdx.z * zchunk;
+  const int K1 = min(K0 + zchunk, gc.N3);
+  const int off = gf.bc == 0 ? 1 : 0;
+  const int fi = 2 * (I + off) - off, fj = 2 * (J + off) - off;
+  for (int K = K0; K < K1; ++K) {
+    const int fk = 2 * (K + off) - off;
+    R are = 0, aim = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int z = fk + dz;
+      if (z < 0 || z >= gf.N3) continue;
+      const R wz = dz ? (R)1 : (R)2;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int y = fj + dy;
+        if (y < 0 || y >= gf.N2) continue;
+        const R wyz = wz * (dy ? (R)1 : (R)2);
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int x = fi + dx;
+          if (x < 0 || x >= gf.N1) continue;
+          const R w = wyz * (dx ? (R)1 : (R)2);
+          const cx<R> v = ldg(r + gidx(x, y, z, gf.N1, gf.N2));
+          are = fma(w, v.re, are);
+          aim = fma(w, v.im, aim);
+        }
+      }
+    }
+    out[gidx(I, J, K, gc.N1, gc.N2)] = mkc<R>(are * (R)(1.0 / 64.0), aim * (R)(1.0 / 64.0));
+  }
+}
+
+// Trilinear interpolation (Sec. 3.4.3) added to u1: out = u1 + I_H^h e.  A fine node at
+// an odd node index along an axis averages the two coarse nodes either side; coarse
+// values outside the unknown set (Dirichlet boundary) are 0.
+template <typename R>
+__global__ void __launch_bounds__(TX* TY)
+    k_prolong_add(Grid gf, Grid gc, const cx<R>* __restrict__ u1, const cx<R>* __restrict__ e,
+                  cx<R>* __restrict__ out, int zchunk, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const int i = blockIdx.x * TX + threadIdx.x;
+  const int j = blockIdx.y * TY + threadIdx.y;
+  if (i >= gf.N1 || j >= gf.N2) return;
+  const int k0 = blockIdx.z * zchunk;
+  const int k1 = min(k0 + zchunk, gf.N3);
+  const int off = gf.bc == 0 ? 1 : 0;
+  int cx_[2], cy_[2];
+  const int fi = i + off, fj = j + off;
+  cx_[0] = (fi >> 1) - off; cx_[1] = ((fi + 1) >> 1) - off;
+  cy_[0] = (fj >> 1) - off; cy_[1] = ((fj + 1) >> 1) - off;
+  const int nx = (cx_[0] == cx_[1]) ? 1 : 2, ny = (cy_[0] == cy_[1]) ? 1 : 2;
+  for (int k = k0; k < k1; ++k) {
+    const int fk = k + off;
+    int cz_[2] = {(fk >> 1) - off, ((fk + 1) >> 1) - off};
+    const int nz = (cz_[0] == cz_[1]) ? 1 : 2;
+    R are = 0, aim = 0;
+    for (int c = 0; c < nz; ++c) {
+      if (cz_[c] < 0 || cz_[c] >= gc.N3) continue;
+      for (int bq = 0; bq < ny; ++bq) {
+        if (cy_[bq] < 0 || cy_[bq] >= gc.N2) continue;
+        for (int a = 0; a < nx; ++a) {
+          if (cx_[a] < 0 || cx_[a] >= gc.N1) continue;
+          const cx<R> v = ldg(e + gidx(cx_[a], cy_[bq], cz_[c], gc.N1, gc.N2));
+          are += v.re;
+          aim += v.im;
+        }
+      }
+    }
+    const R s = (R)1 / (R)(nx * ny * nz);
+    const size_t p = gidx(i, j, k, gf.N1, gf.N2);
+    const cx<R> base = ldg(u1 + p);
+    out[p] = mkc<R>(fma(are, s, base.re), fma(aim, s, base.im));
+  }
+}
+
+// k^2 on a coarse grid by injection (coarse node c = fine node 2c, Sec. 3.4.4 DCG).
+__global__ void k_inject(Grid gf, Grid gc, const double* __restrict__ kf, double* __restrict__ kc) {
+  const size_t n = gc.npts();
+  const int off = gf.bc == 0 ? 1 : 0;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+    const int I = (int)(p % gc.N1);
+    const int J = (int)((p / gc.N1) % gc.N2);
+    const int K = (int)(p / ((size_t)gc.N1 * gc.N2));
+    kc[p] = kf[gidx(2 * (I + off) - off, 2 * (J + off) - off, 2 * (K + off) - off, gf.N1, gf.N2)];
+  }
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+    b[p] = (float)a[p];
+}
+
+// k^2 sanity check at set-up: counts non-finite or non-positive entries.
+__global__ void k_check_k2(const double* __restrict__ a, size_t n, int* __restrict__ bad) {
+  int local = 0;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+    local += !(isfinite(a[p]) && a[p] > 0.0);
+  if (local) atomicAdd(bad, local);
+}
+
+// Exact coarsest-grid solve as a dense FP64 product with the precomputed inverse:
+// one warp per row, lanes over columns in a fixed order.
+template <typename TI, typename TO>
+__global__ void k_coarse(int nc, const z128* __restrict__ Minv, const cx<TI>* __restrict__ b,
+                         cx<TO>* __restrict__ e, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= nc) return;
+  double re = 0, im = 0;
+  const z128* a = Minv + (size_t)row * nc;
+  for (int c = lane; c < nc; c += 32) {
+    const z128 m = a[c];
+    const z128 v = cvt<double>(ldg(b + c));
+    re = fma(m.re, v.re, re);
+    re = fma(-m.im, v.im, re);
+    im = fma(m.re, v.im, im);
+    im = fma(m.im, v.re, im);
+  }
+  for (int o = 16; o; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) e[row] = mkc<TO>((TO)re, (TO)im);
+}
+
+// Discrete Dirac sources (Sec. 2.4): b(node) += 1/h^3, sources applied in order.
+__global__ void k_rhs_point(Grid g, int nsrc, const int* __restrict__ idx, double amp, z128* __restrict__ b) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int s = 0; s < nsrc; ++s) {
+    const int q = idx[s];
+    if (q >= 0) b[q].re += amp;
+  }
+}
+
+dim3 grid_for(const Grid& g, int& zchunk) {
+  const int bx = (g.N1 + TX - 1) / TX, by = (g.N2 + TY - 1) / TY;
+  const int target = 152 * 8;
+  int zsplit = target / (bx * by);
+  if (zsplit < 1) zsplit = 1;
+  if (zsplit > g.N3) zsplit = g.N3;
+  zchunk = (g.N3 + zsplit - 1) / zsplit;
+  const int bz = (g.N3 + zchunk - 1) / zchunk;
+  return dim3(bx, by, bz);
+}
+
+template <typename R>
+OpCoef<R> coef_for(double h, double s_re, double s_im, double omega) {
+  OpCoef<R> c;
+  c.ih2 = (R)(1.0 / (h * h));
+  c.six_ih2 = (R)(6.0 / (h * h));
+  c.s_re = (R)s_re;
+  c.s_im = (R)s_im;
+  c.two_over_h = (R)(2.0 / h);
+  c.omega = (R)omega;
+  return c;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// Launchers
+// ------------------------------------------------------------------------------------
+template <typename R, typename TU, typename TO>
+void launch_apply(const Grid& g, double s_re, double s_im, const R* k2, const cx<TU>* u, cx<TO>* v,
+                  cudaStream_t st, const int* active) {
+  int zc;
+  dim3 gr = grid_for(g, zc);
+  k_stencil<R, 0, false, TU, TU, TO><<<gr, dim3(TX, TY), 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr, u,
+                                                                   nullptr, v, zc, active);
+}
+
+template <typename R, typename TU, typename TB, typename TO>
+void launch_resid(const Grid& g, double s_re, double s_im, const R* k2, const cx<TU>* u, const cx<TB>* b,
+                  cx<TO>* out, cudaStream_t st, const int* active) {
+  int zc;
+  dim3 gr = grid_for(g, zc);
+  k_stencil<R, 1, false, TU, TB, TO><<<gr, dim3(TX, TY), 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr,
+                                                                   u, b, out, zc, active);
+}
+
+template <typename R, typename TB, typename TO>
+void launch_jacobi(const Grid& g, double s_re, double s_im, double omega, const R* k2, const cx<R>* dinv,
+                   const cx<R>* u, const cx<TB>* b, cx<TO>* out, cudaStream_t st, const int* active) {
+  int zc;
+  dim3 gr = grid_for(g, zc);
+  OpCoef<R> c = coef_for<R>(g.h, s_re, s_im, omega);
+  if (dinv)
+    k_stencil<R, 2, true, R, TB, TO><<<gr, dim3(TX, TY), 0, st>>>(g, c, k2, dinv, u, b, out, zc, active);
+  else
+    k_stencil<R, 2, false, R, TB, TO><<<gr, dim3(TX, TY), 0, st>>>(g, c, k2, dinv, u, b, out, zc, active);
+}
+
+template <typename R, typename TB>
+void launch_smooth0(const Grid& g, double s_re, double s_im, double omega, const R* k2, const cx<R>* dinv,
+                    const cx<TB>* b, cx<R>* out, cudaStream_t st, const int* active) {
+  int zc;
+  dim3 gr = grid_for(g, zc);
+  OpCoef<R> c = coef_for<R>(g.h, s_re, s_im, omega);
+  if (dinv)
+    k_smooth0<R, true, TB><<<gr, dim3(TX, TY), 0, st>>>(g, c, k2, dinv, b, out, zc, active);
+  else
+    k_smooth0<R, false, TB><<<gr, dim3(TX, TY), 0, st>>>(g, c, k2, dinv, b, out, zc, active);
+}
+
+template <typename R>
+void launch_restrict(const Grid& gf, const Grid& gc, const cx<R>* r, cx<R>* out, cudaStream_t st, const int* active) {
+  int zc;
+  dim3 gr = grid_for(gc, zc);
+  k_restrict<R><<<gr, dim3(TX, TY), 0, st>>>(gf, gc, r, out, zc, active);
+}
+
+template <typename R>
+void launch_prolong_add(const Grid& gf, const Grid& gc, const cx<R>* u1, const cx<R>* e, cx<R>* out, cudaStream_t st,
+                        const int* active) {
+  int zc;
+  dim3 gr = grid_for(gf, zc);
+  k_prolong_add<R><<<gr, dim3(TX, TY), 0, st>>>(gf, gc, u1, e, out, zc, active);
+}
+
+template <typename TI, typename TO>
+void launch_coarse(int nc, const z128* Minv, const cx<TI>* b, cx<TO>* e, cudaStream_t st, const int* active) {
+  const int wpb = 8;
+  k_coarse<TI, TO><<<(nc + wpb - 1) / wpb, wpb * 32, 0, st>>>(nc, Minv, b, e, active);
+}
+
+void launch_dinv(const Grid& g, double s_re, double s_im, double omega, const double* k2, z128* out, cudaStream_t st) {
+  k_dinv<<<1216, 256, 0, st>>>(g, coef_for<double>(g.h, s_re, s_im, omega), k2, out);
+}
+
+void launch_inject(const Grid& gf, const Grid& gc, const double* kf, double* kc, cudaStream_t st) {
+  k_inject<<<1216, 256, 0, st>>>(gf, gc, kf, kc);
+}
+
+void launch_to_float(const double* a, float* b, size_t n, cudaStream_t st) {
+  k_to_float<<<1216, 256, 0, st>>>(a, b, n);
+}
+
+void launch_check_k2(const double* a, size_t n, int* bad, cudaStream_t st) {
+  k_check_k2<<<1216, 256, 0, st>>>(a, n, bad);
+}
+
+void launch_rhs_point(const Grid& g, int nsrc, const int* idx, double amp, z128* b, cudaStream_t st) {
+  k_rhs_point<<<1, 32, 0, st>>>(g, nsrc, idx, amp, b);
+}
+
+// explicit instantiations used by the library
+#define HELM_INST_R(R)                                                                                   \
+  template void launch_restrict<R>(const Grid&, const Grid&, const cx<R>*, cx<R>*, cudaStream_t, const int*); \
+  template void launch_prolong_add<R>(const Grid&, const Grid&, const cx<R>*, const cx<R>*, cx<R>*, cudaStream_t, const int*);
+HELM_INST_R(double)
+HELM_INST_R(float)
+
+template void launch_apply<double, double, double>(const Grid&, double, double, const double*, const z128*, z128*, cudaStream_t, const int*);
+template void launch_apply<double, float, double>(const Grid&, double, double, const double*, const z64*, z128*, cudaStream_t, const int*);
+template void launch_apply<float, float, float>(const Grid&, double, double, const float*, const z64*, z64*, cudaStream_t, const int*);
+template void launch_resid<double, double, double, double>(const Grid&, double, double, const double*, const z128*, const z128*, z128*, cudaStream_t, const int*);
+template void launch_resid<double, double, double, float>(const Grid&, double, double, const double*, const z128*, const z128*, z64*, cudaStream_t, const int*);
+template void launch_resid<float, float, float, float>(const Grid&, double, double, const float*, const z64*, const z64*, z64*, cudaStream_t, const int*);
+template void launch_resid<float, float, double, float>(const Grid&, double, double, const float*, const z64*, const z128*, z64*, cudaStream_t, const int*);
+template void launch_jacobi<double, double, double>(const Grid&, double, double, double, const double*, const z128*, const z128*, const z128*, z128*, cudaStream_t, const int*);
+template void launch_jacobi<float, float, float>(const Grid&, double, double, double, const float*, const z64*, const z64*, const z64*, z64*, cudaStream_t, const int*);
+template void launch_jacobi<float, double, float>(const Grid&, double, double, double, const float*, const z64*, const z64*, const z128*, z64*, cudaStream_t, const int*);
+template void launch_jacobi<float, double, double>(const Grid&, double, double, double, const float*, const z64*, const z64*, const z128*, z128*, cudaStream_t, const int*);
+template void launch_jacobi<float, float, double>(const Grid&, double, double, double, const float*, const z64*, const z64*, const z64*, z128*, cudaStream_t, const int*);
+template void launch_jacobi<double, double, float>(const Grid&, double, double, double, const double*, const z128*, const z128*, const z128*, z64*, cudaStream_t, const int*);
+template void launch_smooth0<double, double>(const Grid&, double, double, double, const double*, const z128*, const z128*, z128*, cudaStream_t, const int*);
+template void launch_smooth0<float, float>(const Grid&, double, double, double, const float*, const z64*, const z64*, z64*, cudaStream_t, const int*);
+template void launch_smooth0<float, double>(const Grid&, double, double, double, const float*, const z64*, const z128*, z64*, cudaStream_t, const int*);
+template void launch_coarse<double, double>(int, const z128*, const z128*, z128*, cudaStream_t, const int*);
+template void launch_coarse<float, float>(int, const z128*, const z64*, z64*, cudaStream_t, const int*);
+template void launch_coarse<double, float>(int, const z128*, const z128*, z64*, cudaStream_t, const int*);
+template void launch_coarse<float, double>(int, const z128*, const z64*, z128*, cudaStream_t, const int*);
+
+}  // namespace helm

@@ -1,0 +1,221 @@
+"""Python binding of libhelm (include/helm.h): argument marshalling only.
+
+Every step of the solve runs in the CUDA kernels of ``libhelm.so``; this module converts
+torch tensors to pointers, passes torch's current CUDA stream, and raises on error codes.
+There is no CPU fallback: without the built library every call raises.
+
+Tensor layout: a grid vector is a contiguous tensor shaped (N3, N2, N1) (x fastest) of
+dtype complex128 (FP64 path) or complex64 (FP32 path) on a CUDA device.  k^2 is float64.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhelm.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ENUMERIC = range(7)
+STATUS = {0: "HELM_OK", 1: "HELM_EINVAL", 2: "HELM_ENOMEM", 3: "HELM_ECUDA", 4: "HELM_ENOCONV",
+          5: "HELM_ETIMEOUT", 6: "HELM_ENUMERIC"}
+DIRICHLET, SOMMERFELD = 0, 1
+C128, C64 = 0, 1
+OP_A, OP_M = 0, 1
+GMRES, FGMRES = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class HelmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("beta1", C.c_double), ("beta2", C.c_double), ("omega", C.c_double), ("nu1", C.c_int),
+                ("nu2", C.c_int), ("coarsest_n", C.c_int), ("krylov", C.c_int), ("restart", C.c_int),
+                ("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("status", C.c_int),
+                ("rel_residual", C.c_double), ("ms_total", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libhelm.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libhelm.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    L.helm_default_params.argtypes = [C.POINTER(Params)]
+    L.helm_default_params.restype = None
+    L.helm_create.argtypes = [i, i, i, d, vp, i, C.POINTER(Params), vp, C.POINTER(vp)]
+    L.helm_destroy.argtypes = [vp]
+    L.helm_levels.argtypes = [vp, C.POINTER(i)]
+    L.helm_level_dims.argtypes = [vp, i, C.POINTER(i), C.POINTER(d)]
+    L.helm_apply.argtypes = [vp, i, i, vp, vp, vp]
+    L.cslp_vcycle.argtypes = [vp, i, vp, vp, vp]
+    L.helm_vcycle_stage.argtypes = [vp, i, i, i, vp, vp, vp, vp]
+    L.helm_rhs_point.argtypes = [vp, i, C.POINTER(i), vp, vp]
+    L.helm_solve.argtypes = [vp, vp, vp, C.POINTER(SolveInfo), vp]
+    L.helm_last_error.argtypes = [vp]
+    L.helm_last_error.restype = C.c_char_p
+    for f in ("helm_create", "helm_destroy", "helm_levels", "helm_level_dims", "helm_apply", "cslp_vcycle",
+              "helm_vcycle_stage", "helm_rhs_point", "helm_solve"):
+        getattr(L, f).restype = i
+    _lib = L
+    return L
+
+
+def default_params():
+    p = Params()
+    lib().helm_default_params(C.byref(p))
+    return p
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+_DT = {torch.complex128: C128, torch.complex64: C64}
+
+
+class Solver:
+    """A libhelm context: hierarchy, coarsest inverse and Krylov workspace on one GPU."""
+
+    def __init__(self, n, h, k2, bc=SOMMERFELD, *, beta1=1.0, beta2=-0.5, omega=0.8, coarsest_n=4,
+                 krylov="gmres", restart=30, tol=1e-6, max_iter=2000, precision="fp64", device=None):
+        n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(int(x) for x in n)
+        self.n = (n1, n2, n3)
+        self.h = float(h)
+        self.bc = bc
+        d = -1 if bc == DIRICHLET else 1
+        self.shape = (n3 + d, n2 + d, n1 + d)
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        k2t = torch.as_tensor(k2, dtype=torch.float64)
+        if tuple(k2t.shape) != self.shape:
+            k2t = k2t.reshape(self.shape)
+        k2t = k2t.to(self.device).contiguous()
+        p = default_params()
+        p.beta1, p.beta2, p.omega, p.coarsest_n = beta1, beta2, omega, coarsest_n
+        p.krylov = {"gmres": GMRES, "fgmres": FGMRES}[krylov]
+        p.restart, p.tol, p.max_iter = restart, tol, max_iter
+        p.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
+        self.params = p
+        ctx = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = lib().helm_create(n1, n2, n3, self.h, _ptr(k2t), bc, C.byref(p), _stream(), C.byref(ctx))
+        if st != OK:
+            raise HelmError(st, lib().helm_last_error(None).decode())
+        self._ctx = ctx
+
+    # -- housekeeping -----------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().helm_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            raise HelmError(st, lib().helm_last_error(self._ctx).decode())
+
+    @property
+    def nlevels(self):
+        n = C.c_int()
+        self._check(lib().helm_levels(self._ctx, C.byref(n)))
+        return n.value
+
+    def level_dims(self, level):
+        dims = (C.c_int * 6)()
+        h = C.c_double()
+        self._check(lib().helm_level_dims(self._ctx, level, dims, C.byref(h)))
+        return {"n": (dims[0], dims[1], dims[2]), "shape": (dims[5], dims[4], dims[3]), "h": h.value}
+
+    def _vec(self, t, shape=None, dtype=None):
+        shape = self.shape if shape is None else shape
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+            raise TypeError("expected a CUDA tensor")
+        if dtype is not None and t.dtype != dtype:
+            raise TypeError(f"expected {dtype}, got {t.dtype}")
+        if t.dtype not in _DT:
+            raise TypeError("grid vectors are complex128 or complex64")
+        if tuple(t.shape) != tuple(shape):
+            t = t.reshape(shape)
+        return t.contiguous()
+
+    # -- operators ----------------------------------------------------------------------
+    def apply(self, u, op="A", out=None):
+        u = self._vec(u)
+        v = torch.empty_like(u) if out is None else out
+        self._check(lib().helm_apply(self._ctx, {"A": OP_A, "M": OP_M}[op], _DT[u.dtype], _ptr(u), _ptr(v), _stream()))
+        return v
+
+    def vcycle(self, r, out=None):
+        r = self._vec(r)
+        z = torch.empty_like(r) if out is None else out
+        self._check(lib().cslp_vcycle(self._ctx, _DT[r.dtype], _ptr(r), _ptr(z), _stream()))
+        return z
+
+    def vcycle_stage(self, level, stage, b, e=None):
+        L = self.nlevels
+        dt = b.dtype
+        if stage == 0:
+            out = torch.empty(self.level_dims(level + 1)["shape"], dtype=dt, device=b.device)
+        else:
+            out = torch.empty(self.level_dims(level)["shape"], dtype=dt, device=b.device)
+        b = self._vec(b, self.level_dims(level)["shape"])
+        ep = None
+        if stage == 1:
+            e = self._vec(e, self.level_dims(level + 1)["shape"], dt)
+            ep = _ptr(e)
+        assert 0 <= level < L
+        self._check(lib().helm_vcycle_stage(self._ctx, level, stage, _DT[dt], _ptr(b), ep, _ptr(out), _stream()))
+        return out
+
+    def rhs_point(self, nodes):
+        nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.int32).reshape(-1, 3))
+        b = torch.empty(self.shape, dtype=torch.complex128, device=self.device)
+        self._check(lib().helm_rhs_point(self._ctx, len(nodes), nodes.ctypes.data_as(C.POINTER(C.c_int)), _ptr(b),
+                                         _stream()))
+        return b
+
+    def solve(self, b, x=None):
+        """Solve A x = b.  b (and x, the initial guess) are complex128 tensors on the GPU, or
+        both on the host (pinned or pageable), in which case the library stages the copies."""
+        host = b.device.type == "cpu"
+        b = b.reshape(self.shape).contiguous()
+        if b.dtype != torch.complex128:
+            raise TypeError("helm_solve takes complex128 vectors")
+        if x is None:
+            x = torch.zeros_like(b)
+        x = x.reshape(self.shape)
+        if (x.device.type == "cpu") != host or not x.is_contiguous():
+            raise TypeError("x must be a contiguous tensor on the same kind of device as b")
+        info = SolveInfo()
+        st = lib().helm_solve(self._ctx, _ptr(b), _ptr(x), C.byref(info), _stream())
+        if st not in (OK, ENOCONV):
+            self._check(st)
+        return x, info.as_dict()

@@ -1,0 +1,241 @@
+"""GPU parity: every step of the hot path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs.
+
+Tolerances (relative, in the 2-norm over the whole grid unless stated):
+  FP64 operator, V-cycle stages, full V-cycle : 1e-12   (both sides FP64; only rounding order
+                                                          and FMA contraction differ)
+  FP32 operator / V-cycle (complex64)          : 1e-5 / 2e-5 (unit roundoff 6e-8 times the
+                                                          stencil's cancellation, see design notes)
+  solves (FP64)  : true relative residual <= tol, iterations within +-1 of the oracle,
+                   solution difference <= 1e-5
+Grids are chosen to span several 32 x 8 thread tiles with ragged tails in x and y, odd
+unknown counts, non-cubic boxes and the degenerate one-level hierarchy.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2308_06085_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+D, S = 0, 1
+CASES = [
+    ("dir_ragged", (40, 20, 12), D, 2),
+    ("som_ragged", (40, 20, 12), S, 2),
+    ("som_wedge32", (32, 32, 32), S, 4),
+    ("som_noncubic", (24, 8, 16), S, 2),
+]
+
+
+@pytest.fixture(scope="module")
+def helm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2308_06085_gb300 import helm as h
+
+    torch.cuda.set_device(0)
+    return h
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def make(helm, name, n, bc, coarsest, **kw):
+    h = 1.0 / max(n)
+    shape = I.unknown_shape(n, bc)
+    if name.endswith("wedge32"):
+        k2 = I.workload("wedge", 32)["k2"]
+    else:
+        k2 = I.random_k2(shape, seed=sum(map(ord, name)), kmin=2.0, kmax=0.6 / h)
+    s = helm.Solver(n, h, k2, bc, coarsest_n=coarsest, **kw)
+    o = oracle.Solver(n, h, bc, k2, coarsest_n=coarsest)
+    return s, o, k2, h, shape
+
+
+@pytest.mark.parametrize("name,n,bc,coarsest", CASES)
+@pytest.mark.parametrize("op", ["A", "M"])
+def test_apply_c128(helm, name, n, bc, coarsest, op):
+    s, o, k2, h, shape = make(helm, name, n, bc, coarsest)
+    u = I.random_vector(shape, 3)
+    v = s.apply(dev(u), op).cpu().numpy()
+    shift = (1.0, 0.0) if op == "A" else (1.0, 0.5)
+    vo = oracle.apply(u, k2, h, bc, shift)
+    assert np.abs(v - vo).max() <= 1e-12 * np.abs(vo).max()
+    assert rel(v, vo) <= 1e-12
+
+
+@pytest.mark.parametrize("name,n,bc,coarsest", CASES)
+def test_apply_c64(helm, name, n, bc, coarsest):
+    s, o, k2, h, shape = make(helm, name, n, bc, coarsest)
+    u = I.random_vector(shape, 4)
+    v = s.apply(dev(u.astype(np.complex64)), "M").cpu().numpy()
+    vo = oracle.apply(u.astype(np.complex64).astype(np.complex128), k2, h, bc, (1.0, 0.5))
+    assert rel(v, vo) <= 1e-5
+
+
+@pytest.mark.parametrize("name,n,bc,coarsest", CASES)
+def test_vcycle_stages_c128(helm, name, n, bc, coarsest):
+    s, o, k2, h, shape = make(helm, name, n, bc, coarsest)
+    L = s.nlevels
+    assert L == o.nlevels
+    for l in range(L - 1):
+        fs = s.level_dims(l)["shape"]
+        cs = s.level_dims(l + 1)["shape"]
+        b = I.random_vector(fs, 10 + l)
+        e = I.random_vector(cs, 20 + l)
+        down = s.vcycle_stage(l, 0, dev(b)).cpu().numpy()
+        assert rel(down, o.vcycle_down(l, b)) <= 1e-12, l
+        up = s.vcycle_stage(l, 1, dev(b), dev(e)).cpu().numpy()
+        assert rel(up, o.vcycle_up(l, b, e)) <= 1e-12, l
+    bl = I.random_vector(s.level_dims(L - 1)["shape"], 5)
+    ec = s.vcycle_stage(L - 1, 2, dev(bl)).cpu().numpy()
+    assert rel(ec, o.coarse_solve(bl)) <= 1e-12
+
+
+@pytest.mark.parametrize("name,n,bc,coarsest", CASES)
+def test_vcycle_c128(helm, name, n, bc, coarsest):
+    s, o, k2, h, shape = make(helm, name, n, bc, coarsest)
+    r = I.random_vector(shape, 6)
+    z = s.vcycle(dev(r)).cpu().numpy()
+    assert rel(z, o.vcycle(r)) <= 1e-12
+
+
+@pytest.mark.parametrize("name,n,bc,coarsest", CASES)
+def test_vcycle_c64(helm, name, n, bc, coarsest):
+    s, o, k2, h, shape = make(helm, name, n, bc, coarsest)
+    r = I.random_vector(shape, 7).astype(np.complex64)
+    z = s.vcycle(dev(r)).cpu().numpy()
+    err = rel(z, o.vcycle(r.astype(np.complex128)))
+    assert err <= 2e-5, err
+
+
+def test_rhs_point_bit_exact(helm):
+    for n, bc, src in [((16, 16, 16), S, [(8, 8, 0), (0, 0, 0), (16, 3, 16), (8, 8, 0)]),
+                       ((16, 12, 8), D, [(8, 6, 4), (0, 6, 4), (15, 11, 7)])]:
+        shape = I.unknown_shape(n, bc)
+        s = helm.Solver(n, 1 / 16, np.ones(shape), bc)
+        b = s.rhs_point(src).cpu().numpy()
+        np.testing.assert_array_equal(b, oracle.rhs_point(shape, bc, 1 / 16, src))
+
+
+@pytest.mark.parametrize("krylov,restart", [("gmres", 30), ("fgmres", 30), ("gmres", 200)])
+def test_solve_small_dirichlet(helm, krylov, restart):
+    """The small workload itself: n = 32, constant k = 20 (kh = 0.625), Dirichlet, centre source."""
+    w = I.workload("small")
+    s = helm.Solver(w["n"], w["h"], w["k2"], D, krylov=krylov, restart=restart, max_iter=600)
+    o = oracle.Solver(w["n"], w["h"], D, w["k2"])
+    b = s.rhs_point(w["sources"])
+    x, info = s.solve(b)
+    ro = o.gmres(b.cpu().numpy(), restart=restart, tol=1e-6, max_iter=600, flexible=krylov == "fgmres")
+    assert info["status"] == 0 and ro["status"] == 0
+    assert info["rel_residual"] <= 1e-6
+    assert abs(info["iterations"] - ro["iters"]) <= 1, (info, ro["iters"])
+    assert rel(x.cpu().numpy(), ro["x"]) <= 1e-5
+    # independent check of the residual with the oracle's operator
+    ax = oracle.apply(x.cpu().numpy(), w["k2"], w["h"], D)
+    assert np.linalg.norm(b.cpu().numpy() - ax) / np.linalg.norm(b.cpu().numpy()) <= 1.01e-6
+
+
+@pytest.mark.parametrize("krylov", ["gmres", "fgmres"])
+def test_solve_wedge_scaled(helm, krylov):
+    w = I.workload("wedge", 32)
+    s = helm.Solver(w["n"], w["h"], w["k2"], S, krylov=krylov)
+    o = oracle.Solver(w["n"], w["h"], S, w["k2"])
+    b = s.rhs_point(w["sources"])
+    x, info = s.solve(b)
+    ro = o.gmres(b.cpu().numpy(), restart=30, tol=1e-6, flexible=krylov == "fgmres")
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-6
+    assert abs(info["iterations"] - ro["iters"]) <= 1, (info, ro["iters"])
+    assert rel(x.cpu().numpy(), ro["x"]) <= 1e-5
+
+
+def test_solve_mixed_precision(helm):
+    """complex64 V-cycle under FP64 FGMRES(30): the true residual still reaches 1e-6; the
+    error against a tight FP64 oracle solution is reported (the paper fixes no bound)."""
+    w = I.workload("mixed", 32)
+    s = helm.Solver(w["n"], w["h"], w["k2"], S, precision="mixed")
+    o = oracle.Solver(w["n"], w["h"], S, w["k2"])
+    b = s.rhs_point(w["sources"])
+    x, info = s.solve(b)
+    ro = o.gmres(b.cpu().numpy(), restart=30, tol=1e-10, max_iter=2000)
+    ro6 = o.gmres(b.cpu().numpy(), restart=30, tol=1e-6)
+    err = rel(x.cpu().numpy(), ro["x"])
+    print(f"mixed: iters {info['iterations']} (fp64 oracle {ro6['iters']}), relres {info['rel_residual']:.2e}, "
+          f"error vs tight oracle {err:.2e}")
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-6
+    assert abs(info["iterations"] - ro6["iters"]) <= 3
+    assert err <= 1e-4
+
+
+def test_solve_host_buffers_and_warm_start(helm):
+    w = I.workload("wedge", 16)
+    s = helm.Solver(w["n"], w["h"], w["k2"], S)
+    b = s.rhs_point(w["sources"])
+    xd, infod = s.solve(b)
+    bh = b.cpu().pin_memory()
+    xh, infoh = s.solve(bh, torch.zeros_like(bh).pin_memory())
+    assert infoh["iterations"] == infod["iterations"]
+    np.testing.assert_array_equal(xh.numpy(), xd.cpu().numpy())
+    # pageable host memory works too
+    xp, infop = s.solve(b.cpu().clone(), torch.zeros(s.shape, dtype=torch.complex128))
+    np.testing.assert_array_equal(xp.numpy(), xd.cpu().numpy())
+    # warm start from the solution: converged at entry, no Arnoldi step
+    x2, info2 = s.solve(b, xd.clone())
+    assert info2["iterations"] == 0 and info2["rel_residual"] <= 1e-6
+
+
+def test_solve_edge_cases(helm):
+    # zero right-hand side
+    w = I.workload("wedge", 16)
+    s = helm.Solver(w["n"], w["h"], w["k2"], S, max_iter=1)
+    x, info = s.solve(torch.zeros(s.shape, dtype=torch.complex128, device="cuda"))
+    assert info["iterations"] == 0 and torch.count_nonzero(x) == 0
+    # iteration cap
+    b = s.rhs_point(w["sources"])
+    x, info = s.solve(b)
+    assert info["status"] == 4 and info["iterations"] == 1
+    # one-level hierarchies (coarsest solve only) and the smallest grids
+    for n, bc in [((2, 2, 2), D), ((2, 2, 2), S), ((6, 10, 8), S), ((3, 5, 7), D)]:
+        shape = I.unknown_shape(n, bc)
+        k2 = I.random_k2(shape, 3, 1.0, 3.0)
+        s = helm.Solver(n, 0.2, k2, bc)
+        o = oracle.Solver(n, 0.2, bc, k2)
+        assert s.nlevels == o.nlevels == 1
+        r = I.random_vector(shape, 8)
+        assert rel(s.vcycle(dev(r)).cpu().numpy(), o.vcycle(r)) <= 1e-12
+        x, info = s.solve(dev(r))
+        assert info["status"] == 0 and info["iterations"] <= 30
+
+
+def test_full_size_wedge_apply_and_vcycle(helm):
+    """The n = 128 wedge (129^3 unknowns) in the configuration the benchmark times: the
+    operator and one V-cycle against the oracle on the whole grid."""
+    w = I.workload("wedge")
+    s = helm.Solver(w["n"], w["h"], w["k2"], S)
+    o = oracle.Solver(w["n"], w["h"], S, w["k2"])
+    u = I.random_vector(s.shape, 12)
+    v = s.apply(dev(u)).cpu().numpy()
+    assert rel(v, oracle.apply(u, w["k2"], w["h"], S)) <= 1e-12
+    z = s.vcycle(dev(u)).cpu().numpy()
+    assert rel(z, o.vcycle(u)) <= 1e-12
+
+
+def test_full_size_wedge_solve_residual(helm):
+    """Full-size FP64 solve: the oracle's own operator confirms ||b - A x|| / ||b|| <= 1e-6."""
+    w = I.workload("wedge")
+    s = helm.Solver(w["n"], w["h"], w["k2"], S)
+    b = s.rhs_point(w["sources"])
+    x, info = s.solve(b)
+    assert info["status"] == 0
+    bn = b.cpu().numpy()
+    ax = oracle.apply(x.cpu().numpy(), w["k2"], w["h"], S)
+    rr = np.linalg.norm(bn - ax) / np.linalg.norm(bn)
+    assert rr <= 1.01e-6 and abs(rr - info["rel_residual"]) <= 1e-9
