@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark: time-to-1e-6 of the CSLP-preconditioned matrix-free Helmholtz solve on one GB300.
+
+Workload (one step = one full solve, the whole hot path): the three-layer wedge model on the
+unit cube, n = 128 intervals per direction (129^3 = 2,146,689 unknowns, Sommerfeld on every
+face), max k h = 0.625, point source at the top-face centre, complex128 throughout:
+right-preconditioned GMRES(30) with one CSLP V-cycle per step, to ||b - A x|| / ||b|| <= 1e-6.
+
+Printed (one JSON line on rank 0): value = device time per solve (ms), the dominant kernel's
+roofline from live CUDA-event timings inside the timed region, the end-to-end time through the
+C ABI with host buffers, the FP64 CPU oracle timed on a bounded sample, clocks sampled during
+the timed region, and variants (mixed precision; n = 256) when --variants is on.
+
+--impl reference times the FP64 CPU oracle (the reference for this build) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-6 solve & stencil HBM GB/s at 1 GB300: FP64 vs mixed vs batched"
+UNIT = "ms"
+# FP64 peak derived from the nominal 1.25 TFLOP/s at 2070 MHz on 152 SMs: 2 FP64 FMA per SM
+# per clock, so 152 * 2 * 2 flop * 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+SAMPLE_STEPS = 30  # Arnoldi steps in the oracle sample (one GMRES(30) restart cycle)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=128, help="intervals per direction of the wedge workload")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", type=int, default=1, help="also time mixed precision and n = 256")
+    ap.add_argument("--orth", choices=["fp64", "df"], default="fp64",
+                    help="Gram-Schmidt arithmetic: native FP64 or double-float FP32 pairs")
+    ap.add_argument("--reorth", choices=["selective", "always"], default="selective",
+                    help="second Gram-Schmidt pass on every step, or only when the first pass lost half of |w|")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel timed leg")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# clocks
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.f = open(self.path, "w")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle sample (runs in a child process so its OpenMP runtime stays apart from torch)
+# ------------------------------------------------------------------------------------------
+ORACLE_CHILD = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import oracle
+from paper_2308_06085_gb300 import inputs as I
+w = I.workload("wedge", {n})
+o = oracle.Solver(w["n"], w["h"], oracle.SOMMERFELD, w["k2"])
+b = oracle.rhs_point(o.shape, oracle.SOMMERFELD, w["h"], w["sources"])
+out = {{}}
+if {full}:
+    t = time.perf_counter(); r = o.gmres(b, restart=30, tol=1e-6); out["full_ms"] = 1e3 * (time.perf_counter() - t)
+    out["full_iters"] = r["iters"]
+ts = []
+for _ in range({reps}):
+    t = time.perf_counter(); o.gmres(b, restart=30, tol=1e-6, max_iter={steps}); ts.append(time.perf_counter() - t)
+out["sample_s"] = ts
+print(json.dumps(out))
+"""
+
+
+def oracle_sample(n, reps, full=False, steps=SAMPLE_STEPS):
+    from oracle import build_oracle
+
+    build_oracle.build()
+    cores = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores))
+    code = ORACLE_CHILD.format(root=ROOT, n=n, full=bool(full), reps=reps, steps=steps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1]), cores
+
+
+# ------------------------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+# ------------------------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    res, cores = oracle_sample(args.n, args.warmup + args.steps, full=True)
+    per_step = res["sample_s"][args.warmup:]
+    iters = res["full_iters"]
+    ms = 1e3 * statistics.mean(per_step) / SAMPLE_STEPS * iters
+    n = args.n
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": workload_config(n),
+        "cpu_baseline": {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: {SAMPLE_STEPS} Arnoldi steps (one GMRES(30) cycle) of the FP64 oracle on "
+                                   f"the {n}^3-interval wedge, per-step time x the oracle's #Matvec ({iters}); "
+                                   f"full oracle solve once: {res['full_ms']:.0f} ms"},
+        "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "oracle_full_solve_ms": res["full_ms"], "oracle_iterations": iters,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(n):
+    return {"workload": f"wedge n={n} ({n + 1}^3 = {(n + 1) ** 3:,} unknowns), Sommerfeld, point source at top-face "
+                        f"centre, max kh 0.625, FP64 right-preconditioned GMRES(30) + 1 CSLP V-cycle, tol 1e-6",
+            "n": n, "unknowns": (n + 1) ** 3, "krylov": "GMRES(30)", "precision": "complex128",
+            "beta": [1.0, -0.5], "omega": 0.8,
+            "l2": "working set > L2: the Krylov basis alone is 31 x 34 MB = 1.06 GB, so every step streams from HBM"}
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2308_06085_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_name):
+    """DRAM bytes per launch of `kernel_name` from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except ValueError:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel_name)
+    return None if k is None else k
+
+
+def time_solves(torch, s, b, steps, x=None):
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x = torch.zeros_like(b) if x is None else x
+    infos = []
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(steps):
+        x.zero_()
+        _, info = s.solve(b, x)
+        infos.append(info)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, infos, x
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from paper_2308_06085_gb300 import helm, inputs
+
+    n = args.n
+    w = inputs.workload("wedge", n)
+    s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov="gmres", restart=30, tol=1e-6,
+                    orth=args.orth, reorth=args.reorth)
+    b = s.rhs_point(w["sources"])
+    for _ in range(args.warmup):
+        _, info = s.solve(b)
+    # timed region: K full solves, device time by CUDA events on the launching stream
+    clocks = ClockSampler(local)
+    s.profile(False)  # resets the launch counter
+    if dist:
+        dist.barrier()
+    ms, infos, x = time_solves(torch, s, b, args.steps)
+    if dist:
+        dist.barrier()
+    _, launches = s.profile_read()
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    iters = infos[-1]["iterations"]
+    relres = infos[-1]["rel_residual"]
+    # the same K solves again with per-kernel CUDA events (kernel roofline)
+    ms_prof = None
+    fams = [{"name": "none", "launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0}]
+    if not args.no_profile:
+        s.profile(True)
+        ms_prof, _, _ = time_solves(torch, s, b, args.steps)
+        fams, _ = s.profile_read()
+        s.profile(False)
+    fams.sort(key=lambda f: -f["ms"])
+    total_ms = sum(f["ms"] for f in fams)
+    top = fams[0]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    fp64_kernels = ("k_mdot", "k_gs_update")
+    if top["ms"] <= 0:
+        roof = {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None}
+    elif top["name"] in fp64_kernels and args.orth == "fp64":
+        achieved = top["flops"] / (top["ms"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)"}
+    else:
+        achieved = top["bytes"] / (top["ms"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"}
+    roof["kernel"] = top["name"] + ("_df" if args.orth == "df" and top["name"] in fp64_kernels else "")
+    roof["launches"] = top["launches"]
+    roof["avg_launch_us"] = 1e3 * top["ms"] / max(top["launches"], 1)
+    roof["share_of_kernel_time"] = top["ms"] / total_ms if total_ms else None
+    roof["hbm_gbs_achieved"] = top["bytes"] / (top["ms"] * 1e-3) / 1e9 if top["ms"] > 0 else None
+    tr = ncu_traffic(top["name"])
+    roof["traffic"] = None if tr is None else tr.get("dram_bytes_per_launch")
+    if tr is not None:
+        roof["traffic_note"] = tr.get("note")
+    kernels = [{"name": f["name"], "launches": f["launches"], "ms_per_step": f["ms"] / args.steps,
+                "share": f["ms"] / total_ms if total_ms else None,
+                "gbs": f["bytes"] / (f["ms"] * 1e-3) / 1e9 if f["ms"] else None,
+                "fp64_tflops": f["flops"] / (f["ms"] * 1e-3) / 1e12 if f["ms"] else None}
+               for f in fams if f["launches"]]
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(torch, s, b, args.steps)
+
+    variants = {}
+    if args.variants and rank == 0:
+        variants = run_variants(torch, helm, inputs, args)
+
+    line = {
+        "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(n),
+        "iterations": iters, "rel_residual": relres, "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk, "ms_per_step_profiled": ms_prof, "kernels": kernels, "variants": variants,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        res, cores = oracle_sample(n, 1)
+        t = res["sample_s"][0]
+        line["cpu_baseline"] = {
+            "value": 1e3 * t / SAMPLE_STEPS * iters, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{SAMPLE_STEPS} Arnoldi steps (one GMRES(30) cycle) of the FP64 oracle on the same workload, "
+                      f"{t:.2f} s; per-step time x the GPU solve's #Matvec ({iters})"}
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    s.close()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def end_to_end(torch, s, b, steps):
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    xh.zero_()
+    s.solve(bh, xh)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        xh.zero_()
+        s.solve(bh, xh)
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / steps
+    nbytes = b.numel() * 16
+    return {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes,
+            "note": "helm_solve with pinned host b and x: H2D of b and x0, D2H of x inside each step"}
+
+
+def run_variants(torch, helm, inputs, args):
+    out = {}
+    for name, n, prec, krylov in [("wedge_n128_mixed", 128, "mixed", "fgmres"),
+                                  ("wedge_n128_fp64_fgmres", 128, "fp64", "fgmres"),
+                                  ("mixed_n256_fp64", 256, "fp64", "gmres"),
+                                  ("mixed_n256_mixed", 256, "mixed", "fgmres")]:
+        w = inputs.workload("mixed" if n == 256 else "wedge", n)
+        s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov=krylov, precision=prec, orth=args.orth,
+                        reorth=args.reorth)
+        b = s.rhs_point(w["sources"])
+        s.solve(b)
+        ms, infos, _ = time_solves(torch, s, b, 2)
+        out[name] = {"ms": ms, "iterations": infos[-1]["iterations"], "rel_residual": infos[-1]["rel_residual"],
+                     "unknowns": (n + 1) ** 3}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -61,6 +61,8 @@ typedef enum { HELM_C128 = 0, HELM_C64 = 1 } helm_dtype;
 typedef enum { HELM_OP_A = 0, HELM_OP_M = 1 } helm_op;
 typedef enum { HELM_GMRES = 0, HELM_FGMRES = 1 } helm_krylov;
 typedef enum { HELM_PREC_FP64 = 0, HELM_PREC_MIXED = 1 } helm_precision;
+typedef enum { HELM_ORTH_FP64 = 0, HELM_ORTH_DF = 1 } helm_orth;
+typedef enum { HELM_REORTH_ALWAYS = 0, HELM_REORTH_SELECTIVE = 1 } helm_reorth;
 
 /* Solver parameters (Sec. 3.3-3.4 and Sec. 5).  helm_default_params fills the paper's
  * values: beta1 = 1, beta2 = -0.5 (M = -Lap - (beta1 - beta2 i) k^2, Sec. 3.3 Eq.
@@ -80,6 +82,14 @@ typedef struct {
   int max_iter;     /* cap on products with A in the Arnoldi process (#Matvec) */
   int precision;    /* helm_precision: HELM_PREC_MIXED runs the V-cycle in complex64
                        under an FP64 flexible outer Krylov (forces HELM_FGMRES) */
+  int orth;         /* helm_orth: arithmetic of the Gram-Schmidt inner products and updates.
+                       HELM_ORTH_FP64: native FP64.  HELM_ORTH_DF: the Krylov basis is held
+                       as pairs of FP32 values (hi + lo, about 48 significant bits) and the
+                       products and sums use error-free FP32 transformations; vectors
+                       outside the basis, norms and the Hessenberg problem stay FP64. */
+  int reorth;       /* helm_reorth: classical Gram-Schmidt with a second pass on every Arnoldi
+                       step (ALWAYS), or only when the first pass removed more than half of
+                       |w|^2 (SELECTIVE, the Daniel-Gragg-Kaufman-Stewart test) */
 } helm_params;
 
 /* Per-solve report (host struct). */
@@ -158,6 +168,27 @@ HELM_API helm_status helm_rhs_point(helm_ctx* ctx, int nsrc, const int* nodes, v
  * iterate) or HELM_ENUMERIC (breakdown to NaN/Inf). */
 HELM_API helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_info* info,
                        void* stream);
+
+/* Per-kernel-family statistics of the opt-in profiler. */
+typedef struct {
+  const char* name;   /* kernel function(s) of the family; static string */
+  long long launches; /* timed launches */
+  double ms;          /* sum of CUDA-event durations of those launches */
+  double bytes;       /* algorithmic bytes moved by those launches (minimum reads + writes) */
+  double flops;       /* algorithmic floating-point operations (an FMA counts 2) */
+} helm_kernel_stat;
+
+/* Library instrumentation (not part of the paper's method).  enable = 1 brackets every
+ * kernel launch of this context with CUDA events on the launching stream and accumulates
+ * per-family durations; enable = 0 stops timing.  Either call resets the totals.  Launch
+ * counting is always on. */
+HELM_API helm_status helm_profile(helm_ctx* ctx, int enable);
+
+/* Read the profiler: up to `cap` families into `stats` (count receives the number of
+ * families), and the number of kernel launches this context made since the last reset
+ * into *launches (either pointer may be NULL).  Waits for pending timed launches. */
+HELM_API helm_status helm_profile_read(helm_ctx* ctx, helm_kernel_stat* stats, int cap, int* count,
+                                       long long* launches);
 
 /* Message for the last failing call on ctx (or for the last failing helm_create when
  * ctx is NULL).  The string is owned by the library. */

@@ -63,6 +63,73 @@ __device__ __forceinline__ cx<float> ldg(const cx<float>* p) {
   return mkc<float>(v.x, v.y);
 }
 
+// Double-float complex: each FP64 component held as an unevaluated sum hi + lo of two FP32
+// values (about 48 significant bits).  Layout (re_hi, im_hi, re_lo, im_lo), 16 bytes, so
+// the first 8 bytes are the value rounded to complex64.
+struct alignas(16) zdf {
+  float rh, ih, rl, il;
+};
+
+__device__ __forceinline__ zdf ldg(const zdf* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  zdf z;
+  z.rh = v.x; z.ih = v.y; z.rl = v.z; z.il = v.w;
+  return z;
+}
+
+// x = hi + lo with hi = fl32(x), lo = fl32(x - hi).
+__device__ __forceinline__ void df_split(double x, float& hi, float& lo) {
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(x - (double)hi);
+}
+__device__ __forceinline__ zdf df_from(cx<double> z) {
+  zdf r;
+  df_split(z.re, r.rh, r.rl);
+  df_split(z.im, r.ih, r.il);
+  return r;
+}
+__device__ __forceinline__ cx<double> df_to_c128(const zdf& z) {
+  return mkc<double>((double)z.rh + (double)z.rl, (double)z.ih + (double)z.il);
+}
+
+// (s, c) += (ah + al) (bh + bl), dropping al*bl (about 2^-48 relative).  The product's
+// rounding error comes from an FMA (TwoProduct), the sum's from Knuth's TwoSum; both are
+// exact in round-to-nearest FP32.  The _rn intrinsics are never contracted into FMAs, which
+// keeps the error-free transformations intact.  (s, c) stays unnormalised: |c| << |s|.
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& s, float& c) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// Double-float arithmetic on (hi, lo) pairs; results renormalised so |lo| <= ulp(hi)/2.
+__device__ __forceinline__ void df_renorm(float s, float e, float& hi, float& lo) {
+  hi = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+// (ah + al) + (bh + bl): TwoSum of the leading parts, trailing parts added to the error.
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& hi, float& lo) {
+  const float s = __fadd_rn(ah, bh);
+  const float bp = __fsub_rn(s, ah);
+  float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bp)), __fsub_rn(bh, bp));
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  df_renorm(s, e, hi, lo);
+}
+// (ah + al) (bh + bl) with the product error from an FMA; al*bl is dropped.
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& hi, float& lo) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  df_renorm(p, e, hi, lo);
+}
+
 // Grid of unknowns: N_d per direction, x fastest; bc 0 = Dirichlet, 1 = Sommerfeld.
 struct Grid {
   int N1, N2, N3;
@@ -130,6 +197,7 @@ struct KrylovCtl {
   int jend;    // last Arnoldi column completed in this cycle
   int flag;    // 1 = estimate reached tol, 2 = breakdown (zero or non-finite norm)
   int iter0;   // #Matvec before this cycle
+  int pass2;   // 1 when the current Arnoldi step takes the second Gram-Schmidt pass
   double bnorm;
   double beta;
   double est;

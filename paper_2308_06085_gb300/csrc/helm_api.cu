@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/helm.h"
@@ -54,6 +55,32 @@ template <> struct LevelBufs<float> {
   static const z64* dinv(Level&) { return nullptr; }
 };
 
+// Kernel families for the opt-in profiler (names match the kernel functions).
+enum Fam {
+  F_APPLY, F_RESID, F_JACOBI, F_SMOOTH0, F_RESTRICT, F_PROLONG, F_COARSE, F_MDOT, F_REDUCE_DOTS, F_GS_UPDATE,
+  F_NORM, F_REDUCE_NORM, F_SCALE, F_GIVENS, F_SOLUPDATE, F_MISC, F_COUNT
+};
+const char* const FAM_NAMES[F_COUNT] = {
+    "k_stencil(apply)", "k_stencil(resid)", "k_stencil(jacobi)", "k_smooth0", "k_restrict", "k_prolong_add",
+    "k_coarse", "k_mdot", "k_reduce_dots", "k_gs_update", "k_norm2_part", "k_reduce_norm", "k_scale_inv",
+    "k_givens", "k_xupdate/k_combine/k_axpy1/k_trisolve", "other"};
+
+struct ProfRec {
+  int fam, j, e0, e1;
+  int cond;  // 1: second Gram-Schmidt pass, which ran only if the step's log entry is set
+  double bytes, flops;
+};
+
+struct Prof {
+  bool on = false;
+  long long launches = 0;  // every kernel launch of this context, always counted
+  double ms[F_COUNT] = {}, bytes[F_COUNT] = {}, flops[F_COUNT] = {};
+  long long cnt[F_COUNT] = {};
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  int used = 0;
+};
+
 }  // namespace
 
 struct helm_ctx {
@@ -70,10 +97,13 @@ struct helm_ctx {
   z128* Z64 = nullptr;    // m x n0, FGMRES in FP64
   z64* Z32 = nullptr;     // m x n0, mixed precision
   z128* zs = nullptr;     // n0 scratch (V-cycle output, GMRES)
+  zdf* wdf = nullptr;     // n0 new Arnoldi vector, double-float (double-float basis)
+  z128* vcur64 = nullptr; // V-cycle input v_j as c128 (double-float basis, FP64 V-cycle)
+  z64* vcur32 = nullptr;  // V-cycle input v_j as c64 (double-float basis, mixed precision)
   z128* r = nullptr;      // n0 residual
   z128* xs = nullptr;     // staging for host x
   z128* bs = nullptr;     // staging for host b
-  z128* part = nullptr;   // (m+1) x RED_BLOCKS partial dots
+  z128* part = nullptr;   // (m+2) x RED_STRIDE partial dots
   double* partr = nullptr;
   z128 *hpass = nullptr, *hacc = nullptr;
   z128* H = nullptr;
@@ -95,6 +125,12 @@ struct helm_ctx {
   std::vector<void*> allocs;
   std::string err;
   double s_re = 1.0, s_im = 0.0;  // CSLP shift beta1 - beta2 i
+  Prof prof;
+  int cur_j = -1;  // Arnoldi column being enqueued (-1 outside the Arnoldi loop)
+  int cur_cond = 0;
+  int* reorth_log = nullptr;   // device, per Arnoldi step: second pass taken
+  int* hreorth_log = nullptr;  // pinned host copy
+  long long reorth_steps = 0, arnoldi_steps = 0;
 };
 
 namespace {
@@ -153,6 +189,61 @@ helm_status check_launch(helm_ctx* c, const char* what) {
   if (e != cudaSuccess) return fail(c, HELM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
   return HELM_OK;
 }
+
+int prof_event(helm_ctx* c) {
+  Prof& P = c->prof;
+  if (P.used == (int)P.pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    P.pool.push_back(e);
+  }
+  return P.used++;
+}
+
+void prof_pre(helm_ctx* c, cudaStream_t st, int& e0) {
+  ++c->prof.launches;
+  e0 = -1;
+  if (!c->prof.on) return;
+  e0 = prof_event(c);
+  if (e0 >= 0) cudaEventRecord(c->prof.pool[e0], st);
+}
+
+void prof_post(helm_ctx* c, cudaStream_t st, int e0, int fam, double bytes, double flops) {
+  if (!c->prof.on || e0 < 0) return;
+  const int e1 = prof_event(c);
+  if (e1 < 0) return;
+  cudaEventRecord(c->prof.pool[e1], st);
+  c->prof.recs.push_back(ProfRec{fam, c->cur_j, e0, e1, c->cur_cond, bytes, flops});
+}
+
+// Fold timed launches into the totals once their events completed.  Launches of Arnoldi
+// columns beyond `jend` returned at once (the cycle had stopped) and are dropped.
+void prof_flush(helm_ctx* c, int jend) {
+  Prof& P = c->prof;
+  if (!P.on || P.recs.empty()) { P.used = 0; P.recs.clear(); return; }
+  cudaEventSynchronize(P.pool[P.recs.back().e1]);
+  for (const ProfRec& r : P.recs) {
+    if (r.j >= 0 && r.j > jend) continue;
+    if (r.cond && r.j >= 0 && !c->hreorth_log[r.j]) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, P.pool[r.e0], P.pool[r.e1]) != cudaSuccess) { cudaGetLastError(); continue; }
+    P.ms[r.fam] += ms;
+    P.bytes[r.fam] += r.bytes;
+    P.flops[r.fam] += r.flops;
+    P.cnt[r.fam] += 1;
+  }
+  P.recs.clear();
+  P.used = 0;
+}
+
+// Launch wrapper: counts the launch and, when profiling, brackets it with events.
+#define KL(fam, bytes, flops, stmt)                      \
+  do {                                                   \
+    int e0_;                                             \
+    prof_pre(c, st, e0_);                                \
+    stmt;                                                \
+    prof_post(c, st, e0_, fam, (double)(bytes), (double)(flops)); \
+  } while (0)
 
 // Dense coarsest operator M_L (row-major), entries as in the grid kernels: diagonal
 // 6/h^2 - s k^2 - i (2 k / h) per Sommerfeld face, -1/h^2 per in-grid neighbour, and a
@@ -231,40 +322,49 @@ void run_vcycle(helm_ctx* c, const cx<TI>* rin, cx<TO>* zout, cudaStream_t st, c
   using B = LevelBufs<R>;
   const double sr = c->s_re, si = c->s_im, om = c->p.omega;
   const int L = c->nlev;
+  const double cb = 2.0 * sizeof(R);               // bytes of one complex value
+  const double kb = sizeof(R), ib = 2.0 * sizeof(TI), ob = 2.0 * sizeof(TO);
+  const double db = std::is_same<R, double>::value ? 16.0 : 0.0;  // omega/d array (FP64 path)
+  const double nc = c->nc;
   if (L == 1) {
-    launch_coarse<TI, TO>(c->nc, c->Minv, rin, zout, st, active);
+    KL(F_COARSE, nc * nc * 16 + nc * (ib + ob), 8 * nc * nc, (launch_coarse<TI, TO>(c->nc, c->Minv, rin, zout, st, active)));
     return;
   }
   // down: pre-smooth from zero, residual, restriction
   for (int l = 0; l < L - 1; ++l) {
     Level& F = c->L[l];
     Level& C = c->L[l + 1];
+    const double n = (double)F.g.npts(), ncn = (double)C.g.npts();
+    const double bi = l == 0 ? ib : cb;
     if (l == 0) {
-      launch_smooth0<R, TI>(F.g, sr, si, om, B::k2(F), B::dinv(F), rin, B::U1(F), st, active);
-      launch_resid<R, R, TI, R>(F.g, sr, si, B::k2(F), B::U1(F), rin, B::T(F), st, active);
+      KL(F_SMOOTH0, n * (bi + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, TI>(F.g, sr, si, om, B::k2(F), B::dinv(F), rin, B::U1(F), st, active)));
+      KL(F_RESID, n * (cb + bi + kb + cb), 24 * n, (launch_resid<R, R, TI, R>(F.g, sr, si, B::k2(F), B::U1(F), rin, B::T(F), st, active)));
     } else {
-      launch_smooth0<R, R>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::B(F), B::U1(F), st, active);
-      launch_resid<R, R, R, R>(F.g, sr, si, B::k2(F), B::U1(F), B::B(F), B::T(F), st, active);
+      KL(F_SMOOTH0, n * (bi + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, R>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::B(F), B::U1(F), st, active)));
+      KL(F_RESID, n * (cb + bi + kb + cb), 24 * n, (launch_resid<R, R, R, R>(F.g, sr, si, B::k2(F), B::U1(F), B::B(F), B::T(F), st, active)));
     }
-    launch_restrict<R>(F.g, C.g, B::T(F), B::B(C), st, active);
+    KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, B::T(F), B::B(C), st, active)));
   }
   // coarsest: exact FP64 solve
-  launch_coarse<R, R>(c->nc, c->Minv, B::B(c->L[L - 1]), B::E(c->L[L - 1]), st, active);
+  KL(F_COARSE, nc * nc * 16 + nc * 2 * cb, 8 * nc * nc, (launch_coarse<R, R>(c->nc, c->Minv, B::B(c->L[L - 1]), B::E(c->L[L - 1]), st, active)));
   // up: prolongation + correction, post-smoothing
   for (int l = L - 2; l >= 0; --l) {
     Level& F = c->L[l];
     Level& C = c->L[l + 1];
-    launch_prolong_add<R>(F.g, C.g, B::U1(F), B::E(C), B::T(F), st, active);
+    const double n = (double)F.g.npts(), ncn = (double)C.g.npts();
+    KL(F_PROLONG, n * 2 * cb + ncn * cb, 6 * n, (launch_prolong_add<R>(F.g, C.g, B::U1(F), B::E(C), B::T(F), st, active)));
     if (l == 0)
-      launch_jacobi<R, TI, TO>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::T(F), rin, zout, st, active);
+      KL(F_JACOBI, n * (cb + ib + kb + db + ob), 32 * n, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::T(F), rin, zout, st, active)));
     else
-      launch_jacobi<R, R, R>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::T(F), B::B(F), B::E(F), st, active);
+      KL(F_JACOBI, n * (3 * cb + kb + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::T(F), B::B(F), B::E(F), st, active)));
   }
 }
 
 void norm_into(helm_ctx* c, const z128* x, double* out, cudaStream_t st, const int* active) {
-  launch_norm2_part(x, c->n0, c->partr, st, active);
-  launch_reduce_norm(c->partr, out, st, active);
+  const double n = (double)c->n0;
+  int nb = 0;
+  KL(F_NORM, 16 * n, 4 * n, nb = launch_norm2_part(x, c->n0, c->partr, st, active));
+  KL(F_REDUCE_NORM, 8.0 * nb, nb, launch_reduce_norm(c->partr, nb, out, st, active));
 }
 
 // GMRES(m) / FGMRES(m) on device-resident b and x.
@@ -277,12 +377,15 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
   const double tol = c->p.tol;
   KrylovCtl* ctl = c->ctl;
   const int* act = &ctl->active;
+  const bool df = c->p.orth == HELM_ORTH_DF;
+  zdf* Vdf = reinterpret_cast<zdf*>(c->V);
 
   norm_into(c, b, &ctl->bnorm, st, c->one);
-  launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, c->r, st, c->one);
+  KL(F_RESID, 56.0 * n, 24.0 * n, (launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, c->r, st, c->one)));
   norm_into(c, c->r, &ctl->beta, st, c->one);
   CU(cudaMemcpyAsync(c->hctl, ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
+  prof_flush(c, -1);
   double bnorm = c->hctl->bnorm;
   int iters = 0, restarts = 0;
   helm_status status = HELM_OK;
@@ -299,30 +402,72 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
     if (relres <= tol) { status = HELM_OK; break; }
     if (iters >= c->p.max_iter) { status = HELM_ENOCONV; break; }
     const int jmax = std::min(m, c->p.max_iter - iters);
-    launch_cycle_init(ctl, c->gv, m, iters, st);
-    launch_scale_inv(c->r, &ctl->beta, c->V, n, st, act);
+    KL(F_MISC, 0, 0, launch_cycle_init(ctl, c->gv, m, iters, st));
+    if (df) {
+      if (mixed) KL(F_SCALE, 40.0 * n, 2.0 * n, (launch_scale_df<z128, float>(c->r, &ctl->beta, Vdf, c->vcur32, n, st, act)));
+      else KL(F_SCALE, 48.0 * n, 2.0 * n, (launch_scale_df<z128, double>(c->r, &ctl->beta, Vdf, c->vcur64, n, st, act)));
+    } else {
+      KL(F_SCALE, 32.0 * n, 2.0 * n, launch_scale_inv(c->r, &ctl->beta, c->V, n, st, act));
+    }
     for (int j = 0; j < jmax; ++j) {
       z128* vj = c->V + (size_t)j * n;
-      z128* w = c->V + (size_t)(j + 1) * n;
+      z128* w = c->V + (size_t)(j + 1) * n;  // FP64 Gram-Schmidt works in place in V
+      zdf* wd = c->wdf;                      // double-float Gram-Schmidt works in wdf
+      c->cur_j = j;
+      const double nd = (double)n, nv = j + 1;
       if (mixed) {
         z64* zj = c->Z32 + (size_t)j * n;
-        run_vcycle<float, double, float>(c, vj, zj, st, act);
-        launch_apply<double, float, double>(F.g, 1.0, 0.0, F.k2, zj, w, st, act);
+        if (df) {
+          run_vcycle<float, float, float>(c, c->vcur32, zj, st, act);
+          KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply_split<float>(F.g, 1.0, 0.0, F.k2, zj, wd, st, act)));
+        } else {
+          run_vcycle<float, double, float>(c, vj, zj, st, act);
+          KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply<double, float, double>(F.g, 1.0, 0.0, F.k2, zj, w, st, act)));
+        }
       } else {
         z128* zj = flexible ? c->Z64 + (size_t)j * n : c->zs;
-        run_vcycle<double, double, double>(c, vj, zj, st, act);
-        launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, zj, w, st, act);
+        run_vcycle<double, double, double>(c, df ? c->vcur64 : vj, zj, st, act);
+        if (df)
+          KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply_split<double>(F.g, 1.0, 0.0, F.k2, zj, wd, st, act)));
+        else
+          KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, zj, w, st, act)));
       }
-      // classical Gram-Schmidt, two passes
-      launch_mdot(c->V, n, j + 1, w, n, c->part, st, act);
-      launch_reduce_dots(c->part, j + 1, c->hpass, c->hacc, 0, st, act);
-      launch_gs_update(c->V, n, j + 1, c->hpass, w, n, st, act);
-      launch_mdot(c->V, n, j + 1, w, n, c->part, st, act);
-      launch_reduce_dots(c->part, j + 1, c->hpass, c->hacc, 1, st, act);
-      launch_gs_update(c->V, n, j + 1, c->hpass, w, n, st, act);
-      norm_into(c, w, c->hnorm, st, act);
-      launch_givens(ctl, c->H, m, j, jmax, c->hacc, c->hnorm, c->cs, c->sn, c->gv, tol, c->hist, c->hist_len, st);
-      launch_scale_inv(w, c->hnorm, w, n, st, act);
+      // classical Gram-Schmidt: first pass always; the second on every step (ALWAYS) or when
+      // the first pass's projection removed more than half of |w|^2 (SELECTIVE)
+      const bool sel = c->p.reorth == HELM_REORTH_SELECTIVE;
+      for (int pass = 0; pass < 2; ++pass) {
+        const int* a2 = (pass == 1 && sel) ? &ctl->pass2 : act;
+        c->cur_cond = (pass == 1 && sel) ? 1 : 0;
+        const int wn = (pass == 0 && sel) ? 1 : 0;
+        int nb = 0;
+        if (df)
+          KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nb = launch_mdot_df(Vdf, n, j + 1, wd, n, c->part, wn, st, a2));
+        else
+          KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nb = launch_mdot(c->V, n, j + 1, w, n, c->part, wn, st, a2));
+        KL(F_REDUCE_DOTS, 16.0 * nv * nb, 2.0 * nv * nb,
+           launch_reduce_dots(c->part, j + 1, nb, c->hpass, c->hacc, pass, wn ? j : -1, &ctl->pass2, c->reorth_log,
+                              st, a2));
+        if (df)
+          KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_gs_update_df(Vdf, n, j + 1, c->hpass, wd, n, st, a2));
+        else
+          KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_gs_update(c->V, n, j + 1, c->hpass, w, n, st, a2));
+      }
+      c->cur_cond = 0;
+      if (df) {
+        int nb = 0;
+        KL(F_NORM, 16.0 * nd, 4.0 * nd, nb = launch_norm2_part_df(wd, n, c->partr, st, act));
+        KL(F_REDUCE_NORM, 8.0 * nb, nb, launch_reduce_norm(c->partr, nb, c->hnorm, st, act));
+      } else {
+        norm_into(c, w, c->hnorm, st, act);
+      }
+      KL(F_GIVENS, 0, 0, launch_givens(ctl, c->H, m, j, jmax, c->hacc, c->hnorm, c->cs, c->sn, c->gv, tol, c->hist, c->hist_len, st));
+      if (df) {
+        zdf* vn = Vdf + (size_t)(j + 1) * n;
+        if (mixed) KL(F_SCALE, 40.0 * nd, 2.0 * nd, (launch_scale_df<zdf, float>(wd, c->hnorm, vn, c->vcur32, n, st, act)));
+        else KL(F_SCALE, 48.0 * nd, 2.0 * nd, (launch_scale_df<zdf, double>(wd, c->hnorm, vn, c->vcur64, n, st, act)));
+      } else {
+        KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_scale_inv(w, c->hnorm, w, n, st, act));
+      }
       TRY(check_launch(c, "Arnoldi step"));
       CU(cudaMemcpyAsync(c->hflags + j, act, sizeof(int), cudaMemcpyDeviceToHost, st));
       CU(cudaEventRecord(c->ev[j % c->nev], st));
@@ -331,28 +476,41 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
         if (c->hflags[j - FLAG_LAG] == 0) break;
       }
     }
+    c->cur_j = -1;
     CU(cudaMemcpyAsync(c->hctl, ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(c->hreorth_log, c->reorth_log, sizeof(int) * m, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     const int jend = c->hctl->jend;
+    if (c->p.reorth == HELM_REORTH_SELECTIVE)
+      for (int q = 0; q <= jend; ++q) c->reorth_steps += c->hreorth_log[q];
+    else
+      c->reorth_steps += jend + 1;
+    c->arnoldi_steps += jend + 1;
+    prof_flush(c, jend);
     iters += jend + 1;
     ++restarts;
     if (jend >= 0) {
-      launch_trisolve(ctl, c->H, m, c->gv, c->y, st);
+      const double nd = (double)n, k = jend + 1;
+      KL(F_SOLUPDATE, 0, 0, launch_trisolve(ctl, c->H, m, c->gv, c->y, st));
       if (mixed) {
-        launch_xupdate<float>(ctl, c->Z32, n, c->y, x, n, st);
+        KL(F_SOLUPDATE, (8.0 * k + 32.0) * nd, 8.0 * k * nd, launch_xupdate<float>(ctl, c->Z32, n, c->y, x, n, st));
       } else if (flexible) {
-        launch_xupdate<double>(ctl, c->Z64, n, c->y, x, n, st);
+        KL(F_SOLUPDATE, (16.0 * k + 32.0) * nd, 8.0 * k * nd, launch_xupdate<double>(ctl, c->Z64, n, c->y, x, n, st));
       } else {
-        launch_combine(ctl, c->V, n, c->y, c->r, n, st);
+        if (df)
+          KL(F_SOLUPDATE, (16.0 * k + 16.0) * nd, 8.0 * k * nd, launch_combine_df(ctl, Vdf, n, c->y, c->r, n, st));
+        else
+          KL(F_SOLUPDATE, (16.0 * k + 16.0) * nd, 8.0 * k * nd, launch_combine(ctl, c->V, n, c->y, c->r, n, st));
         run_vcycle<double, double, double>(c, c->r, c->zs, st, c->one);
-        launch_axpy1(c->zs, x, n, st);
+        KL(F_SOLUPDATE, 48.0 * nd, 2.0 * nd, launch_axpy1(c->zs, x, n, st));
       }
     }
-    launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, c->r, st, c->one);
+    KL(F_RESID, 56.0 * n, 24.0 * n, (launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, c->r, st, c->one)));
     norm_into(c, c->r, &ctl->beta, st, c->one);
     TRY(check_launch(c, "solution update"));
     CU(cudaMemcpyAsync(c->hctl, ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
+    prof_flush(c, -1);
     relres = c->hctl->beta / bnorm;
     if (c->hctl->flag == 2 && !(relres <= tol)) { status = HELM_ENUMERIC; break; }
     if (jend < 0) { status = HELM_ENUMERIC; break; }
@@ -402,15 +560,46 @@ void helm_default_params(helm_params* p) {
   p->tol = 1e-6;
   p->max_iter = 2000;
   p->precision = HELM_PREC_FP64;
+  p->orth = HELM_ORTH_FP64;
+  p->reorth = HELM_REORTH_SELECTIVE;
 }
 
 const char* helm_last_error(const helm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
+helm_status helm_profile(helm_ctx* c, int enable) {
+  if (!c) return HELM_EINVAL;
+  prof_flush(c, 1 << 30);
+  Prof& P = c->prof;
+  for (int f = 0; f < F_COUNT; ++f) { P.ms[f] = P.bytes[f] = P.flops[f] = 0.0; P.cnt[f] = 0; }
+  P.launches = 0;
+  P.on = enable != 0;
+  return HELM_OK;
+}
+
+helm_status helm_profile_read(helm_ctx* c, helm_kernel_stat* stats, int cap, int* count, long long* launches) {
+  if (!c) return HELM_EINVAL;
+  prof_flush(c, 1 << 30);
+  const Prof& P = c->prof;
+  int k = 0;
+  for (int f = 0; f < F_COUNT && stats && k < cap; ++f, ++k) {
+    stats[k].name = FAM_NAMES[f];
+    stats[k].launches = P.cnt[f];
+    stats[k].ms = P.ms[f];
+    stats[k].bytes = P.bytes[f];
+    stats[k].flops = P.flops[f];
+  }
+  if (count) *count = stats ? k : F_COUNT;
+  if (launches) *launches = P.launches;
+  return HELM_OK;
+}
+
 helm_status helm_destroy(helm_ctx* ctx) {
   if (!ctx) return HELM_OK;
+  for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
   for (void* q : ctx->allocs) cudaFree(q);
   if (ctx->hflags) cudaFreeHost(ctx->hflags);
   if (ctx->hctl) cudaFreeHost(ctx->hctl);
+  if (ctx->hreorth_log) cudaFreeHost(ctx->hreorth_log);
   for (int i = 0; i < ctx->nev; ++i) cudaEventDestroy(ctx->ev[i]);
   delete ctx;
   return HELM_OK;
@@ -497,11 +686,16 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
   if (P.precision == HELM_PREC_MIXED) TRY(dalloc(c, &c->Z32, (size_t)m * n0));
   else if (P.krylov == HELM_FGMRES) TRY(dalloc(c, &c->Z64, (size_t)m * n0));
   TRY(dalloc(c, &c->zs, n0));
+  if (P.orth == HELM_ORTH_DF) {
+    TRY(dalloc(c, &c->wdf, n0));
+    if (P.precision == HELM_PREC_MIXED) TRY(dalloc(c, &c->vcur32, n0));
+    else TRY(dalloc(c, &c->vcur64, n0));
+  }
   TRY(dalloc(c, &c->r, n0));
   TRY(dalloc(c, &c->xs, n0));
   TRY(dalloc(c, &c->bs, n0));
-  TRY(dalloc(c, &c->part, (size_t)(m + 1) * RED_BLOCKS));
-  TRY(dalloc(c, &c->partr, RED_BLOCKS));
+  TRY(dalloc(c, &c->part, (size_t)(m + 2) * RED_STRIDE));
+  TRY(dalloc(c, &c->partr, RED_STRIDE));
   TRY(dalloc(c, &c->hpass, MAX_BASIS));
   TRY(dalloc(c, &c->hacc, MAX_BASIS));
   TRY(dalloc(c, &c->H, (size_t)(m + 1) * m));
@@ -519,6 +713,9 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
   CU(cudaMemset(c->ctl, 0, sizeof(KrylovCtl)));
   CU(cudaHostAlloc((void**)&c->hflags, sizeof(int) * (m + FLAG_LAG + 1), cudaHostAllocDefault));
   CU(cudaHostAlloc((void**)&c->hctl, sizeof(KrylovCtl), cudaHostAllocDefault));
+  CU(cudaHostAlloc((void**)&c->hreorth_log, sizeof(int) * m, cudaHostAllocDefault));
+  TRY(dalloc(c, &c->reorth_log, m));
+  CU(cudaMemset(c->reorth_log, 0, sizeof(int) * m));
   c->nev = FLAG_LAG + 2;
   for (int i = 0; i < c->nev; ++i) CU(cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming));
   CU(cudaStreamSynchronize(st));
@@ -545,6 +742,9 @@ helm_status helm_create(int n1, int n2, int n3, double h, const double* k2, helm
   if (P.krylov != HELM_GMRES && P.krylov != HELM_FGMRES) return fail(nullptr, HELM_EINVAL, "unknown krylov %d", P.krylov);
   if (P.precision != HELM_PREC_FP64 && P.precision != HELM_PREC_MIXED) return fail(nullptr, HELM_EINVAL, "unknown precision %d", P.precision);
   if (!std::isfinite(P.beta1) || !std::isfinite(P.beta2)) return fail(nullptr, HELM_EINVAL, "beta1, beta2 must be finite");
+  if (P.orth != HELM_ORTH_FP64 && P.orth != HELM_ORTH_DF) return fail(nullptr, HELM_EINVAL, "unknown orth %d", P.orth);
+  if (P.reorth != HELM_REORTH_ALWAYS && P.reorth != HELM_REORTH_SELECTIVE)
+    return fail(nullptr, HELM_EINVAL, "unknown reorth %d", P.reorth);
   if (P.precision == HELM_PREC_MIXED) P.krylov = HELM_FGMRES;
   helm_ctx* c = new (std::nothrow) helm_ctx();
   if (!c) return fail(nullptr, HELM_ENOMEM, "host allocation failed");
@@ -581,10 +781,11 @@ helm_status helm_apply(helm_ctx* c, helm_op op, helm_dtype dt, const void* u, vo
   const double sr = op == HELM_OP_A ? 1.0 : c->s_re, si = op == HELM_OP_A ? 0.0 : c->s_im;
   cudaStream_t st = (cudaStream_t)stream;
   Level& L = c->L[0];
+  const double n = (double)L.g.npts();
   if (dt == HELM_C128)
-    launch_apply<double, double, double>(L.g, sr, si, L.k2, (const z128*)u, (z128*)v, st, nullptr);
+    KL(F_APPLY, 40.0 * n, 22.0 * n, (launch_apply<double, double, double>(L.g, sr, si, L.k2, (const z128*)u, (z128*)v, st, nullptr)));
   else if (dt == HELM_C64)
-    launch_apply<float, float, float>(L.g, sr, si, L.k2f, (const z64*)u, (z64*)v, st, nullptr);
+    KL(F_APPLY, 20.0 * n, 22.0 * n, (launch_apply<float, float, float>(L.g, sr, si, L.k2f, (const z64*)u, (z64*)v, st, nullptr)));
   else
     return fail(c, HELM_EINVAL, "unknown dtype %d", (int)dt);
   return check_launch(c, "helm_apply");

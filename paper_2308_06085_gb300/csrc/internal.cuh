@@ -9,6 +9,11 @@ namespace helm {
 template <typename R, typename TU, typename TO>
 void launch_apply(const Grid& g, double s_re, double s_im, const R* k2, const cx<TU>* u, cx<TO>* v, cudaStream_t st,
                   const int* active);
+// FP64 operator product written as double-float (the Arnoldi vector of the double-float
+// Gram-Schmidt)
+template <typename TU>
+void launch_apply_split(const Grid& g, double s_re, double s_im, const double* k2, const cx<TU>* u, zdf* v,
+                        cudaStream_t st, const int* active);
 template <typename R, typename TU, typename TB, typename TO>
 void launch_resid(const Grid& g, double s_re, double s_im, const R* k2, const cx<TU>* u, const cx<TB>* b, cx<TO>* out,
                   cudaStream_t st, const int* active);
@@ -32,22 +37,25 @@ void launch_check_k2(const double* a, size_t n, int* bad, cudaStream_t st);
 void launch_rhs_point(const Grid& g, int nsrc, const int* idx, double amp, z128* b, cudaStream_t st);
 
 // ---- Krylov kernels (krylov.cu) ----
-constexpr int RED_BLOCKS = 608;  // fixed grid for reductions: partial sums combine in a fixed order
+constexpr int RED_STRIDE = 2048;  // row stride of partial-sum buffers: max blocks of a reduction grid
 constexpr int MAX_BASIS = 257;   // restart <= 256
 
-// part[i * RED_BLOCKS + blk] = sum over blk's points of conj(V_i) w, i < nv
-void launch_mdot(const z128* V, size_t ld, int nv, const z128* w, size_t n, z128* part, cudaStream_t st,
-                 const int* active);
-// hpass[i] = sum_blk part[i * RED_BLOCKS + blk]; hacc[i] = hpass[i] (accumulate 0) or += (1)
-void launch_reduce_dots(const z128* part, int nv, z128* hpass, z128* hacc, int accumulate, cudaStream_t st,
-                        const int* active);
+// part[i * RED_STRIDE + blk] = sum over blk's points of conj(V_i) w, i < nv; with_norm also
+// writes the partial |w|^2 to slot nv.  Returns the number of blocks (partials per row).
+int launch_mdot(const z128* V, size_t ld, int nv, const z128* w, size_t n, z128* part, int with_norm,
+                cudaStream_t st, const int* active);
+// hpass[i] = sum_{blk < nb} part[i * RED_STRIDE + blk]; hacc[i] = hpass[i] (accumulate 0) or
+// += (1).  decide_j >= 0: also read |w|^2 from slot nv and set *pass2 = log[decide_j] =
+// (second Gram-Schmidt pass needed)
+void launch_reduce_dots(const z128* part, int nv, int nb, z128* hpass, z128* hacc, int accumulate, int decide_j,
+                        int* pass2, int* log, cudaStream_t st, const int* active);
 // w -= sum_i h[i] V_i
 void launch_gs_update(const z128* V, size_t ld, int nv, const z128* h, z128* w, size_t n, cudaStream_t st,
                       const int* active);
-// partial sums of |x|^2 into partr[RED_BLOCKS]
-void launch_norm2_part(const z128* x, size_t n, double* partr, cudaStream_t st, const int* active);
-// *out = sqrt(sum partr)
-void launch_reduce_norm(const double* partr, double* out, cudaStream_t st, const int* active);
+// partial sums of |x|^2 into partr[0..nb); returns nb
+int launch_norm2_part(const z128* x, size_t n, double* partr, cudaStream_t st, const int* active);
+// *out = sqrt(sum_{b < nb} partr[b])
+void launch_reduce_norm(const double* partr, int nb, double* out, cudaStream_t st, const int* active);
 // out = in * (1 / *s)   (when *s != 0)
 void launch_scale_inv(const z128* in, const double* s, z128* out, size_t n, cudaStream_t st, const int* active);
 // start a restart cycle: active = 1, g = (beta, 0, ...), iter0 recorded
@@ -65,6 +73,20 @@ void launch_xupdate(const KrylovCtl* ctl, const cx<TZ>* Z, size_t ld, const z128
 // w = sum_{i<=jend} y_i V_i
 void launch_combine(const KrylovCtl* ctl, const z128* V, size_t ld, const z128* y, z128* w, size_t n,
                     cudaStream_t st);
+// double-float Gram-Schmidt (basis stored as zdf)
+int launch_mdot_df(const zdf* V, size_t ld, int nv, const zdf* w, size_t n, z128* part, int with_norm,
+                   cudaStream_t st, const int* active);
+void launch_gs_update_df(const zdf* V, size_t ld, int nv, const z128* h, zdf* w, size_t n, cudaStream_t st,
+                         const int* active);
+// partial sums of |x|^2 (double-float x) into partr; returns nb
+int launch_norm2_part_df(const zdf* x, size_t n, double* partr, cudaStream_t st, const int* active);
+// out = in / *s as double-float, and a copy as c128 (exact) or c64 (leading part); in is
+// c128 (TI = z128) or double-float (TI = zdf)
+template <typename TI, typename TC>
+void launch_scale_df(const TI* in, const double* s, zdf* out, cx<TC>* copy, size_t n, cudaStream_t st,
+                     const int* active);
+void launch_combine_df(const KrylovCtl* ctl, const zdf* V, size_t ld, const z128* y, z128* w, size_t n,
+                       cudaStream_t st);
 void launch_c128_to_c64(const z128* a, z64* b, size_t n, cudaStream_t st);
 void launch_c64_to_c128(const z64* a, z128* b, size_t n, cudaStream_t st);
 void launch_set_active(KrylovCtl* ctl, int v, cudaStream_t st);

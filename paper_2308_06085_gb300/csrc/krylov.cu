@@ -3,8 +3,8 @@
 // one reorthogonalisation pass, norms, and the Hessenberg least-squares problem solved by
 // complex Givens rotations on the device, so the host never waits inside an Arnoldi step.
 //
-// Reductions are deterministic: a fixed grid of RED_BLOCKS blocks writes partial sums,
-// combined by a second kernel in a fixed order.
+// Reductions are deterministic: a grid of exactly one wave (SMs x resident blocks, fixed for
+// a device) writes partial sums, combined by a second kernel in a fixed order.
 #include "internal.cuh"
 
 namespace helm {
@@ -13,66 +13,149 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int NW = NT / 32;
-constexpr int G = 8;  // basis vectors per pass of the inner-product kernel
 
 __device__ __forceinline__ void block_range(size_t n, size_t& p0, size_t& p1) {
-  const size_t chunk = (n + RED_BLOCKS - 1) / RED_BLOCKS;
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
   p0 = blockIdx.x * chunk;
   p1 = p0 + chunk < n ? p0 + chunk : n;
 }
 
-__global__ void __launch_bounds__(NT)
-    k_mdot(const z128* __restrict__ V, size_t ld, int nv, const z128* __restrict__ w, size_t n,
-           z128* __restrict__ part, const int* __restrict__ active) {
-  if (active && *active == 0) return;
-  __shared__ double sred[NW][2 * G];
-  size_t p0, p1;
-  block_range(n, p0, p1);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* partd = reinterpret_cast<double*>(part);
-  for (int g0 = 0; g0 < nv; g0 += G) {
-    double re[G], im[G];
-#pragma unroll
-    for (int q = 0; q < G; ++q) re[q] = im[q] = 0.0;
-    for (size_t p = p0 + threadIdx.x; p < p1; p += NT) {
-      const z128 wv = ldg(w + p);
-#pragma unroll
-      for (int q = 0; q < G; ++q)
-        if (g0 + q < nv) cdot_acc(ldg(V + (size_t)(g0 + q) * ld + p), wv, re[q], im[q]);
+// ---- inner products conj(V_i) . w of nv basis vectors against one vector --------------------
+// A block stages tiles of w in shared memory; each warp owns "slots" (a basis vector, or the
+// extra slot nv for |w|^2 when with_norm is set).  With fewer slots than warps, several
+// consecutive warps share a slot and split the tile's points.  A lane accumulates its slots
+// over all the block's points, so the per-slot epilogue (warp reduction) is amortised over
+// ~50-100 points per lane.  Partials per block go to part[slot * RED_STRIDE + block].
+constexpr int TILE = NT;  // points of w staged per tile
+constexpr int KS = 4;     // slots per warp per pass over the block's points
+
+struct AccD {  // FP64 accumulator
+  double re, im;
+  __device__ void zero() { re = im = 0.0; }
+  __device__ void mac(const z128& v, const z128& w) { cdot_acc(v, w, re, im); }
+  __device__ void norm(const z128& w) {
+    re = fma(w.re, w.re, re);
+    re = fma(w.im, w.im, re);
+  }
+  __device__ void reduce_warp(double& r, double& i) {
+    r = re;
+    i = im;
+    for (int o = 16; o; o >>= 1) {
+      r += __shfl_xor_sync(0xffffffffu, r, o);
+      i += __shfl_xor_sync(0xffffffffu, i, o);
     }
-#pragma unroll
-    for (int q = 0; q < G; ++q)
-      for (int o = 16; o; o >>= 1) {
-        re[q] += __shfl_xor_sync(0xffffffffu, re[q], o);
-        im[q] += __shfl_xor_sync(0xffffffffu, im[q], o);
-      }
-    if (lane == 0)
-#pragma unroll
-      for (int q = 0; q < G; ++q) {
-        sred[warp][2 * q] = re[q];
-        sred[warp][2 * q + 1] = im[q];
-      }
-    __syncthreads();
-    if (threadIdx.x < 2 * G) {
-      const int q = threadIdx.x >> 1, comp = threadIdx.x & 1;
-      double s = 0.0;
-      for (int wi = 0; wi < NW; ++wi) s += sred[wi][threadIdx.x];
-      if (g0 + q < nv) partd[2 * ((size_t)(g0 + q) * RED_BLOCKS + blockIdx.x) + comp] = s;
-    }
-    __syncthreads();
+  }
+};
+
+__device__ __forceinline__ void df_shfl_reduce(float& s, float& c) {
+  for (int o = 16; o; o >>= 1) {
+    const float os = __shfl_xor_sync(0xffffffffu, s, o), oc = __shfl_xor_sync(0xffffffffu, c, o);
+    float hi, lo;
+    df_add(s, c, os, oc, hi, lo);
+    s = hi;
+    c = lo;
   }
 }
 
-// One warp per basis vector: lanes sum the RED_BLOCKS partials in a fixed order.
+struct AccF {  // double-float accumulator, FP32 arithmetic only
+  float rs, rc, is, ic;
+  __device__ void zero() { rs = rc = is = ic = 0.f; }
+  __device__ void mac(const zdf& v, const zdf& w) {
+    // re += vr wr + vi wi ; im += vr wi - vi wr
+    df_mac(v.rh, v.rl, w.rh, w.rl, rs, rc);
+    df_mac(v.ih, v.il, w.ih, w.il, rs, rc);
+    df_mac(v.rh, v.rl, w.ih, w.il, is, ic);
+    df_mac(-v.ih, -v.il, w.rh, w.rl, is, ic);
+  }
+  __device__ void norm(const zdf& w) {
+    df_mac(w.rh, w.rl, w.rh, w.rl, rs, rc);
+    df_mac(w.ih, w.il, w.ih, w.il, rs, rc);
+  }
+  __device__ void reduce_warp(double& r, double& i) {
+    float a = rs, b = rc, x = is, y = ic;
+    df_renorm(a, b, a, b);
+    df_renorm(x, y, x, y);
+    df_shfl_reduce(a, b);
+    df_shfl_reduce(x, y);
+    r = (double)a + (double)b;
+    i = (double)x + (double)y;
+  }
+};
+
+template <typename E, typename ACC>
 __global__ void __launch_bounds__(NT)
-    k_reduce_dots(const z128* __restrict__ part, int nv, z128* __restrict__ hpass, z128* __restrict__ hacc,
-                  int accumulate, const int* __restrict__ active) {
+    k_mdot(const E* __restrict__ V, size_t ld, int nv, const E* __restrict__ w, size_t n, z128* __restrict__ part,
+           int with_norm, const int* __restrict__ active) {
   if (active && *active == 0) return;
+  __shared__ E sw[TILE];
+  __shared__ double sred[NW][2];
+  size_t p0, p1;
+  block_range(n, p0, p1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = warp; i < nv; i += NW) {
+  const int nslot = nv + (with_norm ? 1 : 0);
+  const int wps = nslot >= NW ? 1 : NW / nslot;  // warps sharing one slot
+  const int sub = warp % wps, sfirst = warp / wps, sstep = NW / wps;
+  double* partd = reinterpret_cast<double*>(part);
+  for (int sbase = 0; sbase * sstep < nslot; sbase += KS) {
+    ACC acc[KS];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) acc[k].zero();
+    for (size_t t0 = p0; t0 < p1; t0 += TILE) {
+      const int tn = (int)min((size_t)TILE, p1 - t0);
+      __syncthreads();
+      if ((int)threadIdx.x < tn) sw[threadIdx.x] = ldg(w + t0 + threadIdx.x);
+      __syncthreads();
+      for (int q = sub * 32 + lane; q < tn; q += 32 * wps) {
+        const E wv = sw[q];
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+          const int sl = sfirst + (sbase + k) * sstep;
+          if (sl < nv) acc[k].mac(ldg(V + (size_t)sl * ld + t0 + q), wv);
+          else if (sl == nv && with_norm) acc[k].norm(wv);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int sl = sfirst + (sbase + k) * sstep;
+      double r, i;
+      acc[k].reduce_warp(r, i);
+      __syncthreads();
+      if (lane == 0) {
+        sred[warp][0] = r;
+        sred[warp][1] = i;
+      }
+      __syncthreads();
+      if (sub == 0 && lane == 0 && sl < nslot) {
+        double tr = 0.0, ti = 0.0;
+        for (int u = 0; u < wps; ++u) {
+          tr += sred[warp + u][0];
+          ti += sred[warp + u][1];
+        }
+        partd[2 * ((size_t)sl * RED_STRIDE + blockIdx.x)] = tr;
+        partd[2 * ((size_t)sl * RED_STRIDE + blockIdx.x) + 1] = sl == nv ? 0.0 : ti;
+      }
+    }
+  }
+}
+
+// One warp per basis vector: lanes sum the nb partials in a fixed order.
+// decide_j >= 0 (first pass): slot nv holds partial |w|^2; the block then applies the
+// Daniel-Gragg-Kaufman-Stewart test -- a second pass is needed when the projection removed
+// more than half of |w|^2 (|w - V h|^2 = |w|^2 - |h|^2 < |w|^2 / 2) -- and records the
+// decision in *pass2 and log[decide_j].
+__global__ void __launch_bounds__(NT)
+    k_reduce_dots(const z128* __restrict__ part, int nv, int nb, z128* __restrict__ hpass, z128* __restrict__ hacc,
+                  int accumulate, int decide_j, int* __restrict__ pass2, int* __restrict__ log,
+                  const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ double sw2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nsum = decide_j >= 0 ? nv + 1 : nv;
+  for (int i = warp; i < nsum; i += NW) {
     double re = 0.0, im = 0.0;
-    for (int b = lane; b < RED_BLOCKS; b += 32) {
-      const z128 v = part[(size_t)i * RED_BLOCKS + b];
+    for (int b = lane; b < nb; b += 32) {
+      const z128 v = part[(size_t)i * RED_STRIDE + b];
       re += v.re;
       im += v.im;
     }
@@ -81,14 +164,27 @@ __global__ void __launch_bounds__(NT)
       im += __shfl_xor_sync(0xffffffffu, im, o);
     }
     if (lane == 0) {
-      hpass[i] = mkc<double>(re, im);
-      if (accumulate) {
-        hacc[i].re += re;
-        hacc[i].im += im;
+      if (i == nv) {
+        sw2 = re;
       } else {
-        hacc[i] = mkc<double>(re, im);
+        hpass[i] = mkc<double>(re, im);
+        if (accumulate) {
+          hacc[i].re += re;
+          hacc[i].im += im;
+        } else {
+          hacc[i] = mkc<double>(re, im);
+        }
       }
     }
+  }
+  if (decide_j < 0) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double h2 = 0.0;
+    for (int i = 0; i < nv; ++i) h2 += hpass[i].re * hpass[i].re + hpass[i].im * hpass[i].im;
+    const int again = !(sw2 - h2 >= 0.5 * sw2);  // NaN also takes the second pass
+    *pass2 = again;
+    log[decide_j] = again;
   }
 }
 
@@ -136,11 +232,11 @@ __global__ void __launch_bounds__(NT)
 }
 
 __global__ void __launch_bounds__(NT)
-    k_reduce_norm(const double* __restrict__ part, double* __restrict__ out, const int* __restrict__ active) {
+    k_reduce_norm(const double* __restrict__ part, int nb, double* __restrict__ out, const int* __restrict__ active) {
   if (active && *active == 0) return;
   __shared__ double sred[NW];
   double s = 0.0;
-  for (int b = threadIdx.x; b < RED_BLOCKS; b += NT) s += part[b];
+  for (int b = threadIdx.x; b < nb; b += NT) s += part[b];
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -167,6 +263,7 @@ __global__ void __launch_bounds__(NT)
 __global__ void k_cycle_init(KrylovCtl* ctl, z128* g, int m, int iter0) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     ctl->active = 1;
+    ctl->pass2 = 0;
     ctl->jend = -1;
     ctl->flag = 0;
     ctl->iter0 = iter0;
@@ -235,6 +332,7 @@ __global__ void k_givens(KrylovCtl* ctl, z128* H, int m, int j, int jmax, const 
   } else if (j + 1 >= jmax) {
     ctl->active = 0;
   }
+  if (ctl->active == 0) ctl->pass2 = 0;
 }
 
 __global__ void k_trisolve(const KrylovCtl* ctl, const z128* H, int m, const z128* g, z128* y) {
@@ -282,6 +380,113 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
+// ---- double-float Gram-Schmidt: basis in zdf, arithmetic on the FP32 pipes ----------------
+// w -= sum_i h_i v_i, all in double-float.
+__global__ void __launch_bounds__(NT)
+    k_gs_update_df(const zdf* __restrict__ V, size_t ld, int nv, const z128* __restrict__ h, zdf* __restrict__ w,
+                   size_t n, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ zdf sh[MAX_BASIS];
+  for (int i = threadIdx.x; i < nv; i += NT) sh[i] = df_from(h[i]);
+  __syncthreads();
+  for (size_t p = blockIdx.x * (size_t)NT + threadIdx.x; p < n; p += (size_t)gridDim.x * NT) {
+    float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
+    for (int i = 0; i < nv; ++i) {
+      const zdf v = ldg(V + (size_t)i * ld + p);
+      const zdf c = sh[i];
+      // re += cr vr - ci vi ; im += cr vi + ci vr
+      df_mac(c.rh, c.rl, v.rh, v.rl, rs, rc);
+      df_mac(-c.ih, -c.il, v.ih, v.il, rs, rc);
+      df_mac(c.rh, c.rl, v.ih, v.il, is, ic);
+      df_mac(c.ih, c.il, v.rh, v.rl, is, ic);
+    }
+    const zdf a = w[p];
+    zdf o;
+    df_add(a.rh, a.rl, -rs, -rc, o.rh, o.rl);
+    df_add(a.ih, a.il, -is, -ic, o.ih, o.il);
+    w[p] = o;
+  }
+}
+
+__global__ void __launch_bounds__(NT)
+    k_norm2_part_df(const zdf* __restrict__ x, size_t n, double* __restrict__ part, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ double sred[NW];
+  size_t p0, p1;
+  block_range(n, p0, p1);
+  float ss = 0.f, sc = 0.f;
+  for (size_t p = p0 + threadIdx.x; p < p1; p += NT) {
+    const zdf v = ldg(x + p);
+    df_mac(v.rh, v.rl, v.rh, v.rl, ss, sc);
+    df_mac(v.ih, v.il, v.ih, v.il, ss, sc);
+  }
+  df_renorm(ss, sc, ss, sc);
+  df_shfl_reduce(ss, sc);
+  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = (double)ss + (double)sc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int wi = 0; wi < NW; ++wi) t += sred[wi];
+    part[blockIdx.x] = t;
+  }
+}
+
+// out = in / *s stored as double-float; `copy` receives the same vector as c128 (TC =
+// double, exactly the double-float value) or complex64 (TC = float, its leading part).
+__device__ __forceinline__ zdf scale_to_df(const z128& v, double inv, float, float) {
+  return df_from(mkc<double>(v.re * inv, v.im * inv));
+}
+__device__ __forceinline__ zdf scale_to_df(const zdf& v, double, float ih, float il) {
+  zdf z;
+  df_mul(v.rh, v.rl, ih, il, z.rh, z.rl);
+  df_mul(v.ih, v.il, ih, il, z.ih, z.il);
+  return z;
+}
+
+template <typename TI, typename TC>
+__global__ void __launch_bounds__(NT)
+    k_scale_df(const TI* __restrict__ in, const double* __restrict__ s, zdf* __restrict__ out,
+               cx<TC>* __restrict__ copy, size_t n, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const double d = *s;
+  if (!(d != 0.0)) return;
+  const double inv = 1.0 / d;
+  float ih, il;
+  df_split(inv, ih, il);
+  for (size_t p = blockIdx.x * (size_t)NT + threadIdx.x; p < n; p += (size_t)gridDim.x * NT) {
+    const zdf z = scale_to_df(in[p], inv, ih, il);
+    out[p] = z;
+    if (sizeof(TC) == 8) {
+      const z128 c = df_to_c128(z);
+      copy[p] = mkc<TC>((TC)c.re, (TC)c.im);
+    } else {
+      copy[p] = mkc<TC>((TC)z.rh, (TC)z.ih);
+    }
+  }
+}
+
+// w = sum_{i<=jend} y_i V_i, double-float accumulation.
+__global__ void __launch_bounds__(NT)
+    k_combine_df(const KrylovCtl* __restrict__ ctl, const zdf* __restrict__ V, size_t ld, const z128* __restrict__ y,
+                 z128* __restrict__ w, size_t n) {
+  __shared__ zdf sy[MAX_BASIS];
+  const int k = ctl->jend + 1;
+  for (int i = threadIdx.x; i < k; i += NT) sy[i] = df_from(y[i]);
+  __syncthreads();
+  for (size_t p = blockIdx.x * (size_t)NT + threadIdx.x; p < n; p += (size_t)gridDim.x * NT) {
+    float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
+    for (int i = 0; i < k; ++i) {
+      const zdf v = ldg(V + (size_t)i * ld + p);
+      const zdf c = sy[i];
+      df_mac(c.rh, c.rl, v.rh, v.rl, rs, rc);
+      df_mac(-c.ih, -c.il, v.ih, v.il, rs, rc);
+      df_mac(c.rh, c.rl, v.ih, v.il, is, ic);
+      df_mac(c.ih, c.il, v.rh, v.rl, is, ic);
+    }
+    w[p] = mkc<double>((double)rs + (double)rc, (double)is + (double)ic);
+  }
+}
+
 __global__ void k_c128_to_c64(const z128* __restrict__ a, z64* __restrict__ b, size_t n) {
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
     b[p] = cvt<float>(a[p]);
@@ -298,6 +503,17 @@ __global__ void k_axpy1(const z128* __restrict__ z, z128* __restrict__ x, size_t
   }
 }
 
+// One full wave of `kern` at NT threads: SMs x resident blocks (capped at RED_STRIDE).
+template <typename K>
+int wave_blocks(K kern) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, 0);
+  const int nb = sms * (per > 0 ? per : 1);
+  return nb < RED_STRIDE ? nb : RED_STRIDE;
+}
+
 int stream_blocks(size_t n) {
   size_t b = (n + NT - 1) / NT;
   const size_t cap = 152 * 8;
@@ -306,23 +522,27 @@ int stream_blocks(size_t n) {
 
 }  // namespace
 
-void launch_mdot(const z128* V, size_t ld, int nv, const z128* w, size_t n, z128* part, cudaStream_t st,
-                 const int* active) {
-  k_mdot<<<RED_BLOCKS, NT, 0, st>>>(V, ld, nv, w, n, part, active);
+int launch_mdot(const z128* V, size_t ld, int nv, const z128* w, size_t n, z128* part, int with_norm,
+                cudaStream_t st, const int* active) {
+  static const int nb = wave_blocks(k_mdot<z128, AccD>);
+  k_mdot<z128, AccD><<<nb, NT, 0, st>>>(V, ld, nv, w, n, part, with_norm, active);
+  return nb;
 }
-void launch_reduce_dots(const z128* part, int nv, z128* hpass, z128* hacc, int accumulate, cudaStream_t st,
-                        const int* active) {
-  k_reduce_dots<<<1, NT, 0, st>>>(part, nv, hpass, hacc, accumulate, active);
+void launch_reduce_dots(const z128* part, int nv, int nb, z128* hpass, z128* hacc, int accumulate, int decide_j,
+                        int* pass2, int* log, cudaStream_t st, const int* active) {
+  k_reduce_dots<<<1, NT, 0, st>>>(part, nv, nb, hpass, hacc, accumulate, decide_j, pass2, log, active);
 }
 void launch_gs_update(const z128* V, size_t ld, int nv, const z128* h, z128* w, size_t n, cudaStream_t st,
                       const int* active) {
   k_gs_update<<<stream_blocks(n), NT, 0, st>>>(V, ld, nv, h, w, n, active);
 }
-void launch_norm2_part(const z128* x, size_t n, double* partr, cudaStream_t st, const int* active) {
-  k_norm2_part<<<RED_BLOCKS, NT, 0, st>>>(x, n, partr, active);
+int launch_norm2_part(const z128* x, size_t n, double* partr, cudaStream_t st, const int* active) {
+  static const int nb = wave_blocks(k_norm2_part);
+  k_norm2_part<<<nb, NT, 0, st>>>(x, n, partr, active);
+  return nb;
 }
-void launch_reduce_norm(const double* partr, double* out, cudaStream_t st, const int* active) {
-  k_reduce_norm<<<1, NT, 0, st>>>(partr, out, active);
+void launch_reduce_norm(const double* partr, int nb, double* out, cudaStream_t st, const int* active) {
+  k_reduce_norm<<<1, NT, 0, st>>>(partr, nb, out, active);
 }
 void launch_scale_inv(const z128* in, const double* s, z128* out, size_t n, cudaStream_t st, const int* active) {
   k_scale_inv<<<stream_blocks(n), NT, 0, st>>>(in, s, out, n, active);
@@ -347,6 +567,34 @@ template void launch_xupdate<float>(const KrylovCtl*, const z64*, size_t, const 
 void launch_combine(const KrylovCtl* ctl, const z128* V, size_t ld, const z128* y, z128* w, size_t n,
                     cudaStream_t st) {
   k_combine<<<stream_blocks(n), NT, 0, st>>>(ctl, V, ld, y, w, n);
+}
+int launch_mdot_df(const zdf* V, size_t ld, int nv, const zdf* w, size_t n, z128* part, int with_norm,
+                   cudaStream_t st, const int* active) {
+  static const int nb = wave_blocks(k_mdot<zdf, AccF>);
+  k_mdot<zdf, AccF><<<nb, NT, 0, st>>>(V, ld, nv, w, n, part, with_norm, active);
+  return nb;
+}
+void launch_gs_update_df(const zdf* V, size_t ld, int nv, const z128* h, zdf* w, size_t n, cudaStream_t st,
+                         const int* active) {
+  k_gs_update_df<<<stream_blocks(n), NT, 0, st>>>(V, ld, nv, h, w, n, active);
+}
+int launch_norm2_part_df(const zdf* x, size_t n, double* partr, cudaStream_t st, const int* active) {
+  static const int nb = wave_blocks(k_norm2_part_df);
+  k_norm2_part_df<<<nb, NT, 0, st>>>(x, n, partr, active);
+  return nb;
+}
+template <typename TI, typename TC>
+void launch_scale_df(const TI* in, const double* s, zdf* out, cx<TC>* copy, size_t n, cudaStream_t st,
+                     const int* active) {
+  k_scale_df<TI, TC><<<stream_blocks(n), NT, 0, st>>>(in, s, out, copy, n, active);
+}
+template void launch_scale_df<z128, double>(const z128*, const double*, zdf*, z128*, size_t, cudaStream_t, const int*);
+template void launch_scale_df<z128, float>(const z128*, const double*, zdf*, z64*, size_t, cudaStream_t, const int*);
+template void launch_scale_df<zdf, double>(const zdf*, const double*, zdf*, z128*, size_t, cudaStream_t, const int*);
+template void launch_scale_df<zdf, float>(const zdf*, const double*, zdf*, z64*, size_t, cudaStream_t, const int*);
+void launch_combine_df(const KrylovCtl* ctl, const zdf* V, size_t ld, const z128* y, z128* w, size_t n,
+                       cudaStream_t st) {
+  k_combine_df<<<stream_blocks(n), NT, 0, st>>>(ctl, V, ld, y, w, n);
 }
 void launch_c128_to_c64(const z128* a, z64* b, size_t n, cudaStream_t st) {
   k_c128_to_c64<<<stream_blocks(n), NT, 0, st>>>(a, b, n);

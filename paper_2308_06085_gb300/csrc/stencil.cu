@@ -26,7 +26,7 @@ __device__ __forceinline__ cx<T> zero_c() {
 // with Op = -Lap_h - s k^2 (s in OpCoef).  DINV: read omega/d from a precomputed array
 // (FP64 path, where a complex division costs more than the 16-byte read) instead of
 // computing it.
-template <typename R, int MODE, bool DINV, typename TU, typename TB, typename TO>
+template <typename R, int MODE, bool DINV, typename TU, typename TB, typename TO, bool SPLIT = false>
 __global__ void __launch_bounds__(TX* TY)
     k_stencil(Grid g, OpCoef<R> c, const R* __restrict__ k2, const cx<R>* __restrict__ dinv,
               const cx<TU>* __restrict__ u, const cx<TB>* __restrict__ b, cx<TO>* __restrict__ out,
@@ -66,7 +66,10 @@ __global__ void __launch_bounds__(TX* TY)
     const cx<R> d = op_diag(c, kk, nf);
     const cx<R> v = op_combine(d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
     if (MODE == 0) {
-      out[p] = cvt<TO>(v);
+      if (SPLIT)  // the output buffer holds double-float values (16 bytes, like complex128)
+        reinterpret_cast<zdf*>(out)[p] = df_from(cvt<double>(v));
+      else
+        out[p] = cvt<TO>(v);
     } else {
       const cx<R> r = csub(cvt<R>(ldg(b + p)), v);
       if (MODE == 1) {
@@ -303,6 +306,19 @@ void launch_apply(const Grid& g, double s_re, double s_im, const R* k2, const cx
   k_stencil<R, 0, false, TU, TU, TO><<<gr, dim3(TX, TY), 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr, u,
                                                                    nullptr, v, zc, active);
 }
+
+template <typename TU>
+void launch_apply_split(const Grid& g, double s_re, double s_im, const double* k2, const cx<TU>* u, zdf* v,
+                        cudaStream_t st, const int* active) {
+  int zc;
+  dim3 gr = grid_for(g, zc);
+  k_stencil<double, 0, false, TU, TU, double, true><<<gr, dim3(TX, TY), 0, st>>>(
+      g, coef_for<double>(g.h, s_re, s_im, 0.0), k2, nullptr, u, nullptr, reinterpret_cast<z128*>(v), zc, active);
+}
+template void launch_apply_split<double>(const Grid&, double, double, const double*, const z128*, zdf*, cudaStream_t,
+                                         const int*);
+template void launch_apply_split<float>(const Grid&, double, double, const double*, const z64*, zdf*, cudaStream_t,
+                                        const int*);
 
 template <typename R, typename TU, typename TB, typename TO>
 void launch_resid(const Grid& g, double s_re, double s_im, const R* k2, const cx<TU>* u, const cx<TB>* b,

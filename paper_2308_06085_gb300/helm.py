@@ -26,6 +26,8 @@ C128, C64 = 0, 1
 OP_A, OP_M = 0, 1
 GMRES, FGMRES = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
+ORTH_FP64, ORTH_DF = 0, 1
+REORTH_ALWAYS, REORTH_SELECTIVE = 0, 1
 
 
 class HelmError(RuntimeError):
@@ -37,7 +39,13 @@ class HelmError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("beta1", C.c_double), ("beta2", C.c_double), ("omega", C.c_double), ("nu1", C.c_int),
                 ("nu2", C.c_int), ("coarsest_n", C.c_int), ("krylov", C.c_int), ("restart", C.c_int),
-                ("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int)]
+                ("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int), ("orth", C.c_int),
+                ("reorth", C.c_int)]
+
+
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("launches", C.c_longlong), ("ms", C.c_double), ("bytes", C.c_double),
+                ("flops", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -71,10 +79,12 @@ def lib():
     L.helm_vcycle_stage.argtypes = [vp, i, i, i, vp, vp, vp, vp]
     L.helm_rhs_point.argtypes = [vp, i, C.POINTER(i), vp, vp]
     L.helm_solve.argtypes = [vp, vp, vp, C.POINTER(SolveInfo), vp]
+    L.helm_profile.argtypes = [vp, i]
+    L.helm_profile_read.argtypes = [vp, C.POINTER(KernelStat), i, C.POINTER(i), C.POINTER(C.c_longlong)]
     L.helm_last_error.argtypes = [vp]
     L.helm_last_error.restype = C.c_char_p
     for f in ("helm_create", "helm_destroy", "helm_levels", "helm_level_dims", "helm_apply", "cslp_vcycle",
-              "helm_vcycle_stage", "helm_rhs_point", "helm_solve"):
+              "helm_vcycle_stage", "helm_rhs_point", "helm_solve", "helm_profile", "helm_profile_read"):
         getattr(L, f).restype = i
     _lib = L
     return L
@@ -101,7 +111,8 @@ class Solver:
     """A libhelm context: hierarchy, coarsest inverse and Krylov workspace on one GPU."""
 
     def __init__(self, n, h, k2, bc=SOMMERFELD, *, beta1=1.0, beta2=-0.5, omega=0.8, coarsest_n=4,
-                 krylov="gmres", restart=30, tol=1e-6, max_iter=2000, precision="fp64", device=None):
+                 krylov="gmres", restart=30, tol=1e-6, max_iter=2000, precision="fp64", orth=None,
+                 reorth=None, device=None):
         n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(int(x) for x in n)
         self.n = (n1, n2, n3)
         self.h = float(h)
@@ -118,6 +129,10 @@ class Solver:
         p.krylov = {"gmres": GMRES, "fgmres": FGMRES}[krylov]
         p.restart, p.tol, p.max_iter = restart, tol, max_iter
         p.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
+        if orth is not None:
+            p.orth = {"fp64": ORTH_FP64, "df": ORTH_DF}[orth]
+        if reorth is not None:
+            p.reorth = {"always": REORTH_ALWAYS, "selective": REORTH_SELECTIVE}[reorth]
         self.params = p
         ctx = C.c_void_p()
         with torch.cuda.device(self.device):
@@ -201,6 +216,20 @@ class Solver:
         self._check(lib().helm_rhs_point(self._ctx, len(nodes), nodes.ctypes.data_as(C.POINTER(C.c_int)), _ptr(b),
                                          _stream()))
         return b
+
+    # -- instrumentation ----------------------------------------------------------------
+    def profile(self, enable=True):
+        """Turn per-kernel CUDA-event timing on/off (resets the totals and launch count)."""
+        self._check(lib().helm_profile(self._ctx, int(enable)))
+
+    def profile_read(self):
+        stats = (KernelStat * 32)()
+        cnt = C.c_int()
+        launches = C.c_longlong()
+        self._check(lib().helm_profile_read(self._ctx, stats, 32, C.byref(cnt), C.byref(launches)))
+        fams = [{"name": s.name.decode(), "launches": s.launches, "ms": s.ms, "bytes": s.bytes, "flops": s.flops}
+                for s in stats[: cnt.value]]
+        return fams, launches.value
 
     def solve(self, b, x=None):
         """Solve A x = b.  b (and x, the initial guess) are complex128 tensors on the GPU, or

@@ -126,11 +126,12 @@ def test_rhs_point_bit_exact(helm):
         np.testing.assert_array_equal(b, oracle.rhs_point(shape, bc, 1 / 16, src))
 
 
+@pytest.mark.parametrize("orth", ["fp64", "df"])
 @pytest.mark.parametrize("krylov,restart", [("gmres", 30), ("fgmres", 30), ("gmres", 200)])
-def test_solve_small_dirichlet(helm, krylov, restart):
+def test_solve_small_dirichlet(helm, krylov, restart, orth):
     """The small workload itself: n = 32, constant k = 20 (kh = 0.625), Dirichlet, centre source."""
     w = I.workload("small")
-    s = helm.Solver(w["n"], w["h"], w["k2"], D, krylov=krylov, restart=restart, max_iter=600)
+    s = helm.Solver(w["n"], w["h"], w["k2"], D, krylov=krylov, restart=restart, max_iter=600, orth=orth)
     o = oracle.Solver(w["n"], w["h"], D, w["k2"])
     b = s.rhs_point(w["sources"])
     x, info = s.solve(b)
@@ -144,10 +145,11 @@ def test_solve_small_dirichlet(helm, krylov, restart):
     assert np.linalg.norm(b.cpu().numpy() - ax) / np.linalg.norm(b.cpu().numpy()) <= 1.01e-6
 
 
+@pytest.mark.parametrize("orth", ["fp64", "df"])
 @pytest.mark.parametrize("krylov", ["gmres", "fgmres"])
-def test_solve_wedge_scaled(helm, krylov):
+def test_solve_wedge_scaled(helm, krylov, orth):
     w = I.workload("wedge", 32)
-    s = helm.Solver(w["n"], w["h"], w["k2"], S, krylov=krylov)
+    s = helm.Solver(w["n"], w["h"], w["k2"], S, krylov=krylov, orth=orth)
     o = oracle.Solver(w["n"], w["h"], S, w["k2"])
     b = s.rhs_point(w["sources"])
     x, info = s.solve(b)
@@ -157,11 +159,12 @@ def test_solve_wedge_scaled(helm, krylov):
     assert rel(x.cpu().numpy(), ro["x"]) <= 1e-5
 
 
-def test_solve_mixed_precision(helm):
+@pytest.mark.parametrize("orth", ["fp64", "df"])
+def test_solve_mixed_precision(helm, orth):
     """complex64 V-cycle under FP64 FGMRES(30): the true residual still reaches 1e-6; the
     error against a tight FP64 oracle solution is reported (the paper fixes no bound)."""
     w = I.workload("mixed", 32)
-    s = helm.Solver(w["n"], w["h"], w["k2"], S, precision="mixed")
+    s = helm.Solver(w["n"], w["h"], w["k2"], S, precision="mixed", orth=orth)
     o = oracle.Solver(w["n"], w["h"], S, w["k2"])
     b = s.rhs_point(w["sources"])
     x, info = s.solve(b)
@@ -228,10 +231,11 @@ def test_full_size_wedge_apply_and_vcycle(helm):
     assert rel(z, o.vcycle(u)) <= 1e-12
 
 
-def test_full_size_wedge_solve_residual(helm):
+@pytest.mark.parametrize("orth", ["fp64", "df"])
+def test_full_size_wedge_solve_residual(helm, orth):
     """Full-size FP64 solve: the oracle's own operator confirms ||b - A x|| / ||b|| <= 1e-6."""
     w = I.workload("wedge")
-    s = helm.Solver(w["n"], w["h"], w["k2"], S)
+    s = helm.Solver(w["n"], w["h"], w["k2"], S, orth=orth)
     b = s.rhs_point(w["sources"])
     x, info = s.solve(b)
     assert info["status"] == 0
