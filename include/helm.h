@@ -190,6 +190,31 @@ HELM_API helm_status helm_profile(helm_ctx* ctx, int enable);
 HELM_API helm_status helm_profile_read(helm_ctx* ctx, helm_kernel_stat* stats, int cap, int* count,
                                        long long* launches);
 
+/* Allocation-free variant of the finest-level down stage (helm_vcycle_stage with level 0,
+ * stage 0), with no context.  The paper has no counterpart; it exists for callers that may
+ * not call cudaMalloc themselves -- code inside a host framework whose memory pool owns
+ * every device allocation, or a plug-in allowed to allocate only at start-up -- but still
+ * want one multigrid restriction step on their own buffers.
+ *
+ * Computes out = R (b - M u1), u1 = omega D^{-1} b, on the grid of n1 x n2 x n3 intervals
+ * (each even, >= 2) with spacing h, boundary bc and the CSLP shift (beta1 - beta2 i):
+ *   k2  : device, FP64, k^2 at the fine unknowns
+ *   b   : device, c128, fine unknowns;  out : device, c128, unknowns of the n/2 grid
+ * The intermediate u1 and residual live in a static device array of
+ * 2 x HELM_NOALLOC_MAX_POINTS complex128 values (8 MiB) that every GPU loading the library
+ * holds until exit; grids with more fine unknowns than HELM_NOALLOC_MAX_POINTS are rejected
+ * with HELM_EINVAL (message in helm_last_error(NULL)).  Nothing is allocated: no cudaMalloc,
+ * no cudaFree, no allocating library call.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before capturing a stream into a graph.
+ * Every call on a device shares the one array and overwrites all of its live part, so
+ * nothing in it needs to start at zero, but calls that overlap on the GPU (other streams,
+ * other threads) race on it: order them. */
+#define HELM_NOALLOC_MAX_POINTS 262144
+HELM_API helm_status helm_vcycle_down_noalloc(int n1, int n2, int n3, double h, const double* k2, helm_bc bc,
+                                              double beta1, double beta2, double omega, const void* b, void* out,
+                                              void* stream);
+
 /* Message for the last failing call on ctx (or for the last failing helm_create when
  * ctx is NULL).  The string is owned by the library. */
 HELM_API const char* helm_last_error(const helm_ctx* ctx);

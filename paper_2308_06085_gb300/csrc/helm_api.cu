@@ -545,6 +545,9 @@ void stage_impl(helm_ctx* c, int l, int stage, const cx<R>* b, const cx<R>* e, c
 
 }  // namespace
 
+// Message slot of helm_last_error(NULL), shared with the context-free entry point.
+void helm_set_global_error(const char* msg) { g_create_error = msg; }
+
 extern "C" {
 
 void helm_default_params(helm_params* p) {

@@ -81,6 +81,8 @@ def lib():
     L.helm_solve.argtypes = [vp, vp, vp, C.POINTER(SolveInfo), vp]
     L.helm_profile.argtypes = [vp, i]
     L.helm_profile_read.argtypes = [vp, C.POINTER(KernelStat), i, C.POINTER(i), C.POINTER(C.c_longlong)]
+    L.helm_vcycle_down_noalloc.argtypes = [i, i, i, d, vp, i, d, d, d, vp, vp, vp]
+    L.helm_vcycle_down_noalloc.restype = i
     L.helm_last_error.argtypes = [vp]
     L.helm_last_error.restype = C.c_char_p
     for f in ("helm_create", "helm_destroy", "helm_levels", "helm_level_dims", "helm_apply", "cslp_vcycle",
@@ -105,6 +107,25 @@ def _ptr(t):
 
 
 _DT = {torch.complex128: C128, torch.complex64: C64}
+
+
+NOALLOC_MAX_POINTS = 262144
+
+
+def vcycle_down_noalloc(n, h, k2, b, bc=SOMMERFELD, beta1=1.0, beta2=-0.5, omega=0.8):
+    """Finest-level down stage R(b - M omega D^-1 b) with no context and no device allocation
+    inside the library (for callers that may not allocate).  k2: float64 CUDA tensor at the
+    fine unknowns; b: complex128 CUDA tensor; returns the coarse right-hand side (the output
+    tensor is the caller's allocation)."""
+    n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(int(x) for x in n)
+    d = -1 if bc == DIRICHLET else 1
+    cshape = (n3 // 2 + d, n2 // 2 + d, n1 // 2 + d)
+    out = torch.empty(cshape, dtype=torch.complex128, device=b.device)
+    st = lib().helm_vcycle_down_noalloc(n1, n2, n3, float(h), _ptr(k2), bc, beta1, beta2, omega, _ptr(b), _ptr(out),
+                                        _stream())
+    if st != OK:
+        raise HelmError(st, lib().helm_last_error(None).decode())
+    return out
 
 
 class Solver:
