@@ -176,28 +176,29 @@ def workload_config(n):
 # ------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------
-def source_hash():
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2308_06085_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
-    return h.hexdigest()[:16]
+def file_hash(rel):
+    return hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()[:16]
 
 
 def ncu_traffic(kernel_name):
-    """DRAM bytes per launch of `kernel_name` from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    """DRAM traffic of one launch of `kernel_name` from the committed ncu summary
+    (profiles/ncu_traffic.json), or None when a source file of that kernel changed since the
+    counters were taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     try:
-        d = json.load(open(path))
+        k = json.load(open(path)).get("kernels", {}).get(kernel_name)
     except ValueError:
         return None
-    if d.get("source_hash") != source_hash():
+    if not k:
         return None
-    k = d.get("kernels", {}).get(kernel_name)
-    return None if k is None else k
+    try:
+        if any(file_hash(f) != h for f, h in k.get("source_files", {}).items()):
+            return None
+    except OSError:
+        return None
+    return k
 
 
 def time_solves(torch, s, b, steps, x=None):
@@ -291,9 +292,10 @@ def run_ours(args):
     roof["avg_launch_us"] = 1e3 * top["ms"] / max(top["launches"], 1)
     roof["share_of_kernel_time"] = top["ms"] / total_ms if total_ms else None
     roof["hbm_gbs_achieved"] = top["bytes"] / (top["ms"] * 1e-3) / 1e9 if top["ms"] > 0 else None
-    tr = ncu_traffic(top["name"])
+    tr = ncu_traffic(roof["kernel"])
     roof["traffic"] = None if tr is None else tr.get("dram_bytes_per_launch")
     if tr is not None:
+        roof["traffic_algorithmic_bytes"] = tr.get("algorithmic_bytes_per_launch")
         roof["traffic_note"] = tr.get("note")
     kernels = [{"name": f["name"], "launches": f["launches"], "ms_per_step": f["ms"] / args.steps,
                 "share": f["ms"] / total_ms if total_ms else None,

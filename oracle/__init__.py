@@ -50,6 +50,9 @@ def lib():
         L.oracle_gmres.restype = i
         L.oracle_rhs_point.argtypes = [i, i, i, i, d, i, ip, dp]
         L.oracle_rhs_closed_off.argtypes = [i, d, dp]
+        L.oracle_adjoint_rhs.argtypes = [i, i, i, i, dp, dp]
+        L.oracle_adjoint_finish.argtypes = [i, i, i, i, dp, dp]
+        L.oracle_grad_k2.argtypes = [i, i, i, d, i, dp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -132,6 +135,15 @@ def rhs_closed_off(n, k):
     return b
 
 
+def grad_k2(u, lam, k2, h, bc, grad=None):
+    """grad += -Re(conj(lambda) dA/dk2 u) at every node (adjoint-state gradient)."""
+    u, lam, k2 = _c128(u), _c128(lam), _f64(k2)
+    N3, N2, N1 = u.shape
+    g = np.zeros(u.shape) if grad is None else np.ascontiguousarray(grad, dtype=np.float64)
+    lib().oracle_grad_k2(N1, N2, N3, h, bc, _dp(k2), _dp(u), _dp(lam), _dp(g))
+    return g
+
+
 class Solver:
     """Oracle multigrid hierarchy + V-cycle + right-preconditioned GMRES(m)."""
 
@@ -192,6 +204,36 @@ class Solver:
         e = np.empty_like(b)
         lib().oracle_coarse_solve(self._ctx, _dp(b), _dp(e))
         return e
+
+    def solve_adjoint(self, g, restart=30, tol=1e-6, max_iter=1000):
+        """lambda with A^H lambda = g: solve A nu = D^-1 conj(g) by the same GMRES, then
+        lambda = conj(D nu), D = diag(2^-faces)."""
+        g = _c128(g).reshape(self.shape)
+        N3, N2, N1 = self.shape
+        q = np.empty_like(g)
+        lib().oracle_adjoint_rhs(N1, N2, N3, self.bc, _dp(g), _dp(q))
+        r = self.gmres(q, restart=restart, tol=tol, max_iter=max_iter)
+        lam = np.empty_like(g)
+        lib().oracle_adjoint_finish(N1, N2, N3, self.bc, _dp(r["x"]), _dp(lam))
+        r["x"] = lam
+        return r
+
+    def adjoint_grad(self, sources, rec_idx, d_obs, restart=30, tol=1e-6, max_iter=1000):
+        """Loss 1/2 sum_s |u_s(R) - d_s|^2 over point sources and its gradient w.r.t. k^2.
+        rec_idx: flat unknown indices of the receivers; d_obs: (nsrc, nrec) complex."""
+        rec_idx = np.asarray(rec_idx, dtype=np.int64)
+        grad = np.zeros(self.shape)
+        loss = 0.0
+        for s, src in enumerate(sources):
+            b = rhs_point(self.shape, self.bc, self.h, [src])
+            u = self.gmres(b, restart=restart, tol=tol, max_iter=max_iter)["x"]
+            res = u.ravel()[rec_idx] - np.asarray(d_obs)[s]
+            loss += 0.5 * float(np.sum(np.abs(res) ** 2))
+            g = np.zeros(u.size, dtype=np.complex128)
+            g[rec_idx] = res
+            lam = self.solve_adjoint(g.reshape(self.shape), restart=restart, tol=tol, max_iter=max_iter)["x"]
+            grad = grad_k2(u, lam, self._k2, self.h, self.bc, grad)
+        return loss, grad
 
     def gmres(self, b, x0=None, restart=30, tol=1e-6, max_iter=1000, flexible=False, history=False):
         b = _c128(b).reshape(self.shape)

@@ -595,3 +595,54 @@ void oracle_rhs_closed_off(int n, double kconst, double* bout) {
         b[at(i, j, k, N, N)] = f + nb * 1.0 / (h * h);
       }
 }
+
+/* ---------------------------------------------------------------------------------
+ * Adjoint state for frequency-domain gradients (not in the paper; its operator and
+ * boundary scheme are).  With D = diag(2^-faces) the row scaling that makes D A symmetric
+ * (Sommerfeld; D = I for Dirichlet), A^T = D A D^-1, so A^H lambda = g is solved with the
+ * forward operator: A nu = D^-1 conj(g), lambda = conj(D nu).
+ * --------------------------------------------------------------------------------- */
+static int face_count(int i, int j, int k, int N1, int N2, int N3, int bc) {
+  if (bc != BC_SOMMERFELD) return 0;
+  return (i == 0) + (i == N1 - 1) + (j == 0) + (j == N2 - 1) + (k == 0) + (k == N3 - 1);
+}
+
+/* q = D^-1 conj(g) */
+void oracle_adjoint_rhs(int N1, int N2, int N3, int bc, const double* gin, double* qout) {
+  const cplx* g = (const cplx*)gin;
+  cplx* q = (cplx*)qout;
+  for (int k = 0; k < N3; ++k)
+    for (int j = 0; j < N2; ++j)
+      for (int i = 0; i < N1; ++i) {
+        size_t p = at(i, j, k, N1, N2);
+        q[p] = ldexp(1.0, face_count(i, j, k, N1, N2, N3, bc)) * conj(g[p]);
+      }
+}
+
+/* lambda = conj(D nu) */
+void oracle_adjoint_finish(int N1, int N2, int N3, int bc, const double* nuin, double* lout) {
+  const cplx* nu = (const cplx*)nuin;
+  cplx* l = (cplx*)lout;
+  for (int k = 0; k < N3; ++k)
+    for (int j = 0; j < N2; ++j)
+      for (int i = 0; i < N1; ++i) {
+        size_t p = at(i, j, k, N1, N2);
+        l[p] = conj(ldexp(1.0, -face_count(i, j, k, N1, N2, N3, bc)) * nu[p]);
+      }
+}
+
+/* grad[p] += -Re(conj(lambda_p) (dA_pp / dk2_p) u_p): A depends on k^2_p only through its
+ * diagonal entry -k^2_p - i (2 k_p / h) nf_p, whose derivative is -1 - i nf_p / (h k_p). */
+void oracle_grad_k2(int N1, int N2, int N3, double h, int bc, const double* k2, const double* uin,
+                    const double* lin, double* grad) {
+  const cplx* u = (const cplx*)uin;
+  const cplx* l = (const cplx*)lin;
+  for (int k = 0; k < N3; ++k)
+    for (int j = 0; j < N2; ++j)
+      for (int i = 0; i < N1; ++i) {
+        size_t p = at(i, j, k, N1, N2);
+        int nf = face_count(i, j, k, N1, N2, N3, bc);
+        cplx da = -1.0 - I * (double)nf / (h * sqrt(k2[p]));
+        grad[p] += -creal(conj(l[p]) * da * u[p]);
+      }
+}
