@@ -169,6 +169,38 @@ HELM_API helm_status helm_rhs_point(helm_ctx* ctx, int nsrc, const int* nodes, v
 HELM_API helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_info* info,
                        void* stream);
 
+/* Adjoint solve for frequency-domain gradients (the paper solves forward problems only;
+ * the operator and boundary scheme are its Sec. 2.4).  Solves A^H lambda = g, where A^H is the
+ * conjugate transpose of A_h, with the same preconditioned Krylov method as helm_solve: the
+ * rows eliminated at Sommerfeld faces make D A symmetric for D = diag(2^-faces) (D = I for
+ * Dirichlet), so A^T = D A D^-1 and the library solves A nu = D^-1 conj(g), lambda = conj(D nu).
+ *   g, lambda : device c128 vectors (lambda is overwritten; the solve starts from zero)
+ *   info      : optional host report of the inner forward-type solve
+ * Waits for the solve.  Errors as helm_solve. */
+HELM_API helm_status helm_solve_adjoint(helm_ctx* ctx, const void* g, void* lambda, helm_solve_info* info,
+                                        void* stream);
+
+/* Accumulate the adjoint-state gradient with respect to k^2 at every node:
+ *   grad_k2[p] += -Re( conj(lambda_p) * dA_pp/dk^2_p * u_p ),  dA_pp/dk^2_p = -1 - i nf_p / (h k_p)
+ * (nf_p = Sommerfeld faces at p).  u: the forward solution, lambda: the adjoint solution for
+ * g = dL/d conj(u) of a real loss L; the sum over sources is the gradient of L.
+ * u, lambda: device c128; grad_k2: device FP64, N1*N2*N3 values, accumulated into. */
+HELM_API helm_status helm_grad_k2(helm_ctx* ctx, const void* u, const void* lambda, double* grad_k2, void* stream);
+
+/* Full-waveform-style gradient for point sources and a receiver set:
+ *   L = 1/2 sum_s sum_{r in R} |u_s(r) - d_obs[s][r]|^2,  A u_s = b_s (discrete Dirac, Sec. 2.4),
+ *   grad_k2 = dL/dk^2 (one forward and one adjoint solve per source, helm_grad_k2 summed).
+ *   src_nodes : HOST, 3*nsrc node coordinates (as helm_rhs_point)
+ *   rec_idx   : HOST, nrec distinct unknown indices (layout index (i3*N2 + i2)*N1 + i1)
+ *   d_obs     : device c128, nsrc x nrec (row per source)
+ *   grad_k2   : device FP64, N1*N2*N3, overwritten;  loss : host double
+ *   info      : optional host report (iterations summed over all solves, worst residual)
+ * The forward wavefield of one source is held on the device until its adjoint step (one
+ * source at a time).  Waits for completion.  HELM_ENOCONV if any solve hit max_iter. */
+HELM_API helm_status helm_adjoint_grad(helm_ctx* ctx, int nsrc, const int* src_nodes, int nrec, const int* rec_idx,
+                                       const void* d_obs, double* grad_k2, double* loss, helm_solve_info* info,
+                                       void* stream);
+
 /* Per-kernel-family statistics of the opt-in profiler. */
 typedef struct {
   const char* name;   /* kernel function(s) of the family; static string */

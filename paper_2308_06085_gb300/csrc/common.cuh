@@ -135,8 +135,26 @@ struct Grid {
   int N1, N2, N3;
   int bc;
   double h;
+  // sqrt(k^2) per node (FP64 and FP32 copies), read only at Sommerfeld face nodes; NULL when
+  // the caller has none (the kernels then take the square root themselves)
+  const double* sqk = nullptr;
+  const float* sqkf = nullptr;
   __host__ __device__ size_t npts() const { return (size_t)N1 * N2 * N3; }
 };
+
+template <typename R>
+__device__ __forceinline__ const R* grid_sqk(const Grid& g);
+template <>
+__device__ __forceinline__ const double* grid_sqk<double>(const Grid& g) { return g.sqk; }
+template <>
+__device__ __forceinline__ const float* grid_sqk<float>(const Grid& g) { return g.sqkf; }
+
+// k at node p for the face term: from the per-node table when present.
+template <typename R>
+__device__ __forceinline__ R face_k(const Grid& g, size_t p, R k2p) {
+  const R* t = grid_sqk<R>(g);
+  return t ? __ldg(t + p) : sqrt(k2p);
+}
 
 __host__ __device__ __forceinline__ size_t gidx(int i, int j, int k, int N1, int N2) {
   return ((size_t)k * N2 + j) * N1 + i;
@@ -153,15 +171,16 @@ struct OpCoef {
   R omega;       // damped-Jacobi relaxation (used by smoothing kernels)
 };
 
-// Diagonal of the operator at a node lying on `nf` Sommerfeld faces:
+// Diagonal of the operator at a node lying on `nf` Sommerfeld faces (kp = sqrt(k^2), used only
+// when nf > 0):
 // 6/h^2 - s k^2 - i (2 k / h) nf.  The face term comes from eliminating the ghost value
 // u_ghost = u_opposite + 2 h i k u_p (Sec. 2.4 Eq. elimination): its -1/h^2 coefficient
 // moves 2 h i k u_p onto the diagonal.
 template <typename R>
-__device__ __forceinline__ cx<R> op_diag(const OpCoef<R>& c, R k2p, int nf) {
+__device__ __forceinline__ cx<R> op_diag(const OpCoef<R>& c, R k2p, int nf, R kp) {
   R dre = fma(-c.s_re, k2p, c.six_ih2);
   R dim = -c.s_im * k2p;
-  if (nf) dim = fma(-(R)nf * c.two_over_h, sqrt(k2p), dim);
+  if (nf) dim = fma(-(R)nf * c.two_over_h, kp, dim);
   return mkc<R>(dre, dim);
 }
 

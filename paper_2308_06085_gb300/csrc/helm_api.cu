@@ -2,6 +2,7 @@
 // set-up, the V-cycle driver, and the host side of right-preconditioned GMRES(m) /
 // FGMRES(m).  All grid arithmetic runs in the kernels of stencil.cu and krylov.cu; the host
 // only orders launches, except at set-up, where it inverts the small coarsest-grid matrix.
+#include <algorithm>
 #include <chrono>
 #include <complex>
 #include <cstdarg>
@@ -30,6 +31,8 @@ struct Level {
   Grid g;
   double* k2 = nullptr;    // FP64 k^2
   float* k2f = nullptr;    // FP32 copy
+  double* sk = nullptr;    // sqrt(k^2), FP64 (face terms)
+  float* skf = nullptr;    // sqrt(k^2), FP32
   z128* dinv = nullptr;    // omega / diag(M), FP64 path
   // V-cycle work vectors: B = right-hand side (levels >= 1), U1 = pre-smoothed iterate,
   // T = residual / corrected iterate, E = result (levels >= 1)
@@ -131,6 +134,12 @@ struct helm_ctx {
   int* reorth_log = nullptr;   // device, per Arnoldi step: second pass taken
   int* hreorth_log = nullptr;  // pinned host copy
   long long reorth_steps = 0, arnoldi_steps = 0;
+  // adjoint-state gradient buffers (allocated on first use)
+  z128 *adj_u = nullptr, *adj_g = nullptr, *adj_l = nullptr;
+  double* adj_part = nullptr;
+  double* adj_norm = nullptr;
+  int* adj_rec = nullptr;
+  int adj_rec_cap = 0;
 };
 
 namespace {
@@ -642,6 +651,10 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
     const size_t np = L.g.npts();
     TRY(dalloc(c, &L.k2, np));
     TRY(dalloc(c, &L.k2f, np));
+    TRY(dalloc(c, &L.sk, np));
+    TRY(dalloc(c, &L.skf, np));
+    L.g.sqk = L.sk;
+    L.g.sqkf = L.skf;
     TRY(dalloc(c, &L.dinv, np));
     TRY(dalloc(c, &L.U164, np));
     TRY(dalloc(c, &L.T64, np));
@@ -670,6 +683,7 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
   for (int l = 0; l < nl; ++l) {
     Level& L = c->L[l];
     launch_to_float(L.k2, L.k2f, L.g.npts(), st);
+    launch_sqrt_table(L.k2, L.sk, L.skf, L.g.npts(), st);
     launch_dinv(L.g, c->s_re, c->s_im, P.omega, L.k2, L.dinv, st);
   }
   TRY(check_launch(c, "set-up kernels"));
@@ -848,6 +862,113 @@ helm_status helm_rhs_point(helm_ctx* c, int nsrc, const int* nodes, void* b, voi
   CU(cudaMemsetAsync(b, 0, c->n0 * sizeof(z128), st));
   if (nsrc > 0) launch_rhs_point(L.g, nsrc, c->rhs_idx, 1.0 / (L.g.h * L.g.h * L.g.h), (z128*)b, st);
   return check_launch(c, "helm_rhs_point");
+}
+
+helm_status helm_solve_adjoint(helm_ctx* c, const void* g, void* lambda, helm_solve_info* info, void* stream) {
+  if (!c) return HELM_EINVAL;
+  if (!g || !lambda || g == lambda) return fail(c, HELM_EINVAL, "g and lambda must be distinct non-NULL device pointers");
+  if (!is_device_ptr(g) || !is_device_ptr(lambda)) return fail(c, HELM_EINVAL, "g and lambda must be device pointers");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)stream;
+  const Level& F = c->L[0];
+  launch_adjoint_rhs(F.g, (const z128*)g, c->bs, st);
+  CU(cudaMemsetAsync(lambda, 0, c->n0 * sizeof(z128), st));
+  helm_solve_info tmp;
+  helm_solve_info* inf = info ? info : &tmp;
+  helm_status s = gmres_device(c, c->bs, (z128*)lambda, inf, st);
+  launch_adjoint_finish(F.g, (z128*)lambda, st);
+  TRY(check_launch(c, "helm_solve_adjoint"));
+  CU(cudaStreamSynchronize(st));
+  inf->status = (int)s;
+  inf->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (s == HELM_ENOCONV) fail(c, s, "adjoint solve: max_iter (%d) reached", c->p.max_iter);
+  if (s == HELM_ENUMERIC) fail(c, s, "adjoint solve: non-finite residual or Krylov breakdown");
+  return s;
+}
+
+helm_status helm_grad_k2(helm_ctx* c, const void* u, const void* lambda, double* grad_k2, void* stream) {
+  if (!c) return HELM_EINVAL;
+  if (!u || !lambda || !grad_k2) return fail(c, HELM_EINVAL, "NULL pointer");
+  const Level& F = c->L[0];
+  launch_grad_k2(F.g, F.k2, (const z128*)u, (const z128*)lambda, grad_k2, (cudaStream_t)stream);
+  return check_launch(c, "helm_grad_k2");
+}
+
+helm_status helm_adjoint_grad(helm_ctx* c, int nsrc, const int* src_nodes, int nrec, const int* rec_idx,
+                              const void* d_obs, double* grad_k2, double* loss, helm_solve_info* info, void* stream) {
+  if (!c) return HELM_EINVAL;
+  if (nsrc < 1 || !src_nodes || nrec < 1 || !rec_idx || !d_obs || !grad_k2 || !loss)
+    return fail(c, HELM_EINVAL, "bad source, receiver, data or output arguments");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = c->n0;
+  std::vector<int> rec(rec_idx, rec_idx + nrec);
+  {
+    std::vector<int> sorted(rec);
+    std::sort(sorted.begin(), sorted.end());
+    if (sorted.front() < 0 || (size_t)sorted.back() >= n)
+      return fail(c, HELM_EINVAL, "receiver index outside 0..%zu", n - 1);
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      return fail(c, HELM_EINVAL, "receiver indices must be distinct");
+  }
+  if (!c->adj_u) {
+    TRY(dalloc(c, &c->adj_u, n));
+    TRY(dalloc(c, &c->adj_g, n));
+    TRY(dalloc(c, &c->adj_l, n));
+    TRY(dalloc(c, &c->adj_part, 256));
+    TRY(dalloc(c, &c->adj_norm, 1));
+  }
+  if (nrec > c->adj_rec_cap) {
+    TRY(dalloc(c, &c->adj_rec, nrec));
+    c->adj_rec_cap = nrec;
+  }
+  CU(cudaStreamSynchronize(st));
+  CU(cudaMemcpy(c->adj_rec, rec.data(), sizeof(int) * nrec, cudaMemcpyHostToDevice));
+  CU(cudaMemsetAsync(grad_k2, 0, n * sizeof(double), st));
+  const Level& F = c->L[0];
+  double total = 0.0;
+  int iters = 0, restarts = 0;
+  helm_status worst = HELM_OK;
+  double worst_rr = 0.0;
+  for (int s = 0; s < nsrc; ++s) {
+    TRY(helm_rhs_point(c, 1, src_nodes + 3 * s, c->bs, st));
+    CU(cudaMemsetAsync(c->adj_u, 0, n * sizeof(z128), st));
+    helm_solve_info fi;
+    helm_status fs = gmres_device(c, c->bs, c->adj_u, &fi, st);
+    if (fs == HELM_ENUMERIC || fs == HELM_ECUDA || fs == HELM_ENOMEM) return fs;
+    CU(cudaMemsetAsync(c->adj_g, 0, n * sizeof(z128), st));
+    const int nb = launch_receiver_residual(nrec, c->adj_rec, c->adj_u, (const z128*)d_obs + (size_t)s * nrec, c->adj_g,
+                                            c->adj_part, st);
+    launch_reduce_norm(c->adj_part, nb, c->adj_norm, st, nullptr);
+    double rn = 0.0;
+    CU(cudaMemcpyAsync(&rn, c->adj_norm, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    total += 0.5 * rn * rn;
+    launch_adjoint_rhs(F.g, c->adj_g, c->bs, st);
+    CU(cudaMemsetAsync(c->adj_l, 0, n * sizeof(z128), st));
+    helm_solve_info ai;
+    helm_status as = gmres_device(c, c->bs, c->adj_l, &ai, st);
+    if (as == HELM_ENUMERIC || as == HELM_ECUDA || as == HELM_ENOMEM) return as;
+    launch_adjoint_finish(F.g, c->adj_l, st);
+    launch_grad_k2(F.g, F.k2, c->adj_u, c->adj_l, grad_k2, st);
+    TRY(check_launch(c, "helm_adjoint_grad"));
+    iters += fi.iterations + ai.iterations;
+    restarts += fi.restarts + ai.restarts;
+    if (fs != HELM_OK) worst = fs;
+    if (as != HELM_OK) worst = as;
+    worst_rr = std::max(worst_rr, std::max(fi.rel_residual, ai.rel_residual));
+  }
+  CU(cudaStreamSynchronize(st));
+  *loss = total;
+  if (info) {
+    info->iterations = iters;
+    info->restarts = restarts;
+    info->rel_residual = worst_rr;
+    info->status = (int)worst;
+    info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (worst == HELM_ENOCONV) fail(c, worst, "a forward or adjoint solve reached max_iter");
+  return worst;
 }
 
 helm_status helm_solve(helm_ctx* c, const void* b, void* x, helm_solve_info* info, void* stream) {

@@ -33,6 +33,8 @@ void launch_coarse(int nc, const z128* Minv, const cx<TI>* b, cx<TO>* e, cudaStr
 void launch_dinv(const Grid& g, double s_re, double s_im, double omega, const double* k2, z128* out, cudaStream_t st);
 void launch_inject(const Grid& gf, const Grid& gc, const double* kf, double* kc, cudaStream_t st);
 void launch_to_float(const double* a, float* b, size_t n, cudaStream_t st);
+// sk = sqrt(k2) in FP64, skf = sqrtf(float(k2)) in FP32 (the face terms' k)
+void launch_sqrt_table(const double* k2, double* sk, float* skf, size_t n, cudaStream_t st);
 void launch_check_k2(const double* a, size_t n, int* bad, cudaStream_t st);
 void launch_rhs_point(const Grid& g, int nsrc, const int* idx, double amp, z128* b, cudaStream_t st);
 
@@ -92,5 +94,16 @@ void launch_c64_to_c128(const z64* a, z128* b, size_t n, cudaStream_t st);
 void launch_set_active(KrylovCtl* ctl, int v, cudaStream_t st);
 // x += z
 void launch_axpy1(const z128* z, z128* x, size_t n, cudaStream_t st);
+
+// ---- adjoint-state gradient (adjoint.cu) ----
+// q = D^-1 conj(in), D = diag(2^-faces) (Sommerfeld) or I (Dirichlet)
+void launch_adjoint_rhs(const Grid& g, const z128* in, z128* q, cudaStream_t st);
+// x = conj(D x)
+void launch_adjoint_finish(const Grid& g, z128* x, cudaStream_t st);
+// grad += -Re(conj(lam) (-1 - i nf / (h k)) u)
+void launch_grad_k2(const Grid& g, const double* k2, const z128* u, const z128* lam, double* grad, cudaStream_t st);
+// g(rec[r]) = u(rec[r]) - d[r]; partial sums of |u - d|^2 into part; returns the number of partials
+int launch_receiver_residual(int nrec, const int* rec, const z128* u, const z128* d, z128* g, double* part,
+                             cudaStream_t st);
 
 }  // namespace helm

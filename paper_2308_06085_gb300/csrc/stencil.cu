@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(TX* TY)
     cx<R> ym = hym ? ld(p - N1) : (som ? ld(p + N1) : zero_c<R>());
     cx<R> yp = hyp ? ld(p + N1) : (som ? ld(p - N1) : zero_c<R>());
     const R kk = __ldg(k2 + p);
-    const cx<R> d = op_diag(c, kk, nf);
+    const cx<R> d = op_diag(c, kk, nf, nf ? face_k<R>(g, p, kk) : (R)0);
     const cx<R> v = op_combine(d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
     if (MODE == 0) {
       if (SPLIT)  // the output buffer holds double-float values (16 bytes, like complex128)
@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(TX* TY)
       w = ldg(dinv + p);
     } else {
       const int nf = nfxy + (som ? (k == 0) + (k == g.N3 - 1) : 0);
-      w = omega_over(op_diag(c, __ldg(k2 + p), nf), c.omega);
+      const R kk = __ldg(k2 + p);
+      w = omega_over(op_diag(c, kk, nf, nf ? face_k<R>(g, p, kk) : (R)0), c.omega);
     }
     out[p] = cmul(w, cvt<R>(ldg(b + p)));
   }
@@ -120,7 +121,7 @@ __global__ void k_dinv(Grid g, OpCoef<double> c, const double* __restrict__ k2, 
     const int j = (int)((p / g.N1) % g.N2);
     const int k = (int)(p / ((size_t)g.N1 * g.N2));
     const int nf = g.bc == 1 ? (i == 0) + (i == g.N1 - 1) + (j == 0) + (j == g.N2 - 1) + (k == 0) + (k == g.N3 - 1) : 0;
-    const z128 d = op_diag(c, k2[p], nf);
+    const z128 d = op_diag(c, k2[p], nf, sqrt(k2[p]));
     // omega / d as omega conj(d) / |d|^2 in FP64 (set-up only)
     const double m2 = d.re * d.re + d.im * d.im;
     out[p] = mkc<double>(c.omega * d.re / m2, -c.omega * d.im / m2);
@@ -219,6 +220,14 @@ __global__ void k_inject(Grid gf, Grid gc, const double* __restrict__ kf, double
     const int J = (int)((p / gc.N1) % gc.N2);
     const int K = (int)(p / ((size_t)gc.N1 * gc.N2));
     kc[p] = kf[gidx(2 * (I + off) - off, 2 * (J + off) - off, 2 * (K + off) - off, gf.N1, gf.N2)];
+  }
+}
+
+__global__ void k_sqrt_table(const double* __restrict__ k2, double* __restrict__ sk, float* __restrict__ skf, size_t n) {
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+    const double v = sqrt(k2[p]);
+    sk[p] = v;
+    skf[p] = sqrtf((float)k2[p]);
   }
 }
 
@@ -380,6 +389,10 @@ void launch_dinv(const Grid& g, double s_re, double s_im, double omega, const do
 
 void launch_inject(const Grid& gf, const Grid& gc, const double* kf, double* kc, cudaStream_t st) {
   k_inject<<<1216, 256, 0, st>>>(gf, gc, kf, kc);
+}
+
+void launch_sqrt_table(const double* k2, double* sk, float* skf, size_t n, cudaStream_t st) {
+  k_sqrt_table<<<1216, 256, 0, st>>>(k2, sk, skf, n);
 }
 
 void launch_to_float(const double* a, float* b, size_t n, cudaStream_t st) {

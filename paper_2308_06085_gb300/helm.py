@@ -81,6 +81,12 @@ def lib():
     L.helm_solve.argtypes = [vp, vp, vp, C.POINTER(SolveInfo), vp]
     L.helm_profile.argtypes = [vp, i]
     L.helm_profile_read.argtypes = [vp, C.POINTER(KernelStat), i, C.POINTER(i), C.POINTER(C.c_longlong)]
+    L.helm_solve_adjoint.argtypes = [vp, vp, vp, C.POINTER(SolveInfo), vp]
+    L.helm_grad_k2.argtypes = [vp, vp, vp, vp, vp]
+    L.helm_adjoint_grad.argtypes = [vp, i, C.POINTER(i), i, C.POINTER(i), vp, vp, C.POINTER(d), C.POINTER(SolveInfo),
+                                    vp]
+    for f in ("helm_solve_adjoint", "helm_grad_k2", "helm_adjoint_grad"):
+        getattr(L, f).restype = i
     L.helm_vcycle_down_noalloc.argtypes = [i, i, i, d, vp, i, d, d, d, vp, vp, vp]
     L.helm_vcycle_down_noalloc.restype = i
     L.helm_last_error.argtypes = [vp]
@@ -252,6 +258,43 @@ class Solver:
                 for s in stats[: cnt.value]]
         return fams, launches.value
 
+    def solve_adjoint(self, g):
+        """lambda with A^H lambda = g (device complex128 tensors); returns (lambda, info)."""
+        g = self._vec(g, dtype=torch.complex128)
+        lam = torch.empty_like(g)
+        info = SolveInfo()
+        st = lib().helm_solve_adjoint(self._ctx, _ptr(g), _ptr(lam), C.byref(info), _stream())
+        if st not in (OK, ENOCONV):
+            self._check(st)
+        return lam, info.as_dict()
+
+    def grad_k2(self, u, lam, grad=None):
+        """grad += -Re(conj(lambda) dA/dk^2 u) at every node (float64 tensor shaped like u)."""
+        u = self._vec(u, dtype=torch.complex128)
+        lam = self._vec(lam, dtype=torch.complex128)
+        if grad is None:
+            grad = torch.zeros(self.shape, dtype=torch.float64, device=u.device)
+        self._check(lib().helm_grad_k2(self._ctx, _ptr(u), _ptr(lam), _ptr(grad), _stream()))
+        return grad
+
+    def adjoint_grad(self, sources, rec_idx, d_obs):
+        """Loss 1/2 sum_s |u_s(rec) - d_obs[s]|^2 for point sources and its gradient w.r.t. k^2.
+        rec_idx: distinct flat unknown indices; d_obs: complex128 CUDA tensor (nsrc, nrec)."""
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).reshape(-1, 3))
+        rec = np.ascontiguousarray(np.asarray(rec_idx, dtype=np.int32).ravel())
+        d_obs = d_obs.contiguous()
+        if d_obs.dtype != torch.complex128 or d_obs.numel() != len(src) * len(rec):
+            raise TypeError("d_obs must be complex128 with nsrc * nrec values")
+        grad = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        loss = C.c_double()
+        info = SolveInfo()
+        st = lib().helm_adjoint_grad(self._ctx, len(src), src.ctypes.data_as(C.POINTER(C.c_int)), len(rec),
+                                     rec.ctypes.data_as(C.POINTER(C.c_int)), _ptr(d_obs), _ptr(grad), C.byref(loss),
+                                     C.byref(info), _stream())
+        if st not in (OK, ENOCONV):
+            self._check(st)
+        return loss.value, grad, info.as_dict()
+
     def solve(self, b, x=None):
         """Solve A x = b.  b (and x, the initial guess) are complex128 tensors on the GPU, or
         both on the host (pinned or pageable), in which case the library stages the copies."""
@@ -269,3 +312,40 @@ class Solver:
         if st not in (OK, ENOCONV):
             self._check(st)
         return x, info.as_dict()
+
+
+class HelmholtzSolve(torch.autograd.Function):
+    """x = A(k^2)^{-1} b as a differentiable torch op.
+
+    forward builds a context for k^2 and solves; backward solves the adjoint system
+    A^H lambda = dL/d conj(x) with the same preconditioned solver and returns
+    dL/dk^2 = -Re(conj(lambda) dA/dk^2 x) and dL/d conj(b) = lambda.  With recompute=True the
+    forward wavefield is not kept and backward solves for it again (checkpointing when
+    memory is short)."""
+
+    @staticmethod
+    def forward(ctx, k2, b, n, h, bc, opts=None, recompute=False):
+        opts = dict(opts or {})
+        s = Solver(n, h, k2.detach(), bc, **opts)
+        bb = b.detach().reshape(s.shape).contiguous()
+        x, info = s.solve(bb)
+        if info["status"] not in (OK,):
+            raise HelmError(info["status"], "forward solve did not converge")
+        ctx.solver = s
+        ctx.recompute = recompute
+        ctx.save_for_backward(bb if recompute else x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        s = ctx.solver
+        (saved,) = ctx.saved_tensors
+        x = s.solve(saved)[0] if ctx.recompute else saved
+        lam, info = s.solve_adjoint(gx.reshape(s.shape).contiguous())
+        gk2 = s.grad_k2(x, lam)
+        return gk2, lam, None, None, None, None, None
+
+
+def helmholtz_solve(k2, b, n, h, bc=SOMMERFELD, opts=None, recompute=False):
+    """Differentiable x = A(k^2)^{-1} b (see HelmholtzSolve)."""
+    return HelmholtzSolve.apply(k2, b, n, h, bc, opts, recompute)
