@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=128, help="intervals per direction of the wedge workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", type=int, default=1, help="also time mixed precision and n = 256")
+    ap.add_argument("--variants", type=int, default=2,
+                    help="0: headline only; 1: + mixed precision and n = 256; 2: + batched and adjoint workloads")
     ap.add_argument("--orth", choices=["fp64", "df"], default="fp64",
                     help="Gram-Schmidt arithmetic: native FP64 or double-float FP32 pairs")
     ap.add_argument("--reorth", choices=["selective", "always"], default="selective",
@@ -367,7 +368,79 @@ def run_variants(torch, helm, inputs, args):
         s.close()
         del s
         torch.cuda.empty_cache()
+    if args.variants >= 2:
+        out.update(run_batched_variant(torch, helm, inputs))
+        out.update(run_adjoint_variant(torch, helm, inputs))
     return out
+
+
+def run_batched_variant(torch, helm, inputs):
+    """32 point sources (4 x 8 grid in the plane x3 = 0.1) on the n = 128 wedge: one batched
+    solve (complex64 V-cycle, FP64 FGMRES(30)) against the same 32 sources solved one by one."""
+    w = inputs.workload("batched", 128)
+    s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov="fgmres", precision="mixed")
+    B = torch.stack([s.rhs_point([p]) for p in w["sources"]])
+    s.solve_batched(B[:4])  # warm-up (allocates the 32-wide workspace on the next call)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    X, infos = s.solve_batched(B)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    s.solve(B[0])
+    torch.cuda.synchronize()
+    e0.record(st)
+    seq_iters = []
+    for r in range(B.shape[0]):
+        _, info = s.solve(B[r])
+        seq_iters.append(info["iterations"])
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    res = {"batched_n128_32src_mixed": {
+        "ms": ms_b, "ms_per_source": ms_b / B.shape[0], "sequential_ms": ms_s, "speedup_vs_sequential": ms_s / ms_b,
+        "iterations_max": max(i["iterations"] for i in infos), "iterations_min": min(i["iterations"] for i in infos),
+        "rel_residual_max": max(i["rel_residual"] for i in infos), "sequential_iterations_max": max(seq_iters),
+        "unknowns_per_source": (128 + 1) ** 3}}
+    s.close()
+    del s, B, X
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_adjoint_variant(torch, helm, inputs):
+    """Adjoint-state gradient on the n = 192 smooth random model: 8 sources, receivers on the
+    plane x3 = 0.9, complex64 V-cycle / FP64 FGMRES(30); one forward and one adjoint solve per
+    source.  Observed data come from forward solves on the perturbed model (timing only)."""
+    import numpy as np
+
+    w = inputs.workload("adjoint", 192)
+    shape = inputs.unknown_shape(w["n"], helm.SOMMERFELD)
+    N3, N2, N1 = shape
+    k = w["receiver_plane"]
+    rec = np.arange(k * N2 * N1, (k + 1) * N2 * N1)
+    k2_true = w["k2"] * inputs.gaussian_bump(w["n"], amp=0.05, width=0.1) ** -2
+    st_ = helm.Solver(w["n"], w["h"], k2_true, helm.SOMMERFELD, krylov="fgmres", precision="mixed")
+    recd = torch.from_numpy(rec).cuda()
+    d = torch.stack([st_.solve(st_.rhs_point([p]))[0].reshape(-1)[recd] for p in w["sources"]]).contiguous()
+    st_.close()
+    s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov="fgmres", precision="mixed")
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    loss, grad, info = s.adjoint_grad(w["sources"], rec, d)
+    e1.record(st)
+    torch.cuda.synchronize()
+    res = {"adjoint_n192_8src_mixed": {"ms": e0.elapsed_time(e1), "loss": loss, "solves": 2 * len(w["sources"]),
+                                       "iterations_total": info["iterations"], "rel_residual_max": info["rel_residual"],
+                                       "grad_norm": float(grad.norm()), "unknowns": (192 + 1) ** 3}}
+    s.close()
+    del s, grad
+    torch.cuda.empty_cache()
+    return res
 
 
 def main():

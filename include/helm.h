@@ -169,6 +169,21 @@ HELM_API helm_status helm_rhs_point(helm_ctx* ctx, int nsrc, const int* nodes, v
 HELM_API helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_info* info,
                        void* stream);
 
+/* Solve A_h X_r = B_r for nrhs right-hand sides together (S9 of the build's hot path; the
+ * paper solves one source at a time).  The right-hand sides run through the same
+ * preconditioned flexible GMRES(m) in lockstep, in chunks of up to 32: grid vectors are
+ * stored node-major with the right-hand side innermost, so every stencil, transfer and
+ * V-cycle kernel reads k^2 once per node for the whole chunk and each warp loads one
+ * contiguous row of right-hand sides.  Each right-hand side keeps its own Hessenberg matrix,
+ * rotations and stopping test; a converged one is carried along unchanged.  The V-cycle
+ * runs in the context's precision (complex64 for HELM_PREC_MIXED, FP64 otherwise); the outer
+ * Krylov, Gram-Schmidt and residuals are FP64 (the context's orth setting does not apply).
+ *   B, X : device c128, nrhs consecutive grid vectors (X: initial guesses in, solutions out)
+ *   infos: optional host array of nrhs reports
+ * Waits for completion.  HELM_ENOCONV if any right-hand side missed tol within max_iter. */
+HELM_API helm_status helm_solve_batched(helm_ctx* ctx, int nrhs, const void* B, void* X, helm_solve_info* infos,
+                                        void* stream);
+
 /* Adjoint solve for frequency-domain gradients (the paper solves forward problems only;
  * the operator and boundary scheme are its Sec. 2.4).  Solves A^H lambda = g, where A^H is the
  * conjugate transpose of A_h, with the same preconditioned Krylov method as helm_solve: the

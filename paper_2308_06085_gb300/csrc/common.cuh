@@ -139,6 +139,10 @@ struct Grid {
   // the caller has none (the kernels then take the square root themselves)
   const double* sqk = nullptr;
   const float* sqkf = nullptr;
+  // right-hand sides per node: grid vectors hold nb values per node, right-hand side
+  // innermost (element index = node index * nb + rhs); per-node arrays (k^2, tables) stay
+  // one value per node
+  int nb = 1;
   __host__ __device__ size_t npts() const { return (size_t)N1 * N2 * N3; }
 };
 
@@ -208,6 +212,22 @@ __device__ __forceinline__ cx<R> omega_over(cx<R> d, R omega) {
   R inv = omega / fma(d.re, d.re, d.im * d.im);
   return mkc<R>(d.re * inv, -d.im * inv);
 }
+
+// Device control block of the batched Krylov loop (all pointers are device arrays; per
+// right-hand side r unless stated).
+struct BatchCtl {
+  int any;       // 1 while any right-hand side is active in the current cycle
+  int pass2;     // second Gram-Schmidt pass for the current step
+  int max_iter;  // #Matvec cap per right-hand side
+  int pad;
+  int *act, *jend, *flag, *jmax, *iters;
+  double *bnorm, *beta, *est;
+  cx<double>* H;   // nb x (m+1) x m
+  double* cs;      // nb x m
+  cx<double>* sn;  // nb x m
+  cx<double>* g;   // nb x (m+1)
+  cx<double>* y;   // m x nb
+};
 
 // Device control block for the Krylov loop: kernels of an Arnoldi step return at once
 // when `active` is 0, so the host can enqueue ahead without waiting.

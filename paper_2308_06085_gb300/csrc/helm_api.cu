@@ -84,6 +84,22 @@ struct Prof {
   int used = 0;
 };
 
+// Workspace of the batched solver for nb right-hand sides (allocated on first use, grown when a
+// wider batch is asked for).
+struct BatchWS {
+  int nb = 0;
+  z128 *V = nullptr, *Z64 = nullptr, *w = nullptr, *r = nullptr, *Bt = nullptr, *Xt = nullptr;
+  z64* Z32 = nullptr;
+  z128 *part = nullptr, *hpass = nullptr, *hacc = nullptr;
+  double *partr = nullptr, *hnorm = nullptr;
+  BatchCtl h;               // host copy of the device pointers
+  BatchCtl* ctl = nullptr;  // device
+  int* log = nullptr;
+  z128 *B64[MAX_LEVELS] = {}, *U164[MAX_LEVELS] = {}, *T64[MAX_LEVELS] = {}, *E64[MAX_LEVELS] = {};
+  z64 *B32[MAX_LEVELS] = {}, *U132[MAX_LEVELS] = {}, *T32[MAX_LEVELS] = {}, *E32[MAX_LEVELS] = {};
+  int* hany = nullptr;  // pinned, one slot per Arnoldi step
+};
+
 }  // namespace
 
 struct helm_ctx {
@@ -140,6 +156,7 @@ struct helm_ctx {
   double* adj_norm = nullptr;
   int* adj_rec = nullptr;
   int adj_rec_cap = 0;
+  BatchWS bw;
 };
 
 namespace {
@@ -326,47 +343,71 @@ bool invert_dense(int n, std::vector<std::complex<double>>& A) {
 }
 
 // One V-cycle z ~= M^{-1} r in working precision R (input type TI, output type TO).
+// Buffers and grid of one V-cycle level (single or batched right-hand sides).
+template <typename R>
+struct VLevel {
+  Grid g;
+  const R* k2;
+  const cx<R>* dinv;
+  cx<R> *B, *U1, *T, *E;
+};
+
+// One V-cycle z ~= M^{-1} r in working precision R (input type TI, output type TO) over the
+// levels lv[0..L); g.nb right-hand sides per node.
 template <typename R, typename TI, typename TO>
-void run_vcycle(helm_ctx* c, const cx<TI>* rin, cx<TO>* zout, cudaStream_t st, const int* active) {
-  using B = LevelBufs<R>;
+void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* rin, cx<TO>* zout, cudaStream_t st,
+                       const int* active) {
   const double sr = c->s_re, si = c->s_im, om = c->p.omega;
-  const int L = c->nlev;
-  const double cb = 2.0 * sizeof(R);               // bytes of one complex value
-  const double kb = sizeof(R), ib = 2.0 * sizeof(TI), ob = 2.0 * sizeof(TO);
-  const double db = std::is_same<R, double>::value ? 16.0 : 0.0;  // omega/d array (FP64 path)
+  const int nbv = lv[0].g.nb;
+  const double cb = 2.0 * sizeof(R) * nbv;  // bytes of one node's complex values
+  const double kb = sizeof(R), ib = 2.0 * sizeof(TI) * nbv, ob = 2.0 * sizeof(TO) * nbv;
+  const double db = lv[0].dinv ? 16.0 : 0.0;  // omega/d array (FP64 path)
   const double nc = c->nc;
   if (L == 1) {
-    KL(F_COARSE, nc * nc * 16 + nc * (ib + ob), 8 * nc * nc, (launch_coarse<TI, TO>(c->nc, c->Minv, rin, zout, st, active)));
+    KL(F_COARSE, nc * nc * 16 + nc * (ib + ob), 8 * nc * nc * nbv,
+       (launch_coarse<TI, TO>(c->nc, c->Minv, rin, zout, st, active, nbv)));
     return;
   }
   // down: pre-smooth from zero, residual, restriction
   for (int l = 0; l < L - 1; ++l) {
-    Level& F = c->L[l];
-    Level& C = c->L[l + 1];
+    const VLevel<R>& F = lv[l];
+    const VLevel<R>& C = lv[l + 1];
     const double n = (double)F.g.npts(), ncn = (double)C.g.npts();
     const double bi = l == 0 ? ib : cb;
     if (l == 0) {
-      KL(F_SMOOTH0, n * (bi + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, TI>(F.g, sr, si, om, B::k2(F), B::dinv(F), rin, B::U1(F), st, active)));
-      KL(F_RESID, n * (cb + bi + kb + cb), 24 * n, (launch_resid<R, R, TI, R>(F.g, sr, si, B::k2(F), B::U1(F), rin, B::T(F), st, active)));
+      KL(F_SMOOTH0, n * (bi + (db ? db : kb) + cb), 6 * n * nbv, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
+      KL(F_RESID, n * (cb + bi + kb + cb), 24 * n * nbv, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
     } else {
-      KL(F_SMOOTH0, n * (bi + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, R>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::B(F), B::U1(F), st, active)));
-      KL(F_RESID, n * (cb + bi + kb + cb), 24 * n, (launch_resid<R, R, R, R>(F.g, sr, si, B::k2(F), B::U1(F), B::B(F), B::T(F), st, active)));
+      KL(F_SMOOTH0, n * (bi + (db ? db : kb) + cb), 6 * n * nbv, (launch_smooth0<R, R>(F.g, sr, si, om, F.k2, F.dinv, F.B, F.U1, st, active)));
+      KL(F_RESID, n * (cb + bi + kb + cb), 24 * n * nbv, (launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.B, F.T, st, active)));
     }
-    KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, B::T(F), B::B(C), st, active)));
+    KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn * nbv, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
   }
   // coarsest: exact FP64 solve
-  KL(F_COARSE, nc * nc * 16 + nc * 2 * cb, 8 * nc * nc, (launch_coarse<R, R>(c->nc, c->Minv, B::B(c->L[L - 1]), B::E(c->L[L - 1]), st, active)));
+  KL(F_COARSE, nc * nc * 16 + nc * 2 * cb, 8 * nc * nc * nbv,
+     (launch_coarse<R, R>(c->nc, c->Minv, lv[L - 1].B, lv[L - 1].E, st, active, nbv)));
   // up: prolongation + correction, post-smoothing
   for (int l = L - 2; l >= 0; --l) {
-    Level& F = c->L[l];
-    Level& C = c->L[l + 1];
+    const VLevel<R>& F = lv[l];
+    const VLevel<R>& C = lv[l + 1];
     const double n = (double)F.g.npts(), ncn = (double)C.g.npts();
-    KL(F_PROLONG, n * 2 * cb + ncn * cb, 6 * n, (launch_prolong_add<R>(F.g, C.g, B::U1(F), B::E(C), B::T(F), st, active)));
+    KL(F_PROLONG, n * 2 * cb + ncn * cb, 6 * n * nbv, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
     if (l == 0)
-      KL(F_JACOBI, n * (cb + ib + kb + db + ob), 32 * n, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::T(F), rin, zout, st, active)));
+      KL(F_JACOBI, n * (cb + ib + kb + db + ob), 32 * n * nbv, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, rin, zout, st, active)));
     else
-      KL(F_JACOBI, n * (3 * cb + kb + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::T(F), B::B(F), B::E(F), st, active)));
+      KL(F_JACOBI, n * (3 * cb + kb + db), 32 * n * nbv, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.B, F.E, st, active)));
   }
+}
+
+template <typename R, typename TI, typename TO>
+void run_vcycle(helm_ctx* c, const cx<TI>* rin, cx<TO>* zout, cudaStream_t st, const int* active) {
+  using B = LevelBufs<R>;
+  VLevel<R> lv[MAX_LEVELS];
+  for (int l = 0; l < c->nlev; ++l) {
+    Level& L = c->L[l];
+    lv[l] = VLevel<R>{L.g, B::k2(L), B::dinv(L), B::B(L), B::U1(L), B::T(L), B::E(L)};
+  }
+  run_vcycle_levels<R, TI, TO>(c, lv, c->nlev, rin, zout, st, active);
 }
 
 void norm_into(helm_ctx* c, const z128* x, double* out, cudaStream_t st, const int* active) {
@@ -554,6 +595,160 @@ void stage_impl(helm_ctx* c, int l, int stage, const cx<R>* b, const cx<R>* e, c
 
 }  // namespace
 
+namespace {
+
+helm_status batch_alloc(helm_ctx* c, int nb) {
+  BatchWS& W = c->bw;
+  if (W.nb >= nb) return HELM_OK;
+  const size_t n = c->n0, ne = n * nb;
+  const int m = c->m;
+  const bool mixed = c->p.precision == HELM_PREC_MIXED;
+  TRY(dalloc(c, &W.V, (size_t)(m + 1) * ne));
+  if (mixed) TRY(dalloc(c, &W.Z32, (size_t)m * ne));
+  else TRY(dalloc(c, &W.Z64, (size_t)m * ne));
+  TRY(dalloc(c, &W.r, ne));
+  TRY(dalloc(c, &W.Bt, ne));
+  TRY(dalloc(c, &W.Xt, ne));
+  TRY(dalloc(c, &W.part, (size_t)(m + 2) * nb * RED_STRIDE));
+  TRY(dalloc(c, &W.partr, (size_t)nb * RED_STRIDE));
+  TRY(dalloc(c, &W.hpass, (size_t)(m + 1) * nb));
+  TRY(dalloc(c, &W.hacc, (size_t)(m + 1) * nb));
+  TRY(dalloc(c, &W.hnorm, nb));
+  TRY(dalloc(c, &W.log, m));
+  BatchCtl& h = W.h;
+  h.any = 0; h.pass2 = 0; h.max_iter = c->p.max_iter; h.pad = 0;
+  TRY(dalloc(c, &h.act, nb)); TRY(dalloc(c, &h.jend, nb)); TRY(dalloc(c, &h.flag, nb));
+  TRY(dalloc(c, &h.jmax, nb)); TRY(dalloc(c, &h.iters, nb));
+  TRY(dalloc(c, &h.bnorm, nb)); TRY(dalloc(c, &h.beta, nb)); TRY(dalloc(c, &h.est, nb));
+  TRY(dalloc(c, &h.H, (size_t)nb * (m + 1) * m));
+  TRY(dalloc(c, &h.cs, (size_t)nb * m));
+  TRY(dalloc(c, &h.sn, (size_t)nb * m));
+  TRY(dalloc(c, &h.g, (size_t)nb * (m + 1)));
+  TRY(dalloc(c, &h.y, (size_t)m * nb));
+  TRY(dalloc(c, &W.ctl, 1));
+  CU(cudaMemcpy(W.ctl, &h, sizeof(BatchCtl), cudaMemcpyHostToDevice));
+  for (int l = 0; l < c->nlev; ++l) {
+    const size_t np = c->L[l].g.npts() * nb;
+    if (mixed) {
+      TRY(dalloc(c, &W.U132[l], np)); TRY(dalloc(c, &W.T32[l], np));
+      if (l > 0) { TRY(dalloc(c, &W.B32[l], np)); TRY(dalloc(c, &W.E32[l], np)); }
+    } else {
+      TRY(dalloc(c, &W.U164[l], np)); TRY(dalloc(c, &W.T64[l], np));
+      if (l > 0) { TRY(dalloc(c, &W.B64[l], np)); TRY(dalloc(c, &W.E64[l], np)); }
+    }
+  }
+  if (!W.hany) CU(cudaHostAlloc((void**)&W.hany, sizeof(int) * (m + FLAG_LAG + 1), cudaHostAllocDefault));
+  W.nb = nb;
+  return HELM_OK;
+}
+
+template <typename R> VLevel<R> batch_level(helm_ctx* c, int l, int nb);
+template <>
+VLevel<float> batch_level<float>(helm_ctx* c, int l, int nb) {
+  Level& L = c->L[l];
+  VLevel<float> v{L.g, L.k2f, nullptr, c->bw.B32[l], c->bw.U132[l], c->bw.T32[l], c->bw.E32[l]};
+  v.g.nb = nb;
+  return v;
+}
+template <>
+VLevel<double> batch_level<double>(helm_ctx* c, int l, int nb) {
+  Level& L = c->L[l];
+  VLevel<double> v{L.g, L.k2, L.dinv, c->bw.B64[l], c->bw.U164[l], c->bw.T64[l], c->bw.E64[l]};
+  v.g.nb = nb;
+  return v;
+}
+
+// Lockstep FGMRES(m) for the nb right-hand sides held in bw.Bt / bw.Xt.
+helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
+  BatchWS& W = c->bw;
+  const size_t n = c->n0, ne = n * nb;
+  const int m = c->m;
+  const bool mixed = c->p.precision == HELM_PREC_MIXED;
+  const double tol = c->p.tol;
+  Grid g0 = c->L[0].g;
+  g0.nb = nb;
+  const double* k2 = c->L[0].k2;
+  BatchCtl* ctl = W.ctl;
+  const int* any = &ctl->any;
+  VLevel<float> lv32[MAX_LEVELS];
+  VLevel<double> lv64[MAX_LEVELS];
+  for (int l = 0; l < c->nlev; ++l) {
+    if (mixed) lv32[l] = batch_level<float>(c, l, nb);
+    else lv64[l] = batch_level<double>(c, l, nb);
+  }
+  const double nd = (double)ne;
+  int nblk = launch_bnorm2_part(W.Bt, ne, nb, W.partr, st, c->one);
+  launch_breduce_norm(W.partr, nb, nblk, W.h.bnorm, st, c->one);
+  KL(F_RESID, 56.0 * nd, 24.0 * nd, (launch_resid<double, double, double, double>(g0, 1.0, 0.0, k2, W.Xt, W.Bt, W.r, st, c->one)));
+  nblk = launch_bnorm2_part(W.r, ne, nb, W.partr, st, c->one);
+  launch_breduce_norm(W.partr, nb, nblk, W.h.beta, st, c->one);
+  CU(cudaMemsetAsync(W.h.iters, 0, sizeof(int) * nb, st));
+  for (int cycle = 0;; ++cycle) {
+    launch_bcycle_init(ctl, nb, m, tol, st);
+    CU(cudaMemcpyAsync(W.hany, any, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (W.hany[0] == 0) break;
+    KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_bscale_inv(W.r, W.h.beta, W.V, ne, nb, st, any));
+    for (int j = 0; j < m; ++j) {
+      z128* vj = W.V + (size_t)j * ne;
+      z128* w = W.V + (size_t)(j + 1) * ne;
+      const double nv = j + 1;
+      c->cur_j = j;
+      if (mixed) {
+        z64* zj = W.Z32 + (size_t)j * ne;
+        run_vcycle_levels<float, double, float>(c, lv32, c->nlev, vj, zj, st, any);
+        KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply<double, float, double>(g0, 1.0, 0.0, k2, zj, w, st, any)));
+      } else {
+        z128* zj = W.Z64 + (size_t)j * ne;
+        run_vcycle_levels<double, double, double>(c, lv64, c->nlev, vj, zj, st, any);
+        KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(g0, 1.0, 0.0, k2, zj, w, st, any)));
+      }
+      const bool sel = c->p.reorth == HELM_REORTH_SELECTIVE;
+      for (int pass = 0; pass < 2; ++pass) {
+        const int* a2 = (pass == 1 && sel) ? &ctl->pass2 : any;
+        c->cur_cond = (pass == 1 && sel) ? 1 : 0;
+        const int wn = (pass == 0 && sel) ? 1 : 0;
+        int nbk = 0;
+        KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nbk = launch_bmdot(W.V, ne, j + 1, w, ne, nb, W.part, wn, st, a2));
+        KL(F_REDUCE_DOTS, 16.0 * nv * nb * nbk, 2.0 * nv * nb * nbk,
+           launch_breduce_dots(W.part, j + 1, nb, nbk, W.hpass, W.hacc, pass, wn ? j : -1, W.h.act, &ctl->pass2,
+                               c->reorth_log, st, a2));
+        KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_bgs_update(W.V, ne, j + 1, nb, W.hpass, w, ne, st, a2));
+      }
+      c->cur_cond = 0;
+      int nbn = 0;
+      KL(F_NORM, 16.0 * nd, 4.0 * nd, nbn = launch_bnorm2_part(w, ne, nb, W.partr, st, any));
+      KL(F_REDUCE_NORM, 8.0 * nb * nbn, nb * nbn, launch_breduce_norm(W.partr, nb, nbn, W.hnorm, st, any));
+      KL(F_GIVENS, 0, 0, launch_bgivens(ctl, nb, m, j, W.hacc, W.hnorm, tol, st));
+      KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_bscale_inv(w, W.hnorm, w, ne, nb, st, any));
+      TRY(check_launch(c, "batched Arnoldi step"));
+      CU(cudaMemcpyAsync(W.hany + j, any, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CU(cudaEventRecord(c->ev[j % c->nev], st));
+      if (j >= FLAG_LAG) {
+        CU(cudaEventSynchronize(c->ev[(j - FLAG_LAG) % c->nev]));
+        if (W.hany[j - FLAG_LAG] == 0) break;
+      }
+    }
+    c->cur_j = -1;
+    CU(cudaMemcpyAsync(c->hreorth_log, c->reorth_log, sizeof(int) * m, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    prof_flush(c, m);
+    KL(F_SOLUPDATE, 0, 0, launch_btrisolve(ctl, nb, m, st));
+    if (mixed)
+      KL(F_SOLUPDATE, 8.0 * m * nd, 8.0 * m * nd, launch_bxupdate<float>(ctl, nb, m, W.Z32, ne, W.Xt, ne, st));
+    else
+      KL(F_SOLUPDATE, 16.0 * m * nd, 8.0 * m * nd, launch_bxupdate<double>(ctl, nb, m, W.Z64, ne, W.Xt, ne, st));
+    KL(F_RESID, 56.0 * nd, 24.0 * nd, (launch_resid<double, double, double, double>(g0, 1.0, 0.0, k2, W.Xt, W.Bt, W.r, st, c->one)));
+    nblk = launch_bnorm2_part(W.r, ne, nb, W.partr, st, c->one);
+    launch_breduce_norm(W.partr, nb, nblk, W.h.beta, st, c->one);
+    TRY(check_launch(c, "batched solution update"));
+    prof_flush(c, -1);
+  }
+  return HELM_OK;
+}
+
+}  // namespace
+
 // Message slot of helm_last_error(NULL), shared with the context-free entry point.
 void helm_set_global_error(const char* msg) { g_create_error = msg; }
 
@@ -612,6 +807,7 @@ helm_status helm_destroy(helm_ctx* ctx) {
   if (ctx->hflags) cudaFreeHost(ctx->hflags);
   if (ctx->hctl) cudaFreeHost(ctx->hctl);
   if (ctx->hreorth_log) cudaFreeHost(ctx->hreorth_log);
+  if (ctx->bw.hany) cudaFreeHost(ctx->bw.hany);
   for (int i = 0; i < ctx->nev; ++i) cudaEventDestroy(ctx->ev[i]);
   delete ctx;
   return HELM_OK;
@@ -968,6 +1164,53 @@ helm_status helm_adjoint_grad(helm_ctx* c, int nsrc, const int* src_nodes, int n
     info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   if (worst == HELM_ENOCONV) fail(c, worst, "a forward or adjoint solve reached max_iter");
+  return worst;
+}
+
+helm_status helm_solve_batched(helm_ctx* c, int nrhs, const void* B, void* X, helm_solve_info* infos, void* stream) {
+  if (!c) return HELM_EINVAL;
+  if (nrhs < 1 || !B || !X || B == X) return fail(c, HELM_EINVAL, "bad nrhs or NULL / aliased B, X");
+  if (!is_device_ptr(B) || !is_device_ptr(X)) return fail(c, HELM_EINVAL, "B and X must be device pointers");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = c->n0;
+  helm_status worst = HELM_OK;
+  for (int start = 0; start < nrhs; start += 32) {
+    const int cnt = std::min(32, nrhs - start);
+    int nb = 1;
+    while (nb < cnt) nb <<= 1;
+    TRY(batch_alloc(c, nb));
+    BatchWS& W = c->bw;
+    launch_to_batch((const z128*)B + (size_t)start * n, W.Bt, n, nb, cnt, st);
+    launch_to_batch((const z128*)X + (size_t)start * n, W.Xt, n, nb, cnt, st);
+    TRY(check_launch(c, "batch transpose"));
+    TRY(gmres_batched(c, nb, st));
+    launch_from_batch(W.Xt, (z128*)X + (size_t)start * n, n, nb, cnt, st);
+    std::vector<int> it(nb);
+    std::vector<double> bn(nb), be(nb);
+    CU(cudaMemcpyAsync(it.data(), W.h.iters, sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(bn.data(), W.h.bnorm, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(be.data(), W.h.beta, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int r = 0; r < cnt; ++r) {
+      const double rr = bn[r] > 0.0 ? be[r] / bn[r] : 0.0;
+      helm_status sr = HELM_OK;
+      if (!(rr == rr) || rr == HUGE_VAL) sr = HELM_ENUMERIC;
+      else if (rr > c->p.tol) sr = HELM_ENOCONV;
+      if (sr != HELM_OK && worst != HELM_ENUMERIC) worst = sr;
+      if (infos) {
+        helm_solve_info& I = infos[start + r];
+        I.iterations = it[r];
+        I.restarts = 0;
+        I.rel_residual = rr;
+        I.status = (int)sr;
+        I.ms_total = ms;
+      }
+    }
+  }
+  if (worst == HELM_ENOCONV) fail(c, worst, "some right-hand sides reached max_iter (%d)", c->p.max_iter);
+  if (worst == HELM_ENUMERIC) fail(c, worst, "non-finite residual in a batched solve");
   return worst;
 }
 

@@ -28,8 +28,10 @@ void launch_restrict(const Grid& gf, const Grid& gc, const cx<R>* r, cx<R>* out,
 template <typename R>
 void launch_prolong_add(const Grid& gf, const Grid& gc, const cx<R>* u1, const cx<R>* e, cx<R>* out, cudaStream_t st,
                         const int* active);
+// e = Minv b for nb right-hand sides (node-major, right-hand side innermost)
 template <typename TI, typename TO>
-void launch_coarse(int nc, const z128* Minv, const cx<TI>* b, cx<TO>* e, cudaStream_t st, const int* active);
+void launch_coarse(int nc, const z128* Minv, const cx<TI>* b, cx<TO>* e, cudaStream_t st, const int* active,
+                   int nb = 1);
 void launch_dinv(const Grid& g, double s_re, double s_im, double omega, const double* k2, z128* out, cudaStream_t st);
 void launch_inject(const Grid& gf, const Grid& gc, const double* kf, double* kc, cudaStream_t st);
 void launch_to_float(const double* a, float* b, size_t n, cudaStream_t st);
@@ -94,6 +96,27 @@ void launch_c64_to_c128(const z64* a, z128* b, size_t n, cudaStream_t st);
 void launch_set_active(KrylovCtl* ctl, int v, cudaStream_t st);
 // x += z
 void launch_axpy1(const z128* z, z128* x, size_t n, cudaStream_t st);
+
+// ---- batched FGMRES kernels (krylov_batched.cu); vectors node-major, rhs innermost ----
+int launch_bnorm2_part(const z128* x, size_t ne, int nb, double* part, cudaStream_t st, const int* active);
+void launch_breduce_norm(const double* part, int nb, int nblk, double* out, cudaStream_t st, const int* active);
+int launch_bmdot(const z128* V, size_t ld, int nv, const z128* w, size_t ne, int nb, z128* part, int with_norm,
+                 cudaStream_t st, const int* active);
+void launch_breduce_dots(const z128* part, int nv, int nb, int nblk, z128* hpass, z128* hacc, int accumulate,
+                         int decide_j, const int* act, int* pass2, int* log, cudaStream_t st, const int* active);
+void launch_bgs_update(const z128* V, size_t ld, int nv, int nb, const z128* h, z128* w, size_t ne, cudaStream_t st,
+                       const int* active);
+void launch_bscale_inv(const z128* in, const double* s, z128* out, size_t ne, int nb, cudaStream_t st,
+                       const int* active);
+void launch_bcycle_init(BatchCtl* bc, int nb, int m, double tol, cudaStream_t st);
+void launch_bgivens(BatchCtl* bc, int nb, int m, int j, const z128* hcol, const double* hnorm, double tol,
+                    cudaStream_t st);
+void launch_btrisolve(BatchCtl* bc, int nb, int m, cudaStream_t st);
+template <typename TZ>
+void launch_bxupdate(const BatchCtl* bc, int nb, int m, const cx<TZ>* Z, size_t ld, z128* x, size_t ne,
+                     cudaStream_t st);
+void launch_to_batch(const z128* src, z128* dst, size_t n, int nb, int nrhs, cudaStream_t st);
+void launch_from_batch(const z128* src, z128* dst, size_t n, int nb, int nrhs, cudaStream_t st);
 
 // ---- adjoint-state gradient (adjoint.cu) ----
 // q = D^-1 conj(in), D = diag(2^-faces) (Sommerfeld) or I (Dirichlet)

@@ -1,0 +1,448 @@
+// krylov_batched.cu -- FP64 kernels of right-preconditioned FGMRES(m) for nb right-hand sides
+// solved together (nb a power of two <= 32).  Grid vectors are node-major with the right-hand
+// side innermost (element e = node * nb + rhs), so a warp reads nb right-hand sides of 32/nb
+// nodes in one coalesced row.  Every right-hand side keeps its own Hessenberg matrix, Givens
+// rotations, residual estimate and stopping flag; the Arnoldi steps run in lockstep and a
+// right-hand side that has stopped is carried along but no longer updated.
+//
+// A lane always works on the same right-hand side (thread strides are multiples of nb), so
+// per-right-hand-side sums reduce across lanes of equal (lane mod nb) with shuffles at offsets
+// >= nb, then across warps and blocks in a fixed order (deterministic).
+#include "internal.cuh"
+
+namespace helm {
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int NW = NT / 32;
+constexpr int KS = 4;        // basis vectors per warp per pass
+constexpr int TILE = 1024;   // elements of w staged per shared-memory tile
+
+__device__ __forceinline__ void block_range_e(size_t ne, int nb, size_t& e0, size_t& e1) {
+  // chunk per block, a multiple of the tile and of nb
+  size_t chunk = (ne + gridDim.x - 1) / gridDim.x;
+  chunk = (chunk + TILE - 1) / TILE * TILE;
+  e0 = blockIdx.x * chunk;
+  e1 = e0 + chunk < ne ? e0 + chunk : ne;
+  if (e0 > ne) e0 = ne;
+  (void)nb;
+}
+
+// reduce across lanes with equal lane mod nb
+__device__ __forceinline__ double lane_group_sum(double v, int nb) {
+  for (int o = 16; o >= nb; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// |x_r|^2 partials: part[r * RED_STRIDE + blk]
+__global__ void __launch_bounds__(NT)
+    k_bnorm2_part(const z128* __restrict__ x, size_t ne, int nb, double* __restrict__ part, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ double sred[NW][32];
+  size_t e0, e1;
+  block_range_e(ne, nb, e0, e1);
+  double s = 0.0;
+  for (size_t e = e0 + threadIdx.x; e < e1; e += NT) {
+    const z128 v = ldg(x + e);
+    s = fma(v.re, v.re, s);
+    s = fma(v.im, v.im, s);
+  }
+  s = lane_group_sum(s, nb);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane < nb) sred[warp][lane] = s;
+  __syncthreads();
+  if ((int)threadIdx.x < nb) {
+    double t = 0.0;
+    for (int w = 0; w < NW; ++w) t += sred[w][threadIdx.x];
+    part[(size_t)threadIdx.x * RED_STRIDE + blockIdx.x] = t;
+  }
+}
+
+// out[r] = sqrt(sum_b part[r][b]), one warp per right-hand side
+__global__ void __launch_bounds__(NT)
+    k_breduce_norm(const double* __restrict__ part, int nb, int nblk, double* __restrict__ out, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < nb; r += NW) {
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += part[(size_t)r * RED_STRIDE + b];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[r] = sqrt(s);
+  }
+}
+
+// Inner products conj(V_i) . w per right-hand side; slot nv holds |w_r|^2 when with_norm.
+__global__ void __launch_bounds__(NT)
+    k_bmdot(const z128* __restrict__ V, size_t ld, int nv, const z128* __restrict__ w, size_t ne, int nb,
+            z128* __restrict__ part, int with_norm, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ z128 sw[TILE];
+  __shared__ double sred[NW][32][2];
+  size_t e0, e1;
+  block_range_e(ne, nb, e0, e1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nslot = nv + (with_norm ? 1 : 0);
+  const int wps = nslot >= NW ? 1 : NW / nslot;
+  const int sub = warp % wps, sfirst = warp / wps, sstep = NW / wps;
+  double* partd = reinterpret_cast<double*>(part);
+  for (int sbase = 0; sbase * sstep < nslot; sbase += KS) {
+    double re[KS], im[KS];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) re[k] = im[k] = 0.0;
+    for (size_t t0 = e0; t0 < e1; t0 += TILE) {
+      const int tn = (int)min((size_t)TILE, e1 - t0);
+      __syncthreads();
+      for (int q = threadIdx.x; q < tn; q += NT) sw[q] = ldg(w + t0 + q);
+      __syncthreads();
+      for (int q = sub * 32 + lane; q < tn; q += 32 * wps) {
+        const z128 wv = sw[q];
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+          const int sl = sfirst + (sbase + k) * sstep;
+          if (sl < nv) {
+            cdot_acc(ldg(V + (size_t)sl * ld + t0 + q), wv, re[k], im[k]);
+          } else if (sl == nv && with_norm) {
+            re[k] = fma(wv.re, wv.re, re[k]);
+            re[k] = fma(wv.im, wv.im, re[k]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int sl = sfirst + (sbase + k) * sstep;
+      const double r = lane_group_sum(re[k], nb), i = lane_group_sum(im[k], nb);
+      __syncthreads();
+      if (lane < nb) {
+        sred[warp][lane][0] = r;
+        sred[warp][lane][1] = i;
+      }
+      __syncthreads();
+      if (sub == 0 && lane < nb && sl < nslot) {
+        double tr = 0.0, ti = 0.0;
+        for (int u = 0; u < wps; ++u) {
+          tr += sred[warp + u][lane][0];
+          ti += sred[warp + u][lane][1];
+        }
+        const size_t row = (size_t)sl * nb + lane;
+        partd[2 * (row * RED_STRIDE + blockIdx.x)] = tr;
+        partd[2 * (row * RED_STRIDE + blockIdx.x) + 1] = sl == nv ? 0.0 : ti;
+      }
+    }
+  }
+}
+
+// hpass[i * nb + r] = sum of the partials of (slot i, rhs r); hacc stores or accumulates.
+// decide_j >= 0: a second Gram-Schmidt pass is taken when, for any active right-hand side,
+// the projection removed more than half of |w_r|^2.
+__global__ void __launch_bounds__(NT)
+    k_breduce_dots(const z128* __restrict__ part, int nv, int nb, int nblk, z128* __restrict__ hpass,
+                   z128* __restrict__ hacc, int accumulate, int decide_j, const int* __restrict__ act,
+                   int* __restrict__ pass2, int* __restrict__ log, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ double sw2[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rows = (decide_j >= 0 ? nv + 1 : nv) * nb;
+  for (int row = warp; row < rows; row += NW) {
+    double re = 0.0, im = 0.0;
+    for (int b = lane; b < nblk; b += 32) {
+      const z128 v = part[(size_t)row * RED_STRIDE + b];
+      re += v.re;
+      im += v.im;
+    }
+    for (int o = 16; o; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+      if (row >= nv * nb) {
+        sw2[row - nv * nb] = re;
+      } else {
+        hpass[row] = mkc<double>(re, im);
+        if (accumulate) {
+          hacc[row].re += re;
+          hacc[row].im += im;
+        } else {
+          hacc[row] = mkc<double>(re, im);
+        }
+      }
+    }
+  }
+  if (decide_j < 0) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int again = 0;
+    for (int r = 0; r < nb; ++r) {
+      if (!act[r]) continue;
+      double h2 = 0.0;
+      for (int i = 0; i < nv; ++i) h2 += hpass[i * nb + r].re * hpass[i * nb + r].re + hpass[i * nb + r].im * hpass[i * nb + r].im;
+      again |= !(sw2[r] - h2 >= 0.5 * sw2[r]);
+    }
+    *pass2 = again;
+    log[decide_j] = again;
+  }
+}
+
+// w[e] -= sum_i h[i][r] V_i[e]
+__global__ void __launch_bounds__(NT)
+    k_bgs_update(const z128* __restrict__ V, size_t ld, int nv, int nb, const z128* __restrict__ h, z128* __restrict__ w,
+                 size_t ne, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  extern __shared__ z128 shb[];
+  for (int i = threadIdx.x; i < nv * nb; i += NT) shb[i] = h[i];
+  __syncthreads();
+  const size_t stride = (size_t)gridDim.x * NT;
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
+    const int r = (int)(e % nb);
+    z128 acc = w[e];
+    for (int i = 0; i < nv; ++i) {
+      const z128 v = ldg(V + (size_t)i * ld + e);
+      const z128 c = shb[i * nb + r];
+      acc.re = fma(-c.re, v.re, acc.re);
+      acc.re = fma(c.im, v.im, acc.re);
+      acc.im = fma(-c.re, v.im, acc.im);
+      acc.im = fma(-c.im, v.re, acc.im);
+    }
+    w[e] = acc;
+  }
+}
+
+// out[e] = in[e] / s[r] where s[r] > 0, else 0
+__global__ void __launch_bounds__(NT)
+    k_bscale_inv(const z128* __restrict__ in, const double* __restrict__ s, z128* __restrict__ out, size_t ne, int nb,
+                 const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const size_t stride = (size_t)gridDim.x * NT;
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
+    const double d = s[e % nb];
+    const z128 v = in[e];
+    out[e] = d > 0.0 ? mkc<double>(v.re / d, v.im / d) : mkc<double>(0.0, 0.0);
+  }
+}
+
+// Start a restart cycle: right-hand side r is active when its residual is above tol and it
+// has Arnoldi steps left; g_r = (beta_r, 0, ...).
+__global__ void k_bcycle_init(BatchCtl* bc, int nb, int m, double tol) {
+  const int r = threadIdx.x;
+  __shared__ int any;
+  if (r == 0) any = 0;
+  __syncthreads();
+  if (r < nb) {
+    const int a = bc->bnorm[r] > 0.0 && bc->beta[r] > tol * bc->bnorm[r] && bc->iters[r] < bc->max_iter &&
+                  isfinite(bc->beta[r]);
+    bc->act[r] = a;
+    bc->jend[r] = -1;
+    bc->flag[r] = 0;
+    bc->jmax[r] = min(m, bc->max_iter - bc->iters[r]);
+    for (int i = 0; i <= m; ++i) bc->g[(size_t)r * (m + 1) + i] = mkc<double>(i == 0 ? bc->beta[r] : 0.0, 0.0);
+    if (a) atomicOr(&any, 1);
+  }
+  __syncthreads();
+  if (r == 0) {
+    bc->any = any;
+    bc->pass2 = 0;
+  }
+}
+
+// Arnoldi step j, Givens rotations per right-hand side (one thread each), as in the
+// single-right-hand-side kernel.
+__global__ void k_bgivens(BatchCtl* bc, int nb, int m, int j, const z128* __restrict__ hcol, const double* __restrict__ hnorm,
+                          double tol) {
+  const int r = threadIdx.x;
+  __shared__ int any;
+  if (r == 0) any = 0;
+  __syncthreads();
+  if (r < nb && bc->act[r]) {
+    z128* H = bc->H + (size_t)r * (m + 1) * m;
+    double* cs = bc->cs + (size_t)r * m;
+    z128* sn = bc->sn + (size_t)r * m;
+    z128* g = bc->g + (size_t)r * (m + 1);
+    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i * nb + r];
+    const double hn = hnorm[r];
+    H[(size_t)(j + 1) * m + j] = mkc<double>(hn, 0.0);
+    for (int i = 0; i < j; ++i) {
+      const z128 a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+      const double c = cs[i];
+      const z128 s = sn[i];
+      const z128 sb = cmul(s, b);
+      const z128 t = cmul(mkc<double>(-s.re, s.im), a);
+      H[(size_t)i * m + j] = mkc<double>(c * a.re + sb.re, c * a.im + sb.im);
+      H[(size_t)(i + 1) * m + j] = mkc<double>(t.re + c * b.re, t.im + c * b.im);
+    }
+    const z128 a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
+    const double na = hypot(a.re, a.im), nbv = hypot(b.re, b.im);
+    const double t = hypot(na, nbv);
+    double c;
+    z128 s;
+    if (na == 0.0) {
+      c = 0.0;
+      s = mkc<double>(1.0, 0.0);
+      H[(size_t)j * m + j] = b;
+    } else {
+      const z128 ph = mkc<double>(a.re / na, a.im / na);
+      c = na / t;
+      s = cmul(ph, mkc<double>(b.re / t, -b.im / t));
+      H[(size_t)j * m + j] = mkc<double>(ph.re * t, ph.im * t);
+    }
+    H[(size_t)(j + 1) * m + j] = mkc<double>(0.0, 0.0);
+    cs[j] = c;
+    sn[j] = s;
+    const z128 gj = g[j];
+    g[j + 1] = cmul(mkc<double>(-s.re, s.im), gj);
+    g[j] = mkc<double>(c * gj.re, c * gj.im);
+    const double est = hypot(g[j + 1].re, g[j + 1].im) / bc->bnorm[r];
+    bc->est[r] = est;
+    bc->jend[r] = j;
+    if (!isfinite(est) || !isfinite(hn)) {
+      bc->flag[r] = 2;
+      bc->act[r] = 0;
+    } else if (est <= tol) {
+      bc->flag[r] = 1;
+      bc->act[r] = 0;
+    } else if (j + 1 >= bc->jmax[r]) {
+      bc->act[r] = 0;
+    }
+    if (bc->act[r]) atomicOr(&any, 1);
+  }
+  __syncthreads();
+  if (r == 0) {
+    bc->any = any;
+    if (!any) bc->pass2 = 0;
+  }
+}
+
+// y_r = H_r(0:k, 0:k)^{-1} g_r with k = jend_r + 1 (one thread per right-hand side)
+__global__ void k_btrisolve(BatchCtl* bc, int nb, int m) {
+  const int r = threadIdx.x;
+  if (r >= nb) return;
+  const int k = bc->jend[r] + 1;
+  bc->iters[r] += k;
+  const z128* H = bc->H + (size_t)r * (m + 1) * m;
+  const z128* g = bc->g + (size_t)r * (m + 1);
+  z128* y = bc->y;  // y[i * nb + r]
+  for (int i = k - 1; i >= 0; --i) {
+    z128 s = g[i];
+    for (int q = i + 1; q < k; ++q) {
+      const z128 hy = cmul(H[(size_t)i * m + q], y[q * nb + r]);
+      s.re -= hy.re;
+      s.im -= hy.im;
+    }
+    const z128 d = H[(size_t)i * m + i];
+    const double dd = d.re * d.re + d.im * d.im;
+    y[i * nb + r] = mkc<double>((s.re * d.re + s.im * d.im) / dd, (s.im * d.re - s.re * d.im) / dd);
+  }
+}
+
+// x[e] += sum_{i <= jend_r} y[i][r] Z_i[e]
+template <typename TZ>
+__global__ void __launch_bounds__(NT)
+    k_bxupdate(const BatchCtl* __restrict__ bc, int nb, int m, const cx<TZ>* __restrict__ Z, size_t ld, z128* __restrict__ x,
+               size_t ne) {
+  extern __shared__ z128 sy[];
+  __shared__ int kr[32];
+  __shared__ int kmax;
+  if (threadIdx.x < (unsigned)nb) kr[threadIdx.x] = bc->jend[threadIdx.x] + 1;
+  for (int i = threadIdx.x; i < m * nb; i += NT) sy[i] = bc->y[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int mx = 0;
+    for (int r = 0; r < nb; ++r) mx = max(mx, kr[r]);
+    kmax = mx;
+  }
+  __syncthreads();
+  const size_t stride = (size_t)gridDim.x * NT;
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
+    const int r = (int)(e % nb);
+    const int k = kr[r];
+    z128 acc = x[e];
+    for (int i = 0; i < kmax; ++i)
+      if (i < k) acc = cfma(sy[i * nb + r], cvt<double>(ldg(Z + (size_t)i * ld + e)), acc);
+    x[e] = acc;
+  }
+}
+
+// [rhs][node] <-> [node][rhs] (nb slots; right-hand sides r >= nrhs are zero on the way in)
+__global__ void k_to_batch(const z128* __restrict__ src, z128* __restrict__ dst, size_t n, int nb, int nrhs) {
+  const size_t ne = n * nb;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ne; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = e / nb;
+    const int r = (int)(e - p * nb);
+    dst[e] = r < nrhs ? src[(size_t)r * n + p] : mkc<double>(0.0, 0.0);
+  }
+}
+__global__ void k_from_batch(const z128* __restrict__ src, z128* __restrict__ dst, size_t n, int nb, int nrhs) {
+  const size_t ne = n * nrhs;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < ne; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = t / n, p = t - r * n;
+    dst[t] = src[p * nb + r];
+  }
+}
+
+template <typename K>
+int wave_blocks(K kern, int smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, smem);
+  const int nb = sms * (per > 0 ? per : 1);
+  return nb < RED_STRIDE ? nb : RED_STRIDE;
+}
+
+int stream_blocks(size_t n) {
+  size_t b = (n + NT - 1) / NT;
+  const size_t cap = 152 * 8;
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+}  // namespace
+
+int launch_bnorm2_part(const z128* x, size_t ne, int nb, double* part, cudaStream_t st, const int* active) {
+  static const int nblk = wave_blocks(k_bnorm2_part, 0);
+  k_bnorm2_part<<<nblk, NT, 0, st>>>(x, ne, nb, part, active);
+  return nblk;
+}
+void launch_breduce_norm(const double* part, int nb, int nblk, double* out, cudaStream_t st, const int* active) {
+  k_breduce_norm<<<1, NT, 0, st>>>(part, nb, nblk, out, active);
+}
+int launch_bmdot(const z128* V, size_t ld, int nv, const z128* w, size_t ne, int nb, z128* part, int with_norm,
+                 cudaStream_t st, const int* active) {
+  static const int nblk = wave_blocks(k_bmdot, 0);
+  k_bmdot<<<nblk, NT, 0, st>>>(V, ld, nv, w, ne, nb, part, with_norm, active);
+  return nblk;
+}
+void launch_breduce_dots(const z128* part, int nv, int nb, int nblk, z128* hpass, z128* hacc, int accumulate,
+                         int decide_j, const int* act, int* pass2, int* log, cudaStream_t st, const int* active) {
+  k_breduce_dots<<<1, NT, 0, st>>>(part, nv, nb, nblk, hpass, hacc, accumulate, decide_j, act, pass2, log, active);
+}
+void launch_bgs_update(const z128* V, size_t ld, int nv, int nb, const z128* h, z128* w, size_t ne, cudaStream_t st,
+                       const int* active) {
+  k_bgs_update<<<stream_blocks(ne), NT, sizeof(z128) * nv * nb, st>>>(V, ld, nv, nb, h, w, ne, active);
+}
+void launch_bscale_inv(const z128* in, const double* s, z128* out, size_t ne, int nb, cudaStream_t st,
+                       const int* active) {
+  k_bscale_inv<<<stream_blocks(ne), NT, 0, st>>>(in, s, out, ne, nb, active);
+}
+void launch_bcycle_init(BatchCtl* bc, int nb, int m, double tol, cudaStream_t st) {
+  k_bcycle_init<<<1, 32, 0, st>>>(bc, nb, m, tol);
+}
+void launch_bgivens(BatchCtl* bc, int nb, int m, int j, const z128* hcol, const double* hnorm, double tol,
+                    cudaStream_t st) {
+  k_bgivens<<<1, 32, 0, st>>>(bc, nb, m, j, hcol, hnorm, tol);
+}
+void launch_btrisolve(BatchCtl* bc, int nb, int m, cudaStream_t st) { k_btrisolve<<<1, 32, 0, st>>>(bc, nb, m); }
+template <typename TZ>
+void launch_bxupdate(const BatchCtl* bc, int nb, int m, const cx<TZ>* Z, size_t ld, z128* x, size_t ne,
+                     cudaStream_t st) {
+  k_bxupdate<TZ><<<stream_blocks(ne), NT, sizeof(z128) * m * nb, st>>>(bc, nb, m, Z, ld, x, ne);
+}
+template void launch_bxupdate<double>(const BatchCtl*, int, int, const z128*, size_t, z128*, size_t, cudaStream_t);
+template void launch_bxupdate<float>(const BatchCtl*, int, int, const z64*, size_t, z128*, size_t, cudaStream_t);
+void launch_to_batch(const z128* src, z128* dst, size_t n, int nb, int nrhs, cudaStream_t st) {
+  k_to_batch<<<stream_blocks(n * nb), NT, 0, st>>>(src, dst, n, nb, nrhs);
+}
+void launch_from_batch(const z128* src, z128* dst, size_t n, int nb, int nrhs, cudaStream_t st) {
+  k_from_batch<<<stream_blocks(n * nrhs), NT, 0, st>>>(src, dst, n, nb, nrhs);
+}
+
+}  // namespace helm

@@ -25,31 +25,37 @@ __device__ __forceinline__ cx<T> zero_c() {
 //   JACOBI : out = u + (omega / d) (b - Op u)
 // with Op = -Lap_h - s k^2 (s in OpCoef).  DINV: read omega/d from a precomputed array
 // (FP64 path, where a complex division costs more than the 16-byte read) instead of
-// computing it.
+// computing it.  With g.nb right-hand sides per node, a thread owns one (node column, rhs)
+// pair; for nb = 32 a warp covers the 32 right-hand sides of one node with one 256-byte
+// (complex64) row and reads k^2 once.
 template <typename R, int MODE, bool DINV, typename TU, typename TB, typename TO, bool SPLIT = false>
 __global__ void __launch_bounds__(TX* TY)
     k_stencil(Grid g, OpCoef<R> c, const R* __restrict__ k2, const cx<R>* __restrict__ dinv,
               const cx<TU>* __restrict__ u, const cx<TB>* __restrict__ b, cx<TO>* __restrict__ out,
               int zchunk, const int* __restrict__ active) {
   if (active && *active == 0) return;
-  const int i = blockIdx.x * TX + threadIdx.x;
+  const int nb = g.nb;
+  const int f = blockIdx.x * TX + threadIdx.x;
+  const int i = f / nb, r = f - (f / nb) * nb;
   const int j = blockIdx.y * TY + threadIdx.y;
   if (i >= g.N1 || j >= g.N2) return;
   const int k0 = blockIdx.z * zchunk;
   if (k0 >= g.N3) return;
   const int k1 = min(k0 + zchunk, g.N3);
   const bool som = g.bc == 1;
-  const size_t S = (size_t)g.N1 * g.N2;
-  const long N1 = g.N1;
+  const size_t S = (size_t)g.N1 * g.N2;  // nodes per plane
+  const size_t Se = S * nb;              // elements per plane
+  const long Xe = nb, Ye = (long)g.N1 * nb;
   const bool hxm = i > 0, hxp = i < g.N1 - 1, hym = j > 0, hyp = j < g.N2 - 1;
   const int nfxy = som ? (!hxm) + (!hxp) + (!hym) + (!hyp) : 0;
   auto ld = [&](size_t q) { return cvt<R>(ldg(u + q)); };
-  size_t p = gidx(i, j, k0, g.N1, g.N2);
-  cx<R> uc = ld(p);
-  cx<R> um = (k0 > 0) ? ld(p - S) : zero_c<R>();
-  for (int k = k0; k < k1; ++k, p += S) {
+  size_t p = gidx(i, j, k0, g.N1, g.N2);  // node index
+  size_t e = p * nb + r;                  // element index
+  cx<R> uc = ld(e);
+  cx<R> um = (k0 > 0) ? ld(e - Se) : zero_c<R>();
+  for (int k = k0; k < k1; ++k, p += S, e += Se) {
     const bool hzp = k + 1 < g.N3;
-    cx<R> up = hzp ? ld(p + S) : zero_c<R>();
+    cx<R> up = hzp ? ld(e + Se) : zero_c<R>();
     int nf = nfxy;
     cx<R> zm, zp;
     if (k > 0) zm = um;
@@ -58,25 +64,25 @@ __global__ void __launch_bounds__(TX* TY)
     if (hzp) zp = up;
     else if (som) { zp = um; ++nf; }
     else zp = zero_c<R>();
-    cx<R> xm = hxm ? ld(p - 1) : (som ? ld(p + 1) : zero_c<R>());
-    cx<R> xp = hxp ? ld(p + 1) : (som ? ld(p - 1) : zero_c<R>());
-    cx<R> ym = hym ? ld(p - N1) : (som ? ld(p + N1) : zero_c<R>());
-    cx<R> yp = hyp ? ld(p + N1) : (som ? ld(p - N1) : zero_c<R>());
+    cx<R> xm = hxm ? ld(e - Xe) : (som ? ld(e + Xe) : zero_c<R>());
+    cx<R> xp = hxp ? ld(e + Xe) : (som ? ld(e - Xe) : zero_c<R>());
+    cx<R> ym = hym ? ld(e - Ye) : (som ? ld(e + Ye) : zero_c<R>());
+    cx<R> yp = hyp ? ld(e + Ye) : (som ? ld(e - Ye) : zero_c<R>());
     const R kk = __ldg(k2 + p);
     const cx<R> d = op_diag(c, kk, nf, nf ? face_k<R>(g, p, kk) : (R)0);
     const cx<R> v = op_combine(d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
     if (MODE == 0) {
       if (SPLIT)  // the output buffer holds double-float values (16 bytes, like complex128)
-        reinterpret_cast<zdf*>(out)[p] = df_from(cvt<double>(v));
+        reinterpret_cast<zdf*>(out)[e] = df_from(cvt<double>(v));
       else
-        out[p] = cvt<TO>(v);
+        out[e] = cvt<TO>(v);
     } else {
-      const cx<R> r = csub(cvt<R>(ldg(b + p)), v);
+      const cx<R> res = csub(cvt<R>(ldg(b + e)), v);
       if (MODE == 1) {
-        out[p] = cvt<TO>(r);
+        out[e] = cvt<TO>(res);
       } else {
         const cx<R> w = DINV ? ldg(dinv + p) : omega_over(d, c.omega);
-        out[p] = cvt<TO>(cfma(w, r, uc));
+        out[e] = cvt<TO>(cfma(w, res, uc));
       }
     }
     um = uc;
@@ -91,7 +97,9 @@ __global__ void __launch_bounds__(TX* TY)
               const cx<TB>* __restrict__ b, cx<R>* __restrict__ out, int zchunk,
               const int* __restrict__ active) {
   if (active && *active == 0) return;
-  const int i = blockIdx.x * TX + threadIdx.x;
+  const int nb = g.nb;
+  const int f = blockIdx.x * TX + threadIdx.x;
+  const int i = f / nb, r = f - (f / nb) * nb;
   const int j = blockIdx.y * TY + threadIdx.y;
   if (i >= g.N1 || j >= g.N2) return;
   const int k0 = blockIdx.z * zchunk;
@@ -100,7 +108,8 @@ __global__ void __launch_bounds__(TX* TY)
   const int nfxy = som ? (i == 0) + (i == g.N1 - 1) + (j == 0) + (j == g.N2 - 1) : 0;
   const size_t S = (size_t)g.N1 * g.N2;
   size_t p = gidx(i, j, k0, g.N1, g.N2);
-  for (int k = k0; k < k1; ++k, p += S) {
+  size_t e = p * nb + r;
+  for (int k = k0; k < k1; ++k, p += S, e += S * nb) {
     cx<R> w;
     if (DINV) {
       w = ldg(dinv + p);
@@ -109,7 +118,7 @@ __global__ void __launch_bounds__(TX* TY)
       const R kk = __ldg(k2 + p);
       w = omega_over(op_diag(c, kk, nf, nf ? face_k<R>(g, p, kk) : (R)0), c.omega);
     }
-    out[p] = cmul(w, cvt<R>(ldg(b + p)));
+    out[e] = cmul(w, cvt<R>(ldg(b + e)));
   }
 }
 
@@ -136,7 +145,9 @@ __global__ void __launch_bounds__(TX* TY)
     k_restrict(Grid gf, Grid gc, const cx<R>* __restrict__ r, cx<R>* __restrict__ out, int zchunk,
                const int* __restrict__ active) {
   if (active && *active == 0) return;
-  const int I = blockIdx.x * TX + threadIdx.x;
+  const int nb = gc.nb;
+  const int f = blockIdx.x * TX + threadIdx.x;
+  const int I = f / nb, q = f - (f / nb) * nb;
   const int J = blockIdx.y * TY + threadIdx.y;
   if (I >= gc.N1 || J >= gc.N2) return;
   const int K0 = blockIdx.z * zchunk;
@@ -158,13 +169,13 @@ __global__ void __launch_bounds__(TX* TY)
           const int x = fi + dx;
           if (x < 0 || x >= gf.N1) continue;
           const R w = wyz * (dx ? (R)1 : (R)2);
-          const cx<R> v = ldg(r + gidx(x, y, z, gf.N1, gf.N2));
+          const cx<R> v = ldg(r + gidx(x, y, z, gf.N1, gf.N2) * nb + q);
           are = fma(w, v.re, are);
           aim = fma(w, v.im, aim);
         }
       }
     }
-    out[gidx(I, J, K, gc.N1, gc.N2)] = mkc<R>(are * (R)(1.0 / 64.0), aim * (R)(1.0 / 64.0));
+    out[gidx(I, J, K, gc.N1, gc.N2) * nb + q] = mkc<R>(are * (R)(1.0 / 64.0), aim * (R)(1.0 / 64.0));
   }
 }
 
@@ -176,7 +187,9 @@ __global__ void __launch_bounds__(TX* TY)
     k_prolong_add(Grid gf, Grid gc, const cx<R>* __restrict__ u1, const cx<R>* __restrict__ e,
                   cx<R>* __restrict__ out, int zchunk, const int* __restrict__ active) {
   if (active && *active == 0) return;
-  const int i = blockIdx.x * TX + threadIdx.x;
+  const int nb = gf.nb;
+  const int f = blockIdx.x * TX + threadIdx.x;
+  const int i = f / nb, q = f - (f / nb) * nb;
   const int j = blockIdx.y * TY + threadIdx.y;
   if (i >= gf.N1 || j >= gf.N2) return;
   const int k0 = blockIdx.z * zchunk;
@@ -198,14 +211,14 @@ __global__ void __launch_bounds__(TX* TY)
         if (cy_[bq] < 0 || cy_[bq] >= gc.N2) continue;
         for (int a = 0; a < nx; ++a) {
           if (cx_[a] < 0 || cx_[a] >= gc.N1) continue;
-          const cx<R> v = ldg(e + gidx(cx_[a], cy_[bq], cz_[c], gc.N1, gc.N2));
+          const cx<R> v = ldg(e + gidx(cx_[a], cy_[bq], cz_[c], gc.N1, gc.N2) * nb + q);
           are += v.re;
           aim += v.im;
         }
       }
     }
     const R s = (R)1 / (R)(nx * ny * nz);
-    const size_t p = gidx(i, j, k, gf.N1, gf.N2);
+    const size_t p = gidx(i, j, k, gf.N1, gf.N2) * nb + q;
     const cx<R> base = ldg(u1 + p);
     out[p] = mkc<R>(fma(are, s, base.re), fma(aim, s, base.im));
   }
@@ -270,6 +283,28 @@ __global__ void k_coarse(int nc, const z128* __restrict__ Minv, const cx<TI>* __
   if (lane == 0) e[row] = mkc<TO>((TO)re, (TO)im);
 }
 
+// The same product for nb right-hand sides (row-major Minv, vectors node-major with the
+// right-hand side innermost): one thread per (row, rhs), columns in a fixed order.
+template <typename TI, typename TO>
+__global__ void k_coarse_b(int nc, int nb, const z128* __restrict__ Minv, const cx<TI>* __restrict__ b,
+                           cx<TO>* __restrict__ e, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc * nb) return;
+  const int row = t / nb, q = t - (t / nb) * nb;
+  const z128* a = Minv + (size_t)row * nc;
+  double re = 0, im = 0;
+  for (int c = 0; c < nc; ++c) {
+    const z128 m = a[c];
+    const z128 v = cvt<double>(ldg(b + (size_t)c * nb + q));
+    re = fma(m.re, v.re, re);
+    re = fma(-m.im, v.im, re);
+    im = fma(m.re, v.im, im);
+    im = fma(m.im, v.re, im);
+  }
+  e[t] = mkc<TO>((TO)re, (TO)im);
+}
+
 // Discrete Dirac sources (Sec. 2.4): b(node) += 1/h^3, sources applied in order.
 __global__ void k_rhs_point(Grid g, int nsrc, const int* __restrict__ idx, double amp, z128* __restrict__ b) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -280,7 +315,7 @@ __global__ void k_rhs_point(Grid g, int nsrc, const int* __restrict__ idx, doubl
 }
 
 dim3 grid_for(const Grid& g, int& zchunk) {
-  const int bx = (g.N1 + TX - 1) / TX, by = (g.N2 + TY - 1) / TY;
+  const int bx = (g.N1 * g.nb + TX - 1) / TX, by = (g.N2 + TY - 1) / TY;
   const int target = 152 * 8;
   int zsplit = target / (bx * by);
   if (zsplit < 1) zsplit = 1;
@@ -378,9 +413,13 @@ void launch_prolong_add(const Grid& gf, const Grid& gc, const cx<R>* u1, const c
 }
 
 template <typename TI, typename TO>
-void launch_coarse(int nc, const z128* Minv, const cx<TI>* b, cx<TO>* e, cudaStream_t st, const int* active) {
-  const int wpb = 8;
-  k_coarse<TI, TO><<<(nc + wpb - 1) / wpb, wpb * 32, 0, st>>>(nc, Minv, b, e, active);
+void launch_coarse(int nc, const z128* Minv, const cx<TI>* b, cx<TO>* e, cudaStream_t st, const int* active, int nb) {
+  if (nb == 1) {
+    const int wpb = 8;
+    k_coarse<TI, TO><<<(nc + wpb - 1) / wpb, wpb * 32, 0, st>>>(nc, Minv, b, e, active);
+  } else {
+    k_coarse_b<TI, TO><<<(nc * nb + 255) / 256, 256, 0, st>>>(nc, nb, Minv, b, e, active);
+  }
 }
 
 void launch_dinv(const Grid& g, double s_re, double s_im, double omega, const double* k2, z128* out, cudaStream_t st) {
@@ -430,9 +469,9 @@ template void launch_jacobi<double, double, float>(const Grid&, double, double, 
 template void launch_smooth0<double, double>(const Grid&, double, double, double, const double*, const z128*, const z128*, z128*, cudaStream_t, const int*);
 template void launch_smooth0<float, float>(const Grid&, double, double, double, const float*, const z64*, const z64*, z64*, cudaStream_t, const int*);
 template void launch_smooth0<float, double>(const Grid&, double, double, double, const float*, const z64*, const z128*, z64*, cudaStream_t, const int*);
-template void launch_coarse<double, double>(int, const z128*, const z128*, z128*, cudaStream_t, const int*);
-template void launch_coarse<float, float>(int, const z128*, const z64*, z64*, cudaStream_t, const int*);
-template void launch_coarse<double, float>(int, const z128*, const z128*, z64*, cudaStream_t, const int*);
-template void launch_coarse<float, double>(int, const z128*, const z64*, z128*, cudaStream_t, const int*);
+template void launch_coarse<double, double>(int, const z128*, const z128*, z128*, cudaStream_t, const int*, int);
+template void launch_coarse<float, float>(int, const z128*, const z64*, z64*, cudaStream_t, const int*, int);
+template void launch_coarse<double, float>(int, const z128*, const z128*, z64*, cudaStream_t, const int*, int);
+template void launch_coarse<float, double>(int, const z128*, const z64*, z128*, cudaStream_t, const int*, int);
 
 }  // namespace helm

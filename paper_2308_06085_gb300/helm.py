@@ -81,6 +81,8 @@ def lib():
     L.helm_solve.argtypes = [vp, vp, vp, C.POINTER(SolveInfo), vp]
     L.helm_profile.argtypes = [vp, i]
     L.helm_profile_read.argtypes = [vp, C.POINTER(KernelStat), i, C.POINTER(i), C.POINTER(C.c_longlong)]
+    L.helm_solve_batched.argtypes = [vp, i, vp, vp, C.POINTER(SolveInfo), vp]
+    L.helm_solve_batched.restype = i
     L.helm_solve_adjoint.argtypes = [vp, vp, vp, C.POINTER(SolveInfo), vp]
     L.helm_grad_k2.argtypes = [vp, vp, vp, vp, vp]
     L.helm_adjoint_grad.argtypes = [vp, i, C.POINTER(i), i, C.POINTER(i), vp, vp, C.POINTER(d), C.POINTER(SolveInfo),
@@ -257,6 +259,20 @@ class Solver:
         fams = [{"name": s.name.decode(), "launches": s.launches, "ms": s.ms, "bytes": s.bytes, "flops": s.flops}
                 for s in stats[: cnt.value]]
         return fams, launches.value
+
+    def solve_batched(self, B, X=None):
+        """Solve for nrhs right-hand sides together: B is complex128 CUDA, shaped
+        (nrhs, N3, N2, N1); X the initial guesses (zeros if None).  Returns (X, infos)."""
+        B = B.reshape((-1,) + self.shape).contiguous()
+        if B.dtype != torch.complex128 or B.device.type != "cuda":
+            raise TypeError("B must be a complex128 CUDA tensor")
+        nrhs = B.shape[0]
+        X = torch.zeros_like(B) if X is None else X.reshape(B.shape).contiguous()
+        infos = (SolveInfo * nrhs)()
+        st = lib().helm_solve_batched(self._ctx, nrhs, _ptr(B), _ptr(X), infos, _stream())
+        if st not in (OK, ENOCONV):
+            self._check(st)
+        return X, [infos[r].as_dict() for r in range(nrhs)]
 
     def solve_adjoint(self, g):
         """lambda with A^H lambda = g (device complex128 tensors); returns (lambda, info)."""
