@@ -173,6 +173,7 @@ struct OpCoef {
   R s_re, s_im;
   R two_over_h;  // 2 / h : a Sommerfeld face adds -i (2/h) k to the diagonal
   R omega;       // damped-Jacobi relaxation (used by smoothing kernels)
+  int real_shift;  // s_im == 0 (the operator A): the diagonal is real away from the faces
 };
 
 // Diagonal of the operator at a node lying on `nf` Sommerfeld faces (kp = sqrt(k^2), used only
@@ -183,26 +184,47 @@ struct OpCoef {
 template <typename R>
 __device__ __forceinline__ cx<R> op_diag(const OpCoef<R>& c, R k2p, int nf, R kp) {
   R dre = fma(-c.s_re, k2p, c.six_ih2);
-  R dim = -c.s_im * k2p;
+  R dim = c.real_shift ? (R)0 : -c.s_im * k2p;
   if (nf) dim = fma(-(R)nf * c.two_over_h, kp, dim);
   return mkc<R>(dre, dim);
 }
 
-// v = d u_c - (1/h^2) (sum of the six neighbour values), neighbours already replaced by
-// the opposite value (Sommerfeld) or 0 (Dirichlet) where they fall outside the grid.
+// v = d u_c - (1/h^2) (sum of the six neighbour values) as an FMA chain, neighbours already
+// replaced by the opposite value (Sommerfeld) or 0 (Dirichlet) where they fall outside the
+// grid; real_d skips the d.im terms (d.im = 0).
 template <typename R>
-__device__ __forceinline__ cx<R> op_combine(cx<R> d, cx<R> uc, R ih2, cx<R> a, cx<R> b, cx<R> c,
-                                            cx<R> e, cx<R> f, cx<R> g) {
-  R re = d.re * uc.re;
-  R im = d.re * uc.im;
-  re = fma(-d.im, uc.im, re);
-  im = fma(d.im, uc.re, im);
-  re = fma(-ih2, a.re, re); im = fma(-ih2, a.im, im);
+__device__ __forceinline__ cx<R> op_apply(cx<R> d, bool real_d, cx<R> uc, R ih2, cx<R> a, cx<R> b, cx<R> c,
+                                          cx<R> e, cx<R> f, cx<R> g) {
+  R re = -ih2 * a.re, im = -ih2 * a.im;
   re = fma(-ih2, b.re, re); im = fma(-ih2, b.im, im);
   re = fma(-ih2, c.re, re); im = fma(-ih2, c.im, im);
   re = fma(-ih2, e.re, re); im = fma(-ih2, e.im, im);
   re = fma(-ih2, f.re, re); im = fma(-ih2, f.im, im);
   re = fma(-ih2, g.re, re); im = fma(-ih2, g.im, im);
+  re = fma(d.re, uc.re, re); im = fma(d.re, uc.im, im);
+  if (!real_d) {
+    re = fma(-d.im, uc.im, re);
+    im = fma(d.im, uc.re, im);
+  }
+  return mkc<R>(re, im);
+}
+
+// Residual y - (d u_c - (1/h^2) sum) as one FMA chain starting from y.
+template <typename R>
+__device__ __forceinline__ cx<R> op_resid(cx<R> y, cx<R> d, bool real_d, cx<R> uc, R ih2, cx<R> a, cx<R> b,
+                                          cx<R> c, cx<R> e, cx<R> f, cx<R> g) {
+  R re = y.re, im = y.im;
+  re = fma(ih2, a.re, re); im = fma(ih2, a.im, im);
+  re = fma(ih2, b.re, re); im = fma(ih2, b.im, im);
+  re = fma(ih2, c.re, re); im = fma(ih2, c.im, im);
+  re = fma(ih2, e.re, re); im = fma(ih2, e.im, im);
+  re = fma(ih2, f.re, re); im = fma(ih2, f.im, im);
+  re = fma(ih2, g.re, re); im = fma(ih2, g.im, im);
+  re = fma(-d.re, uc.re, re); im = fma(-d.re, uc.im, im);
+  if (!real_d) {
+    re = fma(d.im, uc.im, re);
+    im = fma(-d.im, uc.re, im);
+  }
   return mkc<R>(re, im);
 }
 

@@ -26,8 +26,7 @@ __device__ __forceinline__ void block_range(size_t n, size_t& p0, size_t& p1) {
 // consecutive warps share a slot and split the tile's points.  A lane accumulates its slots
 // over all the block's points, so the per-slot epilogue (warp reduction) is amortised over
 // ~50-100 points per lane.  Partials per block go to part[slot * RED_STRIDE + block].
-constexpr int TILE = NT;  // points of w staged per tile
-constexpr int KS = 4;     // slots per warp per pass over the block's points
+constexpr int KS = 4;  // slots per warp per pass over the block's points
 
 struct AccD {  // FP64 accumulator
   double re, im;
@@ -82,7 +81,9 @@ struct AccF {  // double-float accumulator, FP32 arithmetic only
   }
 };
 
-template <typename E, typename ACC>
+// TILE points of w per shared-memory tile (16 KB): few barriers per point keep loads in
+// flight.
+template <typename E, typename ACC, int TILE>
 __global__ void __launch_bounds__(NT)
     k_mdot(const E* __restrict__ V, size_t ld, int nv, const E* __restrict__ w, size_t n, z128* __restrict__ part,
            int with_norm, const int* __restrict__ active) {
@@ -103,8 +104,9 @@ __global__ void __launch_bounds__(NT)
     for (size_t t0 = p0; t0 < p1; t0 += TILE) {
       const int tn = (int)min((size_t)TILE, p1 - t0);
       __syncthreads();
-      if ((int)threadIdx.x < tn) sw[threadIdx.x] = ldg(w + t0 + threadIdx.x);
+      for (int q = threadIdx.x; q < tn; q += NT) sw[q] = ldg(w + t0 + q);
       __syncthreads();
+#pragma unroll 2
       for (int q = sub * 32 + lane; q < tn; q += 32 * wps) {
         const E wv = sw[q];
 #pragma unroll
@@ -280,59 +282,72 @@ __global__ void k_cycle_init(KrylovCtl* ctl, z128* g, int m, int iter0) {
 __global__ void k_givens(KrylovCtl* ctl, z128* H, int m, int j, int jmax, const z128* __restrict__ hcol,
                          const double* __restrict__ hnorm, double* cs, z128* sn, z128* g, double tol, double* hist,
                          int hist_len) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // one warp: the column and the previous rotations are staged in shared memory so the
+  // sequential part runs on on-chip data only
+  __shared__ z128 col[MAX_BASIS + 1];
+  __shared__ z128 ssn[MAX_BASIS];
+  __shared__ double scs[MAX_BASIS];
+  if (blockIdx.x != 0) return;
   if (ctl->active == 0) return;
-  for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
-  const double hn = *hnorm;
-  H[(size_t)(j + 1) * m + j] = mkc<double>(hn, 0.0);
-  for (int i = 0; i < j; ++i) {
-    const z128 a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
-    const double c = cs[i];
-    const z128 s = sn[i];
-    // H(i) = c a + s b ; H(i+1) = -conj(s) a + c b
-    const z128 sb = cmul(s, b);
-    const z128 cs_a = mkc<double>(-s.re, s.im);  // -conj(s)
-    const z128 t = cmul(cs_a, a);
-    H[(size_t)i * m + j] = mkc<double>(c * a.re + sb.re, c * a.im + sb.im);
-    H[(size_t)(i + 1) * m + j] = mkc<double>(t.re + c * b.re, t.im + c * b.im);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = hcol[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    scs[i] = cs[i];
+    ssn[i] = sn[i];
   }
-  const z128 a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
-  const double na = hypot(a.re, a.im), nb = hypot(b.re, b.im);
-  const double t = hypot(na, nb);
-  double c;
-  z128 s;
-  if (na == 0.0) {
-    c = 0.0;
-    s = mkc<double>(1.0, 0.0);
-    H[(size_t)j * m + j] = b;
-  } else {
-    const z128 ph = mkc<double>(a.re / na, a.im / na);
-    c = na / t;
-    s = cmul(ph, mkc<double>(b.re / t, -b.im / t));
-    H[(size_t)j * m + j] = mkc<double>(ph.re * t, ph.im * t);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double hn = *hnorm;
+    col[j + 1] = mkc<double>(hn, 0.0);
+    for (int i = 0; i < j; ++i) {
+      const z128 a = col[i], b = col[i + 1];
+      const double c = scs[i];
+      const z128 s = ssn[i];
+      // H(i) = c a + s b ; H(i+1) = -conj(s) a + c b
+      const z128 sb = cmul(s, b);
+      const z128 t = cmul(mkc<double>(-s.re, s.im), a);
+      col[i] = mkc<double>(c * a.re + sb.re, c * a.im + sb.im);
+      col[i + 1] = mkc<double>(t.re + c * b.re, t.im + c * b.im);
+    }
+    const z128 a = col[j], b = col[j + 1];
+    const double na = hypot(a.re, a.im), nb = hypot(b.re, b.im);
+    const double t = hypot(na, nb);
+    double c;
+    z128 s;
+    if (na == 0.0) {
+      c = 0.0;
+      s = mkc<double>(1.0, 0.0);
+      col[j] = b;
+    } else {
+      const z128 ph = mkc<double>(a.re / na, a.im / na);
+      c = na / t;
+      s = cmul(ph, mkc<double>(b.re / t, -b.im / t));
+      col[j] = mkc<double>(ph.re * t, ph.im * t);
+    }
+    col[j + 1] = mkc<double>(0.0, 0.0);
+    cs[j] = c;
+    sn[j] = s;
+    const z128 gj = g[j];
+    const z128 ms = mkc<double>(-s.re, s.im);  // -conj(s)
+    g[j + 1] = cmul(ms, gj);
+    g[j] = mkc<double>(c * gj.re, c * gj.im);
+    const double est = hypot(g[j + 1].re, g[j + 1].im) / ctl->bnorm;
+    ctl->est = est;
+    ctl->jend = j;
+    const int it = ctl->iter0 + j;
+    if (hist && it < hist_len) hist[it] = est;
+    if (!isfinite(est) || !isfinite(hn)) {
+      ctl->flag = 2;
+      ctl->active = 0;
+    } else if (est <= tol) {
+      ctl->flag = 1;
+      ctl->active = 0;
+    } else if (j + 1 >= jmax) {
+      ctl->active = 0;
+    }
+    if (ctl->active == 0) ctl->pass2 = 0;
   }
-  H[(size_t)(j + 1) * m + j] = mkc<double>(0.0, 0.0);
-  cs[j] = c;
-  sn[j] = s;
-  const z128 gj = g[j];
-  const z128 ms = mkc<double>(-s.re, s.im);  // -conj(s)
-  g[j + 1] = cmul(ms, gj);
-  g[j] = mkc<double>(c * gj.re, c * gj.im);
-  const double est = hypot(g[j + 1].re, g[j + 1].im) / ctl->bnorm;
-  ctl->est = est;
-  ctl->jend = j;
-  const int it = ctl->iter0 + j;
-  if (hist && it < hist_len) hist[it] = est;
-  if (!isfinite(est) || !isfinite(hn)) {
-    ctl->flag = 2;
-    ctl->active = 0;
-  } else if (est <= tol) {
-    ctl->flag = 1;
-    ctl->active = 0;
-  } else if (j + 1 >= jmax) {
-    ctl->active = 0;
-  }
-  if (ctl->active == 0) ctl->pass2 = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) H[(size_t)i * m + j] = col[i];
 }
 
 __global__ void k_trisolve(const KrylovCtl* ctl, const z128* H, int m, const z128* g, z128* y) {
@@ -524,8 +539,8 @@ int stream_blocks(size_t n) {
 
 int launch_mdot(const z128* V, size_t ld, int nv, const z128* w, size_t n, z128* part, int with_norm,
                 cudaStream_t st, const int* active) {
-  static const int nb = wave_blocks(k_mdot<z128, AccD>);
-  k_mdot<z128, AccD><<<nb, NT, 0, st>>>(V, ld, nv, w, n, part, with_norm, active);
+  static const int nb = wave_blocks(k_mdot<z128, AccD, 4 * NT>);
+  k_mdot<z128, AccD, 4 * NT><<<nb, NT, 0, st>>>(V, ld, nv, w, n, part, with_norm, active);
   return nb;
 }
 void launch_reduce_dots(const z128* part, int nv, int nb, z128* hpass, z128* hacc, int accumulate, int decide_j,
@@ -570,8 +585,8 @@ void launch_combine(const KrylovCtl* ctl, const z128* V, size_t ld, const z128* 
 }
 int launch_mdot_df(const zdf* V, size_t ld, int nv, const zdf* w, size_t n, z128* part, int with_norm,
                    cudaStream_t st, const int* active) {
-  static const int nb = wave_blocks(k_mdot<zdf, AccF>);
-  k_mdot<zdf, AccF><<<nb, NT, 0, st>>>(V, ld, nv, w, n, part, with_norm, active);
+  static const int nb = wave_blocks(k_mdot<zdf, AccF, 4 * NT>);
+  k_mdot<zdf, AccF, 4 * NT><<<nb, NT, 0, st>>>(V, ld, nv, w, n, part, with_norm, active);
   return nb;
 }
 void launch_gs_update_df(const zdf* V, size_t ld, int nv, const z128* h, zdf* w, size_t n, cudaStream_t st,

@@ -70,14 +70,15 @@ __global__ void __launch_bounds__(TX* TY)
     cx<R> yp = hyp ? ld(e + Ye) : (som ? ld(e - Ye) : zero_c<R>());
     const R kk = __ldg(k2 + p);
     const cx<R> d = op_diag(c, kk, nf, nf ? face_k<R>(g, p, kk) : (R)0);
-    const cx<R> v = op_combine(d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
+    const bool real_d = c.real_shift && nf == 0;
     if (MODE == 0) {
+      const cx<R> v = op_apply(d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
       if (SPLIT)  // the output buffer holds double-float values (16 bytes, like complex128)
         reinterpret_cast<zdf*>(out)[e] = df_from(cvt<double>(v));
       else
         out[e] = cvt<TO>(v);
     } else {
-      const cx<R> res = csub(cvt<R>(ldg(b + e)), v);
+      const cx<R> res = op_resid(cvt<R>(ldg(b + e)), d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
       if (MODE == 1) {
         out[e] = cvt<TO>(res);
       } else {
@@ -334,6 +335,7 @@ OpCoef<R> coef_for(double h, double s_re, double s_im, double omega) {
   c.s_im = (R)s_im;
   c.two_over_h = (R)(2.0 / h);
   c.omega = (R)omega;
+  c.real_shift = s_im == 0.0;
   return c;
 }
 
