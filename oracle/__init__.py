@@ -43,6 +43,8 @@ def lib():
         L.oracle_level_info.argtypes = [vp, i, ip, dp]
         L.oracle_level_k2.argtypes = [vp, i, dp]
         L.oracle_vcycle.argtypes = [vp, dp, dp]
+        L.oracle_fcycle.argtypes = [vp, dp, dp]
+        L.oracle_set_cycle.argtypes = [vp, C.c_int]
         L.oracle_vcycle_down.argtypes = [vp, i, dp, dp]
         L.oracle_vcycle_up.argtypes = [vp, i, dp, dp, dp]
         L.oracle_coarse_solve.argtypes = [vp, dp, dp]
@@ -53,6 +55,10 @@ def lib():
         L.oracle_adjoint_rhs.argtypes = [i, i, i, i, dp, dp]
         L.oracle_adjoint_finish.argtypes = [i, i, i, i, dp, dp]
         L.oracle_grad_k2.argtypes = [i, i, i, d, i, dp, dp, dp, dp]
+        L.oracle_bicgstab.argtypes = [vp, dp, dp, d, i, ip, dp, dp, i]
+        L.oracle_bicgstab.restype = i
+        L.oracle_idrs.argtypes = [vp, i, dp, d, dp, dp, d, i, ip, dp, dp, i]
+        L.oracle_idrs.restype = i
         _lib = L
     return _lib
 
@@ -147,7 +153,7 @@ def grad_k2(u, lam, k2, h, bc, grad=None):
 class Solver:
     """Oracle multigrid hierarchy + V-cycle + right-preconditioned GMRES(m)."""
 
-    def __init__(self, n, h, bc, k2, beta1=1.0, beta2=-0.5, omega=0.8, nu1=1, nu2=1, coarsest_n=4):
+    def __init__(self, n, h, bc, k2, beta1=1.0, beta2=-0.5, omega=0.8, nu1=1, nu2=1, coarsest_n=4, cycle="v"):
         n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(n)
         self.bc = bc
         self.h = h
@@ -157,6 +163,7 @@ class Solver:
         if not self._ctx:
             raise ValueError("oracle_create rejected the arguments")
         self.beta1, self.beta2, self.omega = beta1, beta2, omega
+        lib().oracle_set_cycle(self._ctx, {"v": 0, "f": 1}[cycle])
 
     def __del__(self):
         ctx = getattr(self, "_ctx", None)
@@ -181,6 +188,12 @@ class Solver:
         b = _c128(b).reshape(self.shape)
         z = np.empty_like(b)
         lib().oracle_vcycle(self._ctx, _dp(b), _dp(z))
+        return z
+
+    def fcycle(self, b):
+        b = _c128(b).reshape(self.shape)
+        z = np.empty_like(b)
+        lib().oracle_fcycle(self._ctx, _dp(b), _dp(z))
         return z
 
     def vcycle_down(self, l, b):
@@ -234,6 +247,36 @@ class Solver:
             lam = self.solve_adjoint(g.reshape(self.shape), restart=restart, tol=tol, max_iter=max_iter)["x"]
             grad = grad_k2(u, lam, self._k2, self.h, self.bc, grad)
         return loss, grad
+
+    def bicgstab(self, b, x0=None, tol=1e-6, max_iter=2000, history=False):
+        """Right-preconditioned Bi-CGSTAB with one V-cycle as M^{-1}; iters counts A-products."""
+        b = _c128(b).reshape(self.shape)
+        x = np.zeros_like(b) if x0 is None else _c128(x0).reshape(self.shape).copy()
+        it, rr = C.c_int(), C.c_double()
+        hist = np.zeros(max(max_iter, 1))
+        st = lib().oracle_bicgstab(self._ctx, _dp(b), _dp(x), tol, max_iter, C.byref(it), C.byref(rr), _dp(hist),
+                                   len(hist))
+        out = {"x": x, "iters": it.value, "relres": rr.value, "status": st}
+        if history:
+            out["history"] = hist[: it.value].copy()
+        return out
+
+    def idrs(self, b, P, x0=None, kappa=0.7, tol=1e-6, max_iter=2000, history=False):
+        """Right-preconditioned biorthogonal IDR(s), s = number of shadow vectors in P (shaped
+        (s,) + unknown shape, complex); iters counts A-products."""
+        b = _c128(b).reshape(self.shape)
+        P = _c128(P).reshape((-1,) + self.shape)
+        x = np.zeros_like(b) if x0 is None else _c128(x0).reshape(self.shape).copy()
+        it, rr = C.c_int(), C.c_double()
+        hist = np.zeros(max(max_iter, 1))
+        st = lib().oracle_idrs(self._ctx, P.shape[0], _dp(P), kappa, _dp(b), _dp(x), tol, max_iter, C.byref(it),
+                               C.byref(rr), _dp(hist), len(hist))
+        if st == -2:
+            raise ValueError("s out of range")
+        out = {"x": x, "iters": it.value, "relres": rr.value, "status": st}
+        if history:
+            out["history"] = hist[: it.value].copy()
+        return out
 
     def gmres(self, b, x0=None, restart=30, tol=1e-6, max_iter=1000, flexible=False, history=False):
         b = _c128(b).reshape(self.shape)

@@ -235,6 +235,7 @@ typedef struct {
 
 typedef struct {
   int bc, nlev, nu1, nu2;
+  int cycle;    /* preconditioner of the Krylov methods: 0 one V-cycle, 1 one F-cycle */
   double beta1, beta2, omega;
   olevel L[MAXLEV];
   int nc;       /* coarsest unknown count */
@@ -362,6 +363,59 @@ static void vcycle_level(octx* c, int l, const cplx* b, cplx* u) {
   for (int it = 0; it < c->nu2; ++it) jacobi_sweep(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, s, c->omega, b, u, L->t, L->d);
 }
 
+/* V-cycle on level l started from the current u (not from zero): nu1 Jacobi sweeps from u,
+ * residual, restriction, zero-start V-cycle below, correction, nu2 sweeps. */
+static void vcycle_from(octx* c, int l, const cplx* b, cplx* u) {
+  olevel* L = &c->L[l];
+  size_t n = npts3(L->N1, L->N2, L->N3);
+  if (l == c->nlev - 1) { coarse_solve(c, b, u); return; }
+  cplx s = cslp_shift(c);
+  olevel* C = &c->L[l + 1];
+  for (int it = 0; it < c->nu1; ++it) jacobi_sweep(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, s, c->omega, b, u, L->t, L->d);
+  apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, s, u, L->t);
+  for (size_t p = 0; p < n; ++p) L->r[p] = b[p] - L->t[p];
+  restrict_fw(L->N1, L->N2, L->N3, c->bc, L->r, C->N1, C->N2, C->N3, C->b);
+  vcycle_level(c, l + 1, C->b, C->u);
+  prolong_tl(C->N1, C->N2, C->N3, c->bc, C->u, L->N1, L->N2, L->N3, L->t);
+  for (size_t p = 0; p < n; ++p) u[p] += L->t[p];
+  for (int it = 0; it < c->nu2; ++it) jacobi_sweep(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, s, c->omega, b, u, L->t, L->d);
+}
+
+/* F-cycle (Sec. 3.4.5): like the V-cycle, but the coarse-grid error of every level is an
+ * F-cycle on the next level followed by one more V-cycle there, started from that result.
+ * Each level keeps its own right-hand side copy because the recursion revisits levels. */
+static void fcycle_level(octx* c, int l, const cplx* b, cplx* u) {
+  olevel* L = &c->L[l];
+  size_t n = npts3(L->N1, L->N2, L->N3);
+  if (l == c->nlev - 1) { coarse_solve(c, b, u); return; }
+  cplx s = cslp_shift(c);
+  olevel* C = &c->L[l + 1];
+  size_t nc = npts3(C->N1, C->N2, C->N3);
+  memset(u, 0, n * sizeof(cplx));
+  for (int it = 0; it < c->nu1; ++it) jacobi_sweep(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, s, c->omega, b, u, L->t, L->d);
+  apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, s, u, L->t);
+  for (size_t p = 0; p < n; ++p) L->r[p] = b[p] - L->t[p];
+  cplx* bc = (cplx*)malloc(nc * sizeof(cplx));
+  cplx* ec = (cplx*)malloc(nc * sizeof(cplx));
+  restrict_fw(L->N1, L->N2, L->N3, c->bc, L->r, C->N1, C->N2, C->N3, bc);
+  fcycle_level(c, l + 1, bc, ec);
+  vcycle_from(c, l + 1, bc, ec);
+  prolong_tl(C->N1, C->N2, C->N3, c->bc, ec, L->N1, L->N2, L->N3, L->t);
+  for (size_t p = 0; p < n; ++p) u[p] += L->t[p];
+  for (int it = 0; it < c->nu2; ++it) jacobi_sweep(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, s, c->omega, b, u, L->t, L->d);
+  free(bc);
+  free(ec);
+}
+
+void oracle_fcycle(void* vctx, const double* b, double* z) {
+  octx* c = (octx*)vctx;
+  size_t n = npts3(c->L[0].N1, c->L[0].N2, c->L[0].N3);
+  cplx* bb = (cplx*)malloc(n * sizeof(cplx));
+  memcpy(bb, b, n * sizeof(cplx));
+  fcycle_level(c, 0, bb, (cplx*)z);
+  free(bb);
+}
+
 void oracle_vcycle(void* vctx, const double* b, double* z) {
   octx* c = (octx*)vctx;
   size_t n = npts3(c->L[0].N1, c->L[0].N2, c->L[0].N3);
@@ -370,6 +424,14 @@ void oracle_vcycle(void* vctx, const double* b, double* z) {
   vcycle_level(c, 0, bb, (cplx*)z);
   free(bb);
 }
+
+/* The preconditioner z = M^{-1} b used by the Krylov methods: one V-cycle, or one F-cycle. */
+static void precond(octx* c, const cplx* b, cplx* z) {
+  if (c->cycle == 1) fcycle_level(c, 0, b, z);
+  else vcycle_level(c, 0, b, z);
+}
+
+void oracle_set_cycle(void* vctx, int cycle) { ((octx*)vctx)->cycle = cycle; }
 
 /* Plain building blocks exposed for pins and stage-level parity. */
 void oracle_apply(int N1, int N2, int N3, double h, int bc, const double* k2, double s_re,
@@ -493,7 +555,7 @@ int oracle_gmres(void* vctx, const double* bin, double* xio, int m, double tol, 
     for (int j = 0; j < m; ++j) {
       cplx* vj = V + (size_t)j * n;
       cplx* zj = flexible ? Z + (size_t)j * n : z;
-      vcycle_level(c, 0, vj, zj);                                      /* z_j = M^{-1} v_j */
+      precond(c, vj, zj);                                      /* z_j = M^{-1} v_j */
       apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, zj, w);  /* w = A z_j */
       ++iters;
       for (int i = 0; i <= j; ++i) {                                   /* modified Gram-Schmidt */
@@ -546,7 +608,7 @@ int oracle_gmres(void* vctx, const double* bin, double* xio, int m, double tol, 
       memset(w, 0, n * sizeof(cplx));
       for (int i = 0; i < k; ++i)
         for (size_t p = 0; p < n; ++p) w[p] += y[i] * V[(size_t)i * n + p];
-      vcycle_level(c, 0, w, z);
+      precond(c, w, z);
       for (size_t p = 0; p < n; ++p) x[p] += z[p];
     }
     apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, x, w);
@@ -645,4 +707,205 @@ void oracle_grad_k2(int N1, int N2, int N3, double h, int bc, const double* k2, 
         cplx da = -1.0 - I * (double)nf / (h * sqrt(k2[p]));
         grad[p] += -creal(conj(l[p]) * da * u[p]);
       }
+}
+
+/* ---------------------------------------------------------------------------------
+ * Right-preconditioned Bi-CGSTAB (Sec. 3.1; van der Vorst's method with the CSLP V-cycle as
+ * M^{-1} on the right): x = x0 + M^{-1} y, stopping on ||b - A x|| / ||b|| (Sec. 5 stopping
+ * rule for Bi-CGSTAB and IDR(s)).  The shadow residual is the initial residual.  `iters`
+ * counts products with A (two per full step, one when the half step already converged).
+ * Returns 0 (converged), 1 (max_iter), -1 (breakdown or non-finite).
+ * --------------------------------------------------------------------------------- */
+int oracle_bicgstab(void* vctx, const double* bin, double* xio, double tol, int max_iter, int* iters_out,
+                    double* relres_out, double* hist, int hist_len) {
+  octx* c = (octx*)vctx;
+  olevel* L = &c->L[0];
+  size_t n = npts3(L->N1, L->N2, L->N3);
+  const cplx* b = (const cplx*)bin;
+  cplx* x = (cplx*)xio;
+  cplx* r = (cplx*)calloc(n, sizeof(cplx));
+  cplx* rh = (cplx*)calloc(n, sizeof(cplx));
+  cplx* p = (cplx*)calloc(n, sizeof(cplx));
+  cplx* v = (cplx*)calloc(n, sizeof(cplx));
+  cplx* ph = (cplx*)calloc(n, sizeof(cplx));
+  cplx* s = (cplx*)calloc(n, sizeof(cplx));
+  cplx* sh = (cplx*)calloc(n, sizeof(cplx));
+  cplx* t = (cplx*)calloc(n, sizeof(cplx));
+  int iters = 0, status = 1;
+  double bnorm = vnorm(n, b);
+  if (bnorm == 0.0) bnorm = 1.0;
+  apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, x, t);
+  for (size_t q = 0; q < n; ++q) { r[q] = b[q] - t[q]; rh[q] = r[q]; }
+  double relres = vnorm(n, r) / bnorm;
+  cplx rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+  for (;;) {
+    if (relres <= tol) { status = 0; break; }
+    if (iters >= max_iter) { status = 1; break; }
+    if (!isfinite(relres)) { status = -1; break; }
+    cplx rho = vdot(n, rh, r);
+    if (rho == 0.0 || omega == 0.0) { status = -1; break; }
+    cplx beta = (rho / rho_prev) * (alpha / omega);
+    for (size_t q = 0; q < n; ++q) p[q] = r[q] + beta * (p[q] - omega * v[q]);
+    precond(c, p, ph);                                      /* p^ = M^{-1} p */
+    apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, ph, v);  /* v = A p^ */
+    ++iters;
+    cplx rv = vdot(n, rh, v);
+    if (rv == 0.0) { status = -1; break; }
+    alpha = rho / rv;
+    for (size_t q = 0; q < n; ++q) s[q] = r[q] - alpha * v[q];
+    double snorm = vnorm(n, s) / bnorm;
+    if (hist && iters - 1 < hist_len) hist[iters - 1] = snorm;
+    if (snorm <= tol || iters >= max_iter) {
+      for (size_t q = 0; q < n; ++q) { x[q] += alpha * ph[q]; r[q] = s[q]; }
+      relres = snorm;
+      continue;
+    }
+    precond(c, s, sh);                                      /* s^ = M^{-1} s */
+    apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, sh, t);  /* t = A s^ */
+    ++iters;
+    cplx ts = vdot(n, t, s);
+    double tt = vnorm(n, t);
+    tt *= tt;
+    if (tt == 0.0) { status = -1; break; }
+    omega = ts / tt;
+    for (size_t q = 0; q < n; ++q) {
+      x[q] += alpha * ph[q] + omega * sh[q];
+      r[q] = s[q] - omega * t[q];
+    }
+    relres = vnorm(n, r) / bnorm;
+    if (hist && iters - 1 < hist_len) hist[iters - 1] = relres;
+    rho_prev = rho;
+  }
+  /* report the explicit residual */
+  apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, x, t);
+  for (size_t q = 0; q < n; ++q) r[q] = b[q] - t[q];
+  double rr = vnorm(n, r) / bnorm;
+  if (status == 0 && rr > tol) status = 1;
+  *iters_out = iters;
+  *relres_out = rr;
+  free(r); free(rh); free(p); free(v); free(ph); free(s); free(sh); free(t);
+  return status;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Right-preconditioned IDR(s) (Sec. 3.1; the induced-dimension-reduction method of Sonneveld
+ * and van Gijzen that the paper runs as IDR(4)), in its biorthogonal form: the s directions
+ * G_i = A U_i of a cycle are built so that P_j^H G_i = 0 for j < i, which makes the small
+ * matrix Ms = P^H G lower triangular and keeps f = P^H r up to date by one subtraction per
+ * step.  Each cycle takes s steps that remove one component of P^H r each, then one
+ * dimension-reduction step r -= omega A M^{-1} r with the minimal-residual omega, enlarged to
+ * make the angle between r and A M^{-1} r at least acos(kappa) when it is smaller (kappa = 0
+ * keeps the minimal-residual omega).  The preconditioner enters only through U, so A U = G
+ * holds whatever M^{-1} does and r stays the recursive residual of x.  P holds s vectors of n
+ * complex values (the shadow space; only its span matters).  Stops on ||r|| / ||b|| <= tol
+ * after any step (Sec. 5 stopping rule), reports the explicit residual; `iters` counts
+ * products with A (s + 1 per full cycle).  Returns 0 converged, 1 max_iter, -1 breakdown.
+ * --------------------------------------------------------------------------------- */
+#define IDR_SMAX 16
+int oracle_idrs(void* vctx, int s, const double* Pin, double kappa, const double* bin, double* xio, double tol,
+                int max_iter, int* iters_out, double* relres_out, double* hist, int hist_len) {
+  octx* c = (octx*)vctx;
+  olevel* L = &c->L[0];
+  if (s < 1 || s > IDR_SMAX) return -2;
+  size_t n = npts3(L->N1, L->N2, L->N3);
+  const cplx* b = (const cplx*)bin;
+  const cplx* P = (const cplx*)Pin;
+  cplx* x = (cplx*)xio;
+  cplx* r = (cplx*)calloc(n, sizeof(cplx));
+  cplx* v = (cplx*)calloc(n, sizeof(cplx));
+  cplx* vh = (cplx*)calloc(n, sizeof(cplx));
+  cplx* t = (cplx*)calloc(n, sizeof(cplx));
+  cplx* G = (cplx*)calloc(n * (size_t)s, sizeof(cplx));
+  cplx* U = (cplx*)calloc(n * (size_t)s, sizeof(cplx));
+  cplx Ms[IDR_SMAX][IDR_SMAX], f[IDR_SMAX], cc[IDR_SMAX];
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) Ms[i][j] = i == j ? 1.0 : 0.0;
+  cplx om = 1.0;
+  int iters = 0, status = 1, done = 0;
+  double bnorm = vnorm(n, b);
+  if (bnorm == 0.0) bnorm = 1.0;
+  apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, x, t);
+  for (size_t q = 0; q < n; ++q) r[q] = b[q] - t[q];
+  double relres = vnorm(n, r) / bnorm;
+  if (relres <= tol) { status = 0; done = 1; }
+  while (!done) {
+    if (iters >= max_iter) { status = 1; break; }
+    for (int i = 0; i < s; ++i) f[i] = vdot(n, P + (size_t)i * n, r);
+    for (int k = 0; k < s && !done; ++k) {
+      /* Ms[k.., k..] c = f[k..] (lower triangular) */
+      for (int i = k; i < s; ++i) {
+        cplx acc = f[i];
+        for (int j = k; j < i; ++j) acc -= Ms[i][j] * cc[j];
+        cc[i] = acc / Ms[i][i];
+      }
+      /* v = r - G[:, k..] c; new direction U_k = omega M^{-1} v + U[:, k..] c */
+      for (size_t q = 0; q < n; ++q) {
+        cplx a = r[q];
+        for (int i = k; i < s; ++i) a -= cc[i] * G[(size_t)i * n + q];
+        v[q] = a;
+      }
+      precond(c, v, vh);
+      for (size_t q = 0; q < n; ++q) {
+        cplx a = om * vh[q];
+        for (int i = k; i < s; ++i) a += cc[i] * U[(size_t)i * n + q];
+        t[q] = a;
+      }
+      cplx* Uk = U + (size_t)k * n;
+      cplx* Gk = G + (size_t)k * n;
+      memcpy(Uk, t, n * sizeof(cplx));
+      apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, Uk, Gk);  /* G_k = A U_k */
+      ++iters;
+      /* biorthogonalise G_k against P_0 .. P_{k-1}, carrying U_k along */
+      for (int i = 0; i < k; ++i) {
+        cplx alpha = vdot(n, P + (size_t)i * n, Gk) / Ms[i][i];
+        for (size_t q = 0; q < n; ++q) {
+          Gk[q] -= alpha * G[(size_t)i * n + q];
+          Uk[q] -= alpha * U[(size_t)i * n + q];
+        }
+      }
+      for (int i = k; i < s; ++i) Ms[i][k] = vdot(n, P + (size_t)i * n, Gk);
+      if (Ms[k][k] == 0.0) { status = -1; done = 1; break; }
+      /* remove the k-th component of P^H r */
+      cplx beta = f[k] / Ms[k][k];
+      for (size_t q = 0; q < n; ++q) {
+        r[q] -= beta * Gk[q];
+        x[q] += beta * Uk[q];
+      }
+      relres = vnorm(n, r) / bnorm;
+      if (hist && iters - 1 < hist_len) hist[iters - 1] = relres;
+      if (!isfinite(relres)) { status = -1; done = 1; break; }
+      if (relres <= tol) { status = 0; done = 1; break; }
+      if (iters >= max_iter) { status = 1; done = 1; break; }
+      for (int i = k + 1; i < s; ++i) f[i] -= beta * Ms[i][k];
+    }
+    if (done) break;
+    /* dimension reduction: r -= omega A M^{-1} r */
+    precond(c, r, vh);
+    apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, vh, t);
+    ++iters;
+    cplx tr = vdot(n, t, r);
+    double tn = vnorm(n, t), rn = vnorm(n, r);
+    if (tn == 0.0) { status = -1; break; }
+    om = tr / (tn * tn);
+    double rho = cabs(tr) / (tn * rn);
+    if (rho < kappa) om *= kappa / rho;
+    if (om == 0.0) { status = -1; break; }
+    for (size_t q = 0; q < n; ++q) {
+      r[q] -= om * t[q];
+      x[q] += om * vh[q];
+    }
+    relres = vnorm(n, r) / bnorm;
+    if (hist && iters - 1 < hist_len) hist[iters - 1] = relres;
+    if (!isfinite(relres)) { status = -1; break; }
+    if (relres <= tol) { status = 0; break; }
+  }
+  /* report the explicit residual */
+  apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, x, t);
+  for (size_t q = 0; q < n; ++q) r[q] = b[q] - t[q];
+  double rr = vnorm(n, r) / bnorm;
+  if (status == 0 && rr > tol) status = 1;
+  *iters_out = iters;
+  *relres_out = rr;
+  free(r); free(v); free(vh); free(t); free(G); free(U);
+  return status;
 }

@@ -121,6 +121,21 @@ def random_vector(shape, seed, dtype=np.complex128):
     return (re + 1j * im).astype(dtype)
 
 
+IDR_SEED = 2308060085 + 4
+
+
+def shadow_space(shape, s, seed=IDR_SEED):
+    """The s random shadow vectors of IDR(s), shaped (s,) + shape: independent complex
+    Gaussians of variance 1 / (2 N) per part, so each column has an expected norm of 1 and,
+    at the sizes solved here, nearly orthogonal columns (IDR depends only on their span)."""
+    rng = np.random.default_rng(seed)
+    N = int(np.prod(shape))
+    sd = 1.0 / np.sqrt(2.0 * N)
+    re = rng.normal(0.0, sd, size=(s,) + tuple(shape))
+    im = rng.normal(0.0, sd, size=(s,) + tuple(shape))
+    return re + 1j * im
+
+
 def random_k2(shape, seed, kmin=5.0, kmax=40.0):
     """Seeded positive k^2 field with k uniform in [kmin, kmax] (a rough heterogeneous model)."""
     rng = np.random.default_rng(seed)

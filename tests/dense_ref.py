@@ -140,3 +140,38 @@ def dense_vcycle(n, h, bc, k2, b, shift, omega, coarsest_n):
         return x2 + omega * (bl - M @ x2) / D
 
     return cycle(0, np.asarray(b, dtype=np.complex128).ravel())
+
+
+def dense_fcycle(n, h, bc, k2, b, shift, omega, coarsest_n):
+    """One F-cycle by dense algebra: the coarse-grid error of each level is an F-cycle on the
+    next level followed by one V-cycle there started from it (zero start on the way down)."""
+    levs = levels(n, coarsest_n)
+    k2s = [np.asarray(k2, dtype=np.float64)]
+    for _ in levs[1:]:
+        k2s.append(inject_k2(k2s[-1], bc))
+    hs = [h * 2 ** l for l in range(len(levs))]
+    Ms = [helmholtz_3d(levs[l], hs[l], bc, k2s[l], shift) for l in range(len(levs))]
+    Rs = [restriction_3d(levs[l], bc) for l in range(len(levs) - 1)]
+    Ps = [prolongation_3d(levs[l], bc) for l in range(len(levs) - 1)]
+    last = len(levs) - 1
+
+    def smooth(l, x, bl):
+        return x + omega * (bl - Ms[l] @ x) / np.diag(Ms[l])
+
+    def vcyc(l, x, bl):
+        if l == last:
+            return np.linalg.solve(Ms[l], bl)
+        x = smooth(l, x, bl)
+        e = vcyc(l + 1, np.zeros(Ms[l + 1].shape[0], complex), Rs[l] @ (bl - Ms[l] @ x))
+        return smooth(l, x + Ps[l] @ e, bl)
+
+    def fcyc(l, bl):
+        if l == last:
+            return np.linalg.solve(Ms[l], bl)
+        x = smooth(l, np.zeros(Ms[l].shape[0], complex), bl)
+        bc_ = Rs[l] @ (bl - Ms[l] @ x)
+        e = fcyc(l + 1, bc_)
+        e = vcyc(l + 1, e, bc_)
+        return smooth(l, x + Ps[l] @ e, bl)
+
+    return fcyc(0, np.asarray(b, dtype=np.complex128).ravel())

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from conftest import load_stencil
-from dense_ref import dense_vcycle, helmholtz_3d, inject_k2, levels
+from dense_ref import dense_fcycle, dense_vcycle, helmholtz_3d, inject_k2, levels
 from paper_2308_06085_gb300 import inputs as I
 
 D, S = oracle.DIRICHLET, oracle.SOMMERFELD
@@ -148,3 +148,34 @@ def test_poisson_vcycle_contraction():
     mu = max(abs(1 - 0.8 / 3), abs(1 - 1.6))
     assert all(r < mu**2 for r in rhos), rhos
     assert abs(rhos[1] - rhos[2]) < 0.05 and abs(rhos[0] - rhos[1]) < 0.05, rhos
+
+
+@pytest.mark.parametrize("bc,n,coarsest", [(D, (16, 8, 8), 2), (S, (8, 12, 8), 2), (S, (16, 16, 16), 2)])
+def test_fcycle_matches_dense_composition(bc, n, coarsest):
+    """The F-cycle (Sec. 3.4.5) equals its dense recursive composition."""
+    h = 1.0 / max(n)
+    shape = I.unknown_shape(n, bc)
+    k2 = I.random_k2(shape, seed=33, kmin=2.0, kmax=0.6 / h)
+    b = I.random_vector(shape, 34)
+    o = oracle.Solver(n, h, bc, k2, coarsest_n=coarsest)
+    assert o.nlevels >= 3
+    got = o.fcycle(b).ravel()
+    want = dense_fcycle(n, h, bc, k2, b, 1.0 + 0.5j, 0.8, coarsest)
+    assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+
+
+def test_poisson_fcycle_contracts_at_least_as_well_as_vcycle():
+    n = 32
+    shape = I.unknown_shape(n, D)
+    k2 = np.zeros(shape)
+    o = oracle.Solver(n, 1.0 / n, D, k2, coarsest_n=4)
+    out = {}
+    for name, cyc in (("v", o.vcycle), ("f", o.fcycle)):
+        x = I.random_vector(shape, 78).real.astype(complex)
+        ratios = []
+        for _ in range(10):
+            xn = x + cyc(-oracle.apply(x, k2, 1.0 / n, D))
+            ratios.append(np.linalg.norm(xn) / np.linalg.norm(x))
+            x = xn / np.linalg.norm(xn)
+        out[name] = np.mean(ratios[-4:])
+    assert out["f"] <= out["v"] + 1e-3, out

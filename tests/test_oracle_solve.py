@@ -109,3 +109,127 @@ def test_zero_rhs_and_max_iter():
     b = I.random_vector(shape, 1)
     one = o.gmres(b, max_iter=1, tol=1e-14)
     assert one["status"] == 1 and one["iters"] == 1
+
+
+@pytest.mark.parametrize("bc,n", [(D, 8), (S, (6, 4, 8))])
+def test_bicgstab_tiny_matches_dense(bc, n):
+    nn = (n, n, n) if np.isscalar(n) else n
+    h = 1.0 / max(nn)
+    shape = I.unknown_shape(nn, bc)
+    k2 = I.random_k2(shape, seed=43, kmin=1.0, kmax=0.6 / h)
+    b = I.random_vector(shape, 44)
+    o = oracle.Solver(nn, h, bc, k2, coarsest_n=2)
+    res = o.bicgstab(b, tol=1e-12, max_iter=2000)
+    assert res["status"] == 0 and res["relres"] <= 1e-12
+    x = np.linalg.solve(helmholtz_3d(nn, h, bc, k2), b.ravel())
+    assert np.linalg.norm(res["x"].ravel() - x) <= 1e-9 * np.linalg.norm(x)
+
+
+def test_bicgstab_agrees_with_gmres_and_counts_matvecs():
+    """Both Krylov methods reach the same solution; Bi-CGSTAB spends two A-products per
+    step (Sec. 5 counts #Matvec as products with A)."""
+    n = 16
+    h = 1.0 / n
+    shape = I.unknown_shape(n, S)
+    w = I.workload("wedge", n)
+    b = oracle.rhs_point(shape, S, h, w["sources"])
+    o = oracle.Solver(n, h, S, w["k2"])
+    g = o.gmres(b, restart=200, tol=1e-10, max_iter=400)
+    bi = o.bicgstab(b, tol=1e-10, max_iter=2000, history=True)
+    assert bi["status"] == 0 and bi["relres"] <= 1e-10
+    assert np.linalg.norm(bi["x"] - g["x"]) <= 1e-8 * np.linalg.norm(g["x"])
+    # the recursive residual history ends below tol and the iteration count is the number of
+    # history entries (one per A-product)
+    assert len(bi["history"]) == bi["iters"] and bi["history"][-1] <= 1e-10
+
+
+def test_fcycle_preconditioned_krylov():
+    """Sec. 3.4.5: the F-cycle does more coarse work per application than the V-cycle, so as
+    a preconditioner it needs no more outer iterations; both solves reach the dense solution."""
+    n = (8, 8, 8)
+    h = 1.0 / 8
+    shape = I.unknown_shape(n, S)
+    k2 = I.random_k2(shape, seed=45, kmin=1.0, kmax=0.6 / h)
+    b = I.random_vector(shape, 46)
+    x = np.linalg.solve(helmholtz_3d(n, h, S, k2), b.ravel())
+    ov = oracle.Solver(n, h, S, k2, coarsest_n=2)
+    of = oracle.Solver(n, h, S, k2, coarsest_n=2, cycle="f")
+    for o in (ov, of):
+        r = o.gmres(b, restart=200, tol=1e-12, max_iter=200)
+        assert r["status"] == 0
+        assert np.linalg.norm(r["x"].ravel() - x) <= 1e-10 * np.linalg.norm(x)
+        bi = o.bicgstab(b, tol=1e-12, max_iter=2000)
+        assert bi["status"] == 0
+        assert np.linalg.norm(bi["x"].ravel() - x) <= 1e-9 * np.linalg.norm(x)
+    w = I.workload("wedge", 16)
+    b = oracle.rhs_point(w["k2"].shape, S, w["h"], w["sources"])
+    itv = oracle.Solver(16, w["h"], S, w["k2"]).gmres(b, tol=1e-8)["iters"]
+    itf = oracle.Solver(16, w["h"], S, w["k2"], cycle="f").gmres(b, tol=1e-8)["iters"]
+    assert itf <= itv, (itf, itv)
+
+
+@pytest.mark.parametrize("bc,n,s", [(D, 8, 4), (S, (6, 4, 8), 4), (S, 6, 2)])
+def test_idrs_tiny_matches_dense(bc, n, s):
+    nn = (n, n, n) if np.isscalar(n) else n
+    h = 1.0 / max(nn)
+    shape = I.unknown_shape(nn, bc)
+    k2 = I.random_k2(shape, seed=47, kmin=1.0, kmax=0.6 / h)
+    b = I.random_vector(shape, 48)
+    o = oracle.Solver(nn, h, bc, k2, coarsest_n=2)
+    res = o.idrs(b, I.shadow_space(shape, s), tol=1e-12, max_iter=2000)
+    assert res["status"] == 0 and res["relres"] <= 1e-12
+    x = np.linalg.solve(helmholtz_3d(nn, h, bc, k2), b.ravel())
+    assert np.linalg.norm(res["x"].ravel() - x) <= 1e-9 * np.linalg.norm(x)
+
+
+def test_idr1_is_bicgstab():
+    """IDR(1) with the initial residual as its shadow vector and the minimal-residual omega
+    (kappa = 0) is mathematically Bi-CGSTAB: both build their residuals from the same Krylov
+    polynomials, so the residual norm after every A-product agrees until rounding takes over."""
+    n = 16
+    h = 1.0 / n
+    shape = I.unknown_shape(n, S)
+    w = I.workload("wedge", n)
+    b = oracle.rhs_point(shape, S, h, w["sources"])
+    o = oracle.Solver(n, h, S, w["k2"])
+    bi = o.bicgstab(b, tol=1e-8, max_iter=400, history=True)
+    idr = o.idrs(b, b[None], kappa=0.0, tol=1e-8, max_iter=400, history=True)
+    assert idr["iters"] == bi["iters"] > 20
+    np.testing.assert_allclose(idr["history"], bi["history"], rtol=1e-8)
+
+
+@pytest.mark.parametrize("s", [1, 4, 8])
+def test_idrs_agrees_with_gmres(s):
+    """Every s reaches the GMRES solution; larger s needs fewer A-products (Sec. 3.1: IDR(s)
+    moves from Bi-CGSTAB towards GMRES as s grows), and no method beats GMRES's optimal count."""
+    n = 16
+    h = 1.0 / n
+    shape = I.unknown_shape(n, S)
+    w = I.workload("wedge", n)
+    b = oracle.rhs_point(shape, S, h, w["sources"])
+    o = oracle.Solver(n, h, S, w["k2"])
+    g = o.gmres(b, restart=400, tol=1e-10, max_iter=400)
+    r = o.idrs(b, I.shadow_space(shape, s), tol=1e-10, max_iter=2000, history=True)
+    assert r["status"] == 0 and r["relres"] <= 1e-10
+    assert np.linalg.norm(r["x"] - g["x"]) <= 1e-8 * np.linalg.norm(g["x"])
+    assert r["iters"] >= g["iters"]
+    assert len(r["history"]) == r["iters"]
+
+
+@pytest.mark.parametrize("nn,s,bound", [((3, 3, 3), 8, 8), ((5, 3, 3), 16, 16), ((5, 3, 3), 2, 24),
+                                         ((5, 3, 3), 4, 20), ((5, 5, 3), 2, 48), ((5, 5, 5), 4, 80)])
+def test_idrs_finite_termination(nn, s, bound):
+    """The dimension-reduction theorem: in exact arithmetic IDR(s) reaches r = 0 within
+    N + N / s products with A on N unknowns.  With s = N the first s steps make r orthogonal
+    to a basis of the whole space, so r = 0 after exactly N products."""
+    h = 1.0 / 5
+    shape = I.unknown_shape(nn, D)
+    N = int(np.prod(shape))
+    k2 = I.random_k2(shape, seed=49, kmin=1.0, kmax=3.0 / h)
+    b = I.random_vector(shape, 50)
+    o = oracle.Solver(nn, h, D, k2, coarsest_n=2)
+    r = o.idrs(b, I.shadow_space(shape, s), tol=1e-11, max_iter=500, history=True)
+    assert r["status"] == 0 and r["relres"] <= 1e-11
+    assert r["iters"] <= bound
+    if s == N:
+        assert r["iters"] == N and r["history"][-2] > 1e-6
