@@ -353,13 +353,21 @@ def end_to_end(torch, s, b, steps):
 
 def run_variants(torch, helm, inputs, args):
     out = {}
-    for name, n, prec, krylov in [("wedge_n128_mixed", 128, "mixed", "fgmres"),
-                                  ("wedge_n128_fp64_fgmres", 128, "fp64", "fgmres"),
-                                  ("mixed_n256_fp64", 256, "fp64", "gmres"),
-                                  ("mixed_n256_mixed", 256, "mixed", "fgmres")]:
+    for name, n, prec, krylov, orth, cycle in [
+            ("wedge_n128_mixed", 128, "mixed", "fgmres", args.orth, "v"),
+            ("wedge_n128_mixed_orth_df", 128, "mixed", "fgmres", "df", "v"),
+            ("wedge_n128_fp64_orth_df", 128, "fp64", "gmres", "df", "v"),
+            ("wedge_n128_fp64_fcycle", 128, "fp64", "gmres", args.orth, "f"),
+            ("wedge_n128_mixed_orth_df_fcycle", 128, "mixed", "fgmres", "df", "f"),
+            ("wedge_n128_fp64_bicgstab", 128, "fp64", "bicgstab", args.orth, "v"),
+            ("wedge_n128_mixed_bicgstab", 128, "mixed", "bicgstab", args.orth, "v"),
+            ("mixed_n256_fp64", 256, "fp64", "gmres", args.orth, "v"),
+            ("mixed_n256_mixed", 256, "mixed", "fgmres", args.orth, "v"),
+            ("mixed_n256_mixed_orth_df", 256, "mixed", "fgmres", "df", "v"),
+            ("mixed_n256_mixed_orth_df_fcycle", 256, "mixed", "fgmres", "df", "f")]:
         w = inputs.workload("mixed" if n == 256 else "wedge", n)
-        s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov=krylov, precision=prec, orth=args.orth,
-                        reorth=args.reorth)
+        s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov=krylov, precision=prec, orth=orth,
+                        reorth=args.reorth, cycle=cycle, max_iter=8000)
         b = s.rhs_point(w["sources"])
         s.solve(b)
         ms, infos, _ = time_solves(torch, s, b, 2)
@@ -370,15 +378,16 @@ def run_variants(torch, helm, inputs, args):
         torch.cuda.empty_cache()
     if args.variants >= 2:
         out.update(run_batched_variant(torch, helm, inputs))
+        out.update(run_batched_variant(torch, helm, inputs, orth="df"))
         out.update(run_adjoint_variant(torch, helm, inputs))
     return out
 
 
-def run_batched_variant(torch, helm, inputs):
+def run_batched_variant(torch, helm, inputs, orth="fp64"):
     """32 point sources (4 x 8 grid in the plane x3 = 0.1) on the n = 128 wedge: one batched
     solve (complex64 V-cycle, FP64 FGMRES(30)) against the same 32 sources solved one by one."""
     w = inputs.workload("batched", 128)
-    s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov="fgmres", precision="mixed")
+    s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov="fgmres", precision="mixed", orth=orth)
     B = torch.stack([s.rhs_point([p]) for p in w["sources"]])
     s.solve_batched(B[:4])  # warm-up (allocates the 32-wide workspace on the next call)
     st = torch.cuda.current_stream()
@@ -399,7 +408,7 @@ def run_batched_variant(torch, helm, inputs):
     e1.record(st)
     torch.cuda.synchronize()
     ms_s = e0.elapsed_time(e1)
-    res = {"batched_n128_32src_mixed": {
+    res = {"batched_n128_32src_mixed" + ("_orth_df" if orth == "df" else ""): {
         "ms": ms_b, "ms_per_source": ms_b / B.shape[0], "sequential_ms": ms_s, "speedup_vs_sequential": ms_s / ms_b,
         "iterations_max": max(i["iterations"] for i in infos), "iterations_min": min(i["iterations"] for i in infos),
         "rel_residual_max": max(i["rel_residual"] for i in infos), "sequential_iterations_max": max(seq_iters),

@@ -59,10 +59,11 @@ typedef enum {
 typedef enum { HELM_BC_DIRICHLET = 0, HELM_BC_SOMMERFELD = 1 } helm_bc;
 typedef enum { HELM_C128 = 0, HELM_C64 = 1 } helm_dtype;
 typedef enum { HELM_OP_A = 0, HELM_OP_M = 1 } helm_op;
-typedef enum { HELM_GMRES = 0, HELM_FGMRES = 1 } helm_krylov;
+typedef enum { HELM_GMRES = 0, HELM_FGMRES = 1, HELM_BICGSTAB = 2 } helm_krylov;
 typedef enum { HELM_PREC_FP64 = 0, HELM_PREC_MIXED = 1 } helm_precision;
 typedef enum { HELM_ORTH_FP64 = 0, HELM_ORTH_DF = 1 } helm_orth;
 typedef enum { HELM_REORTH_ALWAYS = 0, HELM_REORTH_SELECTIVE = 1 } helm_reorth;
+typedef enum { HELM_CYCLE_V = 0, HELM_CYCLE_F = 1 } helm_cycle;
 
 /* Solver parameters (Sec. 3.3-3.4 and Sec. 5).  helm_default_params fills the paper's
  * values: beta1 = 1, beta2 = -0.5 (M = -Lap - (beta1 - beta2 i) k^2, Sec. 3.3 Eq.
@@ -76,7 +77,8 @@ typedef struct {
   int nu1, nu2;     /* pre/post smoothing sweeps; this build supports nu1 = nu2 = 1 */
   int coarsest_n;   /* >= 2; coarsen while every n_d is even and n_d/2 >= coarsest_n;
                        the coarsest grid may hold at most 4096 unknowns */
-  int krylov;       /* helm_krylov: right-preconditioned GMRES(m) or flexible GMRES(m) */
+  int krylov;       /* helm_krylov: right-preconditioned GMRES(m), flexible GMRES(m), or
+                       right-preconditioned Bi-CGSTAB (Sec. 3.1; restart is ignored) */
   int restart;      /* m, Krylov vectors per restart cycle, 1..256 */
   double tol;       /* stop when ||b - A x|| / ||b|| <= tol */
   int max_iter;     /* cap on products with A in the Arnoldi process (#Matvec) */
@@ -90,6 +92,9 @@ typedef struct {
   int reorth;       /* helm_reorth: classical Gram-Schmidt with a second pass on every Arnoldi
                        step (ALWAYS), or only when the first pass removed more than half of
                        |w|^2 (SELECTIVE, the Daniel-Gragg-Kaufman-Stewart test) */
+  int cycle;        /* helm_cycle: the preconditioner is one V-cycle (default) or one F-cycle
+                       (Sec. 3.4.5: each coarse-grid error is an F-cycle on the next level followed
+                       by one V-cycle there); the batched solver always uses the V-cycle */
 } helm_params;
 
 /* Per-solve report (host struct). */
@@ -142,6 +147,13 @@ HELM_API helm_status helm_apply(helm_ctx* ctx, helm_op op, helm_dtype dt, const 
  * in FP64; HELM_C64 runs them in FP32 (the coarsest solve stays FP64).  r, z: device. */
 HELM_API helm_status cslp_vcycle(helm_ctx* ctx, helm_dtype dt, const void* r, void* z, void* stream);
 
+/* One multigrid F-cycle z ~= M_h^{-1} r (Sec. 3.4.5): like the V-cycle, but the coarse-grid
+ * error of every level comes from an F-cycle on the next level followed by one V-cycle there,
+ * started from that result.  Works on any context, whatever its `cycle` field (which only
+ * chooses the preconditioner of helm_solve); uses the same work vectors as the V-cycle, so
+ * the same stream rules apply.  dt, r, z as cslp_vcycle. */
+HELM_API helm_status cslp_fcycle(helm_ctx* ctx, helm_dtype dt, const void* r, void* z, void* stream);
+
 /* One stage of the V-cycle on level `level`, for stage-by-stage checks:
  *   stage 0 (down): out = R_l (b - M_l u1), u1 = omega D_l^{-1} b; out is on level l+1
  *   stage 1 (up)  : out = S_l(u1 + P_l e), u1 as above, e on level l+1, out on level l
@@ -177,7 +189,7 @@ HELM_API helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, helm_solv
  * contiguous row of right-hand sides.  Each right-hand side keeps its own Hessenberg matrix,
  * rotations and stopping test; a converged one is carried along unchanged.  The V-cycle
  * runs in the context's precision (complex64 for HELM_PREC_MIXED, FP64 otherwise); the outer
- * Krylov, Gram-Schmidt and residuals are FP64 (the context's orth setting does not apply).
+ * Krylov and residuals are FP64 and the Gram-Schmidt arithmetic follows the context's orth.
  *   B, X : device c128, nrhs consecutive grid vectors (X: initial guesses in, solutions out)
  *   infos: optional host array of nrhs reports
  * Waits for completion.  HELM_ENOCONV if any right-hand side missed tol within max_iter. */

@@ -235,6 +235,18 @@ __device__ __forceinline__ cx<R> omega_over(cx<R> d, R omega) {
   return mkc<R>(d.re * inv, -d.im * inv);
 }
 
+// Device control block of Bi-CGSTAB: all scalars of the recurrence stay on the device.
+struct BicgCtl {
+  int active;  // 1 while the iteration continues
+  int cont;    // 1 while the current step goes on past its half step
+  int flag;    // 1 converged, 2 breakdown
+  int half;    // the half step met tol (or the #Matvec cap)
+  int iters;   // #Matvec
+  int pad;
+  double bnorm, relres;
+  cx<double> rho, rho_prev, alpha, omega, beta;
+};
+
 // Device control block of the batched Krylov loop (all pointers are device arrays; per
 // right-hand side r unless stated).
 struct BatchCtl {

@@ -90,6 +90,9 @@ struct BatchWS {
   int nb = 0;
   z128 *V = nullptr, *Z64 = nullptr, *w = nullptr, *r = nullptr, *Bt = nullptr, *Xt = nullptr;
   z64* Z32 = nullptr;
+  zdf* wdf = nullptr;       // Arnoldi vector, double-float Gram-Schmidt
+  z128* vcur64 = nullptr;   // V-cycle input copy of v_j (double-float basis, FP64 V-cycle)
+  z64* vcur32 = nullptr;    // V-cycle input copy of v_j (double-float basis, mixed precision)
   z128 *part = nullptr, *hpass = nullptr, *hacc = nullptr;
   double *partr = nullptr, *hnorm = nullptr;
   BatchCtl h;               // host copy of the device pointers
@@ -157,6 +160,8 @@ struct helm_ctx {
   int* adj_rec = nullptr;
   int adj_rec_cap = 0;
   BatchWS bw;
+  BicgCtl* bicg = nullptr;  // device
+  BicgCtl* hbicg = nullptr; // pinned
 };
 
 namespace {
@@ -410,6 +415,71 @@ void run_vcycle(helm_ctx* c, const cx<TI>* rin, cx<TO>* zout, cudaStream_t st, c
   run_vcycle_levels<R, TI, TO>(c, lv, c->nlev, rin, zout, st, active);
 }
 
+// V-cycle on level l > 0 started from u (in place): Jacobi from u, residual, restriction, a
+// zero-start V-cycle below, correction, Jacobi.  The level's U1 holds the smoothed iterate: it
+// is free here because the F-cycle on this level has already returned.
+template <typename R>
+void vcycle_from(helm_ctx* c, const VLevel<R>* lv, int L, int l, cudaStream_t st, const int* active) {
+  const double sr = c->s_re, si = c->s_im, om = c->p.omega;
+  const VLevel<R>& F = lv[l];
+  const double nc = c->nc, cb = 2.0 * sizeof(R), kb = sizeof(R), db = F.dinv ? 16.0 : 0.0;
+  if (l == L - 1) {
+    KL(F_COARSE, nc * nc * 16 + nc * 2 * cb, 8 * nc * nc, (launch_coarse<R, R>(c->nc, c->Minv, F.B, F.E, st, active)));
+    return;
+  }
+  const VLevel<R>& C = lv[l + 1];
+  const double n = (double)F.g.npts(), ncn = (double)C.g.npts();
+  KL(F_JACOBI, n * (3 * cb + kb + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.E, F.B, F.U1, st, active)));
+  KL(F_RESID, n * (3 * cb + kb), 24 * n, (launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.B, F.T, st, active)));
+  KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
+  run_vcycle_levels<R, R, R>(c, lv + l + 1, L - l - 1, C.B, C.E, st, active);
+  KL(F_PROLONG, n * 2 * cb + ncn * cb, 6 * n, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
+  KL(F_JACOBI, n * (3 * cb + kb + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.B, F.E, st, active)));
+}
+
+// F-cycle (Sec. 3.4.5) from level l down: pre-smoothing from zero, residual, restriction; the
+// coarse-grid error is an F-cycle on the next level followed by one V-cycle there, started from
+// it; correction and post-smoothing.  Level l + 1 keeps its right-hand side in B and its error
+// in E throughout.
+template <typename R, typename TI, typename TO>
+void fcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, int l, const cx<TI>* rin, cx<TO>* zout,
+                   cudaStream_t st, const int* active) {
+  const double sr = c->s_re, si = c->s_im, om = c->p.omega;
+  const double nc = c->nc, cb = 2.0 * sizeof(R), kb = sizeof(R), ib = 2.0 * sizeof(TI), ob = 2.0 * sizeof(TO);
+  if (l == L - 1) {
+    KL(F_COARSE, nc * nc * 16 + nc * (ib + ob), 8 * nc * nc, (launch_coarse<TI, TO>(c->nc, c->Minv, rin, zout, st, active)));
+    return;
+  }
+  const VLevel<R>& F = lv[l];
+  const VLevel<R>& C = lv[l + 1];
+  const double n = (double)F.g.npts(), ncn = (double)C.g.npts(), db = F.dinv ? 16.0 : 0.0;
+  KL(F_SMOOTH0, n * (ib + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
+  KL(F_RESID, n * (cb + ib + kb + cb), 24 * n, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
+  KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
+  fcycle_levels<R, R, R>(c, lv, L, l + 1, C.B, C.E, st, active);
+  vcycle_from<R>(c, lv, L, l + 1, st, active);
+  KL(F_PROLONG, n * 2 * cb + ncn * cb, 6 * n, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
+  KL(F_JACOBI, n * (cb + ib + kb + db + ob), 32 * n, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, rin, zout, st, active)));
+}
+
+template <typename R, typename TI, typename TO>
+void run_fcycle(helm_ctx* c, const cx<TI>* rin, cx<TO>* zout, cudaStream_t st, const int* active) {
+  using B = LevelBufs<R>;
+  VLevel<R> lv[MAX_LEVELS];
+  for (int l = 0; l < c->nlev; ++l) {
+    Level& L = c->L[l];
+    lv[l] = VLevel<R>{L.g, B::k2(L), B::dinv(L), B::B(L), B::U1(L), B::T(L), B::E(L)};
+  }
+  fcycle_levels<R, TI, TO>(c, lv, c->nlev, 0, rin, zout, st, active);
+}
+
+// The configured multigrid cycle (V or F) as the preconditioner.
+template <typename R, typename TI, typename TO>
+void run_cycle(helm_ctx* c, const cx<TI>* rin, cx<TO>* zout, cudaStream_t st, const int* active) {
+  if (c->p.cycle == HELM_CYCLE_F) run_fcycle<R, TI, TO>(c, rin, zout, st, active);
+  else run_vcycle<R, TI, TO>(c, rin, zout, st, active);
+}
+
 void norm_into(helm_ctx* c, const z128* x, double* out, cudaStream_t st, const int* active) {
   const double n = (double)c->n0;
   int nb = 0;
@@ -468,15 +538,15 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
       if (mixed) {
         z64* zj = c->Z32 + (size_t)j * n;
         if (df) {
-          run_vcycle<float, float, float>(c, c->vcur32, zj, st, act);
+          run_cycle<float, float, float>(c, c->vcur32, zj, st, act);
           KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply_split<float>(F.g, 1.0, 0.0, F.k2, zj, wd, st, act)));
         } else {
-          run_vcycle<float, double, float>(c, vj, zj, st, act);
+          run_cycle<float, double, float>(c, vj, zj, st, act);
           KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply<double, float, double>(F.g, 1.0, 0.0, F.k2, zj, w, st, act)));
         }
       } else {
         z128* zj = flexible ? c->Z64 + (size_t)j * n : c->zs;
-        run_vcycle<double, double, double>(c, df ? c->vcur64 : vj, zj, st, act);
+        run_cycle<double, double, double>(c, df ? c->vcur64 : vj, zj, st, act);
         if (df)
           KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply_split<double>(F.g, 1.0, 0.0, F.k2, zj, wd, st, act)));
         else
@@ -551,7 +621,7 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
           KL(F_SOLUPDATE, (16.0 * k + 16.0) * nd, 8.0 * k * nd, launch_combine_df(ctl, Vdf, n, c->y, c->r, n, st));
         else
           KL(F_SOLUPDATE, (16.0 * k + 16.0) * nd, 8.0 * k * nd, launch_combine(ctl, c->V, n, c->y, c->r, n, st));
-        run_vcycle<double, double, double>(c, c->r, c->zs, st, c->one);
+        run_cycle<double, double, double>(c, c->r, c->zs, st, c->one);
         KL(F_SOLUPDATE, 48.0 * nd, 2.0 * nd, launch_axpy1(c->zs, x, n, st));
       }
     }
@@ -571,6 +641,13 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
     info->rel_residual = relres;
   }
   return status;
+}
+
+helm_status fcycle_entry(helm_ctx* c, helm_dtype dt, const void* r, void* z, cudaStream_t st) {
+  if (dt == HELM_C128) run_fcycle<double, double, double>(c, (const z128*)r, (z128*)z, st, nullptr);
+  else if (dt == HELM_C64) run_fcycle<float, float, float>(c, (const z64*)r, (z64*)z, st, nullptr);
+  else return fail(c, HELM_EINVAL, "unknown dtype %d", (int)dt);
+  return check_launch(c, "cslp_fcycle");
 }
 
 template <typename R>
@@ -607,6 +684,11 @@ helm_status batch_alloc(helm_ctx* c, int nb) {
   if (mixed) TRY(dalloc(c, &W.Z32, (size_t)m * ne));
   else TRY(dalloc(c, &W.Z64, (size_t)m * ne));
   TRY(dalloc(c, &W.r, ne));
+  if (c->p.orth == HELM_ORTH_DF) {
+    TRY(dalloc(c, &W.wdf, ne));
+    if (mixed) TRY(dalloc(c, &W.vcur32, ne));
+    else TRY(dalloc(c, &W.vcur64, ne));
+  }
   TRY(dalloc(c, &W.Bt, ne));
   TRY(dalloc(c, &W.Xt, ne));
   TRY(dalloc(c, &W.part, (size_t)(m + 2) * nb * RED_STRIDE));
@@ -688,7 +770,14 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
     CU(cudaMemcpyAsync(W.hany, any, sizeof(int), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     if (W.hany[0] == 0) break;
-    KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_bscale_inv(W.r, W.h.beta, W.V, ne, nb, st, any));
+    const bool df = c->p.orth == HELM_ORTH_DF;
+    zdf* Vdf = reinterpret_cast<zdf*>(W.V);
+    if (df) {
+      if (mixed) KL(F_SCALE, 40.0 * nd, 2.0 * nd, (launch_bscale_df<z128, float>(W.r, W.h.beta, Vdf, W.vcur32, ne, nb, st, any)));
+      else KL(F_SCALE, 48.0 * nd, 2.0 * nd, (launch_bscale_df<z128, double>(W.r, W.h.beta, Vdf, W.vcur64, ne, nb, st, any)));
+    } else {
+      KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_bscale_inv(W.r, W.h.beta, W.V, ne, nb, st, any));
+    }
     for (int j = 0; j < m; ++j) {
       z128* vj = W.V + (size_t)j * ne;
       z128* w = W.V + (size_t)(j + 1) * ne;
@@ -696,12 +785,20 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
       c->cur_j = j;
       if (mixed) {
         z64* zj = W.Z32 + (size_t)j * ne;
-        run_vcycle_levels<float, double, float>(c, lv32, c->nlev, vj, zj, st, any);
-        KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply<double, float, double>(g0, 1.0, 0.0, k2, zj, w, st, any)));
+        if (df) {
+          run_vcycle_levels<float, float, float>(c, lv32, c->nlev, W.vcur32, zj, st, any);
+          KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply_split<float>(g0, 1.0, 0.0, k2, zj, W.wdf, st, any)));
+        } else {
+          run_vcycle_levels<float, double, float>(c, lv32, c->nlev, vj, zj, st, any);
+          KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply<double, float, double>(g0, 1.0, 0.0, k2, zj, w, st, any)));
+        }
       } else {
         z128* zj = W.Z64 + (size_t)j * ne;
-        run_vcycle_levels<double, double, double>(c, lv64, c->nlev, vj, zj, st, any);
-        KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(g0, 1.0, 0.0, k2, zj, w, st, any)));
+        run_vcycle_levels<double, double, double>(c, lv64, c->nlev, df ? W.vcur64 : vj, zj, st, any);
+        if (df)
+          KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply_split<double>(g0, 1.0, 0.0, k2, zj, W.wdf, st, any)));
+        else
+          KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(g0, 1.0, 0.0, k2, zj, w, st, any)));
       }
       const bool sel = c->p.reorth == HELM_REORTH_SELECTIVE;
       for (int pass = 0; pass < 2; ++pass) {
@@ -709,18 +806,33 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
         c->cur_cond = (pass == 1 && sel) ? 1 : 0;
         const int wn = (pass == 0 && sel) ? 1 : 0;
         int nbk = 0;
-        KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nbk = launch_bmdot(W.V, ne, j + 1, w, ne, nb, W.part, wn, st, a2));
+        if (df)
+          KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nbk = launch_bmdot_df(Vdf, ne, j + 1, W.wdf, ne, nb, W.part, wn, st, a2));
+        else
+          KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nbk = launch_bmdot(W.V, ne, j + 1, w, ne, nb, W.part, wn, st, a2));
         KL(F_REDUCE_DOTS, 16.0 * nv * nb * nbk, 2.0 * nv * nb * nbk,
            launch_breduce_dots(W.part, j + 1, nb, nbk, W.hpass, W.hacc, pass, wn ? j : -1, W.h.act, &ctl->pass2,
                                c->reorth_log, st, a2));
-        KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_bgs_update(W.V, ne, j + 1, nb, W.hpass, w, ne, st, a2));
+        if (df)
+          KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_bgs_update_df(Vdf, ne, j + 1, nb, W.hpass, W.wdf, ne, st, a2));
+        else
+          KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_bgs_update(W.V, ne, j + 1, nb, W.hpass, w, ne, st, a2));
       }
       c->cur_cond = 0;
       int nbn = 0;
-      KL(F_NORM, 16.0 * nd, 4.0 * nd, nbn = launch_bnorm2_part(w, ne, nb, W.partr, st, any));
+      if (df)
+        KL(F_NORM, 16.0 * nd, 4.0 * nd, nbn = launch_bnorm2_part_df(W.wdf, ne, nb, W.partr, st, any));
+      else
+        KL(F_NORM, 16.0 * nd, 4.0 * nd, nbn = launch_bnorm2_part(w, ne, nb, W.partr, st, any));
       KL(F_REDUCE_NORM, 8.0 * nb * nbn, nb * nbn, launch_breduce_norm(W.partr, nb, nbn, W.hnorm, st, any));
       KL(F_GIVENS, 0, 0, launch_bgivens(ctl, nb, m, j, W.hacc, W.hnorm, tol, st));
-      KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_bscale_inv(w, W.hnorm, w, ne, nb, st, any));
+      if (df) {
+        zdf* vn = Vdf + (size_t)(j + 1) * ne;
+        if (mixed) KL(F_SCALE, 40.0 * nd, 2.0 * nd, (launch_bscale_df<zdf, float>(W.wdf, W.hnorm, vn, W.vcur32, ne, nb, st, any)));
+        else KL(F_SCALE, 48.0 * nd, 2.0 * nd, (launch_bscale_df<zdf, double>(W.wdf, W.hnorm, vn, W.vcur64, ne, nb, st, any)));
+      } else {
+        KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_bscale_inv(w, W.hnorm, w, ne, nb, st, any));
+      }
       TRY(check_launch(c, "batched Arnoldi step"));
       CU(cudaMemcpyAsync(W.hany + j, any, sizeof(int), cudaMemcpyDeviceToHost, st));
       CU(cudaEventRecord(c->ev[j % c->nev], st));
@@ -747,6 +859,104 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
   return HELM_OK;
 }
 
+// Right-preconditioned Bi-CGSTAB on device-resident b and x: two V-cycles and two products
+// with A per step, scalars on the device, the host checking the stop flag two steps behind.
+// A converged recursion is confirmed with the explicit residual; if that is still above
+// tol, the method restarts from it.
+helm_status bicgstab_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* info, cudaStream_t st) {
+  const Level& F = c->L[0];
+  const size_t n = c->n0;
+  const bool mixed = c->p.precision == HELM_PREC_MIXED;
+  const double tol = c->p.tol;
+  const int maxit = c->p.max_iter;
+  BicgCtl* bc = c->bicg;
+  z128 *r = c->V, *rh = c->V + n, *p = c->V + 2 * n, *v = c->V + 3 * n, *ph = c->V + 4 * n, *s = c->V + 5 * n,
+       *sh = c->V + 6 * n, *t = c->V + 7 * n;
+  const int* act = &bc->active;
+  const int* cont = &bc->cont;
+  const double nd = (double)n;
+  CU(cudaMemsetAsync(bc, 0, sizeof(BicgCtl), st));
+  norm_into(c, b, &bc->bnorm, st, c->one);
+  CU(cudaMemcpyAsync(c->hbicg, bc, sizeof(BicgCtl), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (c->hbicg->bnorm == 0.0) {
+    CU(cudaMemsetAsync(x, 0, n * sizeof(z128), st));
+    CU(cudaStreamSynchronize(st));
+    if (info) { info->iterations = 0; info->restarts = 0; info->rel_residual = 0.0; }
+    return HELM_OK;
+  }
+  int restarts = 0;
+  helm_status status = HELM_OK;
+  double relres = 0.0;
+  for (;;) {
+    KL(F_RESID, 56.0 * nd, 24.0 * nd, (launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, r, st, c->one)));
+    int nb = 0;
+    KL(F_MDOT, 32.0 * nd, 4.0 * nd, nb = launch_dots2(r, r, nullptr, nullptr, n, c->part, st, c->one));
+    KL(F_MISC, 0, 0, launch_bicg_init(bc, c->part, nb, r, rh, p, v, n, st));
+    CU(cudaMemcpyAsync(c->hbicg, bc, sizeof(BicgCtl), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    relres = c->hbicg->relres;
+    if (relres <= tol) { status = HELM_OK; break; }
+    if (!(relres == relres)) { status = HELM_ENUMERIC; break; }
+    if (c->hbicg->iters >= maxit) { status = HELM_ENOCONV; break; }
+    for (int step = 0;; ++step) {
+      c->cur_j = -1;
+      KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 0, tol, maxit, c->hist, c->hist_len, st));
+      KL(F_GS_UPDATE, 48.0 * nd, 8.0 * nd, launch_bicg_p(r, p, v, bc, n, st));
+      if (mixed) run_cycle<float, double, double>(c, p, ph, st, act);
+      else run_cycle<double, double, double>(c, p, ph, st, act);
+      KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, ph, v, st, act)));
+      KL(F_MDOT, 32.0 * nd, 8.0 * nd, nb = launch_dots2(rh, v, nullptr, nullptr, n, c->part, st, act));
+      KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 1, tol, maxit, c->hist, c->hist_len, st));
+      KL(F_GS_UPDATE, 48.0 * nd, 8.0 * nd, nb = launch_bicg_s(r, v, s, bc, n, c->part, st));
+      KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 2, tol, maxit, c->hist, c->hist_len, st));
+      if (mixed) run_cycle<float, double, double>(c, s, sh, st, cont);
+      else run_cycle<double, double, double>(c, s, sh, st, cont);
+      KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, sh, t, st, cont)));
+      KL(F_MDOT, 48.0 * nd, 12.0 * nd, nb = launch_dots2(t, s, t, t, n, c->part, st, cont));
+      KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 3, tol, maxit, c->hist, c->hist_len, st));
+      KL(F_GS_UPDATE, 112.0 * nd, 20.0 * nd, nb = launch_bicg_xr(x, r, ph, sh, s, t, rh, bc, n, c->part, st));
+      KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 4, tol, maxit, c->hist, c->hist_len, st));
+      TRY(check_launch(c, "Bi-CGSTAB step"));
+      const int slot = step % (c->m + FLAG_LAG + 1);
+      CU(cudaMemcpyAsync(c->hflags + slot, act, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CU(cudaEventRecord(c->ev[step % c->nev], st));
+      if (step >= FLAG_LAG) {
+        CU(cudaEventSynchronize(c->ev[(step - FLAG_LAG) % c->nev]));
+        if (c->hflags[(step - FLAG_LAG) % (c->m + FLAG_LAG + 1)] == 0) break;
+      }
+    }
+    CU(cudaMemcpyAsync(c->hbicg, bc, sizeof(BicgCtl), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    prof_flush(c, -1);
+    const BicgCtl h = *c->hbicg;
+    // explicit residual
+    KL(F_RESID, 56.0 * nd, 24.0 * nd, (launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, r, st, c->one)));
+    norm_into(c, r, &bc->relres, st, c->one);
+    double rn = 0.0;
+    CU(cudaMemcpyAsync(&rn, &bc->relres, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    relres = rn / h.bnorm;
+    if (relres <= tol) { status = HELM_OK; break; }
+    if (h.flag == 2 || !(relres == relres)) { status = HELM_ENUMERIC; break; }
+    if (h.iters >= maxit) { status = HELM_ENOCONV; break; }
+    ++restarts;  // the recursion met tol but the explicit residual did not: restart from it
+  }
+  CU(cudaMemcpyAsync(c->hbicg, bc, sizeof(BicgCtl), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (info) {
+    info->iterations = c->hbicg->iters;
+    info->restarts = restarts;
+    info->rel_residual = relres;
+  }
+  return status;
+}
+
+// The configured outer Krylov method on device-resident vectors.
+helm_status krylov_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* info, cudaStream_t st) {
+  return c->p.krylov == HELM_BICGSTAB ? bicgstab_device(c, b, x, info, st) : gmres_device(c, b, x, info, st);
+}
+
 }  // namespace
 
 // Message slot of helm_last_error(NULL), shared with the context-free entry point.
@@ -769,6 +979,7 @@ void helm_default_params(helm_params* p) {
   p->precision = HELM_PREC_FP64;
   p->orth = HELM_ORTH_FP64;
   p->reorth = HELM_REORTH_SELECTIVE;
+  p->cycle = HELM_CYCLE_V;
 }
 
 const char* helm_last_error(const helm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
@@ -808,6 +1019,7 @@ helm_status helm_destroy(helm_ctx* ctx) {
   if (ctx->hctl) cudaFreeHost(ctx->hctl);
   if (ctx->hreorth_log) cudaFreeHost(ctx->hreorth_log);
   if (ctx->bw.hany) cudaFreeHost(ctx->bw.hany);
+  if (ctx->hbicg) cudaFreeHost(ctx->hbicg);
   for (int i = 0; i < ctx->nev; ++i) cudaEventDestroy(ctx->ev[i]);
   delete ctx;
   return HELM_OK;
@@ -895,7 +1107,8 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
   // Krylov workspace
   const int m = P.restart;
   c->m = m;
-  TRY(dalloc(c, &c->V, (size_t)(m + 1) * n0));
+  // Bi-CGSTAB keeps its eight vectors in the basis storage
+  TRY(dalloc(c, &c->V, (size_t)std::max(m + 1, 8) * n0));
   if (P.precision == HELM_PREC_MIXED) TRY(dalloc(c, &c->Z32, (size_t)m * n0));
   else if (P.krylov == HELM_FGMRES) TRY(dalloc(c, &c->Z64, (size_t)m * n0));
   TRY(dalloc(c, &c->zs, n0));
@@ -920,6 +1133,9 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
   c->hist_len = P.max_iter;
   TRY(dalloc(c, &c->hist, c->hist_len));
   TRY(dalloc(c, &c->ctl, 1));
+  TRY(dalloc(c, &c->bicg, 1));
+  CU(cudaMemset(c->bicg, 0, sizeof(BicgCtl)));
+  CU(cudaHostAlloc((void**)&c->hbicg, sizeof(BicgCtl), cudaHostAllocDefault));
   TRY(dalloc(c, &c->one, 1));
   const int one = 1;
   CU(cudaMemcpy(c->one, &one, sizeof(int), cudaMemcpyHostToDevice));
@@ -952,13 +1168,15 @@ helm_status helm_create(int n1, int n2, int n3, double h, const double* k2, helm
   if (P.restart < 1 || P.restart > MAX_BASIS - 1) return fail(nullptr, HELM_EINVAL, "restart must lie in 1..%d", MAX_BASIS - 1);
   if (!(P.tol > 0.0)) return fail(nullptr, HELM_EINVAL, "tol must be positive");
   if (P.max_iter < 1) return fail(nullptr, HELM_EINVAL, "max_iter must be >= 1");
-  if (P.krylov != HELM_GMRES && P.krylov != HELM_FGMRES) return fail(nullptr, HELM_EINVAL, "unknown krylov %d", P.krylov);
+  if (P.krylov != HELM_GMRES && P.krylov != HELM_FGMRES && P.krylov != HELM_BICGSTAB)
+    return fail(nullptr, HELM_EINVAL, "unknown krylov %d", P.krylov);
   if (P.precision != HELM_PREC_FP64 && P.precision != HELM_PREC_MIXED) return fail(nullptr, HELM_EINVAL, "unknown precision %d", P.precision);
   if (!std::isfinite(P.beta1) || !std::isfinite(P.beta2)) return fail(nullptr, HELM_EINVAL, "beta1, beta2 must be finite");
   if (P.orth != HELM_ORTH_FP64 && P.orth != HELM_ORTH_DF) return fail(nullptr, HELM_EINVAL, "unknown orth %d", P.orth);
+  if (P.cycle != HELM_CYCLE_V && P.cycle != HELM_CYCLE_F) return fail(nullptr, HELM_EINVAL, "unknown cycle %d", P.cycle);
   if (P.reorth != HELM_REORTH_ALWAYS && P.reorth != HELM_REORTH_SELECTIVE)
     return fail(nullptr, HELM_EINVAL, "unknown reorth %d", P.reorth);
-  if (P.precision == HELM_PREC_MIXED) P.krylov = HELM_FGMRES;
+  if (P.precision == HELM_PREC_MIXED && P.krylov == HELM_GMRES) P.krylov = HELM_FGMRES;
   helm_ctx* c = new (std::nothrow) helm_ctx();
   if (!c) return fail(nullptr, HELM_ENOMEM, "host allocation failed");
   c->p = P;
@@ -1017,6 +1235,12 @@ helm_status cslp_vcycle(helm_ctx* c, helm_dtype dt, const void* r, void* z, void
   return check_launch(c, "cslp_vcycle");
 }
 
+helm_status cslp_fcycle(helm_ctx* c, helm_dtype dt, const void* r, void* z, void* stream) {
+  if (!c) return HELM_EINVAL;
+  if (!r || !z || r == z) return fail(c, HELM_EINVAL, "r and z must be distinct non-NULL device pointers");
+  return fcycle_entry(c, dt, r, z, (cudaStream_t)stream);
+}
+
 helm_status helm_vcycle_stage(helm_ctx* c, int level, int stage, helm_dtype dt, const void* b, const void* e,
                               void* out, void* stream) {
   if (!c) return HELM_EINVAL;
@@ -1071,7 +1295,7 @@ helm_status helm_solve_adjoint(helm_ctx* c, const void* g, void* lambda, helm_so
   CU(cudaMemsetAsync(lambda, 0, c->n0 * sizeof(z128), st));
   helm_solve_info tmp;
   helm_solve_info* inf = info ? info : &tmp;
-  helm_status s = gmres_device(c, c->bs, (z128*)lambda, inf, st);
+  helm_status s = krylov_device(c, c->bs, (z128*)lambda, inf, st);
   launch_adjoint_finish(F.g, (z128*)lambda, st);
   TRY(check_launch(c, "helm_solve_adjoint"));
   CU(cudaStreamSynchronize(st));
@@ -1130,7 +1354,7 @@ helm_status helm_adjoint_grad(helm_ctx* c, int nsrc, const int* src_nodes, int n
     TRY(helm_rhs_point(c, 1, src_nodes + 3 * s, c->bs, st));
     CU(cudaMemsetAsync(c->adj_u, 0, n * sizeof(z128), st));
     helm_solve_info fi;
-    helm_status fs = gmres_device(c, c->bs, c->adj_u, &fi, st);
+    helm_status fs = krylov_device(c, c->bs, c->adj_u, &fi, st);
     if (fs == HELM_ENUMERIC || fs == HELM_ECUDA || fs == HELM_ENOMEM) return fs;
     CU(cudaMemsetAsync(c->adj_g, 0, n * sizeof(z128), st));
     const int nb = launch_receiver_residual(nrec, c->adj_rec, c->adj_u, (const z128*)d_obs + (size_t)s * nrec, c->adj_g,
@@ -1143,7 +1367,7 @@ helm_status helm_adjoint_grad(helm_ctx* c, int nsrc, const int* src_nodes, int n
     launch_adjoint_rhs(F.g, c->adj_g, c->bs, st);
     CU(cudaMemsetAsync(c->adj_l, 0, n * sizeof(z128), st));
     helm_solve_info ai;
-    helm_status as = gmres_device(c, c->bs, c->adj_l, &ai, st);
+    helm_status as = krylov_device(c, c->bs, c->adj_l, &ai, st);
     if (as == HELM_ENUMERIC || as == HELM_ECUDA || as == HELM_ENOMEM) return as;
     launch_adjoint_finish(F.g, c->adj_l, st);
     launch_grad_k2(F.g, F.k2, c->adj_u, c->adj_l, grad_k2, st);
@@ -1232,7 +1456,7 @@ helm_status helm_solve(helm_ctx* c, const void* b, void* x, helm_solve_info* inf
   }
   helm_solve_info tmp;
   helm_solve_info* inf = info ? info : &tmp;
-  helm_status s = gmres_device(c, bd, xd, inf, st);
+  helm_status s = krylov_device(c, bd, xd, inf, st);
   if (!bdev && (s == HELM_OK || s == HELM_ENOCONV || s == HELM_ENUMERIC)) {
     CU(cudaMemcpyAsync(x, c->xs, bytes, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));

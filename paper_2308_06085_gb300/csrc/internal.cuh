@@ -97,6 +97,19 @@ void launch_set_active(KrylovCtl* ctl, int v, cudaStream_t st);
 // x += z
 void launch_axpy1(const z128* z, z128* x, size_t n, cudaStream_t st);
 
+// ---- Bi-CGSTAB (bicgstab.cu) ----
+// part slot 0 = conj(a).b, slot 1 = conj(c).d (c may be NULL); returns the number of partials
+int launch_dots2(const z128* a, const z128* b, const z128* c, const z128* d, size_t n, z128* part, cudaStream_t st,
+                 const int* active);
+void launch_bicg_p(const z128* r, z128* p, const z128* v, const BicgCtl* bc, size_t n, cudaStream_t st);
+int launch_bicg_s(const z128* r, const z128* v, z128* s, const BicgCtl* bc, size_t n, z128* part, cudaStream_t st);
+int launch_bicg_xr(z128* x, z128* r, const z128* ph, const z128* sh, const z128* s, const z128* t, const z128* rh,
+                   const BicgCtl* bc, size_t n, z128* part, cudaStream_t st);
+void launch_bicg_scalar(BicgCtl* bc, const z128* part, int nb, int stage, double tol, int max_iter, double* hist,
+                        int hist_len, cudaStream_t st);
+void launch_bicg_init(BicgCtl* bc, const z128* part, int nb, const z128* r, z128* rh, z128* p, z128* v, size_t n,
+                      cudaStream_t st);
+
 // ---- batched FGMRES kernels (krylov_batched.cu); vectors node-major, rhs innermost ----
 int launch_bnorm2_part(const z128* x, size_t ne, int nb, double* part, cudaStream_t st, const int* active);
 void launch_breduce_norm(const double* part, int nb, int nblk, double* out, cudaStream_t st, const int* active);
@@ -108,6 +121,15 @@ void launch_bgs_update(const z128* V, size_t ld, int nv, int nb, const z128* h, 
                        const int* active);
 void launch_bscale_inv(const z128* in, const double* s, z128* out, size_t ne, int nb, cudaStream_t st,
                        const int* active);
+// double-float Gram-Schmidt variants (basis and Arnoldi vector as zdf)
+int launch_bnorm2_part_df(const zdf* x, size_t ne, int nb, double* part, cudaStream_t st, const int* active);
+int launch_bmdot_df(const zdf* V, size_t ld, int nv, const zdf* w, size_t ne, int nb, z128* part, int with_norm,
+                    cudaStream_t st, const int* active);
+void launch_bgs_update_df(const zdf* V, size_t ld, int nv, int nb, const z128* h, zdf* w, size_t ne, cudaStream_t st,
+                          const int* active);
+template <typename TI, typename TC>
+void launch_bscale_df(const TI* in, const double* s, zdf* out, cx<TC>* copy, size_t ne, int nb, cudaStream_t st,
+                      const int* active);
 void launch_bcycle_init(BatchCtl* bc, int nb, int m, double tol, cudaStream_t st);
 void launch_bgivens(BatchCtl* bc, int nb, int m, int j, const z128* hcol, const double* hnorm, double tol,
                     cudaStream_t st);

@@ -35,20 +35,67 @@ __device__ __forceinline__ double lane_group_sum(double v, int nb) {
   return v;
 }
 
+__device__ __forceinline__ void df_group_sum(float& s, float& c, int nb) {
+  for (int o = 16; o >= nb; o >>= 1) {
+    const float os = __shfl_xor_sync(0xffffffffu, s, o), oc = __shfl_xor_sync(0xffffffffu, c, o);
+    float hi, lo;
+    df_add(s, c, os, oc, hi, lo);
+    s = hi;
+    c = lo;
+  }
+}
+
+// Accumulators of one lane: FP64 (z128 vectors) or double-float (zdf vectors, FP32 pipes).
+struct BAccD {
+  double re, im;
+  __device__ void zero() { re = im = 0.0; }
+  __device__ void mac(const z128& v, const z128& w) { cdot_acc(v, w, re, im); }
+  __device__ void norm(const z128& w) {
+    re = fma(w.re, w.re, re);
+    re = fma(w.im, w.im, re);
+  }
+  __device__ void group(int nb, double& r, double& i) {
+    r = lane_group_sum(re, nb);
+    i = lane_group_sum(im, nb);
+  }
+};
+struct BAccF {
+  float rs, rc, is, ic;
+  __device__ void zero() { rs = rc = is = ic = 0.f; }
+  __device__ void mac(const zdf& v, const zdf& w) {
+    df_mac(v.rh, v.rl, w.rh, w.rl, rs, rc);
+    df_mac(v.ih, v.il, w.ih, w.il, rs, rc);
+    df_mac(v.rh, v.rl, w.ih, w.il, is, ic);
+    df_mac(-v.ih, -v.il, w.rh, w.rl, is, ic);
+  }
+  __device__ void norm(const zdf& w) {
+    df_mac(w.rh, w.rl, w.rh, w.rl, rs, rc);
+    df_mac(w.ih, w.il, w.ih, w.il, rs, rc);
+  }
+  __device__ void group(int nb, double& r, double& i) {
+    float a = rs, b = rc, x = is, y = ic;
+    df_renorm(a, b, a, b);
+    df_renorm(x, y, x, y);
+    df_group_sum(a, b, nb);
+    df_group_sum(x, y, nb);
+    r = (double)a + (double)b;
+    i = (double)x + (double)y;
+  }
+};
+
 // |x_r|^2 partials: part[r * RED_STRIDE + blk]
+template <typename E, typename ACC>
 __global__ void __launch_bounds__(NT)
-    k_bnorm2_part(const z128* __restrict__ x, size_t ne, int nb, double* __restrict__ part, const int* __restrict__ active) {
+    k_bnorm2_part(const E* __restrict__ x, size_t ne, int nb, double* __restrict__ part, const int* __restrict__ active) {
   if (active && *active == 0) return;
   __shared__ double sred[NW][32];
   size_t e0, e1;
   block_range_e(ne, nb, e0, e1);
-  double s = 0.0;
-  for (size_t e = e0 + threadIdx.x; e < e1; e += NT) {
-    const z128 v = ldg(x + e);
-    s = fma(v.re, v.re, s);
-    s = fma(v.im, v.im, s);
-  }
-  s = lane_group_sum(s, nb);
+  ACC acc;
+  acc.zero();
+  for (size_t e = e0 + threadIdx.x; e < e1; e += NT) acc.norm(ldg(x + e));
+  double s, unused;
+  acc.group(nb, s, unused);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane < nb) sred[warp][lane] = s;
   __syncthreads();
@@ -73,11 +120,12 @@ __global__ void __launch_bounds__(NT)
 }
 
 // Inner products conj(V_i) . w per right-hand side; slot nv holds |w_r|^2 when with_norm.
+template <typename E, typename ACC>
 __global__ void __launch_bounds__(NT)
-    k_bmdot(const z128* __restrict__ V, size_t ld, int nv, const z128* __restrict__ w, size_t ne, int nb,
+    k_bmdot(const E* __restrict__ V, size_t ld, int nv, const E* __restrict__ w, size_t ne, int nb,
             z128* __restrict__ part, int with_norm, const int* __restrict__ active) {
   if (active && *active == 0) return;
-  __shared__ z128 sw[TILE];
+  __shared__ E sw[TILE];
   __shared__ double sred[NW][32][2];
   size_t e0, e1;
   block_range_e(ne, nb, e0, e1);
@@ -87,32 +135,29 @@ __global__ void __launch_bounds__(NT)
   const int sub = warp % wps, sfirst = warp / wps, sstep = NW / wps;
   double* partd = reinterpret_cast<double*>(part);
   for (int sbase = 0; sbase * sstep < nslot; sbase += KS) {
-    double re[KS], im[KS];
+    ACC acc[KS];
 #pragma unroll
-    for (int k = 0; k < KS; ++k) re[k] = im[k] = 0.0;
+    for (int k = 0; k < KS; ++k) acc[k].zero();
     for (size_t t0 = e0; t0 < e1; t0 += TILE) {
       const int tn = (int)min((size_t)TILE, e1 - t0);
       __syncthreads();
       for (int q = threadIdx.x; q < tn; q += NT) sw[q] = ldg(w + t0 + q);
       __syncthreads();
       for (int q = sub * 32 + lane; q < tn; q += 32 * wps) {
-        const z128 wv = sw[q];
+        const E wv = sw[q];
 #pragma unroll
         for (int k = 0; k < KS; ++k) {
           const int sl = sfirst + (sbase + k) * sstep;
-          if (sl < nv) {
-            cdot_acc(ldg(V + (size_t)sl * ld + t0 + q), wv, re[k], im[k]);
-          } else if (sl == nv && with_norm) {
-            re[k] = fma(wv.re, wv.re, re[k]);
-            re[k] = fma(wv.im, wv.im, re[k]);
-          }
+          if (sl < nv) acc[k].mac(ldg(V + (size_t)sl * ld + t0 + q), wv);
+          else if (sl == nv && with_norm) acc[k].norm(wv);
         }
       }
     }
 #pragma unroll
     for (int k = 0; k < KS; ++k) {
       const int sl = sfirst + (sbase + k) * sstep;
-      const double r = lane_group_sum(re[k], nb), i = lane_group_sum(im[k], nb);
+      double r, i;
+      acc[k].group(nb, r, i);
       __syncthreads();
       if (lane < nb) {
         sred[warp][lane][0] = r;
@@ -205,6 +250,66 @@ __global__ void __launch_bounds__(NT)
       acc.im = fma(-c.im, v.re, acc.im);
     }
     w[e] = acc;
+  }
+}
+
+// double-float: w[e] -= sum_i h[i][r] V_i[e], all on the FP32 pipes
+__global__ void __launch_bounds__(NT)
+    k_bgs_update_df(const zdf* __restrict__ V, size_t ld, int nv, int nb, const z128* __restrict__ h,
+                    zdf* __restrict__ w, size_t ne, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  extern __shared__ zdf shf[];
+  for (int i = threadIdx.x; i < nv * nb; i += NT) shf[i] = df_from(h[i]);
+  __syncthreads();
+  const size_t stride = (size_t)gridDim.x * NT;
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
+    const int r = (int)(e % nb);
+    float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
+    for (int i = 0; i < nv; ++i) {
+      const zdf v = ldg(V + (size_t)i * ld + e);
+      const zdf c = shf[i * nb + r];
+      df_mac(c.rh, c.rl, v.rh, v.rl, rs, rc);
+      df_mac(-c.ih, -c.il, v.ih, v.il, rs, rc);
+      df_mac(c.rh, c.rl, v.ih, v.il, is, ic);
+      df_mac(c.ih, c.il, v.rh, v.rl, is, ic);
+    }
+    const zdf a = w[e];
+    zdf o;
+    df_add(a.rh, a.rl, -rs, -rc, o.rh, o.rl);
+    df_add(a.ih, a.il, -is, -ic, o.ih, o.il);
+    w[e] = o;
+  }
+}
+
+// double-float scaling: out[e] = in[e] / s[r] (0 when s[r] is not positive), and the copy the
+// next V-cycle reads (complex128, exact value; or complex64, the leading parts)
+__device__ __forceinline__ zdf bscale_one(const z128& v, double d) {
+  return d > 0.0 ? df_from(mkc<double>(v.re / d, v.im / d)) : zdf{0.f, 0.f, 0.f, 0.f};
+}
+__device__ __forceinline__ zdf bscale_one(const zdf& v, double d) {
+  if (!(d > 0.0)) return zdf{0.f, 0.f, 0.f, 0.f};
+  float ih, il;
+  df_split(1.0 / d, ih, il);
+  zdf z;
+  df_mul(v.rh, v.rl, ih, il, z.rh, z.rl);
+  df_mul(v.ih, v.il, ih, il, z.ih, z.il);
+  return z;
+}
+template <typename TI, typename TC>
+__global__ void __launch_bounds__(NT)
+    k_bscale_df(const TI* __restrict__ in, const double* __restrict__ s, zdf* __restrict__ out,
+                cx<TC>* __restrict__ copy, size_t ne, int nb, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const size_t stride = (size_t)gridDim.x * NT;
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
+    const zdf z = bscale_one(in[e], s[e % nb]);
+    out[e] = z;
+    if (sizeof(TC) == 8) {
+      const z128 c = df_to_c128(z);
+      copy[e] = mkc<TC>((TC)c.re, (TC)c.im);
+    } else {
+      copy[e] = mkc<TC>((TC)z.rh, (TC)z.ih);
+    }
   }
 }
 
@@ -398,8 +503,13 @@ int stream_blocks(size_t n) {
 }  // namespace
 
 int launch_bnorm2_part(const z128* x, size_t ne, int nb, double* part, cudaStream_t st, const int* active) {
-  static const int nblk = wave_blocks(k_bnorm2_part, 0);
-  k_bnorm2_part<<<nblk, NT, 0, st>>>(x, ne, nb, part, active);
+  static const int nblk = wave_blocks(k_bnorm2_part<z128, BAccD>, 0);
+  k_bnorm2_part<z128, BAccD><<<nblk, NT, 0, st>>>(x, ne, nb, part, active);
+  return nblk;
+}
+int launch_bnorm2_part_df(const zdf* x, size_t ne, int nb, double* part, cudaStream_t st, const int* active) {
+  static const int nblk = wave_blocks(k_bnorm2_part<zdf, BAccF>, 0);
+  k_bnorm2_part<zdf, BAccF><<<nblk, NT, 0, st>>>(x, ne, nb, part, active);
   return nblk;
 }
 void launch_breduce_norm(const double* part, int nb, int nblk, double* out, cudaStream_t st, const int* active) {
@@ -407,10 +517,29 @@ void launch_breduce_norm(const double* part, int nb, int nblk, double* out, cuda
 }
 int launch_bmdot(const z128* V, size_t ld, int nv, const z128* w, size_t ne, int nb, z128* part, int with_norm,
                  cudaStream_t st, const int* active) {
-  static const int nblk = wave_blocks(k_bmdot, 0);
-  k_bmdot<<<nblk, NT, 0, st>>>(V, ld, nv, w, ne, nb, part, with_norm, active);
+  static const int nblk = wave_blocks(k_bmdot<z128, BAccD>, 0);
+  k_bmdot<z128, BAccD><<<nblk, NT, 0, st>>>(V, ld, nv, w, ne, nb, part, with_norm, active);
   return nblk;
 }
+int launch_bmdot_df(const zdf* V, size_t ld, int nv, const zdf* w, size_t ne, int nb, z128* part, int with_norm,
+                    cudaStream_t st, const int* active) {
+  static const int nblk = wave_blocks(k_bmdot<zdf, BAccF>, 0);
+  k_bmdot<zdf, BAccF><<<nblk, NT, 0, st>>>(V, ld, nv, w, ne, nb, part, with_norm, active);
+  return nblk;
+}
+void launch_bgs_update_df(const zdf* V, size_t ld, int nv, int nb, const z128* h, zdf* w, size_t ne, cudaStream_t st,
+                          const int* active) {
+  k_bgs_update_df<<<stream_blocks(ne), NT, sizeof(zdf) * nv * nb, st>>>(V, ld, nv, nb, h, w, ne, active);
+}
+template <typename TI, typename TC>
+void launch_bscale_df(const TI* in, const double* s, zdf* out, cx<TC>* copy, size_t ne, int nb, cudaStream_t st,
+                      const int* active) {
+  k_bscale_df<TI, TC><<<stream_blocks(ne), NT, 0, st>>>(in, s, out, copy, ne, nb, active);
+}
+template void launch_bscale_df<z128, double>(const z128*, const double*, zdf*, z128*, size_t, int, cudaStream_t, const int*);
+template void launch_bscale_df<z128, float>(const z128*, const double*, zdf*, z64*, size_t, int, cudaStream_t, const int*);
+template void launch_bscale_df<zdf, double>(const zdf*, const double*, zdf*, z128*, size_t, int, cudaStream_t, const int*);
+template void launch_bscale_df<zdf, float>(const zdf*, const double*, zdf*, z64*, size_t, int, cudaStream_t, const int*);
 void launch_breduce_dots(const z128* part, int nv, int nb, int nblk, z128* hpass, z128* hacc, int accumulate,
                          int decide_j, const int* act, int* pass2, int* log, cudaStream_t st, const int* active) {
   k_breduce_dots<<<1, NT, 0, st>>>(part, nv, nb, nblk, hpass, hacc, accumulate, decide_j, act, pass2, log, active);

@@ -24,7 +24,7 @@ STATUS = {0: "HELM_OK", 1: "HELM_EINVAL", 2: "HELM_ENOMEM", 3: "HELM_ECUDA", 4: 
 DIRICHLET, SOMMERFELD = 0, 1
 C128, C64 = 0, 1
 OP_A, OP_M = 0, 1
-GMRES, FGMRES = 0, 1
+GMRES, FGMRES, BICGSTAB = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 ORTH_FP64, ORTH_DF = 0, 1
 REORTH_ALWAYS, REORTH_SELECTIVE = 0, 1
@@ -40,7 +40,7 @@ class Params(C.Structure):
     _fields_ = [("beta1", C.c_double), ("beta2", C.c_double), ("omega", C.c_double), ("nu1", C.c_int),
                 ("nu2", C.c_int), ("coarsest_n", C.c_int), ("krylov", C.c_int), ("restart", C.c_int),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int), ("orth", C.c_int),
-                ("reorth", C.c_int)]
+                ("reorth", C.c_int), ("cycle", C.c_int)]
 
 
 class KernelStat(C.Structure):
@@ -76,6 +76,8 @@ def lib():
     L.helm_level_dims.argtypes = [vp, i, C.POINTER(i), C.POINTER(d)]
     L.helm_apply.argtypes = [vp, i, i, vp, vp, vp]
     L.cslp_vcycle.argtypes = [vp, i, vp, vp, vp]
+    L.cslp_fcycle.argtypes = [vp, i, vp, vp, vp]
+    L.cslp_fcycle.restype = i
     L.helm_vcycle_stage.argtypes = [vp, i, i, i, vp, vp, vp, vp]
     L.helm_rhs_point.argtypes = [vp, i, C.POINTER(i), vp, vp]
     L.helm_solve.argtypes = [vp, vp, vp, C.POINTER(SolveInfo), vp]
@@ -141,7 +143,7 @@ class Solver:
 
     def __init__(self, n, h, k2, bc=SOMMERFELD, *, beta1=1.0, beta2=-0.5, omega=0.8, coarsest_n=4,
                  krylov="gmres", restart=30, tol=1e-6, max_iter=2000, precision="fp64", orth=None,
-                 reorth=None, device=None):
+                 reorth=None, cycle="v", device=None):
         n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(int(x) for x in n)
         self.n = (n1, n2, n3)
         self.h = float(h)
@@ -155,11 +157,12 @@ class Solver:
         k2t = k2t.to(self.device).contiguous()
         p = default_params()
         p.beta1, p.beta2, p.omega, p.coarsest_n = beta1, beta2, omega, coarsest_n
-        p.krylov = {"gmres": GMRES, "fgmres": FGMRES}[krylov]
+        p.krylov = {"gmres": GMRES, "fgmres": FGMRES, "bicgstab": BICGSTAB}[krylov]
         p.restart, p.tol, p.max_iter = restart, tol, max_iter
         p.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
         if orth is not None:
             p.orth = {"fp64": ORTH_FP64, "df": ORTH_DF}[orth]
+        p.cycle = {"v": 0, "f": 1}[cycle]
         if reorth is not None:
             p.reorth = {"always": REORTH_ALWAYS, "selective": REORTH_SELECTIVE}[reorth]
         self.params = p
@@ -221,6 +224,12 @@ class Solver:
         r = self._vec(r)
         z = torch.empty_like(r) if out is None else out
         self._check(lib().cslp_vcycle(self._ctx, _DT[r.dtype], _ptr(r), _ptr(z), _stream()))
+        return z
+
+    def fcycle(self, r, out=None):
+        r = self._vec(r)
+        z = torch.empty_like(r) if out is None else out
+        self._check(lib().cslp_fcycle(self._ctx, _DT[r.dtype], _ptr(r), _ptr(z), _stream()))
         return z
 
     def vcycle_stage(self, level, stage, b, e=None):

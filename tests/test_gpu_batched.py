@@ -39,11 +39,12 @@ def sources(n, count):
     return [grid[i % len(grid)] if i < len(grid) else (n // 2, n // 2, (i * 3) % (n + 1)) for i in range(count)]
 
 
+@pytest.mark.parametrize("orth", ["fp64", "df"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("count", [3, 8])
-def test_batched_matches_single(helm, precision, count):
+def test_batched_matches_single(helm, precision, count, orth):
     w = I.workload("batched", 32)
-    s = helm.Solver(w["n"], w["h"], w["k2"], S, krylov="fgmres", precision=precision)
+    s = helm.Solver(w["n"], w["h"], w["k2"], S, krylov="fgmres", precision=precision, orth=orth)
     src = sources(32, count)
     B = torch.stack([s.rhs_point([p]) for p in src])
     X, infos = s.solve_batched(B)
