@@ -278,13 +278,15 @@ class Solver:
             out["history"] = hist[: it.value].copy()
         return out
 
-    def gmres(self, b, x0=None, restart=30, tol=1e-6, max_iter=1000, flexible=False, history=False):
+    def gmres(self, b, x0=None, restart=30, tol=1e-6, max_iter=1000, flexible=False, history=False, left=False):
+        """Right-preconditioned GMRES(m) (FGMRES with flexible=True); left=True runs the paper's
+        left-preconditioned form, whose relres is the preconditioned residual."""
         b = _c128(b).reshape(self.shape)
         x = np.zeros_like(b) if x0 is None else _c128(x0).reshape(self.shape).copy()
         it = C.c_int()
         rr = C.c_double()
         hist = np.zeros(max(max_iter, 1), dtype=np.float64)
-        st = lib().oracle_gmres(self._ctx, _dp(b), _dp(x), restart, tol, max_iter, int(flexible),
+        st = lib().oracle_gmres(self._ctx, _dp(b), _dp(x), restart, tol, max_iter, 2 if left else int(flexible),
                                 C.byref(it), C.byref(rr), _dp(hist), len(hist))
         out = {"x": x, "iters": it.value, "relres": rr.value, "status": st}
         if history:

@@ -500,10 +500,14 @@ void oracle_vcycle_up(void* vctx, int l, const double* b, const double* ecoarse,
 /* ---------------------------------------------------------------------------------
  * Right-preconditioned GMRES(m) (Sec. 3.1-3.2): A M^{-1} y = b, x = M^{-1} y, with
  * M^{-1} one V-cycle.  Arnoldi by modified Gram-Schmidt, Hessenberg least squares by
- * complex Givens rotations.  flexible != 0 stores z_j = M^{-1} v_j and updates
- * x += Z y (FGMRES); otherwise x += M^{-1}(V y).  `iters` counts products with A_h
- * inside the Arnoldi process (#Matvec, Sec. 5).  Returns 0 when the explicit relative
- * residual reached tol, 1 when max_iter was hit first, -1 on breakdown to NaN.
+ * complex Givens rotations.  flexible = 1 stores z_j = M^{-1} v_j and updates
+ * x += Z y (FGMRES); flexible = 0 updates x += M^{-1}(V y).  flexible = 2 is the paper's own
+ * left preconditioning (Sec. 3.2): GMRES on M^{-1} A x = M^{-1} b, Arnoldi vectors
+ * w = M^{-1}(A v_j), x += V y, and the paper's GMRES stopping rule (Sec. 5) on the
+ * preconditioned residual ||M^{-1}(b - A x)|| / ||M^{-1} b||.  `iters` counts products with
+ * A_h inside the Arnoldi process (#Matvec, Sec. 5).  Returns 0 when the explicit relative
+ * residual (preconditioned, for flexible = 2) reached tol, 1 when max_iter was hit first,
+ * -1 on breakdown to NaN.
  * --------------------------------------------------------------------------------- */
 static double vnorm(size_t n, const cplx* x) {
   double s = 0;
@@ -537,11 +541,23 @@ int oracle_gmres(void* vctx, const double* bin, double* xio, int m, double tol, 
   cplx* y = (cplx*)calloc(m, sizeof(cplx));
   (void)one;
   int iters = 0, status = 1;
-  double bnorm = vnorm(n, b);
+  const int left = flexible == 2;
+  if (left) flexible = 0;
+  double bnorm;
+  if (left) {
+    precond(c, b, z);
+    bnorm = vnorm(n, z);
+  } else {
+    bnorm = vnorm(n, b);
+  }
   if (bnorm == 0.0) bnorm = 1.0;
-  /* r = b - A x */
+  /* r = b - A x, and M^{-1} of it when preconditioning from the left */
   apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, x, w);
   for (size_t p = 0; p < n; ++p) r[p] = b[p] - w[p];
+  if (left) {
+    precond(c, r, z);
+    memcpy(r, z, n * sizeof(cplx));
+  }
   double beta = vnorm(n, r);
   double relres = beta / bnorm;
   for (;;) {
@@ -554,9 +570,14 @@ int oracle_gmres(void* vctx, const double* bin, double* xio, int m, double tol, 
     int jend = 0;
     for (int j = 0; j < m; ++j) {
       cplx* vj = V + (size_t)j * n;
-      cplx* zj = flexible ? Z + (size_t)j * n : z;
-      precond(c, vj, zj);                                      /* z_j = M^{-1} v_j */
-      apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, zj, w);  /* w = A z_j */
+      if (left) {
+        apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, vj, z);  /* z = A v_j */
+        precond(c, z, w);                                                /* w = M^{-1} z */
+      } else {
+        cplx* zj = flexible ? Z + (size_t)j * n : z;
+        precond(c, vj, zj);                                      /* z_j = M^{-1} v_j */
+        apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, zj, w);  /* w = A z_j */
+      }
       ++iters;
       for (int i = 0; i <= j; ++i) {                                   /* modified Gram-Schmidt */
         cplx* vi = V + (size_t)i * n;
@@ -601,7 +622,10 @@ int oracle_gmres(void* vctx, const double* bin, double* xio, int m, double tol, 
       for (int q = i + 1; q < k; ++q) s -= H[(size_t)i * m + q] * y[q];
       y[i] = s / H[(size_t)i * m + i];
     }
-    if (flexible) {
+    if (left) {
+      for (int i = 0; i < k; ++i)
+        for (size_t p = 0; p < n; ++p) x[p] += y[i] * V[(size_t)i * n + p];
+    } else if (flexible) {
       for (int i = 0; i < k; ++i)
         for (size_t p = 0; p < n; ++p) x[p] += y[i] * Z[(size_t)i * n + p];
     } else {
@@ -613,6 +637,10 @@ int oracle_gmres(void* vctx, const double* bin, double* xio, int m, double tol, 
     }
     apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, 1.0, x, w);
     for (size_t p = 0; p < n; ++p) r[p] = b[p] - w[p];
+    if (left) {
+      precond(c, r, z);
+      memcpy(r, z, n * sizeof(cplx));
+    }
     beta = vnorm(n, r);
     relres = beta / bnorm;
   }

@@ -1,0 +1,68 @@
+"""The paper's own iteration counts as a soft pin of the whole method (operator, CSLP shift,
+V-cycle, transfers, Krylov methods and their stopping rules): Table 1 of Sec. 5.1.3, the 3D
+closed-off problem at 65^3 nodes and k = 40.
+
+The oracle runs the paper's configuration: coarsest grid 17^3 nodes (coarsest_n = 16
+intervals, which is the paper's 17-node rule on this grid), left-preconditioned full GMRES with
+the preconditioned stopping rule, and Bi-CGSTAB / IDR(4) on the true residual.  GMRES is
+insensitive to rounding order (the paper prints 145 for every layout) and must land within
++-2 of it.  Bi-CGSTAB and IDR(4) move with rounding order and, for IDR, the random shadow
+space (the paper's counts spread 359-407 and 192-211 across layouts); they must fall inside
+that spread widened by 15% / 10%.  The coarsest solve is exact here where the paper runs GMRES
+to 1e-11 on it, a difference far below the outer tolerance.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_06085_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1_matvec.txt")
+
+
+def table1():
+    out = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, *vals = line.split()
+            out[name] = [int(v) for v in vals]
+    return out
+
+
+@pytest.fixture(scope="module")
+def closed_off():
+    n, k = 64, 40.0
+    shape = I.unknown_shape(n, oracle.DIRICHLET)
+    o = oracle.Solver(n, 1.0 / n, oracle.DIRICHLET, np.full(shape, k * k), coarsest_n=16)
+    assert o.nlevels == 3 and o.level(2)["n"] == (16, 16, 16)
+    return o, oracle.rhs_closed_off(n, k), shape
+
+
+@pytest.mark.slow
+def test_table1_gmres(closed_off):
+    o, b, _ = closed_off
+    r = o.gmres(b, restart=400, tol=1e-6, max_iter=400, left=True)
+    assert r["status"] == 0
+    assert abs(r["iters"] - table1()["GMRES"][0]) <= 2, r["iters"]
+
+
+@pytest.mark.slow
+def test_table1_idr4(closed_off):
+    o, b, shape = closed_off
+    r = o.idrs(b, I.shadow_space(shape, 4), tol=1e-6, max_iter=2000)
+    t = table1()["IDR(4)"]
+    assert r["status"] == 0
+    assert 0.9 * min(t) <= r["iters"] <= 1.1 * max(t), r["iters"]
+
+
+@pytest.mark.slow
+def test_table1_bicgstab(closed_off):
+    o, b, _ = closed_off
+    r = o.bicgstab(b, tol=1e-6, max_iter=2000)
+    t = table1()["Bi-CGSTAB"]
+    assert r["status"] == 0
+    assert 0.85 * min(t) <= r["iters"] <= 1.1 * max(t), r["iters"]
