@@ -361,10 +361,13 @@ def run_variants(torch, helm, inputs, args):
             ("wedge_n128_mixed_orth_df_fcycle", 128, "mixed", "fgmres", "df", "f"),
             ("wedge_n128_fp64_bicgstab", 128, "fp64", "bicgstab", args.orth, "v"),
             ("wedge_n128_mixed_bicgstab", 128, "mixed", "bicgstab", args.orth, "v"),
+            ("wedge_n128_fp64_idr4", 128, "fp64", "idrs", args.orth, "v"),
+            ("wedge_n128_mixed_idr4", 128, "mixed", "idrs", args.orth, "v"),
             ("mixed_n256_fp64", 256, "fp64", "gmres", args.orth, "v"),
             ("mixed_n256_mixed", 256, "mixed", "fgmres", args.orth, "v"),
             ("mixed_n256_mixed_orth_df", 256, "mixed", "fgmres", "df", "v"),
-            ("mixed_n256_mixed_orth_df_fcycle", 256, "mixed", "fgmres", "df", "f")]:
+            ("mixed_n256_mixed_orth_df_fcycle", 256, "mixed", "fgmres", "df", "f"),
+            ("mixed_n256_mixed_idr4", 256, "mixed", "idrs", args.orth, "v")]:
         w = inputs.workload("mixed" if n == 256 else "wedge", n)
         s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov=krylov, precision=prec, orth=orth,
                         reorth=args.reorth, cycle=cycle, max_iter=8000)

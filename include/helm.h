@@ -59,7 +59,7 @@ typedef enum {
 typedef enum { HELM_BC_DIRICHLET = 0, HELM_BC_SOMMERFELD = 1 } helm_bc;
 typedef enum { HELM_C128 = 0, HELM_C64 = 1 } helm_dtype;
 typedef enum { HELM_OP_A = 0, HELM_OP_M = 1 } helm_op;
-typedef enum { HELM_GMRES = 0, HELM_FGMRES = 1, HELM_BICGSTAB = 2 } helm_krylov;
+typedef enum { HELM_GMRES = 0, HELM_FGMRES = 1, HELM_BICGSTAB = 2, HELM_IDRS = 3 } helm_krylov;
 typedef enum { HELM_PREC_FP64 = 0, HELM_PREC_MIXED = 1 } helm_precision;
 typedef enum { HELM_ORTH_FP64 = 0, HELM_ORTH_DF = 1 } helm_orth;
 typedef enum { HELM_REORTH_ALWAYS = 0, HELM_REORTH_SELECTIVE = 1 } helm_reorth;
@@ -77,13 +77,18 @@ typedef struct {
   int nu1, nu2;     /* pre/post smoothing sweeps; this build supports nu1 = nu2 = 1 */
   int coarsest_n;   /* >= 2; coarsen while every n_d is even and n_d/2 >= coarsest_n;
                        the coarsest grid may hold at most 4096 unknowns */
-  int krylov;       /* helm_krylov: right-preconditioned GMRES(m), flexible GMRES(m), or
-                       right-preconditioned Bi-CGSTAB (Sec. 3.1; restart is ignored) */
+  int krylov;       /* helm_krylov: right-preconditioned GMRES(m), flexible GMRES(m),
+                       right-preconditioned Bi-CGSTAB, or right-preconditioned IDR(s) in its
+                       biorthogonal form (Sec. 3.1; the paper's solver for its wedge and salt
+                       runs, as IDR(4)).  Bi-CGSTAB and IDR(s) ignore restart; IDR(s) needs a
+                       shadow space from helm_set_shadow_space before helm_solve. */
   int restart;      /* m, Krylov vectors per restart cycle, 1..256 */
   double tol;       /* stop when ||b - A x|| / ||b|| <= tol */
   int max_iter;     /* cap on products with A in the Arnoldi process (#Matvec) */
   int precision;    /* helm_precision: HELM_PREC_MIXED runs the V-cycle in complex64
-                       under an FP64 flexible outer Krylov (forces HELM_FGMRES) */
+                       under an FP64 outer Krylov (turns HELM_GMRES into HELM_FGMRES; Bi-CGSTAB
+                       and IDR(s) keep M^{-1} p as a vector of their own, so they run as they
+                       are) */
   int orth;         /* helm_orth: arithmetic of the Gram-Schmidt inner products and updates.
                        HELM_ORTH_FP64: native FP64.  HELM_ORTH_DF: the Krylov basis is held
                        as pairs of FP32 values (hi + lo, about 48 significant bits) and the
@@ -95,6 +100,10 @@ typedef struct {
   int cycle;        /* helm_cycle: the preconditioner is one V-cycle (default) or one F-cycle
                        (Sec. 3.4.5: each coarse-grid error is an F-cycle on the next level followed
                        by one V-cycle there); the batched solver always uses the V-cycle */
+  double idr_kappa; /* IDR(s) dimension-reduction step: omega minimises |r - omega A M^{-1} r|
+                       and is enlarged so that the cosine of the angle between r and
+                       A M^{-1} r is at least idr_kappa when it is smaller; 0 keeps the
+                       minimal-residual omega.  Default 0.7, in [0, 1). */
 } helm_params;
 
 /* Per-solve report (host struct). */
@@ -180,6 +189,14 @@ HELM_API helm_status helm_rhs_point(helm_ctx* ctx, int nsrc, const int* nodes, v
  * iterate) or HELM_ENUMERIC (breakdown to NaN/Inf). */
 HELM_API helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_info* info,
                        void* stream);
+
+/* Shadow space of IDR(s): s (1..8) device c128 grid vectors P_0 .. P_{s-1}, consecutive, one
+ * grid vector each (the layout of helm_solve's b).  IDR(s) builds its residuals orthogonal to
+ * span(P) step by step (Sec. 3.1); the paper draws P at random, and the caller passes those
+ * random vectors in.  Copied into the context (device-to-device on `stream`; the call waits),
+ * so P may be freed afterwards; allocates 3 s + 4 grid vectors of context memory.  Calling
+ * it again replaces the space.  HELM_EINVAL for s out of range or a NULL P. */
+HELM_API helm_status helm_set_shadow_space(helm_ctx* ctx, int s, const void* P, void* stream);
 
 /* Solve A_h X_r = B_r for nrhs right-hand sides together (S9 of the build's hot path; the
  * paper solves one source at a time).  The right-hand sides run through the same

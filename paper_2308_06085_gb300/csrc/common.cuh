@@ -247,6 +247,22 @@ struct BicgCtl {
   cx<double> rho, rho_prev, alpha, omega, beta;
 };
 
+// Device control block of IDR(s): the scalars of the recurrence and the small s x s system.
+constexpr int IDR_SMAX = 8;
+struct IdrCtl {
+  int active;  // 1 while the iteration continues
+  int flag;    // 1 converged, 2 breakdown
+  int iters;   // #Matvec
+  int s;       // shadow-space dimension
+  double bnorm, relres, kappa, pad;
+  cx<double> om;                          // omega of the last dimension-reduction step
+  cx<double> beta;                        // step size of the current step
+  cx<double> f[IDR_SMAX];                 // P^H r
+  cx<double> c[IDR_SMAX];                 // coefficients of the current step
+  cx<double> alpha[IDR_SMAX];             // biorthogonalisation coefficients of the current step
+  cx<double> Ms[IDR_SMAX * IDR_SMAX];     // P^H G (row i, column k at i * IDR_SMAX + k), lower triangular
+};
+
 // Device control block of the batched Krylov loop (all pointers are device arrays; per
 // right-hand side r unless stated).
 struct BatchCtl {

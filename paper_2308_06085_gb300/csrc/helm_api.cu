@@ -162,6 +162,13 @@ struct helm_ctx {
   BatchWS bw;
   BicgCtl* bicg = nullptr;  // device
   BicgCtl* hbicg = nullptr; // pinned
+  // IDR(s): shadow space P (s vectors), work G, U (s each), r, v, vh, t; control block
+  int idr_s = 0;
+  z128* idrP = nullptr;
+  z128* idrW = nullptr;
+  z128* idr_part = nullptr;  // (IDR_SMAX + 1) x RED_STRIDE
+  IdrCtl* idr = nullptr;     // device
+  IdrCtl* hidr = nullptr;    // pinned
 };
 
 namespace {
@@ -196,6 +203,17 @@ helm_status dalloc(helm_ctx* c, T** p, size_t count) {
   c->allocs.push_back(q);
   *p = static_cast<T*>(q);
   return HELM_OK;
+}
+
+// Free one allocation made by dalloc (and forget it).
+void dfree(helm_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->allocs.size(); ++i)
+    if (c->allocs[i] == p) {
+      cudaFree(p);
+      c->allocs.erase(c->allocs.begin() + (long)i);
+      return;
+    }
 }
 
 #define TRY(x)                          \
@@ -952,8 +970,132 @@ helm_status bicgstab_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info
   return status;
 }
 
+// Right-preconditioned IDR(s), biorthogonal form (Sec. 3.1), on device-resident vectors.
+// The host enqueues whole steps and stops on a lagged copy of the device's active flag.
+helm_status idrs_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* info, cudaStream_t st) {
+  if (c->idr_s < 1) return fail(c, HELM_EINVAL, "IDR(s) needs a shadow space (helm_set_shadow_space)");
+  const Level& F = c->L[0];
+  const size_t n = c->n0;
+  const int s = c->idr_s;
+  const bool mixed = c->p.precision == HELM_PREC_MIXED;
+  const double tol = c->p.tol;
+  const int maxit = c->p.max_iter;
+  IdrCtl* ic = c->idr;
+  z128 *G = c->idrW, *U = G + (size_t)s * n, *r = U + (size_t)s * n, *v = r + n, *vh = v + n, *t = vh + n;
+  const z128* P = c->idrP;
+  z128* part = c->idr_part;
+  const int* act = &ic->active;
+  const double nd = (double)n, sd = (double)s;
+  IdrCtl h0;
+  memset(&h0, 0, sizeof(h0));
+  h0.s = s;
+  h0.kappa = c->p.idr_kappa;
+  CU(cudaMemcpyAsync(ic, &h0, sizeof(IdrCtl), cudaMemcpyHostToDevice, st));
+  norm_into(c, b, &ic->bnorm, st, c->one);
+  CU(cudaMemcpyAsync(c->hidr, ic, sizeof(IdrCtl), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (c->hidr->bnorm == 0.0) {
+    CU(cudaMemsetAsync(x, 0, n * sizeof(z128), st));
+    CU(cudaStreamSynchronize(st));
+    if (info) { info->iterations = 0; info->restarts = 0; info->rel_residual = 0.0; }
+    return HELM_OK;
+  }
+  const int ring = c->m + FLAG_LAG + 1;
+  int restarts = 0;
+  helm_status status = HELM_OK;
+  double relres = 0.0;
+  for (;;) {
+    KL(F_RESID, 56.0 * nd, 24.0 * nd, (launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, r, st, c->one)));
+    CU(cudaMemsetAsync(G, 0, 2 * (size_t)s * n * sizeof(z128), st));
+    int nb = 0;
+    KL(F_MDOT, 16.0 * (sd + 1) * nd, 4.0 * (sd + 1) * nd, nb = launch_idr_pdots(s, true, P, r, n, part, st, c->one));
+    KL(F_MISC, 0, 0, launch_idr_scalar(ic, part, nb, 5, 0, tol, maxit, c->hist, c->hist_len, st));
+    CU(cudaMemcpyAsync(c->hidr, ic, sizeof(IdrCtl), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    relres = c->hidr->relres;
+    if (c->hidr->active == 0) {
+      status = c->hidr->flag == 1 ? HELM_OK : HELM_ENUMERIC;
+      break;
+    }
+    if (c->hidr->iters >= maxit) { status = HELM_ENOCONV; break; }
+    int step = 0;
+    bool stop = false;
+    auto lagged = [&](void) -> helm_status {
+      const int slot = step % ring;
+      CU(cudaMemcpyAsync(c->hflags + slot, act, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CU(cudaEventRecord(c->ev[step % c->nev], st));
+      if (step >= FLAG_LAG) {
+        CU(cudaEventSynchronize(c->ev[(step - FLAG_LAG) % c->nev]));
+        if (c->hflags[(step - FLAG_LAG) % ring] == 0) stop = true;
+      }
+      ++step;
+      return HELM_OK;
+    };
+    while (!stop) {
+      for (int k = 0; k < s && !stop; ++k) {
+        c->cur_j = -1;
+        const double wk = (double)(s - k);
+        KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, 0, 0, k, tol, maxit, c->hist, c->hist_len, st));
+        KL(F_GS_UPDATE, 16.0 * (wk + 2) * nd, 8.0 * wk * nd, launch_idr_v(ic, k, r, G, n, v, st));
+        if (mixed) run_cycle<float, double, double>(c, v, vh, st, act);
+        else run_cycle<double, double, double>(c, v, vh, st, act);
+        KL(F_GS_UPDATE, 16.0 * (wk + 2) * nd, 8.0 * (wk + 1) * nd, launch_idr_u(ic, k, vh, U, n, st));
+        KL(F_APPLY, 40.0 * nd, 22.0 * nd,
+           (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, U + (size_t)k * n, G + (size_t)k * n, st, act)));
+        KL(F_MDOT, 16.0 * (sd + 1) * nd, 8.0 * sd * nd,
+           nb = launch_idr_pdots(s, false, P, G + (size_t)k * n, n, part, st, act));
+        KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, nb, 1, k, tol, maxit, c->hist, c->hist_len, st));
+        KL(F_GS_UPDATE, 16.0 * (2.0 * k + 8) * nd, (16.0 * k + 20) * nd,
+           nb = launch_idr_update(ic, k, G, U, r, x, n, part, st));
+        KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, nb, 2, k, tol, maxit, c->hist, c->hist_len, st));
+        TRY(check_launch(c, "IDR(s) step"));
+        TRY(lagged());
+      }
+      if (stop) break;
+      // dimension reduction
+      if (mixed) run_cycle<float, double, double>(c, r, vh, st, act);
+      else run_cycle<double, double, double>(c, r, vh, st, act);
+      KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, vh, t, st, act)));
+      KL(F_MDOT, 32.0 * nd, 12.0 * nd, nb = launch_dots2(t, r, t, t, n, part, st, act));
+      KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, nb, 3, 0, tol, maxit, c->hist, c->hist_len, st));
+      KL(F_GS_UPDATE, 16.0 * (sd + 6) * nd, (8.0 * sd + 20) * nd,
+         nb = launch_idr_xr(s, ic, P, r, t, x, vh, n, part, st));
+      KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, nb, 4, 0, tol, maxit, c->hist, c->hist_len, st));
+      TRY(check_launch(c, "IDR(s) dimension reduction"));
+      TRY(lagged());
+    }
+    CU(cudaMemcpyAsync(c->hidr, ic, sizeof(IdrCtl), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    prof_flush(c, -1);
+    const IdrCtl h = *c->hidr;
+    // explicit residual
+    KL(F_RESID, 56.0 * nd, 24.0 * nd, (launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, r, st, c->one)));
+    norm_into(c, r, &ic->relres, st, c->one);
+    double rn = 0.0;
+    CU(cudaMemcpyAsync(&rn, &ic->relres, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    relres = rn / h.bnorm;
+    if (relres <= tol) { status = HELM_OK; break; }
+    if (h.flag == 2 || !(relres == relres)) { status = HELM_ENUMERIC; break; }
+    if (h.iters >= maxit) { status = HELM_ENOCONV; break; }
+    ++restarts;  // the recursion met tol but the explicit residual did not: restart from it
+    h0.iters = h.iters;
+    h0.bnorm = h.bnorm;
+    CU(cudaMemcpyAsync(ic, &h0, sizeof(IdrCtl), cudaMemcpyHostToDevice, st));
+  }
+  CU(cudaMemcpyAsync(c->hidr, ic, sizeof(IdrCtl), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (info) {
+    info->iterations = c->hidr->iters;
+    info->restarts = restarts;
+    info->rel_residual = relres;
+  }
+  return status;
+}
+
 // The configured outer Krylov method on device-resident vectors.
 helm_status krylov_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* info, cudaStream_t st) {
+  if (c->p.krylov == HELM_IDRS) return idrs_device(c, b, x, info, st);
   return c->p.krylov == HELM_BICGSTAB ? bicgstab_device(c, b, x, info, st) : gmres_device(c, b, x, info, st);
 }
 
@@ -980,6 +1122,7 @@ void helm_default_params(helm_params* p) {
   p->orth = HELM_ORTH_FP64;
   p->reorth = HELM_REORTH_SELECTIVE;
   p->cycle = HELM_CYCLE_V;
+  p->idr_kappa = 0.7;
 }
 
 const char* helm_last_error(const helm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
@@ -1016,6 +1159,7 @@ helm_status helm_destroy(helm_ctx* ctx) {
   for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
   for (void* q : ctx->allocs) cudaFree(q);
   if (ctx->hflags) cudaFreeHost(ctx->hflags);
+  if (ctx->hidr) cudaFreeHost(ctx->hidr);
   if (ctx->hctl) cudaFreeHost(ctx->hctl);
   if (ctx->hreorth_log) cudaFreeHost(ctx->hreorth_log);
   if (ctx->bw.hany) cudaFreeHost(ctx->bw.hany);
@@ -1168,7 +1312,8 @@ helm_status helm_create(int n1, int n2, int n3, double h, const double* k2, helm
   if (P.restart < 1 || P.restart > MAX_BASIS - 1) return fail(nullptr, HELM_EINVAL, "restart must lie in 1..%d", MAX_BASIS - 1);
   if (!(P.tol > 0.0)) return fail(nullptr, HELM_EINVAL, "tol must be positive");
   if (P.max_iter < 1) return fail(nullptr, HELM_EINVAL, "max_iter must be >= 1");
-  if (P.krylov != HELM_GMRES && P.krylov != HELM_FGMRES && P.krylov != HELM_BICGSTAB)
+  if (!(P.idr_kappa >= 0.0 && P.idr_kappa < 1.0)) return fail(nullptr, HELM_EINVAL, "idr_kappa must lie in [0, 1)");
+  if (P.krylov != HELM_GMRES && P.krylov != HELM_FGMRES && P.krylov != HELM_BICGSTAB && P.krylov != HELM_IDRS)
     return fail(nullptr, HELM_EINVAL, "unknown krylov %d", P.krylov);
   if (P.precision != HELM_PREC_FP64 && P.precision != HELM_PREC_MIXED) return fail(nullptr, HELM_EINVAL, "unknown precision %d", P.precision);
   if (!std::isfinite(P.beta1) || !std::isfinite(P.beta2)) return fail(nullptr, HELM_EINVAL, "beta1, beta2 must be finite");
@@ -1436,6 +1581,32 @@ helm_status helm_solve_batched(helm_ctx* c, int nrhs, const void* B, void* X, he
   if (worst == HELM_ENOCONV) fail(c, worst, "some right-hand sides reached max_iter (%d)", c->p.max_iter);
   if (worst == HELM_ENUMERIC) fail(c, worst, "non-finite residual in a batched solve");
   return worst;
+}
+
+helm_status helm_set_shadow_space(helm_ctx* c, int s, const void* P, void* stream) {
+  if (!c) return HELM_EINVAL;
+  if (s < 1 || s > IDR_SMAX) return fail(c, HELM_EINVAL, "IDR(s): s = %d outside 1..%d", s, IDR_SMAX);
+  if (!P) return fail(c, HELM_EINVAL, "P is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = c->n0;
+  if (s > c->idr_s) {
+    CU(cudaStreamSynchronize(st));
+    dfree(c, c->idrP);
+    dfree(c, c->idrW);
+    c->idrP = c->idrW = nullptr;
+    c->idr_s = 0;
+    TRY(dalloc(c, &c->idrP, (size_t)s * n));
+    TRY(dalloc(c, &c->idrW, (2 * (size_t)s + 4) * n));
+  }
+  if (!c->idr) {
+    TRY(dalloc(c, &c->idr_part, (size_t)(IDR_SMAX + 1) * RED_STRIDE));
+    TRY(dalloc(c, &c->idr, 1));
+    CU(cudaHostAlloc((void**)&c->hidr, sizeof(IdrCtl), cudaHostAllocDefault));
+  }
+  CU(cudaMemcpyAsync(c->idrP, P, (size_t)s * n * sizeof(z128), cudaMemcpyDefault, st));
+  CU(cudaStreamSynchronize(st));
+  c->idr_s = s;
+  return HELM_OK;
 }
 
 helm_status helm_solve(helm_ctx* c, const void* b, void* x, helm_solve_info* info, void* stream) {

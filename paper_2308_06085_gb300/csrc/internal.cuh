@@ -97,6 +97,18 @@ void launch_set_active(KrylovCtl* ctl, int v, cudaStream_t st);
 // x += z
 void launch_axpy1(const z128* z, z128* x, size_t n, cudaStream_t st);
 
+// ---- IDR(s) (idrs.cu); part holds RED_STRIDE-strided slots of complex partial sums ----
+void launch_idr_v(const IdrCtl* ic, int k, const z128* r, const z128* G, size_t n, z128* v, cudaStream_t st);
+void launch_idr_u(const IdrCtl* ic, int k, const z128* vh, z128* U, size_t n, cudaStream_t st);
+int launch_idr_pdots(int s, bool with_norm, const z128* P, const z128* y, size_t n, z128* part, cudaStream_t st,
+                     const int* active);
+int launch_idr_update(const IdrCtl* ic, int k, z128* G, z128* U, z128* r, z128* x, size_t n, z128* part,
+                      cudaStream_t st);
+int launch_idr_xr(int s, const IdrCtl* ic, const z128* P, z128* r, const z128* t, z128* x, const z128* vh, size_t n,
+                  z128* part, cudaStream_t st);
+void launch_idr_scalar(IdrCtl* ic, const z128* part, int nb, int stage, int k, double tol, int max_iter, double* hist,
+                       int hist_len, cudaStream_t st);
+
 // ---- Bi-CGSTAB (bicgstab.cu) ----
 // part slot 0 = conj(a).b, slot 1 = conj(c).d (c may be NULL); returns the number of partials
 int launch_dots2(const z128* a, const z128* b, const z128* c, const z128* d, size_t n, z128* part, cudaStream_t st,

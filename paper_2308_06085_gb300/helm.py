@@ -24,7 +24,7 @@ STATUS = {0: "HELM_OK", 1: "HELM_EINVAL", 2: "HELM_ENOMEM", 3: "HELM_ECUDA", 4: 
 DIRICHLET, SOMMERFELD = 0, 1
 C128, C64 = 0, 1
 OP_A, OP_M = 0, 1
-GMRES, FGMRES, BICGSTAB = 0, 1, 2
+GMRES, FGMRES, BICGSTAB, IDRS = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
 ORTH_FP64, ORTH_DF = 0, 1
 REORTH_ALWAYS, REORTH_SELECTIVE = 0, 1
@@ -40,7 +40,7 @@ class Params(C.Structure):
     _fields_ = [("beta1", C.c_double), ("beta2", C.c_double), ("omega", C.c_double), ("nu1", C.c_int),
                 ("nu2", C.c_int), ("coarsest_n", C.c_int), ("krylov", C.c_int), ("restart", C.c_int),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int), ("orth", C.c_int),
-                ("reorth", C.c_int), ("cycle", C.c_int)]
+                ("reorth", C.c_int), ("cycle", C.c_int), ("idr_kappa", C.c_double)]
 
 
 class KernelStat(C.Structure):
@@ -77,6 +77,8 @@ def lib():
     L.helm_apply.argtypes = [vp, i, i, vp, vp, vp]
     L.cslp_vcycle.argtypes = [vp, i, vp, vp, vp]
     L.cslp_fcycle.argtypes = [vp, i, vp, vp, vp]
+    L.helm_set_shadow_space.argtypes = [vp, i, vp, vp]
+    L.helm_set_shadow_space.restype = i
     L.cslp_fcycle.restype = i
     L.helm_vcycle_stage.argtypes = [vp, i, i, i, vp, vp, vp, vp]
     L.helm_rhs_point.argtypes = [vp, i, C.POINTER(i), vp, vp]
@@ -143,7 +145,7 @@ class Solver:
 
     def __init__(self, n, h, k2, bc=SOMMERFELD, *, beta1=1.0, beta2=-0.5, omega=0.8, coarsest_n=4,
                  krylov="gmres", restart=30, tol=1e-6, max_iter=2000, precision="fp64", orth=None,
-                 reorth=None, cycle="v", device=None):
+                 reorth=None, cycle="v", idr_s=4, idr_kappa=0.7, shadow=None, device=None):
         n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(int(x) for x in n)
         self.n = (n1, n2, n3)
         self.h = float(h)
@@ -157,7 +159,8 @@ class Solver:
         k2t = k2t.to(self.device).contiguous()
         p = default_params()
         p.beta1, p.beta2, p.omega, p.coarsest_n = beta1, beta2, omega, coarsest_n
-        p.krylov = {"gmres": GMRES, "fgmres": FGMRES, "bicgstab": BICGSTAB}[krylov]
+        p.krylov = {"gmres": GMRES, "fgmres": FGMRES, "bicgstab": BICGSTAB, "idrs": IDRS}[krylov]
+        p.idr_kappa = idr_kappa
         p.restart, p.tol, p.max_iter = restart, tol, max_iter
         p.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
         if orth is not None:
@@ -172,6 +175,14 @@ class Solver:
         if st != OK:
             raise HelmError(st, lib().helm_last_error(None).decode())
         self._ctx = ctx
+        if krylov == "idrs":
+            # IDR(s) draws its shadow space at random (Sec. 3.1); by default the seeded draw of
+            # the synthetic-input module, so runs are repeatable
+            if shadow is None:
+                from . import inputs
+
+                shadow = inputs.shadow_space(self.shape, idr_s)
+            self.set_shadow_space(shadow)
 
     # -- housekeeping -----------------------------------------------------------------
     def close(self):
@@ -225,6 +236,13 @@ class Solver:
         z = torch.empty_like(r) if out is None else out
         self._check(lib().cslp_vcycle(self._ctx, _DT[r.dtype], _ptr(r), _ptr(z), _stream()))
         return z
+
+    def set_shadow_space(self, P):
+        """The s shadow vectors of IDR(s), shaped (s,) + grid shape, complex."""
+        P = torch.as_tensor(P, dtype=torch.complex128).to(self.device).contiguous()
+        if P.dim() != 4 or tuple(P.shape[1:]) != self.shape:
+            raise ValueError(f"shadow space must be shaped (s,) + {self.shape}")
+        self._check(lib().helm_set_shadow_space(self._ctx, P.shape[0], _ptr(P), _stream()))
 
     def fcycle(self, r, out=None):
         r = self._vec(r)
