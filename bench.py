@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--n", type=int, default=128, help="intervals per direction of the wedge workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", type=int, default=2,
-                    help="0: headline only; 1: + mixed precision and n = 256; 2: + batched and adjoint workloads")
+                    help="0: headline only; 1: + precision, Krylov and cycle variants at n = 128 and 256; "
+                         "2: + batched and adjoint workloads; 3: + the CSLP shift sweep (beta2 x V/F-cycle)")
     ap.add_argument("--orth", choices=["fp64", "df"], default="fp64",
                     help="Gram-Schmidt arithmetic: native FP64 or double-float FP32 pairs")
     ap.add_argument("--reorth", choices=["selective", "always"], default="selective",
@@ -353,7 +354,8 @@ def end_to_end(torch, s, b, steps):
 
 def run_variants(torch, helm, inputs, args):
     out = {}
-    for name, n, prec, krylov, orth, cycle in [
+    for name, n, prec, krylov, orth, cycle, *nog in [
+            ("wedge_n128_fp64_nographs", 128, "fp64", "gmres", args.orth, "v", "plain launches"),
             ("wedge_n128_mixed", 128, "mixed", "fgmres", args.orth, "v"),
             ("wedge_n128_mixed_orth_df", 128, "mixed", "fgmres", "df", "v"),
             ("wedge_n128_fp64_orth_df", 128, "fp64", "gmres", "df", "v"),
@@ -363,6 +365,8 @@ def run_variants(torch, helm, inputs, args):
             ("wedge_n128_mixed_bicgstab", 128, "mixed", "bicgstab", args.orth, "v"),
             ("wedge_n128_fp64_idr4", 128, "fp64", "idrs", args.orth, "v"),
             ("wedge_n128_mixed_idr4", 128, "mixed", "idrs", args.orth, "v"),
+            ("wedge_n128_fp64_idr4_fcycle", 128, "fp64", "idrs", args.orth, "f"),
+            ("wedge_n128_mixed_idr4_fcycle", 128, "mixed", "idrs", args.orth, "f"),
             ("mixed_n256_fp64", 256, "fp64", "gmres", args.orth, "v"),
             ("mixed_n256_mixed", 256, "mixed", "fgmres", args.orth, "v"),
             ("mixed_n256_mixed_orth_df", 256, "mixed", "fgmres", "df", "v"),
@@ -370,7 +374,7 @@ def run_variants(torch, helm, inputs, args):
             ("mixed_n256_mixed_idr4", 256, "mixed", "idrs", args.orth, "v")]:
         w = inputs.workload("mixed" if n == 256 else "wedge", n)
         s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov=krylov, precision=prec, orth=orth,
-                        reorth=args.reorth, cycle=cycle, max_iter=8000)
+                        reorth=args.reorth, cycle=cycle, max_iter=8000, graphs=not nog)
         b = s.rhs_point(w["sources"])
         s.solve(b)
         ms, infos, _ = time_solves(torch, s, b, 2)
@@ -379,10 +383,65 @@ def run_variants(torch, helm, inputs, args):
         s.close()
         del s
         torch.cuda.empty_cache()
+    out.update(run_closed_off_table1(torch, helm, inputs))
+    if args.variants >= 3:
+        out.update(run_shift_sweep(torch, helm, inputs, args))
     if args.variants >= 2:
         out.update(run_batched_variant(torch, helm, inputs))
         out.update(run_batched_variant(torch, helm, inputs, orth="df"))
         out.update(run_adjoint_variant(torch, helm, inputs))
+    return out
+
+
+def run_closed_off_table1(torch, helm, inputs):
+    """The closed-off problem of Table 1 (Sec. 5.1.3): 65^3 nodes (n = 64, Dirichlet), k = 40,
+    coarsest grid 17^3 nodes (the paper's 17-node rule, coarsest_n = 16), FP64.  The paper
+    prints #Matvec 145 (left-preconditioned GMRES), 359-407 (Bi-CGSTAB), 192-211 (IDR(4)).
+    The GPU runs GMRES(200) (no restart is reached) preconditioned from the left with the
+    paper's stopping rule and from the right, and Bi-CGSTAB and IDR(4) on the true residual."""
+    import numpy as np
+
+    n, k = 64, 40.0
+    shape = inputs.unknown_shape(n, helm.DIRICHLET)
+    k2 = np.full(shape, k * k)
+    b = torch.from_numpy(inputs.closed_off_rhs(n, k)).cuda()
+    out = {}
+    for krylov, side, restart, paper in (("gmres", "left", 200, [145]), ("gmres", "right", 200, [145]),
+                                         ("bicgstab", "right", 30, [359, 359, 403, 407]),
+                                         ("idrs", "right", 30, [192, 211, 192, 201])):
+        s = helm.Solver(n, 1.0 / n, k2, helm.DIRICHLET, coarsest_n=16, krylov=krylov, restart=restart, max_iter=3000,
+                        side=side)
+        s.solve(b)
+        ms, infos, _ = time_solves(torch, s, b, 2)
+        out[f"closed_off_n64_k40_{krylov}" + ("_left" if side == "left" else "")] = {"ms": ms, "iterations": infos[-1]["iterations"],
+                                              "rel_residual": infos[-1]["rel_residual"],
+                                              "paper_matvec_table1": paper, "unknowns": (n - 1) ** 3}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_shift_sweep(torch, helm, inputs, args):
+    """Sec. 5.1.4: the CSLP shift beta2 in [-1, -0.5] against V- and F-cycle preconditioning, on
+    the wedge at n = 128 and 256 (complex64 cycle, FP64 FGMRES(30) with double-float
+    Gram-Schmidt), one timed solve each after a warm-up solve."""
+    out = {}
+    for n in (128, 256):
+        w = inputs.workload("mixed" if n == 256 else "wedge", n)
+        for beta2 in (-0.5, -0.75, -1.0):
+            for cycle in ("v", "f"):
+                s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov="fgmres", precision="mixed",
+                                orth="df", beta2=beta2, cycle=cycle, max_iter=3000)
+                b = s.rhs_point(w["sources"])
+                s.solve(b)
+                ms, infos, _ = time_solves(torch, s, b, 1)
+                out[f"shift_n{n}_beta2_{-beta2:g}_{cycle}cycle"] = {
+                    "ms": ms, "iterations": infos[-1]["iterations"], "rel_residual": infos[-1]["rel_residual"],
+                    "status": infos[-1]["status"]}
+                s.close()
+                del s
+                torch.cuda.empty_cache()
     return out
 
 

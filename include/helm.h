@@ -64,6 +64,7 @@ typedef enum { HELM_PREC_FP64 = 0, HELM_PREC_MIXED = 1 } helm_precision;
 typedef enum { HELM_ORTH_FP64 = 0, HELM_ORTH_DF = 1 } helm_orth;
 typedef enum { HELM_REORTH_ALWAYS = 0, HELM_REORTH_SELECTIVE = 1 } helm_reorth;
 typedef enum { HELM_CYCLE_V = 0, HELM_CYCLE_F = 1 } helm_cycle;
+typedef enum { HELM_SIDE_RIGHT = 0, HELM_SIDE_LEFT = 1 } helm_side;
 
 /* Solver parameters (Sec. 3.3-3.4 and Sec. 5).  helm_default_params fills the paper's
  * values: beta1 = 1, beta2 = -0.5 (M = -Lap - (beta1 - beta2 i) k^2, Sec. 3.3 Eq.
@@ -104,6 +105,21 @@ typedef struct {
                        and is enlarged so that the cosine of the angle between r and
                        A M^{-1} r is at least idr_kappa when it is smaller; 0 keeps the
                        minimal-residual omega.  Default 0.7, in [0, 1). */
+  int graphs;       /* 1 (default): each solver step (an Arnoldi column of a full-length GMRES
+                       cycle, a Bi-CGSTAB step, an IDR(s) step) is captured once into a CUDA graph
+                       and replayed, one launch instead of 30-70; 0: plain launches.  Graphs are
+                       bypassed while helm_profile is on.  Steps that write x are keyed by the x
+                       pointer, so a solve into a new buffer captures its steps again. */
+  int autotune;     /* 1 (default): helm_create times every stencil, smoothing and transfer
+                       kernel of every level over launch shapes (rows of x-lines per CTA x CTA
+                       count) and keeps the fastest, and helm_solve_batched does the same for
+                       its width on first use; 0: the fixed default shape.  Results do not
+                       depend on the shape (no reductions in these kernels). */
+  int side;         /* helm_side: right preconditioning (default; every solver), or the paper's
+                       left-preconditioned GMRES (Sec. 3.2) with its stopping rule
+                       ||M^{-1}(b - A x)|| / ||M^{-1} b|| <= tol (Sec. 5), for which
+                       helm_solve_info.rel_residual reports that preconditioned quantity.  Left
+                       needs krylov = HELM_GMRES with FP64 precision and FP64 orth. */
 } helm_params;
 
 /* Per-solve report (host struct). */

@@ -143,8 +143,18 @@ struct Grid {
   // innermost (element index = node index * nb + rhs); per-node arrays (k^2, tables) stay
   // one value per node
   int nb = 1;
+  // launch shape per kernel family (TILE_*) and arithmetic (slot = family + 4 for FP32): rows
+  // of x-lines per CTA and the CTA count that sets the z-chunk each CTA streams through.  0
+  // selects the default (8 rows, 8 CTAs per SM); helm_create's autotuner fills them.
+  int tile_ty[8] = {};
+  int tile_ctas[8] = {};
   __host__ __device__ size_t npts() const { return (size_t)N1 * N2 * N3; }
 };
+
+// Kernel families with their own launch shape (Grid::tile_*).
+enum { TILE_STENCIL = 0, TILE_SMOOTH0 = 1, TILE_RESTRICT = 2, TILE_PROLONG = 3 };
+template <typename R>
+constexpr int tile_slot(int fam) { return fam + (sizeof(R) == 4 ? 4 : 0); }
 
 template <typename R>
 __device__ __forceinline__ const R* grid_sqk(const Grid& g);

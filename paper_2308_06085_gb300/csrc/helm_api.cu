@@ -88,6 +88,11 @@ struct Prof {
 // wider batch is asked for).
 struct BatchWS {
   int nb = 0;
+  // tuned launch shapes per batch width 2^t: the V-cycle grids of every level and the FP64
+  // finest-level operator
+  bool tuned[6] = {};
+  int tty[6][MAX_LEVELS][8] = {}, tct[6][MAX_LEVELS][8] = {};
+  int g0ty[6][8] = {}, g0ct[6][8] = {};
   z128 *V = nullptr, *Z64 = nullptr, *w = nullptr, *r = nullptr, *Bt = nullptr, *Xt = nullptr;
   z64* Z32 = nullptr;
   zdf* wdf = nullptr;       // Arnoldi vector, double-float Gram-Schmidt
@@ -162,6 +167,16 @@ struct helm_ctx {
   BatchWS bw;
   BicgCtl* bicg = nullptr;  // device
   BicgCtl* hbicg = nullptr; // pinned
+  // CUDA graphs of whole solver steps, captured on gstream on first use and replayed on the
+  // caller's stream (keyed by step kind, step index and a caller pointer the step writes)
+  struct GraphEnt {
+    int tag, j;
+    const void* p;
+    cudaGraphExec_t exec;
+    long long launches;
+  };
+  std::vector<GraphEnt> graphs;
+  cudaStream_t gstream = nullptr;
   // IDR(s): shadow space P (s vectors), work G, U (s each), r, v, vh, t; control block
   int idr_s = 0;
   z128* idrP = nullptr;
@@ -505,6 +520,154 @@ void norm_into(helm_ctx* c, const z128* x, double* out, cudaStream_t st, const i
   KL(F_REDUCE_NORM, 8.0 * nb, nb, launch_reduce_norm(c->partr, nb, out, st, active));
 }
 
+void clear_graphs(helm_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
+// Enqueue one solver step on `st`: replayed from a CUDA graph captured on first use when the
+// context runs with graphs and without per-kernel profiling, else launched kernel by kernel.
+// `enqueue(stream)` must only launch work on `stream` (no host waits, no allocation), and
+// everything it launches must depend only on (tag, j, p) and on the context's own buffers.
+template <typename Fn>
+helm_status graph_step(helm_ctx* c, int tag, int j, const void* p, cudaStream_t st, Fn&& enqueue) {
+  if (!c->p.graphs || c->prof.on) {
+    enqueue(st);
+    return HELM_OK;
+  }
+  for (auto& g : c->graphs)
+    if (g.tag == tag && g.j == j && g.p == p) {
+      CU(cudaGraphLaunch(g.exec, st));
+      c->prof.launches += g.launches;
+      return HELM_OK;
+    }
+  if (c->graphs.size() >= 512) clear_graphs(c);
+  if (!c->gstream) CU(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+  const long long l0 = c->prof.launches;
+  CU(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeRelaxed));
+  enqueue(c->gstream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->gstream, &g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, HELM_ECUDA, "stream capture of a solver step: %s", cudaGetErrorString(e));
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return fail(c, HELM_ECUDA, "graph instantiation: %s", cudaGetErrorString(ei));
+  const long long nl = c->prof.launches - l0;
+  c->graphs.push_back({tag, j, p, ex, nl});
+  CU(cudaGraphLaunch(ex, st));
+  return HELM_OK;
+}
+
+// ---- launch-shape autotuner -------------------------------------------------------------
+// For every level and kernel family, time each (rows per CTA, CTA count) candidate on the
+// level's own work vectors and keep the fastest.  Stencil, transfer and smoothing results do
+// not depend on the launch shape (no reductions), so tuning changes speed only.
+template <typename Fn>
+helm_status tune_slot(helm_ctx* c, Grid& g, int slot, cudaStream_t st, Fn&& run) {
+  static const int tys[] = {1, 2, 4, 8};
+  static const int per_sm[] = {2, 4, 8, 16, 32};
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bty = 0, bct = 0;
+  for (int ty : tys)
+    for (int m : per_sm) {
+      g.tile_ty[slot] = ty;
+      g.tile_ctas[slot] = 152 * m;
+      run(g);  // warm-up
+      float ms = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, st);
+        run(g);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms = std::min(ms, t);
+      }
+      if (ms < best) { best = ms; bty = ty; bct = 152 * m; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g.tile_ty[slot] = bty;
+  g.tile_ctas[slot] = bct;
+  return check_launch(c, "autotune");
+}
+
+// Tune the V-cycle kernels of arithmetic R on the levels lv[0..L) (grids are updated in place).
+template <typename R>
+helm_status tune_vlevels(helm_ctx* c, VLevel<R>* lv, int L, cudaStream_t st) {
+  const double sr = c->s_re, si = c->s_im, om = c->p.omega;
+  for (int l = 0; l < L; ++l) {
+    VLevel<R>& F = lv[l];
+    const size_t ne = F.g.npts() * F.g.nb;
+    CU(cudaMemsetAsync(F.U1, 0, ne * sizeof(cx<R>), st));
+    CU(cudaMemsetAsync(F.T, 0, ne * sizeof(cx<R>), st));
+    if (l == L - 1) break;  // the coarsest level runs the dense solve only
+    TRY(tune_slot(c, F.g, tile_slot<R>(TILE_STENCIL), st, [&](const Grid& g) {
+      launch_jacobi<R, R, R>(g, sr, si, om, F.k2, F.dinv, F.U1, F.U1, F.T, st, nullptr);
+    }));
+    TRY(tune_slot(c, F.g, tile_slot<R>(TILE_SMOOTH0), st, [&](const Grid& g) {
+      launch_smooth0<R, R>(g, sr, si, om, F.k2, F.dinv, F.U1, F.T, st, nullptr);
+    }));
+    VLevel<R>& C = lv[l + 1];
+    CU(cudaMemsetAsync(C.E, 0, C.g.npts() * C.g.nb * sizeof(cx<R>), st));
+    TRY(tune_slot(c, F.g, tile_slot<R>(TILE_PROLONG), st, [&](const Grid& g) {
+      launch_prolong_add<R>(g, C.g, F.U1, C.E, F.T, st, nullptr);
+    }));
+    TRY(tune_slot(c, C.g, tile_slot<R>(TILE_RESTRICT), st, [&](const Grid& g) {
+      launch_restrict<R>(F.g, g, F.T, C.B, st, nullptr);
+    }));
+  }
+  return HELM_OK;
+}
+
+// Tune the single-right-hand-side kernels: the V-cycle in the context's arithmetic on every
+// level, and the FP64 operator of the outer Krylov method on the finest level.
+helm_status autotune(helm_ctx* c, cudaStream_t st) {
+  const bool mixed = c->p.precision == HELM_PREC_MIXED;
+  const int L = c->nlev;
+  if (mixed) {
+    VLevel<float> lv[MAX_LEVELS];
+    for (int l = 0; l < L; ++l) {
+      Level& Lv = c->L[l];
+      lv[l] = VLevel<float>{Lv.g, Lv.k2f, nullptr, Lv.B32, Lv.U132, Lv.T32, Lv.E32};
+    }
+    TRY(tune_vlevels<float>(c, lv, L, st));
+    for (int l = 0; l < L; ++l) c->L[l].g = lv[l].g;
+  }
+  VLevel<double> lv[MAX_LEVELS];
+  for (int l = 0; l < L; ++l) {
+    Level& Lv = c->L[l];
+    lv[l] = VLevel<double>{Lv.g, Lv.k2, Lv.dinv, Lv.B64, Lv.U164, Lv.T64, Lv.E64};
+  }
+  if (!mixed) {
+    TRY(tune_vlevels<double>(c, lv, L, st));
+  } else {
+    // the finest FP64 operator only (A-products and residuals of the outer method)
+    Level& F = c->L[0];
+    const size_t n = F.g.npts();
+    CU(cudaMemsetAsync(F.U164, 0, n * sizeof(z128), st));
+    TRY(tune_slot(c, lv[0].g, tile_slot<double>(TILE_STENCIL), st, [&](const Grid& g) {
+      launch_resid<double, double, double, double>(g, 1.0, 0.0, F.k2, F.U164, F.U164, F.T64, st, nullptr);
+    }));
+  }
+  for (int l = 0; l < L; ++l)
+    for (int q = 0; q < 4; ++q) {
+      c->L[l].g.tile_ty[q] = lv[l].g.tile_ty[q];
+      c->L[l].g.tile_ctas[q] = lv[l].g.tile_ctas[q];
+    }
+  CU(cudaStreamSynchronize(st));
+  return HELM_OK;
+}
+
+enum { G_ARNOLDI = 1, G_BICG = 2, G_IDR = 3, G_IDR_DR = 4 };
+
 // GMRES(m) / FGMRES(m) on device-resident b and x.
 helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* info, cudaStream_t st) {
   const Level& F = c->L[0];
@@ -517,9 +680,22 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
   const int* act = &ctl->active;
   const bool df = c->p.orth == HELM_ORTH_DF;
   zdf* Vdf = reinterpret_cast<zdf*>(c->V);
+  // the paper's left preconditioning (Sec. 3.2): GMRES on M^{-1} A x = M^{-1} b, stopping on
+  // ||M^{-1}(b - A x)|| / ||M^{-1} b|| (Sec. 5); FP64 GMRES only (checked at creation)
+  const bool left = c->p.side == HELM_SIDE_LEFT;
+  auto residual = [&](void) {  // c->r = b - A x, or M^{-1}(b - A x) from the left
+    z128* dst = left ? c->zs : c->r;
+    KL(F_RESID, 56.0 * n, 24.0 * n, (launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, dst, st, c->one)));
+    if (left) run_cycle<double, double, double>(c, c->zs, c->r, st, c->one);
+  };
 
-  norm_into(c, b, &ctl->bnorm, st, c->one);
-  KL(F_RESID, 56.0 * n, 24.0 * n, (launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, c->r, st, c->one)));
+  if (left) {
+    run_cycle<double, double, double>(c, b, c->zs, st, c->one);
+    norm_into(c, c->zs, &ctl->bnorm, st, c->one);
+  } else {
+    norm_into(c, b, &ctl->bnorm, st, c->one);
+  }
+  residual();
   norm_into(c, c->r, &ctl->beta, st, c->one);
   CU(cudaMemcpyAsync(c->hctl, ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
@@ -548,64 +724,72 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
       KL(F_SCALE, 32.0 * n, 2.0 * n, launch_scale_inv(c->r, &ctl->beta, c->V, n, st, act));
     }
     for (int j = 0; j < jmax; ++j) {
-      z128* vj = c->V + (size_t)j * n;
-      z128* w = c->V + (size_t)(j + 1) * n;  // FP64 Gram-Schmidt works in place in V
-      zdf* wd = c->wdf;                      // double-float Gram-Schmidt works in wdf
       c->cur_j = j;
-      const double nd = (double)n, nv = j + 1;
-      if (mixed) {
-        z64* zj = c->Z32 + (size_t)j * n;
-        if (df) {
-          run_cycle<float, float, float>(c, c->vcur32, zj, st, act);
-          KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply_split<float>(F.g, 1.0, 0.0, F.k2, zj, wd, st, act)));
+      auto step = [&](cudaStream_t st) {
+        z128* vj = c->V + (size_t)j * n;
+        z128* w = c->V + (size_t)(j + 1) * n;  // FP64 Gram-Schmidt works in place in V
+        zdf* wd = c->wdf;                      // double-float Gram-Schmidt works in wdf
+        const double nd = (double)n, nv = j + 1;
+        if (mixed) {
+          z64* zj = c->Z32 + (size_t)j * n;
+          if (df) {
+            run_cycle<float, float, float>(c, c->vcur32, zj, st, act);
+            KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply_split<float>(F.g, 1.0, 0.0, F.k2, zj, wd, st, act)));
+          } else {
+            run_cycle<float, double, float>(c, vj, zj, st, act);
+            KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply<double, float, double>(F.g, 1.0, 0.0, F.k2, zj, w, st, act)));
+          }
+        } else if (left) {
+          KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, vj, c->zs, st, act)));
+          run_cycle<double, double, double>(c, c->zs, w, st, act);
         } else {
-          run_cycle<float, double, float>(c, vj, zj, st, act);
-          KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply<double, float, double>(F.g, 1.0, 0.0, F.k2, zj, w, st, act)));
+          z128* zj = flexible ? c->Z64 + (size_t)j * n : c->zs;
+          run_cycle<double, double, double>(c, df ? c->vcur64 : vj, zj, st, act);
+          if (df)
+            KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply_split<double>(F.g, 1.0, 0.0, F.k2, zj, wd, st, act)));
+          else
+            KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, zj, w, st, act)));
         }
-      } else {
-        z128* zj = flexible ? c->Z64 + (size_t)j * n : c->zs;
-        run_cycle<double, double, double>(c, df ? c->vcur64 : vj, zj, st, act);
-        if (df)
-          KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply_split<double>(F.g, 1.0, 0.0, F.k2, zj, wd, st, act)));
-        else
-          KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, zj, w, st, act)));
-      }
-      // classical Gram-Schmidt: first pass always; the second on every step (ALWAYS) or when
-      // the first pass's projection removed more than half of |w|^2 (SELECTIVE)
-      const bool sel = c->p.reorth == HELM_REORTH_SELECTIVE;
-      for (int pass = 0; pass < 2; ++pass) {
-        const int* a2 = (pass == 1 && sel) ? &ctl->pass2 : act;
-        c->cur_cond = (pass == 1 && sel) ? 1 : 0;
-        const int wn = (pass == 0 && sel) ? 1 : 0;
-        int nb = 0;
-        if (df)
-          KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nb = launch_mdot_df(Vdf, n, j + 1, wd, n, c->part, wn, st, a2));
-        else
-          KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nb = launch_mdot(c->V, n, j + 1, w, n, c->part, wn, st, a2));
-        KL(F_REDUCE_DOTS, 16.0 * nv * nb, 2.0 * nv * nb,
-           launch_reduce_dots(c->part, j + 1, nb, c->hpass, c->hacc, pass, wn ? j : -1, &ctl->pass2, c->reorth_log,
-                              st, a2));
-        if (df)
-          KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_gs_update_df(Vdf, n, j + 1, c->hpass, wd, n, st, a2));
-        else
-          KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_gs_update(c->V, n, j + 1, c->hpass, w, n, st, a2));
-      }
-      c->cur_cond = 0;
-      if (df) {
-        int nb = 0;
-        KL(F_NORM, 16.0 * nd, 4.0 * nd, nb = launch_norm2_part_df(wd, n, c->partr, st, act));
-        KL(F_REDUCE_NORM, 8.0 * nb, nb, launch_reduce_norm(c->partr, nb, c->hnorm, st, act));
-      } else {
-        norm_into(c, w, c->hnorm, st, act);
-      }
-      KL(F_GIVENS, 0, 0, launch_givens(ctl, c->H, m, j, jmax, c->hacc, c->hnorm, c->cs, c->sn, c->gv, tol, c->hist, c->hist_len, st));
-      if (df) {
-        zdf* vn = Vdf + (size_t)(j + 1) * n;
-        if (mixed) KL(F_SCALE, 40.0 * nd, 2.0 * nd, (launch_scale_df<zdf, float>(wd, c->hnorm, vn, c->vcur32, n, st, act)));
-        else KL(F_SCALE, 48.0 * nd, 2.0 * nd, (launch_scale_df<zdf, double>(wd, c->hnorm, vn, c->vcur64, n, st, act)));
-      } else {
-        KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_scale_inv(w, c->hnorm, w, n, st, act));
-      }
+        // classical Gram-Schmidt: first pass always; the second on every step (ALWAYS) or when
+        // the first pass's projection removed more than half of |w|^2 (SELECTIVE)
+        const bool sel = c->p.reorth == HELM_REORTH_SELECTIVE;
+        for (int pass = 0; pass < 2; ++pass) {
+          const int* a2 = (pass == 1 && sel) ? &ctl->pass2 : act;
+          c->cur_cond = (pass == 1 && sel) ? 1 : 0;
+          const int wn = (pass == 0 && sel) ? 1 : 0;
+          int nb = 0;
+          if (df)
+            KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nb = launch_mdot_df(Vdf, n, j + 1, wd, n, c->part, wn, st, a2));
+          else
+            KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nb = launch_mdot(c->V, n, j + 1, w, n, c->part, wn, st, a2));
+          KL(F_REDUCE_DOTS, 16.0 * nv * nb, 2.0 * nv * nb,
+             launch_reduce_dots(c->part, j + 1, nb, c->hpass, c->hacc, pass, wn ? j : -1, &ctl->pass2, c->reorth_log,
+                                st, a2));
+          if (df)
+            KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_gs_update_df(Vdf, n, j + 1, c->hpass, wd, n, st, a2));
+          else
+            KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_gs_update(c->V, n, j + 1, c->hpass, w, n, st, a2));
+        }
+        c->cur_cond = 0;
+        if (df) {
+          int nb = 0;
+          KL(F_NORM, 16.0 * nd, 4.0 * nd, nb = launch_norm2_part_df(wd, n, c->partr, st, act));
+          KL(F_REDUCE_NORM, 8.0 * nb, nb, launch_reduce_norm(c->partr, nb, c->hnorm, st, act));
+        } else {
+          norm_into(c, w, c->hnorm, st, act);
+        }
+        KL(F_GIVENS, 0, 0, launch_givens(ctl, c->H, m, j, jmax, c->hacc, c->hnorm, c->cs, c->sn, c->gv, tol, c->hist, c->hist_len, st));
+        if (df) {
+          zdf* vn = Vdf + (size_t)(j + 1) * n;
+          if (mixed) KL(F_SCALE, 40.0 * nd, 2.0 * nd, (launch_scale_df<zdf, float>(wd, c->hnorm, vn, c->vcur32, n, st, act)));
+          else KL(F_SCALE, 48.0 * nd, 2.0 * nd, (launch_scale_df<zdf, double>(wd, c->hnorm, vn, c->vcur64, n, st, act)));
+        } else {
+          KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_scale_inv(w, c->hnorm, w, n, st, act));
+        }
+};
+      // a graph per Arnoldi column, for full-length cycles (the Givens step knows jmax)
+      if (jmax == m) TRY(graph_step(c, G_ARNOLDI, j, nullptr, st, step));
+      else step(st);
       TRY(check_launch(c, "Arnoldi step"));
       CU(cudaMemcpyAsync(c->hflags + j, act, sizeof(int), cudaMemcpyDeviceToHost, st));
       CU(cudaEventRecord(c->ev[j % c->nev], st));
@@ -639,11 +823,15 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
           KL(F_SOLUPDATE, (16.0 * k + 16.0) * nd, 8.0 * k * nd, launch_combine_df(ctl, Vdf, n, c->y, c->r, n, st));
         else
           KL(F_SOLUPDATE, (16.0 * k + 16.0) * nd, 8.0 * k * nd, launch_combine(ctl, c->V, n, c->y, c->r, n, st));
-        run_cycle<double, double, double>(c, c->r, c->zs, st, c->one);
-        KL(F_SOLUPDATE, 48.0 * nd, 2.0 * nd, launch_axpy1(c->zs, x, n, st));
+        if (left) {
+          KL(F_SOLUPDATE, 48.0 * nd, 2.0 * nd, launch_axpy1(c->r, x, n, st));  // x += V y
+        } else {
+          run_cycle<double, double, double>(c, c->r, c->zs, st, c->one);
+          KL(F_SOLUPDATE, 48.0 * nd, 2.0 * nd, launch_axpy1(c->zs, x, n, st));
+        }
       }
     }
-    KL(F_RESID, 56.0 * n, 24.0 * n, (launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, c->r, st, c->one)));
+    residual();
     norm_into(c, c->r, &ctl->beta, st, c->one);
     TRY(check_launch(c, "solution update"));
     CU(cudaMemcpyAsync(c->hctl, ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, st));
@@ -775,6 +963,37 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
   for (int l = 0; l < c->nlev; ++l) {
     if (mixed) lv32[l] = batch_level<float>(c, l, nb);
     else lv64[l] = batch_level<double>(c, l, nb);
+  }
+  if (c->p.autotune) {
+    int t = 0;
+    while ((1 << t) < nb) ++t;
+    if (!W.tuned[t]) {
+      if (mixed) {
+        TRY(tune_vlevels<float>(c, lv32, c->nlev, st));
+        CU(cudaMemsetAsync(W.r, 0, ne * sizeof(z128), st));
+        TRY(tune_slot(c, g0, tile_slot<double>(TILE_STENCIL), st, [&](const Grid& g) {
+          launch_resid<double, double, double, double>(g, 1.0, 0.0, k2, W.r, W.r, W.V, st, nullptr);
+        }));
+      } else {
+        TRY(tune_vlevels<double>(c, lv64, c->nlev, st));
+        for (int q = 0; q < 8; ++q) {
+          g0.tile_ty[q] = lv64[0].g.tile_ty[q];
+          g0.tile_ctas[q] = lv64[0].g.tile_ctas[q];
+        }
+      }
+      for (int l = 0; l < c->nlev; ++l) {
+        const Grid& g = mixed ? lv32[l].g : lv64[l].g;
+        for (int q = 0; q < 8; ++q) { W.tty[t][l][q] = g.tile_ty[q]; W.tct[t][l][q] = g.tile_ctas[q]; }
+      }
+      for (int q = 0; q < 8; ++q) { W.g0ty[t][q] = g0.tile_ty[q]; W.g0ct[t][q] = g0.tile_ctas[q]; }
+      W.tuned[t] = true;
+    } else {
+      for (int l = 0; l < c->nlev; ++l) {
+        Grid& g = mixed ? lv32[l].g : lv64[l].g;
+        for (int q = 0; q < 8; ++q) { g.tile_ty[q] = W.tty[t][l][q]; g.tile_ctas[q] = W.tct[t][l][q]; }
+      }
+      for (int q = 0; q < 8; ++q) { g0.tile_ty[q] = W.g0ty[t][q]; g0.tile_ctas[q] = W.g0ct[t][q]; }
+    }
   }
   const double nd = (double)ne;
   int nblk = launch_bnorm2_part(W.Bt, ne, nb, W.partr, st, c->one);
@@ -919,22 +1138,25 @@ helm_status bicgstab_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info
     if (c->hbicg->iters >= maxit) { status = HELM_ENOCONV; break; }
     for (int step = 0;; ++step) {
       c->cur_j = -1;
-      KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 0, tol, maxit, c->hist, c->hist_len, st));
-      KL(F_GS_UPDATE, 48.0 * nd, 8.0 * nd, launch_bicg_p(r, p, v, bc, n, st));
-      if (mixed) run_cycle<float, double, double>(c, p, ph, st, act);
-      else run_cycle<double, double, double>(c, p, ph, st, act);
-      KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, ph, v, st, act)));
-      KL(F_MDOT, 32.0 * nd, 8.0 * nd, nb = launch_dots2(rh, v, nullptr, nullptr, n, c->part, st, act));
-      KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 1, tol, maxit, c->hist, c->hist_len, st));
-      KL(F_GS_UPDATE, 48.0 * nd, 8.0 * nd, nb = launch_bicg_s(r, v, s, bc, n, c->part, st));
-      KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 2, tol, maxit, c->hist, c->hist_len, st));
-      if (mixed) run_cycle<float, double, double>(c, s, sh, st, cont);
-      else run_cycle<double, double, double>(c, s, sh, st, cont);
-      KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, sh, t, st, cont)));
-      KL(F_MDOT, 48.0 * nd, 12.0 * nd, nb = launch_dots2(t, s, t, t, n, c->part, st, cont));
-      KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 3, tol, maxit, c->hist, c->hist_len, st));
-      KL(F_GS_UPDATE, 112.0 * nd, 20.0 * nd, nb = launch_bicg_xr(x, r, ph, sh, s, t, rh, bc, n, c->part, st));
-      KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 4, tol, maxit, c->hist, c->hist_len, st));
+      auto enq = [&](cudaStream_t st) {
+        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 0, tol, maxit, c->hist, c->hist_len, st));
+        KL(F_GS_UPDATE, 48.0 * nd, 8.0 * nd, launch_bicg_p(r, p, v, bc, n, st));
+        if (mixed) run_cycle<float, double, double>(c, p, ph, st, act);
+        else run_cycle<double, double, double>(c, p, ph, st, act);
+        KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, ph, v, st, act)));
+        KL(F_MDOT, 32.0 * nd, 8.0 * nd, nb = launch_dots2(rh, v, nullptr, nullptr, n, c->part, st, act));
+        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 1, tol, maxit, c->hist, c->hist_len, st));
+        KL(F_GS_UPDATE, 48.0 * nd, 8.0 * nd, nb = launch_bicg_s(r, v, s, bc, n, c->part, st));
+        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 2, tol, maxit, c->hist, c->hist_len, st));
+        if (mixed) run_cycle<float, double, double>(c, s, sh, st, cont);
+        else run_cycle<double, double, double>(c, s, sh, st, cont);
+        KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, sh, t, st, cont)));
+        KL(F_MDOT, 48.0 * nd, 12.0 * nd, nb = launch_dots2(t, s, t, t, n, c->part, st, cont));
+        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 3, tol, maxit, c->hist, c->hist_len, st));
+        KL(F_GS_UPDATE, 112.0 * nd, 20.0 * nd, nb = launch_bicg_xr(x, r, ph, sh, s, t, rh, bc, n, c->part, st));
+        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 4, tol, maxit, c->hist, c->hist_len, st));
+      };
+      TRY(graph_step(c, G_BICG, 0, x, st, enq));
       TRY(check_launch(c, "Bi-CGSTAB step"));
       const int slot = step % (c->m + FLAG_LAG + 1);
       CU(cudaMemcpyAsync(c->hflags + slot, act, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1035,32 +1257,38 @@ helm_status idrs_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* in
       for (int k = 0; k < s && !stop; ++k) {
         c->cur_j = -1;
         const double wk = (double)(s - k);
-        KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, 0, 0, k, tol, maxit, c->hist, c->hist_len, st));
-        KL(F_GS_UPDATE, 16.0 * (wk + 2) * nd, 8.0 * wk * nd, launch_idr_v(ic, k, r, G, n, v, st));
-        if (mixed) run_cycle<float, double, double>(c, v, vh, st, act);
-        else run_cycle<double, double, double>(c, v, vh, st, act);
-        KL(F_GS_UPDATE, 16.0 * (wk + 2) * nd, 8.0 * (wk + 1) * nd, launch_idr_u(ic, k, vh, U, n, st));
-        KL(F_APPLY, 40.0 * nd, 22.0 * nd,
-           (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, U + (size_t)k * n, G + (size_t)k * n, st, act)));
-        KL(F_MDOT, 16.0 * (sd + 1) * nd, 8.0 * sd * nd,
-           nb = launch_idr_pdots(s, false, P, G + (size_t)k * n, n, part, st, act));
-        KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, nb, 1, k, tol, maxit, c->hist, c->hist_len, st));
-        KL(F_GS_UPDATE, 16.0 * (2.0 * k + 8) * nd, (16.0 * k + 20) * nd,
-           nb = launch_idr_update(ic, k, G, U, r, x, n, part, st));
-        KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, nb, 2, k, tol, maxit, c->hist, c->hist_len, st));
+        auto enq = [&](cudaStream_t st) {
+          KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, 0, 0, k, tol, maxit, c->hist, c->hist_len, st));
+          KL(F_GS_UPDATE, 16.0 * (wk + 2) * nd, 8.0 * wk * nd, launch_idr_v(ic, k, r, G, n, v, st));
+          if (mixed) run_cycle<float, double, double>(c, v, vh, st, act);
+          else run_cycle<double, double, double>(c, v, vh, st, act);
+          KL(F_GS_UPDATE, 16.0 * (wk + 2) * nd, 8.0 * (wk + 1) * nd, launch_idr_u(ic, k, vh, U, n, st));
+          KL(F_APPLY, 40.0 * nd, 22.0 * nd,
+             (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, U + (size_t)k * n, G + (size_t)k * n, st, act)));
+          KL(F_MDOT, 16.0 * (sd + 1) * nd, 8.0 * sd * nd,
+             nb = launch_idr_pdots(s, false, P, G + (size_t)k * n, n, part, st, act));
+          KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, nb, 1, k, tol, maxit, c->hist, c->hist_len, st));
+          KL(F_GS_UPDATE, 16.0 * (2.0 * k + 8) * nd, (16.0 * k + 20) * nd,
+             nb = launch_idr_update(ic, k, G, U, r, x, n, part, st));
+          KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, nb, 2, k, tol, maxit, c->hist, c->hist_len, st));
+        };
+        TRY(graph_step(c, G_IDR, k, x, st, enq));
         TRY(check_launch(c, "IDR(s) step"));
         TRY(lagged());
       }
       if (stop) break;
       // dimension reduction
-      if (mixed) run_cycle<float, double, double>(c, r, vh, st, act);
-      else run_cycle<double, double, double>(c, r, vh, st, act);
-      KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, vh, t, st, act)));
-      KL(F_MDOT, 32.0 * nd, 12.0 * nd, nb = launch_dots2(t, r, t, t, n, part, st, act));
-      KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, nb, 3, 0, tol, maxit, c->hist, c->hist_len, st));
-      KL(F_GS_UPDATE, 16.0 * (sd + 6) * nd, (8.0 * sd + 20) * nd,
-         nb = launch_idr_xr(s, ic, P, r, t, x, vh, n, part, st));
-      KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, nb, 4, 0, tol, maxit, c->hist, c->hist_len, st));
+      auto enq_dr = [&](cudaStream_t st) {
+        if (mixed) run_cycle<float, double, double>(c, r, vh, st, act);
+        else run_cycle<double, double, double>(c, r, vh, st, act);
+        KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, vh, t, st, act)));
+        KL(F_MDOT, 32.0 * nd, 12.0 * nd, nb = launch_dots2(t, r, t, t, n, part, st, act));
+        KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, nb, 3, 0, tol, maxit, c->hist, c->hist_len, st));
+        KL(F_GS_UPDATE, 16.0 * (sd + 6) * nd, (8.0 * sd + 20) * nd,
+           nb = launch_idr_xr(s, ic, P, r, t, x, vh, n, part, st));
+        KL(F_GIVENS, 0, 0, launch_idr_scalar(ic, part, nb, 4, 0, tol, maxit, c->hist, c->hist_len, st));
+      };
+      TRY(graph_step(c, G_IDR_DR, 0, x, st, enq_dr));
       TRY(check_launch(c, "IDR(s) dimension reduction"));
       TRY(lagged());
     }
@@ -1123,6 +1351,9 @@ void helm_default_params(helm_params* p) {
   p->reorth = HELM_REORTH_SELECTIVE;
   p->cycle = HELM_CYCLE_V;
   p->idr_kappa = 0.7;
+  p->graphs = 1;
+  p->autotune = 1;
+  p->side = HELM_SIDE_RIGHT;
 }
 
 const char* helm_last_error(const helm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
@@ -1157,6 +1388,8 @@ helm_status helm_profile_read(helm_ctx* c, helm_kernel_stat* stats, int cap, int
 helm_status helm_destroy(helm_ctx* ctx) {
   if (!ctx) return HELM_OK;
   for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+  clear_graphs(ctx);
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   for (void* q : ctx->allocs) cudaFree(q);
   if (ctx->hflags) cudaFreeHost(ctx->hflags);
   if (ctx->hidr) cudaFreeHost(ctx->hidr);
@@ -1292,6 +1525,7 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
   c->nev = FLAG_LAG + 2;
   for (int i = 0; i < c->nev; ++i) CU(cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming));
   CU(cudaStreamSynchronize(st));
+  if (P.autotune) TRY(autotune(c, st));
   return HELM_OK;
 }
 
@@ -1313,6 +1547,10 @@ helm_status helm_create(int n1, int n2, int n3, double h, const double* k2, helm
   if (!(P.tol > 0.0)) return fail(nullptr, HELM_EINVAL, "tol must be positive");
   if (P.max_iter < 1) return fail(nullptr, HELM_EINVAL, "max_iter must be >= 1");
   if (!(P.idr_kappa >= 0.0 && P.idr_kappa < 1.0)) return fail(nullptr, HELM_EINVAL, "idr_kappa must lie in [0, 1)");
+  if (P.side != HELM_SIDE_RIGHT && P.side != HELM_SIDE_LEFT) return fail(nullptr, HELM_EINVAL, "unknown side %d", P.side);
+  if (P.side == HELM_SIDE_LEFT &&
+      (P.krylov != HELM_GMRES || P.precision != HELM_PREC_FP64 || P.orth != HELM_ORTH_FP64))
+    return fail(nullptr, HELM_EINVAL, "left preconditioning needs krylov = HELM_GMRES, FP64 precision and FP64 orth");
   if (P.krylov != HELM_GMRES && P.krylov != HELM_FGMRES && P.krylov != HELM_BICGSTAB && P.krylov != HELM_IDRS)
     return fail(nullptr, HELM_EINVAL, "unknown krylov %d", P.krylov);
   if (P.precision != HELM_PREC_FP64 && P.precision != HELM_PREC_MIXED) return fail(nullptr, HELM_EINVAL, "unknown precision %d", P.precision);
@@ -1589,6 +1827,8 @@ helm_status helm_set_shadow_space(helm_ctx* c, int s, const void* P, void* strea
   if (!P) return fail(c, HELM_EINVAL, "P is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t n = c->n0;
+  CU(cudaStreamSynchronize(st));
+  clear_graphs(c);  // captured IDR steps depend on s and on the workspace addresses
   if (s > c->idr_s) {
     CU(cudaStreamSynchronize(st));
     dfree(c, c->idrP);

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(TX* TY)
   const int nb = g.nb;
   const int f = blockIdx.x * TX + threadIdx.x;
   const int i = f / nb, r = f - (f / nb) * nb;
-  const int j = blockIdx.y * TY + threadIdx.y;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.N1 || j >= g.N2) return;
   const int k0 = blockIdx.z * zchunk;
   if (k0 >= g.N3) return;
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(TX* TY)
   const int nb = g.nb;
   const int f = blockIdx.x * TX + threadIdx.x;
   const int i = f / nb, r = f - (f / nb) * nb;
-  const int j = blockIdx.y * TY + threadIdx.y;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.N1 || j >= g.N2) return;
   const int k0 = blockIdx.z * zchunk;
   const int k1 = min(k0 + zchunk, g.N3);
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(TX* TY)
   const int nb = gc.nb;
   const int f = blockIdx.x * TX + threadIdx.x;
   const int I = f / nb, q = f - (f / nb) * nb;
-  const int J = blockIdx.y * TY + threadIdx.y;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= gc.N1 || J >= gc.N2) return;
   const int K0 = blockIdx.z * zchunk;
   const int K1 = min(K0 + zchunk, gc.N3);
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(TX* TY)
   const int nb = gf.nb;
   const int f = blockIdx.x * TX + threadIdx.x;
   const int i = f / nb, q = f - (f / nb) * nb;
-  const int j = blockIdx.y * TY + threadIdx.y;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= gf.N1 || j >= gf.N2) return;
   const int k0 = blockIdx.z * zchunk;
   const int k1 = min(k0 + zchunk, gf.N3);
@@ -315,14 +315,21 @@ __global__ void k_rhs_point(Grid g, int nsrc, const int* __restrict__ idx, doubl
   }
 }
 
-dim3 grid_for(const Grid& g, int& zchunk) {
-  const int bx = (g.N1 * g.nb + TX - 1) / TX, by = (g.N2 + TY - 1) / TY;
-  const int target = 152 * 8;
+// Launch shape of kernel family `fam` in arithmetic R on grid g: TX x ty threads per CTA
+// covering TX elements of an x-line by ty lines; CTAs along z split the N3 planes into
+// chunks so that about g's CTA target runs (8 per SM unless tuned).
+template <typename R>
+dim3 grid_for(const Grid& g, int fam, int& zchunk, dim3& blk) {
+  const int slot = tile_slot<R>(fam);
+  const int ty = g.tile_ty[slot] > 0 ? g.tile_ty[slot] : TY;
+  const int target = g.tile_ctas[slot] > 0 ? g.tile_ctas[slot] : 152 * 8;
+  const int bx = (g.N1 * g.nb + TX - 1) / TX, by = (g.N2 + ty - 1) / ty;
   int zsplit = target / (bx * by);
   if (zsplit < 1) zsplit = 1;
   if (zsplit > g.N3) zsplit = g.N3;
   zchunk = (g.N3 + zsplit - 1) / zsplit;
   const int bz = (g.N3 + zchunk - 1) / zchunk;
+  blk = dim3(TX, ty);
   return dim3(bx, by, bz);
 }
 
@@ -348,8 +355,8 @@ template <typename R, typename TU, typename TO>
 void launch_apply(const Grid& g, double s_re, double s_im, const R* k2, const cx<TU>* u, cx<TO>* v,
                   cudaStream_t st, const int* active) {
   int zc;
-  dim3 gr = grid_for(g, zc);
-  k_stencil<R, 0, false, TU, TU, TO><<<gr, dim3(TX, TY), 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr, u,
+  dim3 blk, gr = grid_for<R>(g, TILE_STENCIL, zc, blk);
+  k_stencil<R, 0, false, TU, TU, TO><<<gr, blk, 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr, u,
                                                                    nullptr, v, zc, active);
 }
 
@@ -357,8 +364,8 @@ template <typename TU>
 void launch_apply_split(const Grid& g, double s_re, double s_im, const double* k2, const cx<TU>* u, zdf* v,
                         cudaStream_t st, const int* active) {
   int zc;
-  dim3 gr = grid_for(g, zc);
-  k_stencil<double, 0, false, TU, TU, double, true><<<gr, dim3(TX, TY), 0, st>>>(
+  dim3 blk, gr = grid_for<double>(g, TILE_STENCIL, zc, blk);
+  k_stencil<double, 0, false, TU, TU, double, true><<<gr, blk, 0, st>>>(
       g, coef_for<double>(g.h, s_re, s_im, 0.0), k2, nullptr, u, nullptr, reinterpret_cast<z128*>(v), zc, active);
 }
 template void launch_apply_split<double>(const Grid&, double, double, const double*, const z128*, zdf*, cudaStream_t,
@@ -370,8 +377,8 @@ template <typename R, typename TU, typename TB, typename TO>
 void launch_resid(const Grid& g, double s_re, double s_im, const R* k2, const cx<TU>* u, const cx<TB>* b,
                   cx<TO>* out, cudaStream_t st, const int* active) {
   int zc;
-  dim3 gr = grid_for(g, zc);
-  k_stencil<R, 1, false, TU, TB, TO><<<gr, dim3(TX, TY), 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr,
+  dim3 blk, gr = grid_for<R>(g, TILE_STENCIL, zc, blk);
+  k_stencil<R, 1, false, TU, TB, TO><<<gr, blk, 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr,
                                                                    u, b, out, zc, active);
 }
 
@@ -379,39 +386,39 @@ template <typename R, typename TB, typename TO>
 void launch_jacobi(const Grid& g, double s_re, double s_im, double omega, const R* k2, const cx<R>* dinv,
                    const cx<R>* u, const cx<TB>* b, cx<TO>* out, cudaStream_t st, const int* active) {
   int zc;
-  dim3 gr = grid_for(g, zc);
+  dim3 blk, gr = grid_for<R>(g, TILE_STENCIL, zc, blk);
   OpCoef<R> c = coef_for<R>(g.h, s_re, s_im, omega);
   if (dinv)
-    k_stencil<R, 2, true, R, TB, TO><<<gr, dim3(TX, TY), 0, st>>>(g, c, k2, dinv, u, b, out, zc, active);
+    k_stencil<R, 2, true, R, TB, TO><<<gr, blk, 0, st>>>(g, c, k2, dinv, u, b, out, zc, active);
   else
-    k_stencil<R, 2, false, R, TB, TO><<<gr, dim3(TX, TY), 0, st>>>(g, c, k2, dinv, u, b, out, zc, active);
+    k_stencil<R, 2, false, R, TB, TO><<<gr, blk, 0, st>>>(g, c, k2, dinv, u, b, out, zc, active);
 }
 
 template <typename R, typename TB>
 void launch_smooth0(const Grid& g, double s_re, double s_im, double omega, const R* k2, const cx<R>* dinv,
                     const cx<TB>* b, cx<R>* out, cudaStream_t st, const int* active) {
   int zc;
-  dim3 gr = grid_for(g, zc);
+  dim3 blk, gr = grid_for<R>(g, TILE_SMOOTH0, zc, blk);
   OpCoef<R> c = coef_for<R>(g.h, s_re, s_im, omega);
   if (dinv)
-    k_smooth0<R, true, TB><<<gr, dim3(TX, TY), 0, st>>>(g, c, k2, dinv, b, out, zc, active);
+    k_smooth0<R, true, TB><<<gr, blk, 0, st>>>(g, c, k2, dinv, b, out, zc, active);
   else
-    k_smooth0<R, false, TB><<<gr, dim3(TX, TY), 0, st>>>(g, c, k2, dinv, b, out, zc, active);
+    k_smooth0<R, false, TB><<<gr, blk, 0, st>>>(g, c, k2, dinv, b, out, zc, active);
 }
 
 template <typename R>
 void launch_restrict(const Grid& gf, const Grid& gc, const cx<R>* r, cx<R>* out, cudaStream_t st, const int* active) {
   int zc;
-  dim3 gr = grid_for(gc, zc);
-  k_restrict<R><<<gr, dim3(TX, TY), 0, st>>>(gf, gc, r, out, zc, active);
+  dim3 blk, gr = grid_for<R>(gc, TILE_RESTRICT, zc, blk);
+  k_restrict<R><<<gr, blk, 0, st>>>(gf, gc, r, out, zc, active);
 }
 
 template <typename R>
 void launch_prolong_add(const Grid& gf, const Grid& gc, const cx<R>* u1, const cx<R>* e, cx<R>* out, cudaStream_t st,
                         const int* active) {
   int zc;
-  dim3 gr = grid_for(gf, zc);
-  k_prolong_add<R><<<gr, dim3(TX, TY), 0, st>>>(gf, gc, u1, e, out, zc, active);
+  dim3 blk, gr = grid_for<R>(gf, TILE_PROLONG, zc, blk);
+  k_prolong_add<R><<<gr, blk, 0, st>>>(gf, gc, u1, e, out, zc, active);
 }
 
 template <typename TI, typename TO>

@@ -121,6 +121,22 @@ def random_vector(shape, seed, dtype=np.complex128):
     return (re + 1j * im).astype(dtype)
 
 
+def closed_off_rhs(n, k):
+    """Right-hand side of the closed-off problem (Sec. 2.1) on the (n-1)^3 interior unknowns,
+    x1 fastest: the source f = (21 pi^2 - k^2) sin(pi x1) sin(2 pi x2) sin(4 pi x3) - k^2 of the
+    exact solution u = sin(pi x1) sin(2 pi x2) sin(4 pi x3) + 1, plus the Dirichlet data u = 1
+    moved to the right (1 / h^2 for every neighbour on the boundary)."""
+    h = 1.0 / n
+    x = np.arange(1, n) * h
+    f = ((21.0 * np.pi ** 2 - k * k) * np.sin(4 * np.pi * x)[:, None, None] * np.sin(2 * np.pi * x)[None, :, None]
+         * np.sin(np.pi * x)[None, None, :] - k * k)
+    edge = np.zeros(n - 1)
+    edge[0] += 1
+    edge[-1] += 1
+    nb = edge[:, None, None] + edge[None, :, None] + edge[None, None, :]
+    return (f + nb / (h * h)).astype(np.complex128)
+
+
 IDR_SEED = 2308060085 + 4
 
 

@@ -1,0 +1,57 @@
+"""CUDA-graph replay of solver steps (helm_params.graphs): a step captured once and replayed
+runs the same kernels with the same launch shapes and the same deterministic reductions, so a
+solve with graphs must equal the plain-launch solve bit for bit, on first use (capture) and on
+replay, for every Krylov method and precision mode, and into a second solution buffer (steps
+that write x are captured per buffer)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2308_06085_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+S = 1
+
+
+@pytest.fixture(scope="module")
+def helm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2308_06085_gb300 import helm as h
+
+    torch.cuda.set_device(0)
+    return h
+
+
+@pytest.mark.parametrize("krylov,precision,orth,cycle", [
+    ("gmres", "fp64", "fp64", "v"), ("fgmres", "mixed", "df", "v"), ("gmres", "fp64", "df", "f"),
+    ("bicgstab", "fp64", None, "v"), ("idrs", "fp64", None, "v"), ("idrs", "mixed", None, "f")])
+def test_graph_replay_is_bit_exact(helm, krylov, precision, orth, cycle):
+    w = I.workload("wedge", 32)
+    kw = dict(krylov=krylov, precision=precision, orth=orth, cycle=cycle, restart=12, max_iter=4000)
+    plain = helm.Solver(w["n"], w["h"], w["k2"], S, graphs=False, **kw)
+    graph = helm.Solver(w["n"], w["h"], w["k2"], S, graphs=True, **kw)
+    b = plain.rhs_point(w["sources"])
+    x0, i0 = plain.solve(b)
+    x1, i1 = graph.solve(b)                # first use: captures
+    x2, i2 = graph.solve(b)                # replay; steps that write x captured for the new buffer
+    x2b, i3 = graph.solve(b, torch.zeros_like(x2).copy_(x2).zero_())  # replay into another buffer
+    x4, i4 = graph.solve(b, x2.zero_())    # replay into the second solve's buffer
+    for xi, ii in ((x1, i1), (x2b, i3), (x4, i4)):
+        assert ii["status"] == 0 and ii["iterations"] == i0["iterations"], (ii, i0)
+        assert torch.equal(xi, x0)
+    assert i2["iterations"] == i0["iterations"]
+
+
+def test_graph_cycle_shorter_than_restart(helm):
+    """A cycle cut short by max_iter (jmax < m) runs its columns as plain launches."""
+    w = I.workload("wedge", 16)
+    kw = dict(krylov="gmres", restart=30, tol=1e-14, max_iter=35)
+    a = helm.Solver(w["n"], w["h"], w["k2"], S, graphs=False, **kw)
+    g = helm.Solver(w["n"], w["h"], w["k2"], S, graphs=True, **kw)
+    b = a.rhs_point(w["sources"])
+    xa, ia = a.solve(b)
+    xg, ig = g.solve(b)
+    assert ia["iterations"] == ig["iterations"] == 35
+    assert torch.equal(xa, xg)

@@ -378,3 +378,22 @@ def test_idrs_edge_cases(helm):
     assert ic["status"] == helm.ENOCONV and ic["iterations"] == 7
     with pytest.raises(helm.HelmError):
         s.set_shadow_space(I.shadow_space(w["k2"].shape, 9))
+
+
+@pytest.mark.parametrize("bc", [D, S])
+def test_left_preconditioned_gmres_vs_oracle(helm, bc):
+    """The paper's own GMRES (Sec. 3.2): left preconditioning with the preconditioned stopping
+    rule (Sec. 5).  Same iterates as the oracle's left mode: iterations within +-1, solution
+    within 1e-5, and the reported preconditioned relative residual below tol on both sides."""
+    w = I.workload("small") if bc == D else I.workload("wedge", 32)
+    s = helm.Solver(w["n"], w["h"], w["k2"], bc, krylov="gmres", side="left", restart=30)
+    o = oracle.Solver(w["n"], w["h"], bc, w["k2"])
+    b = s.rhs_point(w["sources"])
+    x, info = s.solve(b)
+    ro = o.gmres(b.cpu().numpy(), restart=30, tol=1e-6, left=True)
+    assert info["status"] == 0 and ro["status"] == 0
+    assert info["rel_residual"] <= 1e-6 and abs(info["rel_residual"] - ro["relres"]) <= 1e-3 * ro["relres"] + 1e-12
+    assert abs(info["iterations"] - ro["iters"]) <= 1, (info, ro["iters"])
+    assert rel(x.cpu().numpy(), ro["x"]) <= 1e-5
+    with pytest.raises(helm.HelmError):
+        helm.Solver(w["n"], w["h"], w["k2"], bc, krylov="fgmres", side="left")

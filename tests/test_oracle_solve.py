@@ -233,3 +233,13 @@ def test_idrs_finite_termination(nn, s, bound):
     assert r["iters"] <= bound
     if s == N:
         assert r["iters"] == N and r["history"][-2] > 1e-6
+
+
+def test_closed_off_rhs_generators_agree():
+    """The synthetic-input module's closed-off right-hand side (used by the benchmark) and the
+    oracle's own (used by the pins) are written independently; they must agree."""
+    for n, k in ((8, 5.0), (64, 40.0)):
+        a = I.closed_off_rhs(n, k)
+        b = oracle.rhs_closed_off(n, k)
+        assert a.shape == b.shape
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
