@@ -51,6 +51,9 @@ def parse():
                     help="Gram-Schmidt arithmetic: native FP64 or double-float FP32 pairs")
     ap.add_argument("--reorth", choices=["selective", "always"], default="selective",
                     help="second Gram-Schmidt pass on every step, or only when the first pass lost half of |w|")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="fp64: complex128 throughout (the benchmark); mixed: complex64 cycle under FP64 FGMRES(30)")
+    ap.add_argument("--cycle", choices=["v", "f"], default="v", help="multigrid cycle of the preconditioner")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel timed leg")
     return ap.parse_args()
@@ -167,10 +170,13 @@ def run_reference(args):
     return 0
 
 
-def workload_config(n):
+def workload_config(n, precision="fp64", cycle="v"):
+    outer = "FP64 right-preconditioned GMRES(30)" if precision == "fp64" else "FP64 FGMRES(30), complex64 cycle"
+    cyc = "V-cycle" if cycle == "v" else "F-cycle"
     return {"workload": f"wedge n={n} ({n + 1}^3 = {(n + 1) ** 3:,} unknowns), Sommerfeld, point source at top-face "
-                        f"centre, max kh 0.625, FP64 right-preconditioned GMRES(30) + 1 CSLP V-cycle, tol 1e-6",
-            "n": n, "unknowns": (n + 1) ** 3, "krylov": "GMRES(30)", "precision": "complex128",
+                        f"centre, max kh 0.625, {outer} + 1 CSLP {cyc}, tol 1e-6",
+            "n": n, "unknowns": (n + 1) ** 3, "krylov": "GMRES(30)" if precision == "fp64" else "FGMRES(30)",
+            "precision": "complex128" if precision == "fp64" else "complex64 cycle / complex128 outer",
             "beta": [1.0, -0.5], "omega": 0.8,
             "l2": "working set > L2: the Krylov basis alone is 31 x 34 MB = 1.06 GB, so every step streams from HBM"}
 
@@ -201,6 +207,15 @@ def ncu_traffic(kernel_name):
     except OSError:
         return None
     return k
+
+
+def max_over_ranks(value, dist, device):
+    """The largest per-rank value (the job's time is its slowest replica's)."""
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def time_solves(torch, s, b, steps, x=None):
@@ -242,8 +257,9 @@ def run_ours(args):
 
     n = args.n
     w = inputs.workload("wedge", n)
-    s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov="gmres", restart=30, tol=1e-6,
-                    orth=args.orth, reorth=args.reorth)
+    s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov="gmres" if args.precision == "fp64" else "fgmres",
+                    restart=30, tol=1e-6, orth=args.orth, reorth=args.reorth, precision=args.precision,
+                    cycle=args.cycle)
     b = s.rhs_point(w["sources"])
     for _ in range(args.warmup):
         _, info = s.solve(b)
@@ -258,9 +274,7 @@ def run_ours(args):
     _, launches = s.profile_read()
     clk = clocks.stop()
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
     iters = infos[-1]["iterations"]
     relres = infos[-1]["rel_residual"]
     # the same K solves again with per-kernel CUDA events (kernel roofline)
@@ -316,8 +330,9 @@ def run_ours(args):
 
     line = {
         "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(n),
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32 cycle / f64 outer",
+        "data": "synthetic", "config": workload_config(n, args.precision, args.cycle),
         "iterations": iters, "rel_residual": relres, "roofline": roof, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk, "ms_per_step_profiled": ms_prof, "kernels": kernels, "variants": variants,
     }
@@ -389,6 +404,7 @@ def run_variants(torch, helm, inputs, args):
     if args.variants >= 2:
         out.update(run_batched_variant(torch, helm, inputs))
         out.update(run_batched_variant(torch, helm, inputs, orth="df"))
+        out.update(run_batched_variant(torch, helm, inputs, orth="df", cycle="f"))
         out.update(run_adjoint_variant(torch, helm, inputs))
     return out
 
@@ -445,11 +461,12 @@ def run_shift_sweep(torch, helm, inputs, args):
     return out
 
 
-def run_batched_variant(torch, helm, inputs, orth="fp64"):
+def run_batched_variant(torch, helm, inputs, orth="fp64", cycle="v"):
     """32 point sources (4 x 8 grid in the plane x3 = 0.1) on the n = 128 wedge: one batched
     solve (complex64 V-cycle, FP64 FGMRES(30)) against the same 32 sources solved one by one."""
     w = inputs.workload("batched", 128)
-    s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov="fgmres", precision="mixed", orth=orth)
+    s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov="fgmres", precision="mixed", orth=orth,
+                    cycle=cycle)
     B = torch.stack([s.rhs_point([p]) for p in w["sources"]])
     s.solve_batched(B[:4])  # warm-up (allocates the 32-wide workspace on the next call)
     st = torch.cuda.current_stream()
@@ -470,7 +487,7 @@ def run_batched_variant(torch, helm, inputs, orth="fp64"):
     e1.record(st)
     torch.cuda.synchronize()
     ms_s = e0.elapsed_time(e1)
-    res = {"batched_n128_32src_mixed" + ("_orth_df" if orth == "df" else ""): {
+    res = {"batched_n128_32src_mixed" + ("_orth_df" if orth == "df" else "") + ("_fcycle" if cycle == "f" else ""): {
         "ms": ms_b, "ms_per_source": ms_b / B.shape[0], "sequential_ms": ms_s, "speedup_vs_sequential": ms_s / ms_b,
         "iterations_max": max(i["iterations"] for i in infos), "iterations_min": min(i["iterations"] for i in infos),
         "rel_residual_max": max(i["rel_residual"] for i in infos), "sequential_iterations_max": max(seq_iters),

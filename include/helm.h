@@ -100,7 +100,7 @@ typedef struct {
                        |w|^2 (SELECTIVE, the Daniel-Gragg-Kaufman-Stewart test) */
   int cycle;        /* helm_cycle: the preconditioner is one V-cycle (default) or one F-cycle
                        (Sec. 3.4.5: each coarse-grid error is an F-cycle on the next level followed
-                       by one V-cycle there); the batched solver always uses the V-cycle */
+                       by one V-cycle there); the batched solver follows it too */
   double idr_kappa; /* IDR(s) dimension-reduction step: omega minimises |r - omega A M^{-1} r|
                        and is enlarged so that the cosine of the angle between r and
                        A M^{-1} r is at least idr_kappa when it is smaller; 0 keeps the
@@ -171,6 +171,15 @@ HELM_API helm_status helm_apply(helm_ctx* ctx, helm_op op, helm_dtype dt, const 
  * (Sec. 3.4.3), exact FP64 solve on the coarsest level.  dt = HELM_C128 runs every level
  * in FP64; HELM_C64 runs them in FP32 (the coarsest solve stays FP64).  r, z: device. */
 HELM_API helm_status cslp_vcycle(helm_ctx* ctx, helm_dtype dt, const void* r, void* z, void* stream);
+
+/* v = A_h u (Sec. 2.4, Algorithm 2) for a complex64 u, computed in double-float arithmetic
+ * (pairs of FP32 values, about 48 significant bits; FP32 instructions only): the A-product of the
+ * mixed-precision solver with double-float Gram-Schmidt, exposed for parity checks.  The float
+ * inputs are exact, so v is A u to FP64-class accuracy (2^-46 relative to the largest term).
+ *   u : device c64 grid vector;  v : device c128 grid vector (output)
+ * The context must have precision = HELM_PREC_MIXED and orth = HELM_ORTH_DF (it holds the
+ * double-float k^2 table); HELM_EINVAL otherwise.  Stream-ordered. */
+HELM_API helm_status helm_apply_c64_df(helm_ctx* ctx, const void* u, void* v, void* stream);
 
 /* One multigrid F-cycle z ~= M_h^{-1} r (Sec. 3.4.5): like the V-cycle, but the coarse-grid
  * error of every level comes from an F-cycle on the next level followed by one V-cycle there,

@@ -130,6 +130,20 @@ __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, f
   df_renorm(p, e, hi, lo);
 }
 
+// Error-free sum of two floats (Knuth's TwoSum): s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+// (hi, lo) = (ah + al) * b for a float b: exact leading product by FMA, al*b added to the tail.
+__device__ __forceinline__ void df_mul_f(float ah, float al, float b, float& hi, float& lo) {
+  const float p = __fmul_rn(ah, b);
+  float e = fmaf(ah, b, -p);
+  e = fmaf(al, b, e);
+  df_renorm(p, e, hi, lo);
+}
+
 // Grid of unknowns: N_d per direction, x fastest; bc 0 = Dirichlet, 1 = Sommerfeld.
 struct Grid {
   int N1, N2, N3;

@@ -167,6 +167,10 @@ struct helm_ctx {
   BatchWS bw;
   BicgCtl* bicg = nullptr;  // device
   BicgCtl* hbicg = nullptr; // pinned
+  // (hi, lo) tables of k^2 and k on the finest level for the double-float A-product of the
+  // mixed-precision solver (allocated for mixed precision with double-float Gram-Schmidt)
+  float2* k2df = nullptr;
+  float2* skdf = nullptr;
   // CUDA graphs of whole solver steps, captured on gstream on first use and replayed on the
   // caller's stream (keyed by step kind, step index and a caller pointer the step writes)
   struct GraphEnt {
@@ -457,11 +461,11 @@ void vcycle_from(helm_ctx* c, const VLevel<R>* lv, int L, int l, cudaStream_t st
   const VLevel<R>& F = lv[l];
   const double nc = c->nc, cb = 2.0 * sizeof(R), kb = sizeof(R), db = F.dinv ? 16.0 : 0.0;
   if (l == L - 1) {
-    KL(F_COARSE, nc * nc * 16 + nc * 2 * cb, 8 * nc * nc, (launch_coarse<R, R>(c->nc, c->Minv, F.B, F.E, st, active)));
+    KL(F_COARSE, nc * nc * 16 + nc * 2 * cb, 8 * nc * nc, (launch_coarse<R, R>(c->nc, c->Minv, F.B, F.E, st, active, F.g.nb)));
     return;
   }
   const VLevel<R>& C = lv[l + 1];
-  const double n = (double)F.g.npts(), ncn = (double)C.g.npts();
+  const double n = (double)F.g.npts() * F.g.nb, ncn = (double)C.g.npts() * C.g.nb;
   KL(F_JACOBI, n * (3 * cb + kb + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.E, F.B, F.U1, st, active)));
   KL(F_RESID, n * (3 * cb + kb), 24 * n, (launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.B, F.T, st, active)));
   KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
@@ -480,12 +484,13 @@ void fcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, int l, const cx<TI>*
   const double sr = c->s_re, si = c->s_im, om = c->p.omega;
   const double nc = c->nc, cb = 2.0 * sizeof(R), kb = sizeof(R), ib = 2.0 * sizeof(TI), ob = 2.0 * sizeof(TO);
   if (l == L - 1) {
-    KL(F_COARSE, nc * nc * 16 + nc * (ib + ob), 8 * nc * nc, (launch_coarse<TI, TO>(c->nc, c->Minv, rin, zout, st, active)));
+    KL(F_COARSE, nc * nc * 16 + nc * (ib + ob), 8 * nc * nc,
+       (launch_coarse<TI, TO>(c->nc, c->Minv, rin, zout, st, active, lv[l].g.nb)));
     return;
   }
   const VLevel<R>& F = lv[l];
   const VLevel<R>& C = lv[l + 1];
-  const double n = (double)F.g.npts(), ncn = (double)C.g.npts(), db = F.dinv ? 16.0 : 0.0;
+  const double n = (double)F.g.npts() * F.g.nb, ncn = (double)C.g.npts() * C.g.nb, db = F.dinv ? 16.0 : 0.0;
   KL(F_SMOOTH0, n * (ib + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
   KL(F_RESID, n * (cb + ib + kb + cb), 24 * n, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
   KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
@@ -504,6 +509,14 @@ void run_fcycle(helm_ctx* c, const cx<TI>* rin, cx<TO>* zout, cudaStream_t st, c
     lv[l] = VLevel<R>{L.g, B::k2(L), B::dinv(L), B::B(L), B::U1(L), B::T(L), B::E(L)};
   }
   fcycle_levels<R, TI, TO>(c, lv, c->nlev, 0, rin, zout, st, active);
+}
+
+// The configured cycle over given level arrays (the batched solver's nb-wide grids).
+template <typename R, typename TI, typename TO>
+void run_cycle_levels(helm_ctx* c, const VLevel<R>* lv, const cx<TI>* rin, cx<TO>* zout, cudaStream_t st,
+                      const int* active) {
+  if (c->p.cycle == HELM_CYCLE_F) fcycle_levels<R, TI, TO>(c, lv, c->nlev, 0, rin, zout, st, active);
+  else run_vcycle_levels<R, TI, TO>(c, lv, c->nlev, rin, zout, st, active);
 }
 
 // The configured multigrid cycle (V or F) as the preconditioner.
@@ -734,7 +747,7 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
           z64* zj = c->Z32 + (size_t)j * n;
           if (df) {
             run_cycle<float, float, float>(c, c->vcur32, zj, st, act);
-            KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply_split<float>(F.g, 1.0, 0.0, F.k2, zj, wd, st, act)));
+            KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply_c64_df<zdf>(F.g, c->k2df, c->skdf, zj, wd, st, act)));
           } else {
             run_cycle<float, double, float>(c, vj, zj, st, act);
             KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply<double, float, double>(F.g, 1.0, 0.0, F.k2, zj, w, st, act)));
@@ -1023,15 +1036,15 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
       if (mixed) {
         z64* zj = W.Z32 + (size_t)j * ne;
         if (df) {
-          run_vcycle_levels<float, float, float>(c, lv32, c->nlev, W.vcur32, zj, st, any);
-          KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply_split<float>(g0, 1.0, 0.0, k2, zj, W.wdf, st, any)));
+          run_cycle_levels<float, float, float>(c, lv32, W.vcur32, zj, st, any);
+          KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply_c64_df<zdf>(g0, c->k2df, c->skdf, zj, W.wdf, st, any)));
         } else {
-          run_vcycle_levels<float, double, float>(c, lv32, c->nlev, vj, zj, st, any);
+          run_cycle_levels<float, double, float>(c, lv32, vj, zj, st, any);
           KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply<double, float, double>(g0, 1.0, 0.0, k2, zj, w, st, any)));
         }
       } else {
         z128* zj = W.Z64 + (size_t)j * ne;
-        run_vcycle_levels<double, double, double>(c, lv64, c->nlev, df ? W.vcur64 : vj, zj, st, any);
+        run_cycle_levels<double, double, double>(c, lv64, df ? W.vcur64 : vj, zj, st, any);
         if (df)
           KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply_split<double>(g0, 1.0, 0.0, k2, zj, W.wdf, st, any)));
         else
@@ -1494,6 +1507,11 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
     if (P.precision == HELM_PREC_MIXED) TRY(dalloc(c, &c->vcur32, n0));
     else TRY(dalloc(c, &c->vcur64, n0));
   }
+  if (P.orth == HELM_ORTH_DF && P.precision == HELM_PREC_MIXED) {
+    TRY(dalloc(c, &c->k2df, n0));
+    TRY(dalloc(c, &c->skdf, n0));
+    launch_k2_df(c->L[0].k2, n0, c->k2df, c->skdf, st);
+  }
   TRY(dalloc(c, &c->r, n0));
   TRY(dalloc(c, &c->xs, n0));
   TRY(dalloc(c, &c->bs, n0));
@@ -1616,6 +1634,14 @@ helm_status cslp_vcycle(helm_ctx* c, helm_dtype dt, const void* r, void* z, void
   else
     return fail(c, HELM_EINVAL, "unknown dtype %d", (int)dt);
   return check_launch(c, "cslp_vcycle");
+}
+
+helm_status helm_apply_c64_df(helm_ctx* c, const void* u, void* v, void* stream) {
+  if (!c) return HELM_EINVAL;
+  if (!u || !v || u == v) return fail(c, HELM_EINVAL, "u and v must be distinct non-NULL device pointers");
+  if (!c->k2df) return fail(c, HELM_EINVAL, "the context was created without mixed precision and double-float orth");
+  launch_apply_c64_df<z128>(c->L[0].g, c->k2df, c->skdf, (const z64*)u, (z128*)v, (cudaStream_t)stream, nullptr);
+  return check_launch(c, "helm_apply_c64_df");
 }
 
 helm_status cslp_fcycle(helm_ctx* c, helm_dtype dt, const void* r, void* z, void* stream) {

@@ -97,6 +97,13 @@ void launch_set_active(KrylovCtl* ctl, int v, cudaStream_t st);
 // x += z
 void launch_axpy1(const z128* z, z128* x, size_t n, cudaStream_t st);
 
+// A u for a complex64 u in double-float arithmetic (stencil.cu); k2df / skdf are (hi, lo)
+// tables of k^2 and sqrt(k^2) filled by launch_k2_df.  OUT: zdf or z128.
+template <typename OUT>
+void launch_apply_c64_df(const Grid& g, const float2* k2df, const float2* skdf, const z64* u, OUT* v, cudaStream_t st,
+                         const int* active);
+void launch_k2_df(const double* k2, size_t n, float2* k2df, float2* skdf, cudaStream_t st);
+
 // ---- IDR(s) (idrs.cu); part holds RED_STRIDE-strided slots of complex partial sums ----
 void launch_idr_v(const IdrCtl* ic, int k, const z128* r, const z128* G, size_t n, z128* v, cudaStream_t st);
 void launch_idr_u(const IdrCtl* ic, int k, const z128* vh, z128* U, size_t n, cudaStream_t st);

@@ -8,6 +8,8 @@
 // streaming), the in-plane neighbours come through the read-only L1 path.
 #include "internal.cuh"
 
+#include <type_traits>
+
 namespace helm {
 
 namespace {
@@ -306,6 +308,117 @@ __global__ void k_coarse_b(int nc, int nb, const z128* __restrict__ Minv, const 
   e[t] = mkc<TO>((TO)re, (TO)im);
 }
 
+// v = A u for a complex64 u in double-float arithmetic (FP32 instructions only, about 48
+// significant bits, 2^-46 relative to the largest term): the exact double-float sum of the six
+// neighbours (TwoSum), times 1/h^2, subtracted from the diagonal term d u_c with
+// d = 6/h^2 - k^2 - i (2 k / h) nf (the operator A, Sec. 2.4).  k^2 and k come from
+// double-float tables (hi, lo per node).  The float inputs are exact, so this is A applied to
+// the complex64 vector to FP64-class accuracy without FP64 instructions, whose issue rate on
+// this GPU is 1/64 of FP32's.  OUT: zdf (double-float, 16 B) or z128.
+template <typename OUT>
+__global__ void __launch_bounds__(TX* TY)
+    k_apply_c64_df(Grid g, float2 ih2, float2 six_ih2, float2 two_over_h, const float2* __restrict__ k2df,
+                   const float2* __restrict__ skdf, const z64* __restrict__ u, OUT* __restrict__ out, int zchunk,
+                   const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const int nb = g.nb;
+  const int f = blockIdx.x * TX + threadIdx.x;
+  const int i = f / nb, r = f - (f / nb) * nb;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.N1 || j >= g.N2) return;
+  const int k0 = blockIdx.z * zchunk;
+  if (k0 >= g.N3) return;
+  const int k1 = min(k0 + zchunk, g.N3);
+  const bool som = g.bc == 1;
+  const size_t S = (size_t)g.N1 * g.N2;
+  const size_t Se = S * nb;
+  const long Xe = nb, Ye = (long)g.N1 * nb;
+  const bool hxm = i > 0, hxp = i < g.N1 - 1, hym = j > 0, hyp = j < g.N2 - 1;
+  const int nfxy = som ? (!hxm) + (!hxp) + (!hym) + (!hyp) : 0;
+  auto ld = [&](size_t q) { return ldg(u + q); };
+  const z64 z0 = mkc<float>(0.f, 0.f);
+  size_t p = gidx(i, j, k0, g.N1, g.N2);
+  size_t e = p * nb + r;
+  z64 uc = ld(e);
+  z64 um = (k0 > 0) ? ld(e - Se) : z0;
+  for (int k = k0; k < k1; ++k, p += S, e += Se) {
+    const bool hzp = k + 1 < g.N3;
+    const z64 up = hzp ? ld(e + Se) : z0;
+    int nf = nfxy;
+    z64 zm, zp;
+    if (k > 0) zm = um;
+    else if (som) { zm = up; ++nf; }
+    else zm = z0;
+    if (hzp) zp = up;
+    else if (som) { zp = um; ++nf; }
+    else zp = z0;
+    const z64 xm = hxm ? ld(e - Xe) : (som ? ld(e + Xe) : z0);
+    const z64 xp = hxp ? ld(e + Xe) : (som ? ld(e - Xe) : z0);
+    const z64 ym = hym ? ld(e - Ye) : (som ? ld(e + Ye) : z0);
+    const z64 yp = hyp ? ld(e + Ye) : (som ? ld(e - Ye) : z0);
+    // exact neighbour sums as (hi, lo)
+    float sr, cr, si, ci, t;
+    two_sum(xm.re, xp.re, sr, cr);
+    two_sum(xm.im, xp.im, si, ci);
+    const float nre[4] = {ym.re, yp.re, zm.re, zp.re}, nim[4] = {ym.im, yp.im, zm.im, zp.im};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      two_sum(sr, nre[q], sr, t);
+      cr = __fadd_rn(cr, t);
+      two_sum(si, nim[q], si, t);
+      ci = __fadd_rn(ci, t);
+    }
+    df_renorm(sr, cr, sr, cr);
+    df_renorm(si, ci, si, ci);
+    // N = (1/h^2) * sum
+    float nrh, nrl, nih, nil;
+    df_mul(ih2.x, ih2.y, sr, cr, nrh, nrl);
+    df_mul(ih2.x, ih2.y, si, ci, nih, nil);
+    // d_re = 6/h^2 - k^2
+    const float2 kk = __ldg(k2df + p);
+    float drh, drl;
+    df_add(six_ih2.x, six_ih2.y, -kk.x, -kk.y, drh, drl);
+    // v = d_re u_c - N (+ i d_im u_c at faces)
+    float ah, al, bh, bl, vrh, vrl, vih, vil;
+    df_mul_f(drh, drl, uc.re, ah, al);
+    df_add(ah, al, -nrh, -nrl, vrh, vrl);
+    df_mul_f(drh, drl, uc.im, bh, bl);
+    df_add(bh, bl, -nih, -nil, vih, vil);
+    if (nf) {
+      // d_im = -(2/h) k nf
+      const float2 kf = __ldg(skdf + p);
+      float dih, dil;
+      df_mul(two_over_h.x, two_over_h.y, kf.x, kf.y, dih, dil);
+      df_mul_f(dih, dil, -(float)nf, dih, dil);
+      // re -= d_im u_c.im ; im += d_im u_c.re
+      df_mul_f(dih, dil, uc.im, ah, al);
+      df_add(vrh, vrl, -ah, -al, vrh, vrl);
+      df_mul_f(dih, dil, uc.re, bh, bl);
+      df_add(vih, vil, bh, bl, vih, vil);
+    }
+    if constexpr (std::is_same<OUT, zdf>::value) {
+      zdf o;
+      o.rh = vrh; o.rl = vrl; o.ih = vih; o.il = vil;
+      out[e] = o;
+    } else {
+      out[e] = mkc<double>((double)vrh + (double)vrl, (double)vih + (double)vil);
+    }
+    um = uc;
+    uc = up;
+  }
+}
+
+// (hi, lo) tables of k^2 and k = sqrt(k^2) from the FP64 k^2 (face terms use k).
+__global__ void k_k2_df(const double* __restrict__ k2, size_t n, float2* __restrict__ k2df,
+                        float2* __restrict__ skdf) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const double a = k2[q], b = sqrt(a);
+    const float ah = (float)a, bh = (float)b;
+    k2df[q] = make_float2(ah, (float)(a - (double)ah));
+    skdf[q] = make_float2(bh, (float)(b - (double)bh));
+  }
+}
+
 // Discrete Dirac sources (Sec. 2.4): b(node) += 1/h^3, sources applied in order.
 __global__ void k_rhs_point(Grid g, int nsrc, const int* __restrict__ idx, double amp, z128* __restrict__ b) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -358,6 +471,29 @@ void launch_apply(const Grid& g, double s_re, double s_im, const R* k2, const cx
   dim3 blk, gr = grid_for<R>(g, TILE_STENCIL, zc, blk);
   k_stencil<R, 0, false, TU, TU, TO><<<gr, blk, 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr, u,
                                                                    nullptr, v, zc, active);
+}
+
+static float2 df_const(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+
+template <typename OUT>
+void launch_apply_c64_df(const Grid& g, const float2* k2df, const float2* skdf, const z64* u, OUT* v, cudaStream_t st,
+                         const int* active) {
+  int zc;
+  dim3 blk, gr = grid_for<float>(g, TILE_STENCIL, zc, blk);
+  k_apply_c64_df<OUT><<<gr, blk, 0, st>>>(g, df_const(1.0 / (g.h * g.h)), df_const(6.0 / (g.h * g.h)),
+                                          df_const(2.0 / g.h), k2df, skdf, u, v, zc, active);
+}
+template void launch_apply_c64_df<zdf>(const Grid&, const float2*, const float2*, const z64*, zdf*, cudaStream_t,
+                                       const int*);
+template void launch_apply_c64_df<z128>(const Grid&, const float2*, const float2*, const z64*, z128*, cudaStream_t,
+                                        const int*);
+
+void launch_k2_df(const double* k2, size_t n, float2* k2df, float2* skdf, cudaStream_t st) {
+  size_t b = (n + 255) / 256;
+  k_k2_df<<<(int)(b < 4096 ? (b ? b : 1) : 4096), 256, 0, st>>>(k2, n, k2df, skdf);
 }
 
 template <typename TU>

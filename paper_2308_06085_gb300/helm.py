@@ -79,6 +79,8 @@ def lib():
     L.cslp_vcycle.argtypes = [vp, i, vp, vp, vp]
     L.cslp_fcycle.argtypes = [vp, i, vp, vp, vp]
     L.helm_set_shadow_space.argtypes = [vp, i, vp, vp]
+    L.helm_apply_c64_df.argtypes = [vp, vp, vp, vp]
+    L.helm_apply_c64_df.restype = i
     L.helm_set_shadow_space.restype = i
     L.cslp_fcycle.restype = i
     L.helm_vcycle_stage.argtypes = [vp, i, i, i, vp, vp, vp, vp]
@@ -240,6 +242,16 @@ class Solver:
         z = torch.empty_like(r) if out is None else out
         self._check(lib().cslp_vcycle(self._ctx, _DT[r.dtype], _ptr(r), _ptr(z), _stream()))
         return z
+
+    def apply_c64_df(self, u):
+        """A u for a complex64 u in double-float arithmetic (mixed precision + double-float
+        orth contexts), returned as complex128."""
+        u = self._vec(u)
+        if u.dtype != torch.complex64:
+            raise TypeError("apply_c64_df takes a complex64 vector")
+        v = torch.empty(u.shape, dtype=torch.complex128, device=u.device)
+        self._check(lib().helm_apply_c64_df(self._ctx, _ptr(u), _ptr(v), _stream()))
+        return v
 
     def set_shadow_space(self, P):
         """The s shadow vectors of IDR(s), shaped (s,) + grid shape, complex."""

