@@ -172,6 +172,17 @@ HELM_API helm_status helm_apply(helm_ctx* ctx, helm_op op, helm_dtype dt, const 
  * in FP64; HELM_C64 runs them in FP32 (the coarsest solve stays FP64).  r, z: device. */
 HELM_API helm_status cslp_vcycle(helm_ctx* ctx, helm_dtype dt, const void* r, void* z, void* stream);
 
+/* Launch shapes in use on `level` (library instrumentation, no paper counterpart): for each of
+ * the 8 slots (kernel family stencil / pre-smoothing / restriction / prolongation, FP64 then
+ * FP32) the rows of x-lines per CTA (ty) and the CTA count the z-chunking aims at (ctas); 0 means
+ * the default shape (8 rows, 8 CTAs per SM).  ty and ctas: host arrays of 8. */
+HELM_API helm_status helm_launch_shapes(const helm_ctx* ctx, int level, int* ty, int* ctas);
+
+/* The autotuner's measurements (library instrumentation): *count = number of timed shapes; the
+ * first min(cap, count) are written as rec[4 i .. 4 i + 3] = (level, slot, ty, ctas) and ms[i] =
+ * the best of three timings of three back-to-back launches, per launch.  rec / ms may be NULL. */
+HELM_API helm_status helm_tune_log(const helm_ctx* ctx, int* rec, float* ms, int cap, int* count);
+
 /* v = A_h u (Sec. 2.4, Algorithm 2) for a complex64 u, computed in double-float arithmetic
  * (pairs of FP32 values, about 48 significant bits; FP32 instructions only): the A-product of the
  * mixed-precision solver with double-float Gram-Schmidt, exposed for parity checks.  The float

@@ -68,6 +68,11 @@ const char* const FAM_NAMES[F_COUNT] = {
     "k_coarse", "k_mdot", "k_reduce_dots", "k_gs_update", "k_norm2_part", "k_reduce_norm", "k_scale_inv",
     "k_givens", "k_xupdate/k_combine/k_axpy1/k_trisolve", "other"};
 
+struct TuneRec {
+  int level, slot, ty, ctas;
+  float ms;
+};
+
 struct ProfRec {
   int fam, j, e0, e1;
   int cond;  // 1: second Gram-Schmidt pass, which ran only if the step's log entry is set
@@ -180,6 +185,7 @@ struct helm_ctx {
     long long launches;
   };
   std::vector<GraphEnt> graphs;
+  std::vector<TuneRec> tune_log;  // every launch shape the autotuner timed
   cudaStream_t gstream = nullptr;
   // IDR(s): shadow space P (s vectors), work G, U (s each), r, v, vh, t; control block
   int idr_s = 0;
@@ -580,9 +586,10 @@ helm_status graph_step(helm_ctx* c, int tag, int j, const void* p, cudaStream_t 
 // level's own work vectors and keep the fastest.  Stencil, transfer and smoothing results do
 // not depend on the launch shape (no reductions), so tuning changes speed only.
 template <typename Fn>
-helm_status tune_slot(helm_ctx* c, Grid& g, int slot, cudaStream_t st, Fn&& run) {
+helm_status tune_slot(helm_ctx* c, Grid& g, int slot, int level, cudaStream_t st, Fn&& run) {
   static const int tys[] = {1, 2, 4, 8};
-  static const int per_sm[] = {2, 4, 8, 16, 32};
+  static const int per_sm[] = {4, 8, 16, 32};
+  constexpr int kBurst = 3;  // back-to-back launches per timing, as in a solve
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
@@ -595,14 +602,15 @@ helm_status tune_slot(helm_ctx* c, Grid& g, int slot, cudaStream_t st, Fn&& run)
       run(g);  // warm-up
       float ms = 1e30f;
       for (int rep = 0; rep < 3; ++rep) {
-        cudaEventRecord(e0, st);
-        run(g);
-        cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
+        CU(cudaEventRecord(e0, st));
+        for (int b = 0; b < kBurst; ++b) run(g);
+        CU(cudaEventRecord(e1, st));
+        CU(cudaEventSynchronize(e1));
         float t = 0.f;
-        cudaEventElapsedTime(&t, e0, e1);
-        ms = std::min(ms, t);
+        CU(cudaEventElapsedTime(&t, e0, e1));
+        ms = std::min(ms, t / kBurst);
       }
+      c->tune_log.push_back(TuneRec{level, slot, ty, 152 * m, ms});
       if (ms < best) { best = ms; bty = ty; bct = 152 * m; }
     }
   cudaEventDestroy(e0);
@@ -619,21 +627,22 @@ helm_status tune_vlevels(helm_ctx* c, VLevel<R>* lv, int L, cudaStream_t st) {
   for (int l = 0; l < L; ++l) {
     VLevel<R>& F = lv[l];
     const size_t ne = F.g.npts() * F.g.nb;
-    CU(cudaMemsetAsync(F.U1, 0, ne * sizeof(cx<R>), st));
-    CU(cudaMemsetAsync(F.T, 0, ne * sizeof(cx<R>), st));
+    // finite nonzero bytes (0x3f.. is about 0.75 in FP32 and 4.8e-4 in FP64)
+    CU(cudaMemsetAsync(F.U1, 0x3f, ne * sizeof(cx<R>), st));
+    CU(cudaMemsetAsync(F.T, 0x3f, ne * sizeof(cx<R>), st));
     if (l == L - 1) break;  // the coarsest level runs the dense solve only
-    TRY(tune_slot(c, F.g, tile_slot<R>(TILE_STENCIL), st, [&](const Grid& g) {
+    TRY(tune_slot(c, F.g, tile_slot<R>(TILE_STENCIL), l, st, [&](const Grid& g) {
       launch_jacobi<R, R, R>(g, sr, si, om, F.k2, F.dinv, F.U1, F.U1, F.T, st, nullptr);
     }));
-    TRY(tune_slot(c, F.g, tile_slot<R>(TILE_SMOOTH0), st, [&](const Grid& g) {
+    TRY(tune_slot(c, F.g, tile_slot<R>(TILE_SMOOTH0), l, st, [&](const Grid& g) {
       launch_smooth0<R, R>(g, sr, si, om, F.k2, F.dinv, F.U1, F.T, st, nullptr);
     }));
     VLevel<R>& C = lv[l + 1];
-    CU(cudaMemsetAsync(C.E, 0, C.g.npts() * C.g.nb * sizeof(cx<R>), st));
-    TRY(tune_slot(c, F.g, tile_slot<R>(TILE_PROLONG), st, [&](const Grid& g) {
+    CU(cudaMemsetAsync(C.E, 0x3f, C.g.npts() * C.g.nb * sizeof(cx<R>), st));
+    TRY(tune_slot(c, F.g, tile_slot<R>(TILE_PROLONG), l, st, [&](const Grid& g) {
       launch_prolong_add<R>(g, C.g, F.U1, C.E, F.T, st, nullptr);
     }));
-    TRY(tune_slot(c, C.g, tile_slot<R>(TILE_RESTRICT), st, [&](const Grid& g) {
+    TRY(tune_slot(c, C.g, tile_slot<R>(TILE_RESTRICT), l + 1, st, [&](const Grid& g) {
       launch_restrict<R>(F.g, g, F.T, C.B, st, nullptr);
     }));
   }
@@ -665,8 +674,8 @@ helm_status autotune(helm_ctx* c, cudaStream_t st) {
     // the finest FP64 operator only (A-products and residuals of the outer method)
     Level& F = c->L[0];
     const size_t n = F.g.npts();
-    CU(cudaMemsetAsync(F.U164, 0, n * sizeof(z128), st));
-    TRY(tune_slot(c, lv[0].g, tile_slot<double>(TILE_STENCIL), st, [&](const Grid& g) {
+    CU(cudaMemsetAsync(F.U164, 0x3f, n * sizeof(z128), st));
+    TRY(tune_slot(c, lv[0].g, tile_slot<double>(TILE_STENCIL), 0, st, [&](const Grid& g) {
       launch_resid<double, double, double, double>(g, 1.0, 0.0, F.k2, F.U164, F.U164, F.T64, st, nullptr);
     }));
   }
@@ -983,8 +992,8 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
     if (!W.tuned[t]) {
       if (mixed) {
         TRY(tune_vlevels<float>(c, lv32, c->nlev, st));
-        CU(cudaMemsetAsync(W.r, 0, ne * sizeof(z128), st));
-        TRY(tune_slot(c, g0, tile_slot<double>(TILE_STENCIL), st, [&](const Grid& g) {
+        CU(cudaMemsetAsync(W.r, 0x3f, ne * sizeof(z128), st));
+        TRY(tune_slot(c, g0, tile_slot<double>(TILE_STENCIL), 0, st, [&](const Grid& g) {
           launch_resid<double, double, double, double>(g, 1.0, 0.0, k2, W.r, W.r, W.V, st, nullptr);
         }));
       } else {
@@ -1634,6 +1643,26 @@ helm_status cslp_vcycle(helm_ctx* c, helm_dtype dt, const void* r, void* z, void
   else
     return fail(c, HELM_EINVAL, "unknown dtype %d", (int)dt);
   return check_launch(c, "cslp_vcycle");
+}
+
+helm_status helm_launch_shapes(const helm_ctx* c, int level, int* ty, int* ctas) {
+  if (!c || !ty || !ctas || level < 0 || level >= c->nlev) return HELM_EINVAL;
+  for (int q = 0; q < 8; ++q) {
+    ty[q] = c->L[level].g.tile_ty[q];
+    ctas[q] = c->L[level].g.tile_ctas[q];
+  }
+  return HELM_OK;
+}
+
+helm_status helm_tune_log(const helm_ctx* c, int* rec, float* ms, int cap, int* count) {
+  if (!c || !count) return HELM_EINVAL;
+  *count = (int)c->tune_log.size();
+  for (int i = 0; i < cap && i < *count; ++i) {
+    const TuneRec& t = c->tune_log[i];
+    if (rec) { rec[4 * i] = t.level; rec[4 * i + 1] = t.slot; rec[4 * i + 2] = t.ty; rec[4 * i + 3] = t.ctas; }
+    if (ms) ms[i] = t.ms;
+  }
+  return HELM_OK;
 }
 
 helm_status helm_apply_c64_df(helm_ctx* c, const void* u, void* v, void* stream) {

@@ -29,6 +29,7 @@ __device__ __forceinline__ void block_range(size_t n, size_t& p0, size_t& p1) {
 constexpr int KS = 4;  // slots per warp per pass over the block's points
 
 struct AccD {  // FP64 accumulator
+  static constexpr bool kBalanced = false;
   double re, im;
   __device__ void zero() { re = im = 0.0; }
   __device__ void mac(const z128& v, const z128& w) { cdot_acc(v, w, re, im); }
@@ -57,6 +58,7 @@ __device__ __forceinline__ void df_shfl_reduce(float& s, float& c) {
 }
 
 struct AccF {  // double-float accumulator, FP32 arithmetic only
+  static constexpr bool kBalanced = true;
   float rs, rc, is, ic;
   __device__ void zero() { rs = rc = is = ic = 0.f; }
   __device__ void mac(const zdf& v, const zdf& w) {
@@ -81,6 +83,19 @@ struct AccF {  // double-float accumulator, FP32 arithmetic only
   }
 };
 
+// Warps sharing one slot: the groups of NW / wps warps take the slots round-robin, so the
+// busiest group holds ceil(nslot / groups) of them.  Take the least sharing that leaves at most
+// 1/8 of the warp-slots idle: less sharing means more points per lane between warp reductions,
+// and fewer idle warps means more loads in flight.
+__device__ __forceinline__ int share_width(int nslot) {
+  for (int wps = 1; wps < NW; wps <<= 1) {
+    const int groups = NW / wps;
+    const int cap = (nslot + groups - 1) / groups * groups;
+    if (8 * (cap - nslot) <= cap) return wps;
+  }
+  return NW;
+}
+
 // TILE points of w per shared-memory tile (16 KB): few barriers per point keep loads in
 // flight.
 template <typename E, typename ACC, int TILE>
@@ -94,7 +109,10 @@ __global__ void __launch_bounds__(NT)
   block_range(n, p0, p1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nslot = nv + (with_norm ? 1 : 0);
-  const int wps = nslot >= NW ? 1 : NW / nslot;  // warps sharing one slot
+  // warps sharing one slot: FP64 accumulation is bound by FP64 issue, where the least sharing
+  // (longest runs between reductions) is fastest; double-float accumulation is bound by
+  // latency, where evenly loaded warps keep more loads in flight
+  const int wps = ACC::kBalanced ? share_width(nslot) : (nslot >= NW ? 1 : NW / nslot);
   const int sub = warp % wps, sfirst = warp / wps, sstep = NW / wps;
   double* partd = reinterpret_cast<double*>(part);
   for (int sbase = 0; sbase * sstep < nslot; sbase += KS) {

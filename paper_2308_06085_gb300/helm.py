@@ -80,6 +80,10 @@ def lib():
     L.cslp_fcycle.argtypes = [vp, i, vp, vp, vp]
     L.helm_set_shadow_space.argtypes = [vp, i, vp, vp]
     L.helm_apply_c64_df.argtypes = [vp, vp, vp, vp]
+    L.helm_launch_shapes.argtypes = [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.helm_launch_shapes.restype = i
+    L.helm_tune_log.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_float), i, C.POINTER(C.c_int)]
+    L.helm_tune_log.restype = i
     L.helm_apply_c64_df.restype = i
     L.helm_set_shadow_space.restype = i
     L.cslp_fcycle.restype = i
@@ -242,6 +246,22 @@ class Solver:
         z = torch.empty_like(r) if out is None else out
         self._check(lib().cslp_vcycle(self._ctx, _DT[r.dtype], _ptr(r), _ptr(z), _stream()))
         return z
+
+    def launch_shapes(self, level):
+        """(rows per CTA, CTA target) per slot on `level`: slots 0-3 FP64 stencil / pre-smoothing /
+        restriction / prolongation, 4-7 the same in FP32; (0, 0) = default."""
+        ty, ct = (C.c_int * 8)(), (C.c_int * 8)()
+        self._check(lib().helm_launch_shapes(self._ctx, level, ty, ct))
+        return [(ty[q], ct[q]) for q in range(8)]
+
+    def tune_log(self):
+        """Every launch shape the autotuner timed: (level, slot, ty, ctas, ms per launch)."""
+        cnt = C.c_int()
+        self._check(lib().helm_tune_log(self._ctx, None, None, 0, C.byref(cnt)))
+        n = cnt.value
+        rec, ms = (C.c_int * (4 * max(n, 1)))(), (C.c_float * max(n, 1))()
+        self._check(lib().helm_tune_log(self._ctx, rec, ms, n, C.byref(cnt)))
+        return [(rec[4 * i], rec[4 * i + 1], rec[4 * i + 2], rec[4 * i + 3], ms[i]) for i in range(n)]
 
     def apply_c64_df(self, u):
         """A u for a complex64 u in double-float arithmetic (mixed precision + double-float
