@@ -120,6 +120,13 @@ typedef struct {
                        ||M^{-1}(b - A x)|| / ||M^{-1} b|| <= tol (Sec. 5), for which
                        helm_solve_info.rel_residual reports that preconditioned quantity.  Left
                        needs krylov = HELM_GMRES with FP64 precision and FP64 orth. */
+  int fuse_coarse;  /* 1: the coarse levels of every V-cycle whose vectors fit in one CTA's
+                       shared memory (about 200 KB; from 17^3 nodes down in complex64, 9^3 in
+                       complex128) run as one single-CTA kernel instead of five kernels per
+                       level, with the same arithmetic per point (bit-identical results).
+                       0 (default): level by level, which measures faster on GB300 (one SM
+                       cannot hide the latency of the coarse-grid product and coefficient
+                       loads that many small grids spread over all SMs). */
 } helm_params;
 
 /* Per-solve report (host struct). */

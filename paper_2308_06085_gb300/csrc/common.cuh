@@ -165,6 +165,30 @@ struct Grid {
   __host__ __device__ size_t npts() const { return (size_t)N1 * N2 * N3; }
 };
 
+// One level of a coarse sub-cycle run by a single CTA in shared memory (k_coarse_cycle):
+// the level's grid (one right-hand side), k^2, the FP64 omega/diag(M) table (NULL in FP32) and
+// the offsets of its vectors in the CTA's shared buffer: B (right-hand side), U (pre-smoothed
+// iterate, then the level's result E) and T (residual / corrected iterate; unused on the
+// coarsest level).
+constexpr int CC_MAX_LEVELS = 6;
+template <typename R>
+struct CLevel {
+  Grid g;
+  const R* k2;
+  const cx<R>* dinv;
+  int off_b, off_u, off_t;  // complex vectors (units of cx<R>)
+  int off_k, off_s;         // k^2 and sqrt(k^2) copies (units of R)
+  int off_d;                // omega/diag(M) copy (units of cx<R>; FP64 path), -1 without
+};
+template <typename R>
+struct CCycle {
+  int L;           // levels in the sub-cycle, the last one solved exactly
+  int nc;          // unknowns of the coarsest level
+  const cx<double>* Minv;
+  double s_re, s_im, omega;
+  CLevel<R> lev[CC_MAX_LEVELS];
+};
+
 // Kernel families with their own launch shape (Grid::tile_*).
 enum { TILE_STENCIL = 0, TILE_SMOOTH0 = 1, TILE_RESTRICT = 2, TILE_PROLONG = 3 };
 template <typename R>

@@ -61,12 +61,12 @@ template <> struct LevelBufs<float> {
 // Kernel families for the opt-in profiler (names match the kernel functions).
 enum Fam {
   F_APPLY, F_RESID, F_JACOBI, F_SMOOTH0, F_RESTRICT, F_PROLONG, F_COARSE, F_MDOT, F_REDUCE_DOTS, F_GS_UPDATE,
-  F_NORM, F_REDUCE_NORM, F_SCALE, F_GIVENS, F_SOLUPDATE, F_MISC, F_COUNT
+  F_NORM, F_REDUCE_NORM, F_SCALE, F_GIVENS, F_SOLUPDATE, F_MISC, F_CCYCLE, F_COUNT
 };
 const char* const FAM_NAMES[F_COUNT] = {
     "k_stencil(apply)", "k_stencil(resid)", "k_stencil(jacobi)", "k_smooth0", "k_restrict", "k_prolong_add",
     "k_coarse", "k_mdot", "k_reduce_dots", "k_gs_update", "k_norm2_part", "k_reduce_norm", "k_scale_inv",
-    "k_givens", "k_xupdate/k_combine/k_axpy1/k_trisolve", "other"};
+    "k_givens", "k_xupdate/k_combine/k_axpy1/k_trisolve", "other", "k_coarse_cycle"};
 
 struct TuneRec {
   int level, slot, ty, ctas;
@@ -400,6 +400,53 @@ struct VLevel {
   cx<R> *B, *U1, *T, *E;
 };
 
+// Levels from which the rest of a V-cycle over lv[0..L) runs in one CTA (k_coarse_cycle):
+// the first relative level lf >= 1 whose sub-cycle (at least two levels, one right-hand side)
+// fits the shared-memory budget, with its vectors laid out in *cc and the byte count in
+// *bytes; L when none fits or the context runs without it.
+template <typename R>
+int plan_coarse_cycle(helm_ctx* c, const VLevel<R>* lv, int L, CCycle<R>* cc, size_t* bytes) {
+  if (!c->p.fuse_coarse || lv[0].g.nb != 1 || !coarse_cycle_ready<R>()) return L;
+  for (int lf = 1; lf <= L - 2; ++lf) {
+    if (L - lf > CC_MAX_LEVELS) continue;
+    // layout in units of cx<R>: per level B, U (and T), then the FP64 omega/d copy, then the
+    // k^2 and sqrt(k^2) copies (two R per cx<R> slot)
+    size_t off = 0;
+    for (int l = lf; l < L; ++l) {
+      const size_t n = lv[l].g.npts();
+      const size_t nv = (l == L - 1) ? 2 : 3;
+      CLevel<R>& C = cc->lev[l - lf];
+      C.g = lv[l].g;
+      C.k2 = lv[l].k2;
+      C.dinv = lv[l].dinv;
+      C.off_b = (int)off;
+      C.off_u = (int)(off + n);
+      C.off_t = l == L - 1 ? -1 : (int)(off + 2 * n);
+      off += nv * n;
+      C.off_d = -1;
+      if (lv[l].dinv) {
+        C.off_d = (int)off;
+        off += n;
+      }
+      C.off_k = (int)(2 * off);      // in units of R
+      C.off_s = (int)(2 * off + n);
+      off += n;                      // 2 n values of R
+    }
+    const size_t b = off * sizeof(cx<R>);
+    if (b <= CC_SMEM_MAX) {
+      cc->L = L - lf;
+      cc->nc = c->nc;
+      cc->Minv = c->Minv;
+      cc->s_re = c->s_re;
+      cc->s_im = c->s_im;
+      cc->omega = c->p.omega;
+      *bytes = b;
+      return lf;
+    }
+  }
+  return L;
+}
+
 // One V-cycle z ~= M^{-1} r in working precision R (input type TI, output type TO) over the
 // levels lv[0..L); g.nb right-hand sides per node.
 template <typename R, typename TI, typename TO>
@@ -416,8 +463,13 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
        (launch_coarse<TI, TO>(c->nc, c->Minv, rin, zout, st, active, nbv)));
     return;
   }
+  // levels lf.. run as one single-CTA sub-cycle when they fit in shared memory
+  CCycle<R> cc;
+  size_t cc_bytes = 0;
+  const int lf = plan_coarse_cycle<R>(c, lv, L, &cc, &cc_bytes);
+  const int Ld = lf < L ? lf + 1 : L;  // levels run kernel by kernel, the sub-cycle's first included
   // down: pre-smooth from zero, residual, restriction
-  for (int l = 0; l < L - 1; ++l) {
+  for (int l = 0; l < Ld - 1; ++l) {
     const VLevel<R>& F = lv[l];
     const VLevel<R>& C = lv[l + 1];
     const double n = (double)F.g.npts(), ncn = (double)C.g.npts();
@@ -431,11 +483,17 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
     }
     KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn * nbv, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
   }
-  // coarsest: exact FP64 solve
-  KL(F_COARSE, nc * nc * 16 + nc * 2 * cb, 8 * nc * nc * nbv,
-     (launch_coarse<R, R>(c->nc, c->Minv, lv[L - 1].B, lv[L - 1].E, st, active, nbv)));
+  if (lf < L) {
+    // the sub-cycle lv[lf].B -> lv[lf].E in one CTA
+    KL(F_CCYCLE, 2.0 * cb * lv[lf].g.npts() + nc * nc * 16, 8 * nc * nc,
+       launch_coarse_cycle<R>(cc, cc_bytes, lv[lf].B, lv[lf].E, st, active));
+  } else {
+    // coarsest: exact FP64 solve
+    KL(F_COARSE, nc * nc * 16 + nc * 2 * cb, 8 * nc * nc * nbv,
+       (launch_coarse<R, R>(c->nc, c->Minv, lv[L - 1].B, lv[L - 1].E, st, active, nbv)));
+  }
   // up: prolongation + correction, post-smoothing
-  for (int l = L - 2; l >= 0; --l) {
+  for (int l = Ld - 2; l >= 0; --l) {
     const VLevel<R>& F = lv[l];
     const VLevel<R>& C = lv[l + 1];
     const double n = (double)F.g.npts(), ncn = (double)C.g.npts();
@@ -1376,6 +1434,7 @@ void helm_default_params(helm_params* p) {
   p->graphs = 1;
   p->autotune = 1;
   p->side = HELM_SIDE_RIGHT;
+  p->fuse_coarse = 0;
 }
 
 const char* helm_last_error(const helm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }

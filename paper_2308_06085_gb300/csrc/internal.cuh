@@ -104,6 +104,18 @@ void launch_apply_c64_df(const Grid& g, const float2* k2df, const float2* skdf, 
                          const int* active);
 void launch_k2_df(const double* k2, size_t n, float2* k2df, float2* skdf, cudaStream_t st);
 
+// The V-cycle on the coarse levels of cc in one CTA with every vector in shared memory
+// (stencil.cu): b = the first level's right-hand side, e = its result; smem_bytes <=
+// CC_SMEM_MAX.  coarse_cycle_ready() configures the kernel's shared-memory limit once and says
+// whether it can run.
+constexpr size_t CC_SMEM_MAX = 200 * 1024;
+constexpr int CC_THREADS = 1024;
+template <typename R>
+bool coarse_cycle_ready();
+template <typename R>
+void launch_coarse_cycle(const CCycle<R>& cc, size_t smem_bytes, const cx<R>* b, cx<R>* e, cudaStream_t st,
+                         const int* active);
+
 // ---- IDR(s) (idrs.cu); part holds RED_STRIDE-strided slots of complex partial sums ----
 void launch_idr_v(const IdrCtl* ic, int k, const z128* r, const z128* G, size_t n, z128* v, cudaStream_t st);
 void launch_idr_u(const IdrCtl* ic, int k, const z128* vh, z128* U, size_t n, cudaStream_t st);

@@ -419,6 +419,238 @@ __global__ void k_k2_df(const double* __restrict__ k2, size_t n, float2* __restr
   }
 }
 
+// ---- coarse sub-cycle in one CTA -------------------------------------------------------
+// The V-cycle on the levels of cc (Sec. 3.4.5: zero start, one damped-Jacobi sweep before and
+// after each coarse correction, the coarsest level solved exactly), run by one CTA with every
+// vector in shared memory.  On grids of a few thousand unknowns each kernel of the level-by-level
+// cycle is dominated by its launch and ramp; here the whole sub-cycle is one launch.  Every point
+// takes the same arithmetic, in the same order, as the grid kernels (op_diag / op_resid /
+// omega_over, the restriction's 27 weights, the interpolation average, the coarse product's
+// lane-strided sum), so the results are those of the level-by-level cycle.
+// q / d for 0 <= q < 2^22 and d >= 1 by a float reciprocal and one correction each way
+// (an integer division takes tens of issue slots; the float estimate is within one of q / d).
+__device__ __forceinline__ int cc_div(int q, int d, float rd) {
+  int t = __float2int_rz((float)q * rd);
+  if (t * d > q) --t;
+  if ((t + 1) * d <= q) ++t;
+  return t;
+}
+template <typename R>
+__device__ __forceinline__ void cc_ijk(const Grid& g, int q, int& i, int& j, int& k) {
+  const int t = cc_div(q, g.N1, 1.0f / (float)g.N1);
+  i = q - t * g.N1;
+  k = cc_div(t, g.N2, 1.0f / (float)g.N2);
+  j = t - k * g.N2;
+}
+
+template <typename R>
+__device__ __forceinline__ OpCoef<R> cc_coef(const CCycle<R>& cc, double h) {
+  OpCoef<R> c;
+  c.ih2 = (R)(1.0 / (h * h));
+  c.six_ih2 = (R)(6.0 / (h * h));
+  c.s_re = (R)cc.s_re;
+  c.s_im = (R)cc.s_im;
+  c.two_over_h = (R)(2.0 / h);
+  c.omega = (R)cc.omega;
+  c.real_shift = cc.s_im == 0.0;
+  return c;
+}
+
+// out = b - M u (MODE 1) or u + (omega/d)(b - M u) (MODE 2) on one level, all in shared memory
+// (k^2, sqrt(k^2) and omega/diag(M) read from their shared copies).
+template <typename R, int MODE>
+__device__ void cc_stencil(const CLevel<R>& F, const OpCoef<R>& c, const cx<R>* sm, const R* smr, int off_in,
+                           cx<R>* out) {
+  const Grid& g = F.g;
+  const int n = (int)g.npts();
+  const bool som = g.bc == 1;
+  const cx<R> z0 = zero_c<R>();
+  const cx<R>* u = sm + off_in;
+  const cx<R>* b = sm + F.off_b;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    int i, j, k;
+    cc_ijk<R>(g, q, i, j, k);
+    const bool hxm = i > 0, hxp = i < g.N1 - 1, hym = j > 0, hyp = j < g.N2 - 1, hzp = k + 1 < g.N3;
+    const int S = g.N1 * g.N2;
+    int nf = som ? (!hxm) + (!hxp) + (!hym) + (!hyp) : 0;
+    const cx<R> um = k > 0 ? u[q - S] : z0;
+    const cx<R> up = hzp ? u[q + S] : z0;
+    cx<R> zm, zp;
+    if (k > 0) zm = um;
+    else if (som) { zm = up; ++nf; }
+    else zm = z0;
+    if (hzp) zp = up;
+    else if (som) { zp = um; ++nf; }
+    else zp = z0;
+    const cx<R> xm = hxm ? u[q - 1] : (som ? u[q + 1] : z0);
+    const cx<R> xp = hxp ? u[q + 1] : (som ? u[q - 1] : z0);
+    const cx<R> ym = hym ? u[q - g.N1] : (som ? u[q + g.N1] : z0);
+    const cx<R> yp = hyp ? u[q + g.N1] : (som ? u[q - g.N1] : z0);
+    const R kk = smr[F.off_k + q];
+    const cx<R> d = op_diag(c, kk, nf, nf ? smr[F.off_s + q] : (R)0);
+    const bool real_d = c.real_shift && nf == 0;
+    const cx<R> uc = u[q];
+    const cx<R> res = op_resid(b[q], d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
+    if (MODE == 1) {
+      out[q] = res;
+    } else {
+      const cx<R> w = F.off_d >= 0 ? sm[F.off_d + q] : omega_over(d, c.omega);
+      out[q] = cfma(w, res, uc);
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(CC_THREADS)
+    k_coarse_cycle(CCycle<R> cc, const cx<R>* __restrict__ bin, cx<R>* __restrict__ eout,
+                   const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  extern __shared__ __align__(16) unsigned char cc_smem[];
+  cx<R>* sm = reinterpret_cast<cx<R>*>(cc_smem);
+  const R* smr = reinterpret_cast<const R*>(cc_smem);
+  const int L = cc.L;
+  // shared copies of the per-node coefficients, and the right-hand side
+  for (int l = 0; l < L; ++l) {
+    const CLevel<R>& F = cc.lev[l];
+    const int n = (int)F.g.npts();
+    R* sk = reinterpret_cast<R*>(cc_smem);
+    const R* tab = grid_sqk<R>(F.g);
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      const R kk = F.k2[q];
+      sk[F.off_k + q] = kk;
+      sk[F.off_s + q] = tab ? tab[q] : sqrt(kk);
+      if (F.off_d >= 0) sm[F.off_d + q] = F.dinv[q];
+    }
+  }
+  {
+    const CLevel<R>& F = cc.lev[0];
+    const int n = (int)F.g.npts();
+    for (int q = threadIdx.x; q < n; q += blockDim.x) sm[F.off_b + q] = bin[q];
+  }
+  __syncthreads();
+  // down: pre-smoothing from zero, residual, full weighting
+  for (int l = 0; l < L - 1; ++l) {
+    const CLevel<R>& F = cc.lev[l];
+    const CLevel<R>& C = cc.lev[l + 1];
+    const OpCoef<R> c = cc_coef(cc, F.g.h);
+    const Grid& g = F.g;
+    const int n = (int)g.npts();
+    const bool som = g.bc == 1;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      cx<R> w;
+      if (F.off_d >= 0) {
+        w = sm[F.off_d + q];
+      } else {
+        int i, j, k;
+        cc_ijk<R>(g, q, i, j, k);
+        const int nf = som ? (i == 0) + (i == g.N1 - 1) + (j == 0) + (j == g.N2 - 1) + (k == 0) + (k == g.N3 - 1) : 0;
+        const R kk = smr[F.off_k + q];
+        w = omega_over(op_diag(c, kk, nf, nf ? smr[F.off_s + q] : (R)0), c.omega);
+      }
+      sm[F.off_u + q] = cmul(w, sm[F.off_b + q]);
+    }
+    __syncthreads();
+    cc_stencil<R, 1>(F, c, sm, smr, F.off_u, sm + F.off_t);
+    __syncthreads();
+    const Grid& gc = C.g;
+    const int nC = (int)gc.npts();
+    const int off = g.bc == 0 ? 1 : 0;
+    const cx<R>* r = sm + F.off_t;
+    for (int Q = threadIdx.x; Q < nC; Q += blockDim.x) {
+      int I, J, K;
+      cc_ijk<R>(gc, Q, I, J, K);
+      const int fi = 2 * (I + off) - off, fj = 2 * (J + off) - off, fk = 2 * (K + off) - off;
+      R are = 0, aim = 0;
+      for (int dz = -1; dz <= 1; ++dz) {
+        const int z = fk + dz;
+        if (z < 0 || z >= g.N3) continue;
+        const R wz = dz ? (R)1 : (R)2;
+        for (int dy = -1; dy <= 1; ++dy) {
+          const int y = fj + dy;
+          if (y < 0 || y >= g.N2) continue;
+          const R wyz = wz * (dy ? (R)1 : (R)2);
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int x = fi + dx;
+            if (x < 0 || x >= g.N1) continue;
+            const R wgt = wyz * (dx ? (R)1 : (R)2);
+            const cx<R> v = r[(z * g.N2 + y) * g.N1 + x];
+            are = fma(wgt, v.re, are);
+            aim = fma(wgt, v.im, aim);
+          }
+        }
+      }
+      sm[C.off_b + Q] = mkc<R>(are * (R)(1.0 / 64.0), aim * (R)(1.0 / 64.0));
+    }
+    __syncthreads();
+  }
+  // coarsest: E = Minv B, one warp per row, lane-strided columns, fixed shuffle tree
+  {
+    const CLevel<R>& Cl = cc.lev[L - 1];
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int row = threadIdx.x >> 5; row < cc.nc; row += nw) {
+      double re = 0, im = 0;
+      const z128* a = cc.Minv + (size_t)row * cc.nc;
+      for (int col = lane; col < cc.nc; col += 32) {
+        const z128 m = a[col];
+        const z128 v = cvt<double>(sm[Cl.off_b + col]);
+        re = fma(m.re, v.re, re);
+        re = fma(-m.im, v.im, re);
+        im = fma(m.re, v.im, im);
+        im = fma(m.im, v.re, im);
+      }
+      for (int o = 16; o; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      if (lane == 0) sm[Cl.off_u + row] = mkc<R>((R)re, (R)im);
+    }
+  }
+  __syncthreads();
+  // up: interpolation + correction, post-smoothing
+  for (int l = L - 2; l >= 0; --l) {
+    const CLevel<R>& F = cc.lev[l];
+    const CLevel<R>& C = cc.lev[l + 1];
+    const Grid& gf = F.g;
+    const Grid& gc = C.g;
+    const int n = (int)gf.npts();
+    const int off = gf.bc == 0 ? 1 : 0;
+    const cx<R>* e = sm + C.off_u;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      int i, j, k;
+      cc_ijk<R>(gf, q, i, j, k);
+      const int fi = i + off, fj = j + off, fk = k + off;
+      const int cx_[2] = {(fi >> 1) - off, ((fi + 1) >> 1) - off};
+      const int cy_[2] = {(fj >> 1) - off, ((fj + 1) >> 1) - off};
+      const int cz_[2] = {(fk >> 1) - off, ((fk + 1) >> 1) - off};
+      const int nx = (cx_[0] == cx_[1]) ? 1 : 2, ny = (cy_[0] == cy_[1]) ? 1 : 2, nz = (cz_[0] == cz_[1]) ? 1 : 2;
+      R are = 0, aim = 0;
+      for (int c = 0; c < nz; ++c) {
+        if (cz_[c] < 0 || cz_[c] >= gc.N3) continue;
+        for (int bq = 0; bq < ny; ++bq) {
+          if (cy_[bq] < 0 || cy_[bq] >= gc.N2) continue;
+          for (int a = 0; a < nx; ++a) {
+            if (cx_[a] < 0 || cx_[a] >= gc.N1) continue;
+            const cx<R> v = e[(cz_[c] * gc.N2 + cy_[bq]) * gc.N1 + cx_[a]];
+            are += v.re;
+            aim += v.im;
+          }
+        }
+      }
+      const R s = (R)1 / (R)(nx * ny * nz);
+      const cx<R> base = sm[F.off_u + q];
+      sm[F.off_t + q] = mkc<R>(fma(are, s, base.re), fma(aim, s, base.im));
+    }
+    __syncthreads();
+    cc_stencil<R, 2>(F, cc_coef(cc, gf.h), sm, smr, F.off_t, sm + F.off_u);
+    __syncthreads();
+  }
+  {
+    const CLevel<R>& F = cc.lev[0];
+    const int n = (int)F.g.npts();
+    for (int q = threadIdx.x; q < n; q += blockDim.x) eout[q] = sm[F.off_u + q];
+  }
+}
+
 // Discrete Dirac sources (Sec. 2.4): b(node) += 1/h^3, sources applied in order.
 __global__ void k_rhs_point(Grid g, int nsrc, const int* __restrict__ idx, double amp, z128* __restrict__ b) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -590,6 +822,26 @@ void launch_check_k2(const double* a, size_t n, int* bad, cudaStream_t st) {
 void launch_rhs_point(const Grid& g, int nsrc, const int* idx, double amp, z128* b, cudaStream_t st) {
   k_rhs_point<<<1, 32, 0, st>>>(g, nsrc, idx, amp, b);
 }
+
+template <typename R>
+bool coarse_cycle_ready() {
+  static const bool ok = [] {
+    const bool r = cudaFuncSetAttribute(k_coarse_cycle<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)CC_SMEM_MAX) == cudaSuccess;
+    cudaGetLastError();
+    return r;
+  }();
+  return ok;
+}
+template <typename R>
+void launch_coarse_cycle(const CCycle<R>& cc, size_t smem_bytes, const cx<R>* b, cx<R>* e, cudaStream_t st,
+                         const int* active) {
+  k_coarse_cycle<R><<<1, CC_THREADS, smem_bytes, st>>>(cc, b, e, active);
+}
+template bool coarse_cycle_ready<double>();
+template bool coarse_cycle_ready<float>();
+template void launch_coarse_cycle<double>(const CCycle<double>&, size_t, const z128*, z128*, cudaStream_t, const int*);
+template void launch_coarse_cycle<float>(const CCycle<float>&, size_t, const z64*, z64*, cudaStream_t, const int*);
 
 // explicit instantiations used by the library
 #define HELM_INST_R(R)                                                                                   \

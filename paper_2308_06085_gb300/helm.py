@@ -41,7 +41,8 @@ class Params(C.Structure):
                 ("nu2", C.c_int), ("coarsest_n", C.c_int), ("krylov", C.c_int), ("restart", C.c_int),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int), ("orth", C.c_int),
                 ("reorth", C.c_int), ("cycle", C.c_int), ("idr_kappa", C.c_double),
-                ("graphs", C.c_int), ("autotune", C.c_int), ("side", C.c_int)]
+                ("graphs", C.c_int), ("autotune", C.c_int), ("side", C.c_int),
+                ("fuse_coarse", C.c_int)]
 
 
 class KernelStat(C.Structure):
@@ -152,7 +153,7 @@ class Solver:
 
     def __init__(self, n, h, k2, bc=SOMMERFELD, *, beta1=1.0, beta2=-0.5, omega=0.8, coarsest_n=4,
                  krylov="gmres", restart=30, tol=1e-6, max_iter=2000, precision="fp64", orth=None,
-                 reorth=None, cycle="v", idr_s=4, idr_kappa=0.7, shadow=None, graphs=True, autotune=True, side="right", device=None):
+                 reorth=None, cycle="v", idr_s=4, idr_kappa=0.7, shadow=None, graphs=True, autotune=True, side="right", fuse_coarse=False, device=None):
         n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(int(x) for x in n)
         self.n = (n1, n2, n3)
         self.h = float(h)
@@ -171,6 +172,7 @@ class Solver:
         p.graphs = int(bool(graphs))
         p.autotune = int(bool(autotune))
         p.side = {"right": 0, "left": 1}[side]
+        p.fuse_coarse = int(bool(fuse_coarse))
         p.restart, p.tol, p.max_iter = restart, tol, max_iter
         p.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
         if orth is not None:

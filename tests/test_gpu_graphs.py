@@ -55,3 +55,24 @@ def test_graph_cycle_shorter_than_restart(helm):
     xg, ig = g.solve(b)
     assert ia["iterations"] == ig["iterations"] == 35
     assert torch.equal(xa, xg)
+
+
+@pytest.mark.parametrize("n,bc,coarsest", [((32, 32, 32), 1, 4), ((40, 20, 12), 0, 2), ((24, 8, 16), 1, 2)])
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_fused_coarse_cycle_is_bit_exact(helm, n, bc, coarsest, dtype):
+    """The coarse levels run as one single-CTA kernel (helm_params.fuse_coarse) with the same
+    arithmetic per point as the level-by-level kernels: V-cycles, F-cycles and whole solves
+    must agree bit for bit with fusion off."""
+    h = 1.0 / max(n)
+    shape = I.unknown_shape(n, bc)
+    k2 = I.random_k2(shape, seed=5, kmin=2.0, kmax=0.6 / h)
+    a = helm.Solver(n, h, k2, bc, coarsest_n=coarsest, fuse_coarse=False)
+    f = helm.Solver(n, h, k2, bc, coarsest_n=coarsest, fuse_coarse=True)
+    r = torch.from_numpy(I.random_vector(shape, 12)).cuda().to(dtype)
+    assert torch.equal(a.vcycle(r), f.vcycle(r))
+    assert torch.equal(a.fcycle(r), f.fcycle(r))
+    if dtype == torch.complex128:
+        b = a.rhs_point([(n[0] // 2, n[1] // 2, n[2] // 2)])
+        xa, ia = a.solve(b)
+        xf, i_f = f.solve(b)
+        assert ia["iterations"] == i_f["iterations"] and torch.equal(xa, xf)
