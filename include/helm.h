@@ -106,10 +106,11 @@ typedef struct {
                        A M^{-1} r is at least idr_kappa when it is smaller; 0 keeps the
                        minimal-residual omega.  Default 0.7, in [0, 1). */
   int graphs;       /* 1 (default): each solver step (an Arnoldi column of a full-length GMRES
-                       cycle, a Bi-CGSTAB step, an IDR(s) step) is captured once into a CUDA graph
-                       and replayed, one launch instead of 30-70; 0: plain launches.  Graphs are
-                       bypassed while helm_profile is on.  Steps that write x are keyed by the x
-                       pointer, so a solve into a new buffer captures its steps again. */
+                       cycle, single or batched, a Bi-CGSTAB step, an IDR(s) step) is captured
+                       once into a CUDA graph and replayed, one launch instead of 30-70;
+                       0: plain launches.  Graphs are bypassed while helm_profile is on.  Steps
+                       that write x are keyed by the x pointer, so a solve into a new buffer
+                       captures its steps again. */
   int autotune;     /* 1 (default): helm_create times every stencil, smoothing and transfer
                        kernel of every level over launch shapes (rows of x-lines per CTA x CTA
                        count) and keeps the fastest, and helm_solve_batched does the same for

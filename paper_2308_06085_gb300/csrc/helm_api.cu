@@ -746,7 +746,7 @@ helm_status autotune(helm_ctx* c, cudaStream_t st) {
   return HELM_OK;
 }
 
-enum { G_ARNOLDI = 1, G_BICG = 2, G_IDR = 3, G_IDR_DR = 4 };
+enum { G_ARNOLDI = 1, G_BICG = 2, G_IDR = 3, G_IDR_DR = 4, G_BATCH = 100 };
 
 // GMRES(m) / FGMRES(m) on device-resident b and x.
 helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* info, cudaStream_t st) {
@@ -963,6 +963,7 @@ namespace {
 helm_status batch_alloc(helm_ctx* c, int nb) {
   BatchWS& W = c->bw;
   if (W.nb >= nb) return HELM_OK;
+  clear_graphs(c);  // captured batched steps hold the old workspace addresses
   const size_t n = c->n0, ne = n * nb;
   const int m = c->m;
   const bool mixed = c->p.precision == HELM_PREC_MIXED;
@@ -1096,60 +1097,65 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
       KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_bscale_inv(W.r, W.h.beta, W.V, ne, nb, st, any));
     }
     for (int j = 0; j < m; ++j) {
-      z128* vj = W.V + (size_t)j * ne;
-      z128* w = W.V + (size_t)(j + 1) * ne;
-      const double nv = j + 1;
       c->cur_j = j;
-      if (mixed) {
-        z64* zj = W.Z32 + (size_t)j * ne;
-        if (df) {
-          run_cycle_levels<float, float, float>(c, lv32, W.vcur32, zj, st, any);
-          KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply_c64_df<zdf>(g0, c->k2df, c->skdf, zj, W.wdf, st, any)));
+      auto step = [&](cudaStream_t st) {
+        z128* vj = W.V + (size_t)j * ne;
+        z128* w = W.V + (size_t)(j + 1) * ne;
+        const double nv = j + 1;
+        if (mixed) {
+          z64* zj = W.Z32 + (size_t)j * ne;
+          if (df) {
+            run_cycle_levels<float, float, float>(c, lv32, W.vcur32, zj, st, any);
+            KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply_c64_df<zdf>(g0, c->k2df, c->skdf, zj, W.wdf, st, any)));
+          } else {
+            run_cycle_levels<float, double, float>(c, lv32, vj, zj, st, any);
+            KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply<double, float, double>(g0, 1.0, 0.0, k2, zj, w, st, any)));
+          }
         } else {
-          run_cycle_levels<float, double, float>(c, lv32, vj, zj, st, any);
-          KL(F_APPLY, 32.0 * nd, 22.0 * nd, (launch_apply<double, float, double>(g0, 1.0, 0.0, k2, zj, w, st, any)));
+          z128* zj = W.Z64 + (size_t)j * ne;
+          run_cycle_levels<double, double, double>(c, lv64, df ? W.vcur64 : vj, zj, st, any);
+          if (df)
+            KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply_split<double>(g0, 1.0, 0.0, k2, zj, W.wdf, st, any)));
+          else
+            KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(g0, 1.0, 0.0, k2, zj, w, st, any)));
         }
-      } else {
-        z128* zj = W.Z64 + (size_t)j * ne;
-        run_cycle_levels<double, double, double>(c, lv64, df ? W.vcur64 : vj, zj, st, any);
+        const bool sel = c->p.reorth == HELM_REORTH_SELECTIVE;
+        for (int pass = 0; pass < 2; ++pass) {
+          const int* a2 = (pass == 1 && sel) ? &ctl->pass2 : any;
+          c->cur_cond = (pass == 1 && sel) ? 1 : 0;
+          const int wn = (pass == 0 && sel) ? 1 : 0;
+          int nbk = 0;
+          if (df)
+            KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nbk = launch_bmdot_df(Vdf, ne, j + 1, W.wdf, ne, nb, W.part, wn, st, a2));
+          else
+            KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nbk = launch_bmdot(W.V, ne, j + 1, w, ne, nb, W.part, wn, st, a2));
+          KL(F_REDUCE_DOTS, 16.0 * nv * nb * nbk, 2.0 * nv * nb * nbk,
+             launch_breduce_dots(W.part, j + 1, nb, nbk, W.hpass, W.hacc, pass, wn ? j : -1, W.h.act, &ctl->pass2,
+                                 c->reorth_log, st, a2));
+          if (df)
+            KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_bgs_update_df(Vdf, ne, j + 1, nb, W.hpass, W.wdf, ne, st, a2));
+          else
+            KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_bgs_update(W.V, ne, j + 1, nb, W.hpass, w, ne, st, a2));
+        }
+        c->cur_cond = 0;
+        int nbn = 0;
         if (df)
-          KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply_split<double>(g0, 1.0, 0.0, k2, zj, W.wdf, st, any)));
+          KL(F_NORM, 16.0 * nd, 4.0 * nd, nbn = launch_bnorm2_part_df(W.wdf, ne, nb, W.partr, st, any));
         else
-          KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(g0, 1.0, 0.0, k2, zj, w, st, any)));
-      }
-      const bool sel = c->p.reorth == HELM_REORTH_SELECTIVE;
-      for (int pass = 0; pass < 2; ++pass) {
-        const int* a2 = (pass == 1 && sel) ? &ctl->pass2 : any;
-        c->cur_cond = (pass == 1 && sel) ? 1 : 0;
-        const int wn = (pass == 0 && sel) ? 1 : 0;
-        int nbk = 0;
-        if (df)
-          KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nbk = launch_bmdot_df(Vdf, ne, j + 1, W.wdf, ne, nb, W.part, wn, st, a2));
-        else
-          KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nbk = launch_bmdot(W.V, ne, j + 1, w, ne, nb, W.part, wn, st, a2));
-        KL(F_REDUCE_DOTS, 16.0 * nv * nb * nbk, 2.0 * nv * nb * nbk,
-           launch_breduce_dots(W.part, j + 1, nb, nbk, W.hpass, W.hacc, pass, wn ? j : -1, W.h.act, &ctl->pass2,
-                               c->reorth_log, st, a2));
-        if (df)
-          KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_bgs_update_df(Vdf, ne, j + 1, nb, W.hpass, W.wdf, ne, st, a2));
-        else
-          KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_bgs_update(W.V, ne, j + 1, nb, W.hpass, w, ne, st, a2));
-      }
-      c->cur_cond = 0;
-      int nbn = 0;
-      if (df)
-        KL(F_NORM, 16.0 * nd, 4.0 * nd, nbn = launch_bnorm2_part_df(W.wdf, ne, nb, W.partr, st, any));
-      else
-        KL(F_NORM, 16.0 * nd, 4.0 * nd, nbn = launch_bnorm2_part(w, ne, nb, W.partr, st, any));
-      KL(F_REDUCE_NORM, 8.0 * nb * nbn, nb * nbn, launch_breduce_norm(W.partr, nb, nbn, W.hnorm, st, any));
-      KL(F_GIVENS, 0, 0, launch_bgivens(ctl, nb, m, j, W.hacc, W.hnorm, tol, st));
-      if (df) {
-        zdf* vn = Vdf + (size_t)(j + 1) * ne;
-        if (mixed) KL(F_SCALE, 40.0 * nd, 2.0 * nd, (launch_bscale_df<zdf, float>(W.wdf, W.hnorm, vn, W.vcur32, ne, nb, st, any)));
-        else KL(F_SCALE, 48.0 * nd, 2.0 * nd, (launch_bscale_df<zdf, double>(W.wdf, W.hnorm, vn, W.vcur64, ne, nb, st, any)));
-      } else {
-        KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_bscale_inv(w, W.hnorm, w, ne, nb, st, any));
-      }
+          KL(F_NORM, 16.0 * nd, 4.0 * nd, nbn = launch_bnorm2_part(w, ne, nb, W.partr, st, any));
+        KL(F_REDUCE_NORM, 8.0 * nb * nbn, nb * nbn, launch_breduce_norm(W.partr, nb, nbn, W.hnorm, st, any));
+        KL(F_GIVENS, 0, 0, launch_bgivens(ctl, nb, m, j, W.hacc, W.hnorm, tol, st));
+        if (df) {
+          zdf* vn = Vdf + (size_t)(j + 1) * ne;
+          if (mixed) KL(F_SCALE, 40.0 * nd, 2.0 * nd, (launch_bscale_df<zdf, float>(W.wdf, W.hnorm, vn, W.vcur32, ne, nb, st, any)));
+          else KL(F_SCALE, 48.0 * nd, 2.0 * nd, (launch_bscale_df<zdf, double>(W.wdf, W.hnorm, vn, W.vcur64, ne, nb, st, any)));
+        } else {
+          KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_bscale_inv(w, W.hnorm, w, ne, nb, st, any));
+        }
+      };
+      // one graph per Arnoldi column and batch width (the workspace and the tuned shapes of
+      // that width are fixed)
+      TRY(graph_step(c, G_BATCH + nb, j, W.V, st, step));
       TRY(check_launch(c, "batched Arnoldi step"));
       CU(cudaMemcpyAsync(W.hany + j, any, sizeof(int), cudaMemcpyDeviceToHost, st));
       CU(cudaEventRecord(c->ev[j % c->nev], st));

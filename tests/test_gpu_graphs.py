@@ -76,3 +76,20 @@ def test_fused_coarse_cycle_is_bit_exact(helm, n, bc, coarsest, dtype):
         xa, ia = a.solve(b)
         xf, i_f = f.solve(b)
         assert ia["iterations"] == i_f["iterations"] and torch.equal(xa, xf)
+
+
+@pytest.mark.parametrize("orth,cycle", [("fp64", "v"), ("df", "f")])
+def test_batched_graph_replay_is_bit_exact(helm, orth, cycle):
+    """The batched solver's Arnoldi columns replayed from graphs (per batch width) against plain
+    launches, for two widths in a row (the wider one reallocates the workspace)."""
+    w = I.workload("batched", 16)
+    kw = dict(krylov="fgmres", precision="mixed", orth=orth, cycle=cycle)
+    plain = helm.Solver(w["n"], w["h"], w["k2"], S, graphs=False, **kw)
+    graph = helm.Solver(w["n"], w["h"], w["k2"], S, graphs=True, **kw)
+    src = [(4 + 2 * (i % 4), 4 + 3 * (i // 4), 2) for i in range(8)]
+    B = torch.stack([plain.rhs_point([p]) for p in src])
+    for width in (3, 8, 8):
+        X0, i0 = plain.solve_batched(B[:width])
+        X1, i1 = graph.solve_batched(B[:width])
+        assert [a["iterations"] for a in i0] == [a["iterations"] for a in i1]
+        assert torch.equal(X0, X1)
