@@ -468,7 +468,7 @@ def run_batched_variant(torch, helm, inputs, orth="fp64", cycle="v"):
     s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov="fgmres", precision="mixed", orth=orth,
                     cycle=cycle)
     B = torch.stack([s.rhs_point([p]) for p in w["sources"]])
-    s.solve_batched(B[:4])  # warm-up (allocates the 32-wide workspace on the next call)
+    s.solve_batched(B)  # warm-up: allocates the 32-wide workspace, tunes its launch shapes, captures its graphs
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()

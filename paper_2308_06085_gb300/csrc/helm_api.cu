@@ -105,6 +105,7 @@ struct BatchWS {
   z64* vcur32 = nullptr;    // V-cycle input copy of v_j (double-float basis, mixed precision)
   z128 *part = nullptr, *hpass = nullptr, *hacc = nullptr;
   double *partr = nullptr, *hnorm = nullptr;
+  double* sw2 = nullptr;    // |w|^2 per right-hand side for the reorthogonalisation test
   BatchCtl h;               // host copy of the device pointers
   BatchCtl* ctl = nullptr;  // device
   int* log = nullptr;
@@ -186,6 +187,7 @@ struct helm_ctx {
   };
   std::vector<GraphEnt> graphs;
   std::vector<TuneRec> tune_log;  // every launch shape the autotuner timed
+  int mdot_df_variant = 0;        // slots per warp pass of the double-float inner products
   cudaStream_t gstream = nullptr;
   // IDR(s): shadow space P (s vectors), work G, U (s each), r, v, vh, t; control block
   int idr_s = 0;
@@ -742,6 +744,36 @@ helm_status autotune(helm_ctx* c, cudaStream_t st) {
       c->L[l].g.tile_ty[q] = lv[l].g.tile_ty[q];
       c->L[l].g.tile_ctas[q] = lv[l].g.tile_ctas[q];
     }
+  // double-float inner products: slots per warp pass (logged as level -1, slot 8 + variant)
+  if (c->p.orth == HELM_ORTH_DF && c->m >= 2) {
+    const size_t n = c->n0;
+    const int nv = std::min(16, c->m);
+    zdf* Vdf = reinterpret_cast<zdf*>(c->V);
+    CU(cudaMemsetAsync(c->V, 0x3f, (size_t)(nv + 1) * n * sizeof(z128), st));
+    CU(cudaMemsetAsync(c->wdf, 0x3f, n * sizeof(zdf), st));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int v = 0; v < 3; ++v) {
+      launch_mdot_df(Vdf, n, nv, c->wdf, n, c->part, 1, st, nullptr, v);
+      float ms = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        CU(cudaEventRecord(e0, st));
+        launch_mdot_df(Vdf, n, nv, c->wdf, n, c->part, 1, st, nullptr, v);
+        CU(cudaEventRecord(e1, st));
+        CU(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CU(cudaEventElapsedTime(&t, e0, e1));
+        ms = std::min(ms, t);
+      }
+      c->tune_log.push_back(TuneRec{-1, 8 + v, nv, 0, ms});
+      if (ms < best) { best = ms; c->mdot_df_variant = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TRY(check_launch(c, "autotune (inner products)"));
+  }
   CU(cudaStreamSynchronize(st));
   return HELM_OK;
 }
@@ -839,7 +871,8 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
           const int wn = (pass == 0 && sel) ? 1 : 0;
           int nb = 0;
           if (df)
-            KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nb = launch_mdot_df(Vdf, n, j + 1, wd, n, c->part, wn, st, a2));
+            KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd,
+               nb = launch_mdot_df(Vdf, n, j + 1, wd, n, c->part, wn, st, a2, c->mdot_df_variant));
           else
             KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nb = launch_mdot(c->V, n, j + 1, w, n, c->part, wn, st, a2));
           KL(F_REDUCE_DOTS, 16.0 * nv * nb, 2.0 * nv * nb,
@@ -895,7 +928,10 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
       const double nd = (double)n, k = jend + 1;
       KL(F_SOLUPDATE, 0, 0, launch_trisolve(ctl, c->H, m, c->gv, c->y, st));
       if (mixed) {
-        KL(F_SOLUPDATE, (8.0 * k + 32.0) * nd, 8.0 * k * nd, launch_xupdate<float>(ctl, c->Z32, n, c->y, x, n, st));
+        if (df)
+          KL(F_SOLUPDATE, (8.0 * k + 32.0) * nd, 8.0 * k * nd, launch_xupdate_df(ctl, c->Z32, n, c->y, x, n, st));
+        else
+          KL(F_SOLUPDATE, (8.0 * k + 32.0) * nd, 8.0 * k * nd, launch_xupdate<float>(ctl, c->Z32, n, c->y, x, n, st));
       } else if (flexible) {
         KL(F_SOLUPDATE, (16.0 * k + 32.0) * nd, 8.0 * k * nd, launch_xupdate<double>(ctl, c->Z64, n, c->y, x, n, st));
       } else {
@@ -983,6 +1019,7 @@ helm_status batch_alloc(helm_ctx* c, int nb) {
   TRY(dalloc(c, &W.hpass, (size_t)(m + 1) * nb));
   TRY(dalloc(c, &W.hacc, (size_t)(m + 1) * nb));
   TRY(dalloc(c, &W.hnorm, nb));
+  TRY(dalloc(c, &W.sw2, nb));
   TRY(dalloc(c, &W.log, m));
   BatchCtl& h = W.h;
   h.any = 0; h.pass2 = 0; h.max_iter = c->p.max_iter; h.pad = 0;
@@ -1131,7 +1168,7 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
             KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nbk = launch_bmdot(W.V, ne, j + 1, w, ne, nb, W.part, wn, st, a2));
           KL(F_REDUCE_DOTS, 16.0 * nv * nb * nbk, 2.0 * nv * nb * nbk,
              launch_breduce_dots(W.part, j + 1, nb, nbk, W.hpass, W.hacc, pass, wn ? j : -1, W.h.act, &ctl->pass2,
-                                 c->reorth_log, st, a2));
+                                 c->reorth_log, W.sw2, st, a2));
           if (df)
             KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_bgs_update_df(Vdf, ne, j + 1, nb, W.hpass, W.wdf, ne, st, a2));
           else
@@ -1170,7 +1207,10 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
     prof_flush(c, m);
     KL(F_SOLUPDATE, 0, 0, launch_btrisolve(ctl, nb, m, st));
     if (mixed)
-      KL(F_SOLUPDATE, 8.0 * m * nd, 8.0 * m * nd, launch_bxupdate<float>(ctl, nb, m, W.Z32, ne, W.Xt, ne, st));
+      if (c->p.orth == HELM_ORTH_DF)
+        KL(F_SOLUPDATE, 8.0 * m * nd, 8.0 * m * nd, launch_bxupdate_df(ctl, nb, m, W.Z32, ne, W.Xt, ne, st));
+      else
+        KL(F_SOLUPDATE, 8.0 * m * nd, 8.0 * m * nd, launch_bxupdate<float>(ctl, nb, m, W.Z32, ne, W.Xt, ne, st));
     else
       KL(F_SOLUPDATE, 16.0 * m * nd, 8.0 * m * nd, launch_bxupdate<double>(ctl, nb, m, W.Z64, ne, W.Xt, ne, st));
     KL(F_RESID, 56.0 * nd, 24.0 * nd, (launch_resid<double, double, double, double>(g0, 1.0, 0.0, k2, W.Xt, W.Bt, W.r, st, c->one)));

@@ -70,6 +70,11 @@ void launch_givens(KrylovCtl* ctl, z128* H, int m, int j, int jmax, const z128* 
                    double* cs, z128* sn, z128* gvec, double tol, double* hist, int hist_len, cudaStream_t st);
 // y = H(0:k, 0:k)^{-1} g with k = jend + 1
 void launch_trisolve(const KrylovCtl* ctl, const z128* H, int m, const z128* gvec, z128* y, cudaStream_t st);
+// x += Z y in double-float arithmetic for complex64 Z (x FP64)
+void launch_xupdate_df(const KrylovCtl* ctl, const z64* Z, size_t ld, const z128* y, z128* x, size_t n,
+                       cudaStream_t st);
+void launch_bxupdate_df(const BatchCtl* bc, int nb, int m, const z64* Z, size_t ld, z128* x, size_t ne,
+                        cudaStream_t st);
 // x += sum_{i<=jend} y_i Z_i   (Z c128 or c64)
 template <typename TZ>
 void launch_xupdate(const KrylovCtl* ctl, const cx<TZ>* Z, size_t ld, const z128* y, z128* x, size_t n,
@@ -78,8 +83,9 @@ void launch_xupdate(const KrylovCtl* ctl, const cx<TZ>* Z, size_t ld, const z128
 void launch_combine(const KrylovCtl* ctl, const z128* V, size_t ld, const z128* y, z128* w, size_t n,
                     cudaStream_t st);
 // double-float Gram-Schmidt (basis stored as zdf)
+// variant: slots per warp per pass, 0: 4, 1: 2, 2: 8 (chosen by the autotuner)
 int launch_mdot_df(const zdf* V, size_t ld, int nv, const zdf* w, size_t n, z128* part, int with_norm,
-                   cudaStream_t st, const int* active);
+                   cudaStream_t st, const int* active, int variant = 0);
 void launch_gs_update_df(const zdf* V, size_t ld, int nv, const z128* h, zdf* w, size_t n, cudaStream_t st,
                          const int* active);
 // partial sums of |x|^2 (double-float x) into partr; returns nb
@@ -147,7 +153,8 @@ void launch_breduce_norm(const double* part, int nb, int nblk, double* out, cuda
 int launch_bmdot(const z128* V, size_t ld, int nv, const z128* w, size_t ne, int nb, z128* part, int with_norm,
                  cudaStream_t st, const int* active);
 void launch_breduce_dots(const z128* part, int nv, int nb, int nblk, z128* hpass, z128* hacc, int accumulate,
-                         int decide_j, const int* act, int* pass2, int* log, cudaStream_t st, const int* active);
+                         int decide_j, const int* act, int* pass2, int* log, double* sw2, cudaStream_t st,
+                         const int* active);
 void launch_bgs_update(const z128* V, size_t ld, int nv, int nb, const z128* h, z128* w, size_t ne, cudaStream_t st,
                        const int* active);
 void launch_bscale_inv(const z128* in, const double* s, z128* out, size_t ne, int nb, cudaStream_t st,

@@ -98,7 +98,7 @@ __device__ __forceinline__ int share_width(int nslot) {
 
 // TILE points of w per shared-memory tile (16 KB): few barriers per point keep loads in
 // flight.
-template <typename E, typename ACC, int TILE>
+template <typename E, typename ACC, int TILE, int KSV = KS>
 __global__ void __launch_bounds__(NT)
     k_mdot(const E* __restrict__ V, size_t ld, int nv, const E* __restrict__ w, size_t n, z128* __restrict__ part,
            int with_norm, const int* __restrict__ active) {
@@ -115,10 +115,10 @@ __global__ void __launch_bounds__(NT)
   const int wps = ACC::kBalanced ? share_width(nslot) : (nslot >= NW ? 1 : NW / nslot);
   const int sub = warp % wps, sfirst = warp / wps, sstep = NW / wps;
   double* partd = reinterpret_cast<double*>(part);
-  for (int sbase = 0; sbase * sstep < nslot; sbase += KS) {
-    ACC acc[KS];
+  for (int sbase = 0; sbase * sstep < nslot; sbase += KSV) {
+    ACC acc[KSV];
 #pragma unroll
-    for (int k = 0; k < KS; ++k) acc[k].zero();
+    for (int k = 0; k < KSV; ++k) acc[k].zero();
     for (size_t t0 = p0; t0 < p1; t0 += TILE) {
       const int tn = (int)min((size_t)TILE, p1 - t0);
       __syncthreads();
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(NT)
       for (int q = sub * 32 + lane; q < tn; q += 32 * wps) {
         const E wv = sw[q];
 #pragma unroll
-        for (int k = 0; k < KS; ++k) {
+        for (int k = 0; k < KSV; ++k) {
           const int sl = sfirst + (sbase + k) * sstep;
           if (sl < nv) acc[k].mac(ldg(V + (size_t)sl * ld + t0 + q), wv);
           else if (sl == nv && with_norm) acc[k].norm(wv);
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(NT)
       }
     }
 #pragma unroll
-    for (int k = 0; k < KS; ++k) {
+    for (int k = 0; k < KSV; ++k) {
       const int sl = sfirst + (sbase + k) * sstep;
       double r, i;
       acc[k].reduce_warp(r, i);
@@ -399,6 +399,32 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
+// x += sum_i y_i z_i for complex64 z_i in double-float arithmetic (FP32 instructions only; the
+// z_i are exact, the y_i carried as (hi, lo)): the solution update of the mixed-precision solver
+// with double-float Gram-Schmidt.  x itself stays FP64: the double-float sum is added once.
+__global__ void __launch_bounds__(NT)
+    k_xupdate_df(const KrylovCtl* __restrict__ ctl, const z64* __restrict__ Z, size_t ld, const z128* __restrict__ y,
+                 z128* __restrict__ x, size_t n) {
+  __shared__ zdf sy[MAX_BASIS];
+  const int k = ctl->jend + 1;
+  for (int i = threadIdx.x; i < k; i += NT) sy[i] = df_from(y[i]);
+  __syncthreads();
+  for (size_t p = blockIdx.x * (size_t)NT + threadIdx.x; p < n; p += (size_t)gridDim.x * NT) {
+    float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
+    for (int i = 0; i < k; ++i) {
+      const z64 zv = ldg(Z + (size_t)i * ld + p);
+      const zdf c = sy[i];
+      // re += y.re z.re - y.im z.im ; im += y.re z.im + y.im z.re
+      df_mac(c.rh, c.rl, zv.re, 0.f, rs, rc);
+      df_mac(-c.ih, -c.il, zv.im, 0.f, rs, rc);
+      df_mac(c.rh, c.rl, zv.im, 0.f, is, ic);
+      df_mac(c.ih, c.il, zv.re, 0.f, is, ic);
+    }
+    const z128 xv = x[p];
+    x[p] = mkc<double>(xv.re + ((double)rs + (double)rc), xv.im + ((double)is + (double)ic));
+  }
+}
+
 __global__ void __launch_bounds__(NT)
     k_combine(const KrylovCtl* __restrict__ ctl, const z128* __restrict__ V, size_t ld, const z128* __restrict__ y,
               z128* __restrict__ w, size_t n) {
@@ -597,15 +623,28 @@ void launch_xupdate(const KrylovCtl* ctl, const cx<TZ>* Z, size_t ld, const z128
 }
 template void launch_xupdate<double>(const KrylovCtl*, const z128*, size_t, const z128*, z128*, size_t, cudaStream_t);
 template void launch_xupdate<float>(const KrylovCtl*, const z64*, size_t, const z128*, z128*, size_t, cudaStream_t);
+void launch_xupdate_df(const KrylovCtl* ctl, const z64* Z, size_t ld, const z128* y, z128* x, size_t n,
+                       cudaStream_t st) {
+  k_xupdate_df<<<stream_blocks(n), NT, 0, st>>>(ctl, Z, ld, y, x, n);
+}
 void launch_combine(const KrylovCtl* ctl, const z128* V, size_t ld, const z128* y, z128* w, size_t n,
                     cudaStream_t st) {
   k_combine<<<stream_blocks(n), NT, 0, st>>>(ctl, V, ld, y, w, n);
 }
-int launch_mdot_df(const zdf* V, size_t ld, int nv, const zdf* w, size_t n, z128* part, int with_norm,
-                   cudaStream_t st, const int* active) {
-  static const int nb = wave_blocks(k_mdot<zdf, AccF, 4 * NT>);
-  k_mdot<zdf, AccF, 4 * NT><<<nb, NT, 0, st>>>(V, ld, nv, w, n, part, with_norm, active);
+template <int KSV>
+int mdot_df_ks(const zdf* V, size_t ld, int nv, const zdf* w, size_t n, z128* part, int with_norm, cudaStream_t st,
+               const int* active) {
+  static const int nb = wave_blocks(k_mdot<zdf, AccF, 4 * NT, KSV>);
+  k_mdot<zdf, AccF, 4 * NT, KSV><<<nb, NT, 0, st>>>(V, ld, nv, w, n, part, with_norm, active);
   return nb;
+}
+int launch_mdot_df(const zdf* V, size_t ld, int nv, const zdf* w, size_t n, z128* part, int with_norm,
+                   cudaStream_t st, const int* active, int variant) {
+  switch (variant) {
+    case 1: return mdot_df_ks<2>(V, ld, nv, w, n, part, with_norm, st, active);
+    case 2: return mdot_df_ks<8>(V, ld, nv, w, n, part, with_norm, st, active);
+    default: return mdot_df_ks<4>(V, ld, nv, w, n, part, with_norm, st, active);
+  }
 }
 void launch_gs_update_df(const zdf* V, size_t ld, int nv, const z128* h, zdf* w, size_t n, cudaStream_t st,
                          const int* active) {

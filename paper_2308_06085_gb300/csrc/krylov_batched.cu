@@ -10,6 +10,8 @@
 // >= nb, then across warps and blocks in a fixed order (deterministic).
 #include "internal.cuh"
 
+#include <type_traits>
+
 namespace helm {
 
 namespace {
@@ -183,50 +185,55 @@ __global__ void __launch_bounds__(NT)
 // the projection removed more than half of |w_r|^2.
 __global__ void __launch_bounds__(NT)
     k_breduce_dots(const z128* __restrict__ part, int nv, int nb, int nblk, z128* __restrict__ hpass,
-                   z128* __restrict__ hacc, int accumulate, int decide_j, const int* __restrict__ act,
-                   int* __restrict__ pass2, int* __restrict__ log, const int* __restrict__ active) {
+                   z128* __restrict__ hacc, int accumulate, int decide_j, double* __restrict__ sw2,
+                   const int* __restrict__ active) {
   if (active && *active == 0) return;
-  __shared__ double sw2[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int rows = (decide_j >= 0 ? nv + 1 : nv) * nb;
-  for (int row = warp; row < rows; row += NW) {
-    double re = 0.0, im = 0.0;
-    for (int b = lane; b < nblk; b += 32) {
-      const z128 v = part[(size_t)row * RED_STRIDE + b];
-      re += v.re;
-      im += v.im;
-    }
-    for (int o = 16; o; o >>= 1) {
-      re += __shfl_xor_sync(0xffffffffu, re, o);
-      im += __shfl_xor_sync(0xffffffffu, im, o);
-    }
-    if (lane == 0) {
-      if (row >= nv * nb) {
-        sw2[row - nv * nb] = re;
+  // one warp per (basis vector, right-hand side) row, over every block of the grid
+  const int row = blockIdx.x * NW + (threadIdx.x >> 5);
+  if (row >= rows) return;
+  double re = 0.0, im = 0.0;
+  for (int b = lane; b < nblk; b += 32) {
+    const z128 v = part[(size_t)row * RED_STRIDE + b];
+    re += v.re;
+    im += v.im;
+  }
+  for (int o = 16; o; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) {
+    if (row >= nv * nb) {
+      sw2[row - nv * nb] = re;
+    } else {
+      hpass[row] = mkc<double>(re, im);
+      if (accumulate) {
+        hacc[row].re += re;
+        hacc[row].im += im;
       } else {
-        hpass[row] = mkc<double>(re, im);
-        if (accumulate) {
-          hacc[row].re += re;
-          hacc[row].im += im;
-        } else {
-          hacc[row] = mkc<double>(re, im);
-        }
+        hacc[row] = mkc<double>(re, im);
       }
     }
   }
-  if (decide_j < 0) return;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int again = 0;
-    for (int r = 0; r < nb; ++r) {
-      if (!act[r]) continue;
-      double h2 = 0.0;
-      for (int i = 0; i < nv; ++i) h2 += hpass[i * nb + r].re * hpass[i * nb + r].re + hpass[i * nb + r].im * hpass[i * nb + r].im;
-      again |= !(sw2[r] - h2 >= 0.5 * sw2[r]);
-    }
-    *pass2 = again;
-    log[decide_j] = again;
+}
+
+// The Daniel-Gragg-Kaufman-Stewart test over the active right-hand sides: a second pass when
+// the first one removed more than half of |w|^2 for any of them.
+__global__ void k_bdecide(const z128* __restrict__ hpass, const double* __restrict__ sw2, int nv, int nb,
+                          int decide_j, const int* __restrict__ act, int* __restrict__ pass2, int* __restrict__ log,
+                          const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  if (threadIdx.x != 0) return;
+  int again = 0;
+  for (int r = 0; r < nb; ++r) {
+    if (!act[r]) continue;
+    double h2 = 0.0;
+    for (int i = 0; i < nv; ++i) h2 += hpass[i * nb + r].re * hpass[i * nb + r].re + hpass[i * nb + r].im * hpass[i * nb + r].im;
+    again |= !(sw2[r] - h2 >= 0.5 * sw2[r]);
   }
+  *pass2 = again;
+  log[decide_j] = again;
 }
 
 // w[e] -= sum_i h[i][r] V_i[e]
@@ -238,8 +245,9 @@ __global__ void __launch_bounds__(NT)
   for (int i = threadIdx.x; i < nv * nb; i += NT) shb[i] = h[i];
   __syncthreads();
   const size_t stride = (size_t)gridDim.x * NT;
+  // nb is a power of two <= 32 and divides the stride, so a thread keeps one right-hand side
+  const int r = (int)((blockIdx.x * (size_t)NT + threadIdx.x) & (size_t)(nb - 1));
   for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
-    const int r = (int)(e % nb);
     z128 acc = w[e];
     for (int i = 0; i < nv; ++i) {
       const z128 v = ldg(V + (size_t)i * ld + e);
@@ -262,8 +270,8 @@ __global__ void __launch_bounds__(NT)
   for (int i = threadIdx.x; i < nv * nb; i += NT) shf[i] = df_from(h[i]);
   __syncthreads();
   const size_t stride = (size_t)gridDim.x * NT;
+  const int r = (int)((blockIdx.x * (size_t)NT + threadIdx.x) & (size_t)(nb - 1));  // fixed per thread
   for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
-    const int r = (int)(e % nb);
     float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
     for (int i = 0; i < nv; ++i) {
       const zdf v = ldg(V + (size_t)i * ld + e);
@@ -286,23 +294,39 @@ __global__ void __launch_bounds__(NT)
 __device__ __forceinline__ zdf bscale_one(const z128& v, double d) {
   return d > 0.0 ? df_from(mkc<double>(v.re / d, v.im / d)) : zdf{0.f, 0.f, 0.f, 0.f};
 }
-__device__ __forceinline__ zdf bscale_one(const zdf& v, double d) {
-  if (!(d > 0.0)) return zdf{0.f, 0.f, 0.f, 0.f};
-  float ih, il;
-  df_split(1.0 / d, ih, il);
+// the double-float reciprocal of d (0 when d is not positive), computed once per thread
+struct DfRecip {
+  float hi, lo;
+  bool pos;
+  __device__ explicit DfRecip(double d) : hi(0.f), lo(0.f), pos(d > 0.0) {
+    if (pos) df_split(1.0 / d, hi, lo);
+  }
+};
+__device__ __forceinline__ zdf bscale_one(const zdf& v, const DfRecip& q) {
+  if (!q.pos) return zdf{0.f, 0.f, 0.f, 0.f};
   zdf z;
-  df_mul(v.rh, v.rl, ih, il, z.rh, z.rl);
-  df_mul(v.ih, v.il, ih, il, z.ih, z.il);
+  df_mul(v.rh, v.rl, q.hi, q.lo, z.rh, z.rl);
+  df_mul(v.ih, v.il, q.hi, q.lo, z.ih, z.il);
   return z;
 }
+template <typename TI>
+__device__ __forceinline__ typename std::conditional<std::is_same<TI, zdf>::value, DfRecip, double>::type
+scale_arg(double d) {
+  return typename std::conditional<std::is_same<TI, zdf>::value, DfRecip, double>::type(d);
+}
+
 template <typename TI, typename TC>
 __global__ void __launch_bounds__(NT)
     k_bscale_df(const TI* __restrict__ in, const double* __restrict__ s, zdf* __restrict__ out,
                 cx<TC>* __restrict__ copy, size_t ne, int nb, const int* __restrict__ active) {
   if (active && *active == 0) return;
   const size_t stride = (size_t)gridDim.x * NT;
+  const double sr = s[(blockIdx.x * (size_t)NT + threadIdx.x) & (size_t)(nb - 1)];  // fixed per thread
+  // the scale as the input type wants it: FP64 for complex128 input, a double-float
+  // reciprocal for double-float input (one FP64 division per thread, not per element)
+  const auto sc = scale_arg<TI>(sr);
   for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
-    const zdf z = bscale_one(in[e], s[e % nb]);
+    const zdf z = bscale_one(in[e], sc);
     out[e] = z;
     if (sizeof(TC) == 8) {
       const z128 c = df_to_c128(z);
@@ -319,8 +343,8 @@ __global__ void __launch_bounds__(NT)
                  const int* __restrict__ active) {
   if (active && *active == 0) return;
   const size_t stride = (size_t)gridDim.x * NT;
+  const double d = s[(blockIdx.x * (size_t)NT + threadIdx.x) & (size_t)(nb - 1)];  // fixed per thread
   for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
-    const double d = s[e % nb];
     const z128 v = in[e];
     out[e] = d > 0.0 ? mkc<double>(v.re / d, v.im / d) : mkc<double>(0.0, 0.0);
   }
@@ -457,13 +481,49 @@ __global__ void __launch_bounds__(NT)
   }
   __syncthreads();
   const size_t stride = (size_t)gridDim.x * NT;
+  const int r = (int)((blockIdx.x * (size_t)NT + threadIdx.x) & (size_t)(nb - 1));  // fixed per thread
+  const int k = kr[r];
   for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
-    const int r = (int)(e % nb);
-    const int k = kr[r];
     z128 acc = x[e];
     for (int i = 0; i < kmax; ++i)
       if (i < k) acc = cfma(sy[i * nb + r], cvt<double>(ldg(Z + (size_t)i * ld + e)), acc);
     x[e] = acc;
+  }
+}
+
+// The same update in double-float arithmetic for complex64 Z (mixed precision with
+// double-float Gram-Schmidt): FP32 instructions only, x stays FP64.
+__global__ void __launch_bounds__(NT)
+    k_bxupdate_df(const BatchCtl* __restrict__ bc, int nb, int m, const z64* __restrict__ Z, size_t ld,
+                  z128* __restrict__ x, size_t ne) {
+  extern __shared__ zdf syd[];
+  __shared__ int kr[32];
+  __shared__ int kmax;
+  if (threadIdx.x < (unsigned)nb) kr[threadIdx.x] = bc->jend[threadIdx.x] + 1;
+  for (int i = threadIdx.x; i < m * nb; i += NT) syd[i] = df_from(bc->y[i]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int mx = 0;
+    for (int r = 0; r < nb; ++r) mx = max(mx, kr[r]);
+    kmax = mx;
+  }
+  __syncthreads();
+  const size_t stride = (size_t)gridDim.x * NT;
+  const int r = (int)((blockIdx.x * (size_t)NT + threadIdx.x) & (size_t)(nb - 1));  // fixed per thread
+  const int k = kr[r];
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
+    float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
+    for (int i = 0; i < kmax; ++i)
+      if (i < k) {
+        const z64 zv = ldg(Z + (size_t)i * ld + e);
+        const zdf c = syd[i * nb + r];
+        df_mac(c.rh, c.rl, zv.re, 0.f, rs, rc);
+        df_mac(-c.ih, -c.il, zv.im, 0.f, rs, rc);
+        df_mac(c.rh, c.rl, zv.im, 0.f, is, ic);
+        df_mac(c.ih, c.il, zv.re, 0.f, is, ic);
+      }
+    const z128 xv = x[e];
+    x[e] = mkc<double>(xv.re + ((double)rs + (double)rc), xv.im + ((double)is + (double)ic));
   }
 }
 
@@ -541,8 +601,12 @@ template void launch_bscale_df<z128, float>(const z128*, const double*, zdf*, z6
 template void launch_bscale_df<zdf, double>(const zdf*, const double*, zdf*, z128*, size_t, int, cudaStream_t, const int*);
 template void launch_bscale_df<zdf, float>(const zdf*, const double*, zdf*, z64*, size_t, int, cudaStream_t, const int*);
 void launch_breduce_dots(const z128* part, int nv, int nb, int nblk, z128* hpass, z128* hacc, int accumulate,
-                         int decide_j, const int* act, int* pass2, int* log, cudaStream_t st, const int* active) {
-  k_breduce_dots<<<1, NT, 0, st>>>(part, nv, nb, nblk, hpass, hacc, accumulate, decide_j, act, pass2, log, active);
+                         int decide_j, const int* act, int* pass2, int* log, double* sw2, cudaStream_t st,
+                         const int* active) {
+  const int rows = (decide_j >= 0 ? nv + 1 : nv) * nb;
+  k_breduce_dots<<<(rows + NW - 1) / NW, NT, 0, st>>>(part, nv, nb, nblk, hpass, hacc, accumulate, decide_j, sw2,
+                                                      active);
+  if (decide_j >= 0) k_bdecide<<<1, 32, 0, st>>>(hpass, sw2, nv, nb, decide_j, act, pass2, log, active);
 }
 void launch_bgs_update(const z128* V, size_t ld, int nv, int nb, const z128* h, z128* w, size_t ne, cudaStream_t st,
                        const int* active) {
@@ -567,6 +631,10 @@ void launch_bxupdate(const BatchCtl* bc, int nb, int m, const cx<TZ>* Z, size_t 
 }
 template void launch_bxupdate<double>(const BatchCtl*, int, int, const z128*, size_t, z128*, size_t, cudaStream_t);
 template void launch_bxupdate<float>(const BatchCtl*, int, int, const z64*, size_t, z128*, size_t, cudaStream_t);
+void launch_bxupdate_df(const BatchCtl* bc, int nb, int m, const z64* Z, size_t ld, z128* x, size_t ne,
+                        cudaStream_t st) {
+  k_bxupdate_df<<<stream_blocks(ne), NT, sizeof(zdf) * m * nb, st>>>(bc, nb, m, Z, ld, x, ne);
+}
 void launch_to_batch(const z128* src, z128* dst, size_t n, int nb, int nrhs, cudaStream_t st) {
   k_to_batch<<<stream_blocks(n * nb), NT, 0, st>>>(src, dst, n, nb, nrhs);
 }
