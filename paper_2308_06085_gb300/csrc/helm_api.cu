@@ -96,6 +96,7 @@ struct BatchWS {
   // tuned launch shapes per batch width 2^t: the V-cycle grids of every level and the FP64
   // finest-level operator
   bool tuned[6] = {};
+  int bmdot_variant[6] = {};  // slots per warp pass of the double-float dots, per width
   int tty[6][MAX_LEVELS][8] = {}, tct[6][MAX_LEVELS][8] = {};
   int g0ty[6][8] = {}, g0ct[6][8] = {};
   z128 *V = nullptr, *Z64 = nullptr, *w = nullptr, *r = nullptr, *Bt = nullptr, *Xt = nullptr;
@@ -1104,6 +1105,31 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
         for (int q = 0; q < 8; ++q) { W.tty[t][l][q] = g.tile_ty[q]; W.tct[t][l][q] = g.tile_ctas[q]; }
       }
       for (int q = 0; q < 8; ++q) { W.g0ty[t][q] = g0.tile_ty[q]; W.g0ct[t][q] = g0.tile_ctas[q]; }
+      if (c->p.orth == HELM_ORTH_DF && m >= 2) {
+        // double-float dots: slots per warp pass (logged as level -2, slot 8 + variant)
+        const int nvt = std::min(16, m);
+        zdf* Vd = reinterpret_cast<zdf*>(W.V);
+        CU(cudaMemsetAsync(W.V, 0x3f, (size_t)(nvt + 1) * ne * sizeof(z128), st));
+        CU(cudaMemsetAsync(W.wdf, 0x3f, ne * sizeof(zdf), st));
+        cudaEvent_t e0, e1;
+        CU(cudaEventCreate(&e0));
+        CU(cudaEventCreate(&e1));
+        float best = 1e30f;
+        for (int v = 0; v < 3; ++v) {
+          launch_bmdot_df(Vd, ne, nvt, W.wdf, ne, nb, W.part, 1, st, nullptr, v);
+          CU(cudaEventRecord(e0, st));
+          launch_bmdot_df(Vd, ne, nvt, W.wdf, ne, nb, W.part, 1, st, nullptr, v);
+          CU(cudaEventRecord(e1, st));
+          CU(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CU(cudaEventElapsedTime(&ms, e0, e1));
+          c->tune_log.push_back(TuneRec{-2, 8 + v, nvt, nb, ms});
+          if (ms < best) { best = ms; W.bmdot_variant[t] = v; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        TRY(check_launch(c, "autotune (batched inner products)"));
+      }
       W.tuned[t] = true;
     } else {
       for (int l = 0; l < c->nlev; ++l) {
@@ -1112,6 +1138,12 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
       }
       for (int q = 0; q < 8; ++q) { g0.tile_ty[q] = W.g0ty[t][q]; g0.tile_ctas[q] = W.g0ct[t][q]; }
     }
+  }
+  int bvar = 0;
+  {
+    int t = 0;
+    while ((1 << t) < nb) ++t;
+    bvar = W.bmdot_variant[t];
   }
   const double nd = (double)ne;
   int nblk = launch_bnorm2_part(W.Bt, ne, nb, W.partr, st, c->one);
@@ -1163,7 +1195,8 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
           const int wn = (pass == 0 && sel) ? 1 : 0;
           int nbk = 0;
           if (df)
-            KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nbk = launch_bmdot_df(Vdf, ne, j + 1, W.wdf, ne, nb, W.part, wn, st, a2));
+            KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd,
+               nbk = launch_bmdot_df(Vdf, ne, j + 1, W.wdf, ne, nb, W.part, wn, st, a2, bvar));
           else
             KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nbk = launch_bmdot(W.V, ne, j + 1, w, ne, nb, W.part, wn, st, a2));
           KL(F_REDUCE_DOTS, 16.0 * nv * nb * nbk, 2.0 * nv * nb * nbk,

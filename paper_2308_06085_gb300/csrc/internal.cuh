@@ -162,7 +162,7 @@ void launch_bscale_inv(const z128* in, const double* s, z128* out, size_t ne, in
 // double-float Gram-Schmidt variants (basis and Arnoldi vector as zdf)
 int launch_bnorm2_part_df(const zdf* x, size_t ne, int nb, double* part, cudaStream_t st, const int* active);
 int launch_bmdot_df(const zdf* V, size_t ld, int nv, const zdf* w, size_t ne, int nb, z128* part, int with_norm,
-                    cudaStream_t st, const int* active);
+                    cudaStream_t st, const int* active, int variant = 0);
 void launch_bgs_update_df(const zdf* V, size_t ld, int nv, int nb, const z128* h, zdf* w, size_t ne, cudaStream_t st,
                           const int* active);
 template <typename TI, typename TC>

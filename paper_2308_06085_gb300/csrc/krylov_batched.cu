@@ -49,6 +49,7 @@ __device__ __forceinline__ void df_group_sum(float& s, float& c, int nb) {
 
 // Accumulators of one lane: FP64 (z128 vectors) or double-float (zdf vectors, FP32 pipes).
 struct BAccD {
+  static constexpr bool kBalanced = false;
   double re, im;
   __device__ void zero() { re = im = 0.0; }
   __device__ void mac(const z128& v, const z128& w) { cdot_acc(v, w, re, im); }
@@ -62,6 +63,7 @@ struct BAccD {
   }
 };
 struct BAccF {
+  static constexpr bool kBalanced = true;
   float rs, rc, is, ic;
   __device__ void zero() { rs = rc = is = ic = 0.f; }
   __device__ void mac(const zdf& v, const zdf& w) {
@@ -122,7 +124,18 @@ __global__ void __launch_bounds__(NT)
 }
 
 // Inner products conj(V_i) . w per right-hand side; slot nv holds |w_r|^2 when with_norm.
-template <typename E, typename ACC>
+// Warps sharing one slot for double-float accumulation: the least sharing that leaves at most
+// 1/8 of the warp-slots idle (latency-bound, so evenly loaded warps keep more loads in flight).
+__device__ __forceinline__ int bshare_width(int nslot) {
+  for (int wps = 1; wps < NW; wps <<= 1) {
+    const int groups = NW / wps;
+    const int cap = (nslot + groups - 1) / groups * groups;
+    if (8 * (cap - nslot) <= cap) return wps;
+  }
+  return NW;
+}
+
+template <typename E, typename ACC, int KSV = KS>
 __global__ void __launch_bounds__(NT)
     k_bmdot(const E* __restrict__ V, size_t ld, int nv, const E* __restrict__ w, size_t ne, int nb,
             z128* __restrict__ part, int with_norm, const int* __restrict__ active) {
@@ -133,13 +146,13 @@ __global__ void __launch_bounds__(NT)
   block_range_e(ne, nb, e0, e1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nslot = nv + (with_norm ? 1 : 0);
-  const int wps = nslot >= NW ? 1 : NW / nslot;
+  const int wps = ACC::kBalanced ? bshare_width(nslot) : (nslot >= NW ? 1 : NW / nslot);
   const int sub = warp % wps, sfirst = warp / wps, sstep = NW / wps;
   double* partd = reinterpret_cast<double*>(part);
-  for (int sbase = 0; sbase * sstep < nslot; sbase += KS) {
-    ACC acc[KS];
+  for (int sbase = 0; sbase * sstep < nslot; sbase += KSV) {
+    ACC acc[KSV];
 #pragma unroll
-    for (int k = 0; k < KS; ++k) acc[k].zero();
+    for (int k = 0; k < KSV; ++k) acc[k].zero();
     for (size_t t0 = e0; t0 < e1; t0 += TILE) {
       const int tn = (int)min((size_t)TILE, e1 - t0);
       __syncthreads();
@@ -148,7 +161,7 @@ __global__ void __launch_bounds__(NT)
       for (int q = sub * 32 + lane; q < tn; q += 32 * wps) {
         const E wv = sw[q];
 #pragma unroll
-        for (int k = 0; k < KS; ++k) {
+        for (int k = 0; k < KSV; ++k) {
           const int sl = sfirst + (sbase + k) * sstep;
           if (sl < nv) acc[k].mac(ldg(V + (size_t)sl * ld + t0 + q), wv);
           else if (sl == nv && with_norm) acc[k].norm(wv);
@@ -156,7 +169,7 @@ __global__ void __launch_bounds__(NT)
       }
     }
 #pragma unroll
-    for (int k = 0; k < KS; ++k) {
+    for (int k = 0; k < KSV; ++k) {
       const int sl = sfirst + (sbase + k) * sstep;
       double r, i;
       acc[k].group(nb, r, i);
@@ -581,11 +594,20 @@ int launch_bmdot(const z128* V, size_t ld, int nv, const z128* w, size_t ne, int
   k_bmdot<z128, BAccD><<<nblk, NT, 0, st>>>(V, ld, nv, w, ne, nb, part, with_norm, active);
   return nblk;
 }
-int launch_bmdot_df(const zdf* V, size_t ld, int nv, const zdf* w, size_t ne, int nb, z128* part, int with_norm,
-                    cudaStream_t st, const int* active) {
-  static const int nblk = wave_blocks(k_bmdot<zdf, BAccF>, 0);
-  k_bmdot<zdf, BAccF><<<nblk, NT, 0, st>>>(V, ld, nv, w, ne, nb, part, with_norm, active);
+template <int KSV>
+int bmdot_df_ks(const zdf* V, size_t ld, int nv, const zdf* w, size_t ne, int nb, z128* part, int with_norm,
+                cudaStream_t st, const int* active) {
+  static const int nblk = wave_blocks(k_bmdot<zdf, BAccF, KSV>, 0);
+  k_bmdot<zdf, BAccF, KSV><<<nblk, NT, 0, st>>>(V, ld, nv, w, ne, nb, part, with_norm, active);
   return nblk;
+}
+int launch_bmdot_df(const zdf* V, size_t ld, int nv, const zdf* w, size_t ne, int nb, z128* part, int with_norm,
+                    cudaStream_t st, const int* active, int variant) {
+  switch (variant) {
+    case 1: return bmdot_df_ks<2>(V, ld, nv, w, ne, nb, part, with_norm, st, active);
+    case 2: return bmdot_df_ks<8>(V, ld, nv, w, ne, nb, part, with_norm, st, active);
+    default: return bmdot_df_ks<4>(V, ld, nv, w, ne, nb, part, with_norm, st, active);
+  }
 }
 void launch_bgs_update_df(const zdf* V, size_t ld, int nv, int nb, const z128* h, zdf* w, size_t ne, cudaStream_t st,
                           const int* active) {
