@@ -45,6 +45,7 @@ def lib():
         L.oracle_vcycle.argtypes = [vp, dp, dp]
         L.oracle_fcycle.argtypes = [vp, dp, dp]
         L.oracle_set_cycle.argtypes = [vp, C.c_int]
+        L.oracle_set_coarse_tol.argtypes = [vp, C.c_double]
         L.oracle_vcycle_down.argtypes = [vp, i, dp, dp]
         L.oracle_vcycle_up.argtypes = [vp, i, dp, dp, dp]
         L.oracle_coarse_solve.argtypes = [vp, dp, dp]
@@ -153,7 +154,8 @@ def grad_k2(u, lam, k2, h, bc, grad=None):
 class Solver:
     """Oracle multigrid hierarchy + V-cycle + right-preconditioned GMRES(m)."""
 
-    def __init__(self, n, h, bc, k2, beta1=1.0, beta2=-0.5, omega=0.8, nu1=1, nu2=1, coarsest_n=4, cycle="v"):
+    def __init__(self, n, h, bc, k2, beta1=1.0, beta2=-0.5, omega=0.8, nu1=1, nu2=1, coarsest_n=4, cycle="v",
+                 coarse_tol=0.0):
         n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(n)
         self.bc = bc
         self.h = h
@@ -164,6 +166,8 @@ class Solver:
             raise ValueError("oracle_create rejected the arguments")
         self.beta1, self.beta2, self.omega = beta1, beta2, omega
         lib().oracle_set_cycle(self._ctx, {"v": 0, "f": 1}[cycle])
+        # 0: exact coarsest solve; > 0: the paper's full GMRES to that relative residual
+        lib().oracle_set_coarse_tol(self._ctx, coarse_tol)
 
     def __del__(self):
         ctx = getattr(self, "_ctx", None)

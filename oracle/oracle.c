@@ -236,6 +236,7 @@ typedef struct {
 typedef struct {
   int bc, nlev, nu1, nu2;
   int cycle;    /* preconditioner of the Krylov methods: 0 one V-cycle, 1 one F-cycle */
+  double coarse_tol; /* 0: exact coarsest solve (LU); > 0: full GMRES to this relative residual */
   double beta1, beta2, omega;
   olevel L[MAXLEV];
   int nc;       /* coarsest unknown count */
@@ -333,10 +334,81 @@ void oracle_level_k2(void* vctx, int l, double* out) {
 }
 
 /* Exact coarsest-grid solve e = M_L^{-1} b (Algorithm 1, step 4, on the last level). */
+/* The paper's coarsest-grid solver (Sec. 5): full (unrestarted, unpreconditioned) GMRES on
+ * M_L e = b from e = 0, stopped when ||b - M_L e|| / ||b|| <= coarse_tol; modified
+ * Gram-Schmidt and complex Givens rotations, as the outer GMRES. */
+static void coarse_gmres(octx* c, const cplx* b, cplx* e) {
+  olevel* L = &c->L[c->nlev - 1];
+  const int n = c->nc;
+  const cplx s = cslp_shift(c);
+  const int m = n;  /* at most n steps: the Krylov space is then the whole space */
+  cplx* V = (cplx*)calloc((size_t)(m + 1) * n, sizeof(cplx));
+  cplx* H = (cplx*)calloc((size_t)(m + 1) * m, sizeof(cplx));
+  double* cs = (double*)calloc(m, sizeof(double));
+  cplx* sn = (cplx*)calloc(m, sizeof(cplx));
+  cplx* g = (cplx*)calloc(m + 1, sizeof(cplx));
+  cplx* y = (cplx*)calloc(m, sizeof(cplx));
+  cplx* w = (cplx*)calloc(n, sizeof(cplx));
+  double bn = 0;
+  for (int p = 0; p < n; ++p) bn += creal(b[p]) * creal(b[p]) + cimag(b[p]) * cimag(b[p]);
+  bn = sqrt(bn);
+  memset(e, 0, (size_t)n * sizeof(cplx));
+  if (bn == 0.0) goto done;
+  for (int p = 0; p < n; ++p) V[p] = b[p] / bn;
+  g[0] = bn;
+  int k = 0;
+  for (int j = 0; j < m; ++j) {
+    apply_op(L->N1, L->N2, L->N3, L->h, c->bc, L->k2, s, V + (size_t)j * n, w);
+    for (int i = 0; i <= j; ++i) {
+      cplx hij = 0;
+      for (int p = 0; p < n; ++p) hij += conj(V[(size_t)i * n + p]) * w[p];
+      H[(size_t)i * m + j] = hij;
+      for (int p = 0; p < n; ++p) w[p] -= hij * V[(size_t)i * n + p];
+    }
+    double hn = 0;
+    for (int p = 0; p < n; ++p) hn += creal(w[p]) * creal(w[p]) + cimag(w[p]) * cimag(w[p]);
+    hn = sqrt(hn);
+    H[(size_t)(j + 1) * m + j] = hn;
+    if (hn != 0.0)
+      for (int p = 0; p < n; ++p) V[(size_t)(j + 1) * n + p] = w[p] / hn;
+    for (int i = 0; i < j; ++i) {
+      cplx a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+      H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+      H[(size_t)(i + 1) * m + j] = -conj(sn[i]) * a + cs[i] * bb;
+    }
+    cplx a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+    double na = cabs(a), t = sqrt(na * na + cabs(bb) * cabs(bb));
+    if (na == 0.0) { cs[j] = 0.0; sn[j] = 1.0; H[(size_t)j * m + j] = bb; }
+    else {
+      cplx ph = a / na;
+      cs[j] = na / t;
+      sn[j] = ph * conj(bb) / t;
+      H[(size_t)j * m + j] = ph * t;
+    }
+    H[(size_t)(j + 1) * m + j] = 0;
+    g[j + 1] = -conj(sn[j]) * g[j];
+    g[j] = cs[j] * g[j];
+    k = j + 1;
+    if (cabs(g[j + 1]) / bn <= c->coarse_tol || hn == 0.0) break;
+  }
+  for (int i = k - 1; i >= 0; --i) {
+    cplx acc = g[i];
+    for (int q = i + 1; q < k; ++q) acc -= H[(size_t)i * m + q] * y[q];
+    y[i] = acc / H[(size_t)i * m + i];
+  }
+  for (int i = 0; i < k; ++i)
+    for (int p = 0; p < n; ++p) e[p] += y[i] * V[(size_t)i * n + p];
+done:
+  free(V); free(H); free(cs); free(sn); free(g); free(y); free(w);
+}
+
 static void coarse_solve(octx* c, const cplx* b, cplx* e) {
+  if (c->coarse_tol > 0.0) { coarse_gmres(c, b, e); return; }
   memcpy(e, b, (size_t)c->nc * sizeof(cplx));
   lu_solve(c->nc, c->lu, c->piv, e);
 }
+
+void oracle_set_coarse_tol(void* vctx, double tol) { ((octx*)vctx)->coarse_tol = tol; }
 
 /* Two-grid cycle (Algorithm 1) applied recursively with a zero initial guess on every
  * level: the V-cycle.  Writes u ~= M_l^{-1} b. */

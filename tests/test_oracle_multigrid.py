@@ -179,3 +179,22 @@ def test_poisson_fcycle_contracts_at_least_as_well_as_vcycle():
             x = xn / np.linalg.norm(xn)
         out[name] = np.mean(ratios[-4:])
     assert out["f"] <= out["v"] + 1e-3, out
+
+
+def test_coarse_gmres_matches_exact_coarse_solve():
+    """The paper's coarsest solver (full GMRES to 1e-11, Sec. 5) against the exact LU solve:
+    the coarse error of GMRES is at the 1e-11 level, so one V-cycle agrees to ~1e-9."""
+    import oracle
+    from paper_2308_06085_gb300 import inputs as I
+
+    for bc, n in ((oracle.SOMMERFELD, 16), (oracle.DIRICHLET, 16)):
+        shape = I.unknown_shape(n, bc)
+        k2 = I.random_k2(shape, seed=61, kmin=1.0, kmax=0.6 * n)
+        r = I.random_vector(shape, 62)
+        exact = oracle.Solver(n, 1.0 / n, bc, k2, coarsest_n=4).vcycle(r)
+        for tol, bound in ((1e-11, 1e-8), (1e-14, 1e-11)):
+            z = oracle.Solver(n, 1.0 / n, bc, k2, coarsest_n=4, coarse_tol=tol).vcycle(r)
+            assert np.linalg.norm(z - exact) <= bound * np.linalg.norm(exact), (bc, tol)
+        # GMRES with a loose tolerance leaves a visible coarse error: the option is really used
+        z = oracle.Solver(n, 1.0 / n, bc, k2, coarsest_n=4, coarse_tol=1e-2).vcycle(r)
+        assert np.linalg.norm(z - exact) > 1e-6 * np.linalg.norm(exact)
