@@ -162,6 +162,9 @@ struct Grid {
   // selects the default (8 rows, 8 CTAs per SM); helm_create's autotuner fills them.
   int tile_ty[8] = {};
   int tile_ctas[8] = {};
+  // FP32 7-point kernels (one right-hand side): stage each plane's x-y neighbours in shared
+  // memory (set per level by the autotuner when it measures faster)
+  int tiled = 0;
   __host__ __device__ size_t npts() const { return (size_t)N1 * N2 * N3; }
 };
 

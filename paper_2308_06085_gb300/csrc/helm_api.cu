@@ -22,6 +22,7 @@ namespace {
 
 constexpr int MAX_LEVELS = 32;
 constexpr int MAX_COARSE = 4096;  // unknowns of the dense coarsest solve
+constexpr int TYT_TILED = 8;      // rows of the tiled FP32 stencil CTAs (stencil.cu)
 constexpr int FLAG_LAG = 2;       // Arnoldi steps enqueued ahead of the host's flag check
 
 std::string g_create_error;
@@ -681,6 +682,27 @@ helm_status tune_slot(helm_ctx* c, Grid& g, int slot, int level, cudaStream_t st
   return check_launch(c, "autotune");
 }
 
+// Best of three timings of three back-to-back launches of run(), per launch, in ms.
+template <typename Fn>
+float time_burst(helm_ctx* c, cudaStream_t st, Fn&& run) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return 1e30f;
+  run();
+  float ms = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, st);
+    for (int b = 0; b < 3; ++b) run();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms = std::min(ms, t / 3);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  (void)c;
+  return ms;
+}
+
 // Tune the V-cycle kernels of arithmetic R on the levels lv[0..L) (grids are updated in place).
 template <typename R>
 helm_status tune_vlevels(helm_ctx* c, VLevel<R>* lv, int L, cudaStream_t st) {
@@ -695,6 +717,24 @@ helm_status tune_vlevels(helm_ctx* c, VLevel<R>* lv, int L, cudaStream_t st) {
     TRY(tune_slot(c, F.g, tile_slot<R>(TILE_STENCIL), l, st, [&](const Grid& g) {
       launch_jacobi<R, R, R>(g, sr, si, om, F.k2, F.dinv, F.U1, F.U1, F.T, st, nullptr);
     }));
+    if (std::is_same<R, float>::value && F.g.nb == 1) {
+      // the shared-memory tiled FP32 kernels against the best plain shape (logged as slot 12)
+      const int slot = tile_slot<R>(TILE_STENCIL);
+      auto run = [&] { launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.U1, F.U1, F.T, st, nullptr); };
+      const int ct0 = F.g.tile_ctas[slot];
+      float best = time_burst(c, st, run);
+      int best_ct = -1;
+      F.g.tiled = 1;
+      for (int m : {4, 8, 16, 32}) {
+        F.g.tile_ctas[slot] = 152 * m;
+        const float t = time_burst(c, st, run);
+        c->tune_log.push_back(TuneRec{l, 12, TYT_TILED, 152 * m, t});
+        if (t < best) { best = t; best_ct = 152 * m; }
+      }
+      F.g.tiled = best_ct > 0 ? 1 : 0;
+      F.g.tile_ctas[slot] = best_ct > 0 ? best_ct : ct0;
+      TRY(check_launch(c, "autotune (tiled stencil)"));
+    }
     TRY(tune_slot(c, F.g, tile_slot<R>(TILE_SMOOTH0), l, st, [&](const Grid& g) {
       launch_smooth0<R, R>(g, sr, si, om, F.k2, F.dinv, F.U1, F.T, st, nullptr);
     }));

@@ -93,6 +93,88 @@ __global__ void __launch_bounds__(TX* TY)
   }
 }
 
+// The FP32 7-point kernels (one right-hand side) with the x-y neighbours staged in shared
+// memory: a CTA of 32 x TYT threads covers a 32 x TYT tile of each plane and streams its z-chunk;
+// each plane's values go to a (TYT + 2) x 34 tile (halo loaded by the edge threads), so a point
+// costs one coalesced load of u plus the halo share instead of five L1 requests.  The z
+// neighbours stay in registers.  Same arithmetic per point as k_stencil (op_apply / op_resid /
+// omega_over, same neighbour substitution at Sommerfeld faces), so the results are identical.
+constexpr int TYT = 8;
+template <int MODE, typename TU, typename TB, typename TO>
+__global__ void __launch_bounds__(TX* TYT)
+    k_stencil32_tiled(Grid g, OpCoef<float> c, const float* __restrict__ k2, const cx<TU>* __restrict__ u,
+                      const cx<TB>* __restrict__ b, cx<TO>* __restrict__ out, int zchunk,
+                      const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ z64 tile[TYT + 2][TX + 2];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * TX + tx, j = blockIdx.y * TYT + ty;
+  const int k0 = blockIdx.z * zchunk;
+  if (k0 >= g.N3) return;  // the whole CTA
+  const int k1 = min(k0 + zchunk, g.N3);
+  const bool inside = i < g.N1 && j < g.N2;
+  const bool som = g.bc == 1;
+  const size_t S = (size_t)g.N1 * g.N2;
+  const bool hxm = i > 0, hxp = i < g.N1 - 1, hym = j > 0, hyp = j < g.N2 - 1;
+  const int nfxy = som ? (!hxm) + (!hxp) + (!hym) + (!hyp) : 0;
+  const z64 z0 = mkc<float>(0.f, 0.f);
+  auto ld = [&](size_t q) { return cvt<float>(ldg(u + q)); };
+  // halo duties of this thread (loads that stay inside the grid)
+  const bool ld_xm = inside && tx == 0 && i > 0;
+  const bool ld_xp = inside && tx == TX - 1 && i + 1 < g.N1;
+  const bool ld_ym = inside && ty == 0 && j > 0;
+  const bool ld_yp = inside && ty == TYT - 1 && j + 1 < g.N2;
+  size_t p = inside ? gidx(i, j, k0, g.N1, g.N2) : 0;
+  z64 uc = inside ? ld(p) : z0;
+  z64 um = (inside && k0 > 0) ? ld(p - S) : z0;
+  z64 up = (inside && k0 + 1 < g.N3) ? ld(p + S) : z0;
+  for (int k = k0; k < k1; ++k, p += S) {
+    // stage plane k; load what this plane's update needs besides the neighbours
+    z64 hx0 = z0, hx1 = z0, hy0 = z0, hy1 = z0;
+    if (ld_xm) hx0 = ld(p - 1);
+    if (ld_xp) hx1 = ld(p + 1);
+    if (ld_ym) hy0 = ld(p - g.N1);
+    if (ld_yp) hy1 = ld(p + g.N1);
+    const float kk = inside ? __ldg(k2 + p) : 0.f;
+    const z64 bv = (MODE != 0 && inside) ? cvt<float>(ldg(b + p)) : z0;
+    const bool hzp = k + 1 < g.N3;
+    const z64 un = (inside && k + 2 < g.N3 && k + 1 < k1) ? ld(p + 2 * S) : z0;  // next plane's up
+    __syncthreads();  // the previous plane's readers are done with the tile
+    tile[ty + 1][tx + 1] = uc;
+    if (ld_xm) tile[ty + 1][0] = hx0;
+    if (ld_xp) tile[ty + 1][TX + 1] = hx1;
+    if (ld_ym) tile[0][tx + 1] = hy0;
+    if (ld_yp) tile[TYT + 1][tx + 1] = hy1;
+    __syncthreads();
+    if (inside) {
+      int nf = nfxy;
+      z64 zm, zp;
+      if (k > 0) zm = um;
+      else if (som) { zm = up; ++nf; }
+      else zm = z0;
+      if (hzp) zp = up;
+      else if (som) { zp = um; ++nf; }
+      else zp = z0;
+      const z64 xm = hxm ? tile[ty + 1][tx] : (som ? tile[ty + 1][tx + 2] : z0);
+      const z64 xp = hxp ? tile[ty + 1][tx + 2] : (som ? tile[ty + 1][tx] : z0);
+      const z64 ym = hym ? tile[ty][tx + 1] : (som ? tile[ty + 2][tx + 1] : z0);
+      const z64 yp = hyp ? tile[ty + 2][tx + 1] : (som ? tile[ty][tx + 1] : z0);
+      const z64 d = op_diag(c, kk, nf, nf ? face_k<float>(g, p, kk) : 0.f);
+      const bool real_d = c.real_shift && nf == 0;
+      if (MODE == 0) {
+        out[p] = cvt<TO>(op_apply(d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp));
+      } else {
+        const z64 res = op_resid(bv, d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
+        if (MODE == 1) out[p] = cvt<TO>(res);
+        else out[p] = cvt<TO>(cfma(omega_over(d, c.omega), res, uc));
+      }
+    }
+    um = uc;
+    uc = up;
+    up = un;
+  }
+}
+
 // Pre-smoothing from a zero initial guess: one damped-Jacobi sweep gives u1 = (omega/d) b.
 template <typename R, bool DINV, typename TB>
 __global__ void __launch_bounds__(TX* TY)
@@ -696,10 +778,30 @@ OpCoef<R> coef_for(double h, double s_re, double s_im, double omega) {
 // ------------------------------------------------------------------------------------
 // Launchers
 // ------------------------------------------------------------------------------------
+// Launch shape of the tiled FP32 kernels: 32 x TYT threads, the tuned CTA count for z.
+static dim3 grid_tiled(const Grid& g, int& zchunk) {
+  const int slot = tile_slot<float>(TILE_STENCIL);
+  const int target = g.tile_ctas[slot] > 0 ? g.tile_ctas[slot] : 152 * 8;
+  const int bx = (g.N1 + TX - 1) / TX, by = (g.N2 + TYT - 1) / TYT;
+  int zsplit = target / (bx * by);
+  if (zsplit < 1) zsplit = 1;
+  if (zsplit > g.N3) zsplit = g.N3;
+  zchunk = (g.N3 + zsplit - 1) / zsplit;
+  return dim3(bx, by, (g.N3 + zchunk - 1) / zchunk);
+}
+
 template <typename R, typename TU, typename TO>
 void launch_apply(const Grid& g, double s_re, double s_im, const R* k2, const cx<TU>* u, cx<TO>* v,
                   cudaStream_t st, const int* active) {
   int zc;
+  if constexpr (std::is_same<R, float>::value) {
+    if (g.nb == 1 && g.tiled) {
+      const dim3 gr = grid_tiled(g, zc);
+      k_stencil32_tiled<0, TU, TU, TO><<<gr, dim3(TX, TYT), 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, u,
+                                                                    nullptr, v, zc, active);
+      return;
+    }
+  }
   dim3 blk, gr = grid_for<R>(g, TILE_STENCIL, zc, blk);
   k_stencil<R, 0, false, TU, TU, TO><<<gr, blk, 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr, u,
                                                                    nullptr, v, zc, active);
@@ -745,6 +847,14 @@ template <typename R, typename TU, typename TB, typename TO>
 void launch_resid(const Grid& g, double s_re, double s_im, const R* k2, const cx<TU>* u, const cx<TB>* b,
                   cx<TO>* out, cudaStream_t st, const int* active) {
   int zc;
+  if constexpr (std::is_same<R, float>::value) {
+    if (g.nb == 1 && g.tiled) {
+      const dim3 gr = grid_tiled(g, zc);
+      k_stencil32_tiled<1, TU, TB, TO><<<gr, dim3(TX, TYT), 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, u, b,
+                                                                    out, zc, active);
+      return;
+    }
+  }
   dim3 blk, gr = grid_for<R>(g, TILE_STENCIL, zc, blk);
   k_stencil<R, 1, false, TU, TB, TO><<<gr, blk, 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr,
                                                                    u, b, out, zc, active);
@@ -754,8 +864,15 @@ template <typename R, typename TB, typename TO>
 void launch_jacobi(const Grid& g, double s_re, double s_im, double omega, const R* k2, const cx<R>* dinv,
                    const cx<R>* u, const cx<TB>* b, cx<TO>* out, cudaStream_t st, const int* active) {
   int zc;
-  dim3 blk, gr = grid_for<R>(g, TILE_STENCIL, zc, blk);
   OpCoef<R> c = coef_for<R>(g.h, s_re, s_im, omega);
+  if constexpr (std::is_same<R, float>::value) {
+    if (g.nb == 1 && g.tiled && !dinv) {
+      const dim3 gr = grid_tiled(g, zc);
+      k_stencil32_tiled<2, R, TB, TO><<<gr, dim3(TX, TYT), 0, st>>>(g, c, k2, u, b, out, zc, active);
+      return;
+    }
+  }
+  dim3 blk, gr = grid_for<R>(g, TILE_STENCIL, zc, blk);
   if (dinv)
     k_stencil<R, 2, true, R, TB, TO><<<gr, blk, 0, st>>>(g, c, k2, dinv, u, b, out, zc, active);
   else

@@ -93,3 +93,21 @@ def test_batched_graph_replay_is_bit_exact(helm, orth, cycle):
         X1, i1 = graph.solve_batched(B[:width])
         assert [a["iterations"] for a in i0] == [a["iterations"] for a in i1]
         assert torch.equal(X0, X1)
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_autotuned_shapes_are_bit_exact(helm, n):
+    """Launch shapes (and the shared-memory tiled FP32 stencils the autotuner may pick) change
+    the schedule, not the arithmetic of a point: complex64 V-cycles and mixed-precision solves
+    with the autotuner equal those with the fixed default shape bit for bit."""
+    w = I.workload("wedge", n)
+    a = helm.Solver(w["n"], w["h"], w["k2"], S, krylov="fgmres", precision="mixed", autotune=False)
+    t = helm.Solver(w["n"], w["h"], w["k2"], S, krylov="fgmres", precision="mixed", autotune=True)
+    tiled = any(rec[1] == 12 for rec in t.tune_log())
+    assert tiled, "the tiled FP32 stencil was never timed"
+    r = torch.from_numpy(I.random_vector(t.shape, 13).astype(np.complex64)).cuda()
+    assert torch.equal(a.vcycle(r), t.vcycle(r))
+    b = a.rhs_point(w["sources"])
+    xa, ia = a.solve(b)
+    xt, it = t.solve(b)
+    assert ia["iterations"] == it["iterations"] and torch.equal(xa, xt)
