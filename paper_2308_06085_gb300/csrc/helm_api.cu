@@ -190,6 +190,7 @@ struct helm_ctx {
   std::vector<GraphEnt> graphs;
   std::vector<TuneRec> tune_log;  // every launch shape the autotuner timed
   int mdot_df_variant = 0;        // slots per warp pass of the double-float inner products
+  int mdot_variant = 0;           // FP64 inner products: 0 w staged in shared memory, 1 not
   cudaStream_t gstream = nullptr;
   // IDR(s): shadow space P (s vectors), work G, U (s each), r, v, vh, t; control block
   int idr_s = 0;
@@ -785,6 +786,22 @@ helm_status autotune(helm_ctx* c, cudaStream_t st) {
       c->L[l].g.tile_ty[q] = lv[l].g.tile_ty[q];
       c->L[l].g.tile_ctas[q] = lv[l].g.tile_ctas[q];
     }
+  // FP64 inner products: w staged in shared memory or read by each warp (logged as level -1,
+  // slot 16 + variant)
+  if (c->p.orth == HELM_ORTH_FP64 && c->m >= 2) {
+    const size_t n = c->n0;
+    const int nv = std::min(16, c->m);
+    CU(cudaMemsetAsync(c->V, 0x3f, (size_t)(nv + 1) * n * sizeof(z128), st));
+    float best = 1e30f;
+    for (int v = 0; v < 2; ++v) {
+      const float t = time_burst(c, st, [&] {
+        launch_mdot(c->V, n, nv, c->V + (size_t)nv * n, n, c->part, 1, st, nullptr, v);
+      });
+      c->tune_log.push_back(TuneRec{-1, 16 + v, nv, 0, t});
+      if (t < best) { best = t; c->mdot_variant = v; }
+    }
+    TRY(check_launch(c, "autotune (FP64 inner products)"));
+  }
   // double-float inner products: slots per warp pass (logged as level -1, slot 8 + variant)
   if (c->p.orth == HELM_ORTH_DF && c->m >= 2) {
     const size_t n = c->n0;
@@ -915,7 +932,8 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
             KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd,
                nb = launch_mdot_df(Vdf, n, j + 1, wd, n, c->part, wn, st, a2, c->mdot_df_variant));
           else
-            KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nb = launch_mdot(c->V, n, j + 1, w, n, c->part, wn, st, a2));
+            KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd,
+               nb = launch_mdot(c->V, n, j + 1, w, n, c->part, wn, st, a2, c->mdot_variant));
           KL(F_REDUCE_DOTS, 16.0 * nv * nb, 2.0 * nv * nb,
              launch_reduce_dots(c->part, j + 1, nb, c->hpass, c->hacc, pass, wn ? j : -1, &ctl->pass2, c->reorth_log,
                                 st, a2));

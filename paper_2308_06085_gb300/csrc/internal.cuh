@@ -47,7 +47,7 @@ constexpr int MAX_BASIS = 257;   // restart <= 256
 // part[i * RED_STRIDE + blk] = sum over blk's points of conj(V_i) w, i < nv; with_norm also
 // writes the partial |w|^2 to slot nv.  Returns the number of blocks (partials per row).
 int launch_mdot(const z128* V, size_t ld, int nv, const z128* w, size_t n, z128* part, int with_norm,
-                cudaStream_t st, const int* active);
+                cudaStream_t st, const int* active, int variant = 0);
 // hpass[i] = sum_{blk < nb} part[i * RED_STRIDE + blk]; hacc[i] = hpass[i] (accumulate 0) or
 // += (1).  decide_j >= 0: also read |w|^2 from slot nv and set *pass2 = log[decide_j] =
 // (second Gram-Schmidt pass needed)

@@ -98,7 +98,9 @@ __device__ __forceinline__ int share_width(int nslot) {
 
 // TILE points of w per shared-memory tile (16 KB): few barriers per point keep loads in
 // flight.
-template <typename E, typename ACC, int TILE, int KSV = KS>
+// STAGE: w passes through shared memory tile by tile (two barriers per tile); without it each
+// warp reads w itself (the block's warps share it through L1) and runs barrier-free.
+template <typename E, typename ACC, int TILE, int KSV = KS, bool STAGE = true>
 __global__ void __launch_bounds__(NT)
     k_mdot(const E* __restrict__ V, size_t ld, int nv, const E* __restrict__ w, size_t n, z128* __restrict__ part,
            int with_norm, const int* __restrict__ active) {
@@ -119,18 +121,31 @@ __global__ void __launch_bounds__(NT)
     ACC acc[KSV];
 #pragma unroll
     for (int k = 0; k < KSV; ++k) acc[k].zero();
-    for (size_t t0 = p0; t0 < p1; t0 += TILE) {
-      const int tn = (int)min((size_t)TILE, p1 - t0);
-      __syncthreads();
-      for (int q = threadIdx.x; q < tn; q += NT) sw[q] = ldg(w + t0 + q);
-      __syncthreads();
+    if (STAGE) {
+      for (size_t t0 = p0; t0 < p1; t0 += TILE) {
+        const int tn = (int)min((size_t)TILE, p1 - t0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < tn; q += NT) sw[q] = ldg(w + t0 + q);
+        __syncthreads();
 #pragma unroll 2
-      for (int q = sub * 32 + lane; q < tn; q += 32 * wps) {
-        const E wv = sw[q];
+        for (int q = sub * 32 + lane; q < tn; q += 32 * wps) {
+          const E wv = sw[q];
+#pragma unroll
+          for (int k = 0; k < KSV; ++k) {
+            const int sl = sfirst + (sbase + k) * sstep;
+            if (sl < nv) acc[k].mac(ldg(V + (size_t)sl * ld + t0 + q), wv);
+            else if (sl == nv && with_norm) acc[k].norm(wv);
+          }
+        }
+      }
+    } else {
+#pragma unroll 2
+      for (size_t q = p0 + sub * 32 + lane; q < p1; q += 32 * wps) {
+        const E wv = ldg(w + q);
 #pragma unroll
         for (int k = 0; k < KSV; ++k) {
           const int sl = sfirst + (sbase + k) * sstep;
-          if (sl < nv) acc[k].mac(ldg(V + (size_t)sl * ld + t0 + q), wv);
+          if (sl < nv) acc[k].mac(ldg(V + (size_t)sl * ld + q), wv);
           else if (sl == nv && with_norm) acc[k].norm(wv);
         }
       }
@@ -581,11 +596,17 @@ int stream_blocks(size_t n) {
 
 }  // namespace
 
-int launch_mdot(const z128* V, size_t ld, int nv, const z128* w, size_t n, z128* part, int with_norm,
-                cudaStream_t st, const int* active) {
-  static const int nb = wave_blocks(k_mdot<z128, AccD, 4 * NT>);
-  k_mdot<z128, AccD, 4 * NT><<<nb, NT, 0, st>>>(V, ld, nv, w, n, part, with_norm, active);
+template <bool STAGE>
+int mdot_fp64(const z128* V, size_t ld, int nv, const z128* w, size_t n, z128* part, int with_norm, cudaStream_t st,
+              const int* active) {
+  static const int nb = wave_blocks(k_mdot<z128, AccD, 4 * NT, KS, STAGE>);
+  k_mdot<z128, AccD, 4 * NT, KS, STAGE><<<nb, NT, 0, st>>>(V, ld, nv, w, n, part, with_norm, active);
   return nb;
+}
+int launch_mdot(const z128* V, size_t ld, int nv, const z128* w, size_t n, z128* part, int with_norm,
+                cudaStream_t st, const int* active, int variant) {
+  return variant == 1 ? mdot_fp64<false>(V, ld, nv, w, n, part, with_norm, st, active)
+                      : mdot_fp64<true>(V, ld, nv, w, n, part, with_norm, st, active);
 }
 void launch_reduce_dots(const z128* part, int nv, int nb, z128* hpass, z128* hacc, int accumulate, int decide_j,
                         int* pass2, int* log, cudaStream_t st, const int* active) {
