@@ -412,3 +412,40 @@ def test_apply_c64_double_float(helm, name, n, bc, coarsest):
     vo = oracle.apply(u.astype(np.complex128), k2, h, bc)
     err = rel(v, vo)
     assert err <= 1e-12, err
+
+
+def test_full_size_mixed_n256(helm):
+    """The n = 256 mixed-precision workload (257^3 unknowns) at full size: the complex64
+    V-cycle against the FP64 oracle's on the whole grid, and the mixed-precision double-float
+    solve's true residual from the oracle's own operator."""
+    w = I.workload("mixed", 256)
+    s = helm.Solver(w["n"], w["h"], w["k2"], S, krylov="fgmres", precision="mixed", orth="df")
+    o = oracle.Solver(w["n"], w["h"], S, w["k2"])
+    r = I.random_vector(s.shape, 14).astype(np.complex64)
+    z = s.vcycle(dev(r)).cpu().numpy()
+    err = rel(z, o.vcycle(r.astype(np.complex128)))
+    assert err <= 2e-5, err
+    del o
+    b = s.rhs_point(w["sources"])
+    x, info = s.solve(b)
+    assert info["status"] == 0
+    bn = b.cpu().numpy()
+    ax = oracle.apply(x.cpu().numpy(), w["k2"], w["h"], S)
+    rr = np.linalg.norm(bn - ax) / np.linalg.norm(bn)
+    assert rr <= 1.01e-6 and abs(rr - info["rel_residual"]) <= 1e-3 * rr
+
+
+def test_full_size_batched_sources(helm):
+    """Batched sources on the n = 128 wedge in the benchmark's batched configuration (complex64
+    cycle, double-float Gram-Schmidt, F-cycle): every source's true residual from the oracle's
+    operator."""
+    w = I.workload("batched", 128)
+    s = helm.Solver(w["n"], w["h"], w["k2"], S, krylov="fgmres", precision="mixed", orth="df", cycle="f")
+    B = torch.stack([s.rhs_point([p]) for p in w["sources"][:4]])
+    X, infos = s.solve_batched(B)
+    for r in range(4):
+        assert infos[r]["status"] == 0
+        bn = B[r].cpu().numpy()
+        ax = oracle.apply(X[r].cpu().numpy(), w["k2"], w["h"], S)
+        rr = np.linalg.norm(bn - ax) / np.linalg.norm(bn)
+        assert rr <= 1.01e-6, (r, rr)
