@@ -186,6 +186,11 @@ HELM_API helm_status cslp_vcycle(helm_ctx* ctx, helm_dtype dt, const void* r, vo
  * the default shape (8 rows, 8 CTAs per SM).  ty and ctas: host arrays of 8. */
 HELM_API helm_status helm_launch_shapes(const helm_ctx* ctx, int level, int* ty, int* ctas);
 
+/* Kernel variants the autotuner picked on `level` (library instrumentation): *flags bit 0 =
+ * FP32 7-point kernels with shared-memory tiles, bit 1 = FP32 pre-smoothing and residual fused
+ * into one kernel.  Both change the schedule only, not the arithmetic of a point. */
+HELM_API helm_status helm_kernel_variants(const helm_ctx* ctx, int level, int* flags);
+
 /* The autotuner's measurements (library instrumentation): *count = number of timed shapes; the
  * first min(cap, count) are written as rec[4 i .. 4 i + 3] = (level, slot, ty, ctas) and ms[i] =
  * the best of three timings of three back-to-back launches, per launch.  rec / ms may be NULL. */

@@ -165,6 +165,9 @@ struct Grid {
   // FP32 7-point kernels (one right-hand side): stage each plane's x-y neighbours in shared
   // memory (set per level by the autotuner when it measures faster)
   int tiled = 0;
+  // FP32, one right-hand side: pre-smoothing from zero and the residual as one kernel (the
+  // pre-smoothing slot then holds that kernel's shape); set by the autotuner when faster
+  int fused_down = 0;
   __host__ __device__ size_t npts() const { return (size_t)N1 * N2 * N3; }
 };
 

@@ -405,6 +405,19 @@ struct VLevel {
   cx<R> *B, *U1, *T, *E;
 };
 
+// Whether level F runs its pre-smoothing and residual as one kernel, and that launch (u1 into
+// F.U1, the residual into F.T).
+template <typename R>
+bool down_fused(const VLevel<R>& F) {
+  return std::is_same<R, float>::value && F.g.nb == 1 && F.g.fused_down;
+}
+template <typename R, typename TB>
+void down_fused_launch(const VLevel<R>& F, double sr, double si, double om, const cx<TB>* b, cudaStream_t st,
+                       const int* active) {
+  if constexpr (std::is_same<R, float>::value)
+    launch_smooth0_resid32<TB>(F.g, sr, si, om, F.k2, b, F.U1, F.T, st, active);
+}
+
 // Levels from which the rest of a V-cycle over lv[0..L) runs in one CTA (k_coarse_cycle):
 // the first relative level lf >= 1 whose sub-cycle (at least two levels, one right-hand side)
 // fits the shared-memory budget, with its vectors laid out in *cc and the byte count in
@@ -479,7 +492,11 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
     const VLevel<R>& C = lv[l + 1];
     const double n = (double)F.g.npts(), ncn = (double)C.g.npts();
     const double bi = l == 0 ? ib : cb;
-    if (l == 0) {
+    if (down_fused(F)) {
+      // u1 and the residual in one kernel (FP32, one right-hand side)
+      if (l == 0) KL(F_SMOOTH0, n * (bi + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, rin, st, active));
+      else KL(F_SMOOTH0, n * (bi + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, F.B, st, active));
+    } else if (l == 0) {
       KL(F_SMOOTH0, n * (bi + (db ? db : kb) + cb), 6 * n * nbv, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
       KL(F_RESID, n * (cb + bi + kb + cb), 24 * n * nbv, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
     } else {
@@ -560,8 +577,12 @@ void fcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, int l, const cx<TI>*
   const VLevel<R>& F = lv[l];
   const VLevel<R>& C = lv[l + 1];
   const double n = (double)F.g.npts() * F.g.nb, ncn = (double)C.g.npts() * C.g.nb, db = F.dinv ? 16.0 : 0.0;
-  KL(F_SMOOTH0, n * (ib + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
-  KL(F_RESID, n * (cb + ib + kb + cb), 24 * n, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
+  if (down_fused(F)) {
+    KL(F_SMOOTH0, n * (ib + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, rin, st, active));
+  } else {
+    KL(F_SMOOTH0, n * (ib + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
+    KL(F_RESID, n * (cb + ib + kb + cb), 24 * n, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
+  }
   KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
   fcycle_levels<R, R, R>(c, lv, L, l + 1, C.B, C.E, st, active);
   vcycle_from<R>(c, lv, L, l + 1, st, active);
@@ -739,6 +760,37 @@ helm_status tune_vlevels(helm_ctx* c, VLevel<R>* lv, int L, cudaStream_t st) {
     TRY(tune_slot(c, F.g, tile_slot<R>(TILE_SMOOTH0), l, st, [&](const Grid& g) {
       launch_smooth0<R, R>(g, sr, si, om, F.k2, F.dinv, F.U1, F.T, st, nullptr);
     }));
+    if constexpr (std::is_same<R, float>::value) {
+      if (F.g.nb == 1) {
+        // pre-smoothing + residual in one kernel against the two tuned kernels (logged as slot 13
+        // for the fused shapes); the pre-smoothing slot keeps whichever shape is used
+        const int slot = tile_slot<R>(TILE_SMOOTH0);
+        // scratch for the fused kernel's u1 output: the context's complex128 work vector holds
+        // at least one complex64 grid vector of any level
+        z64* scratch = reinterpret_cast<z64*>(c->zs);
+        const float t_plain =
+            time_burst(c, st, [&] { launch_smooth0<R, R>(F.g, sr, si, om, F.k2, F.dinv, F.U1, F.T, st, nullptr); }) +
+            time_burst(c, st, [&] { launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.U1, F.T, st, nullptr); });
+        const int ty0 = F.g.tile_ty[slot], ct0 = F.g.tile_ctas[slot];
+        float best = 1e30f;
+        int bty = 0, bct = 0;
+        for (int ty : {1, 2, 4, 8})
+          for (int m : {4, 8, 16, 32}) {
+            F.g.tile_ty[slot] = ty;
+            F.g.tile_ctas[slot] = 152 * m;
+            const float t = time_burst(c, st, [&] {
+              launch_smooth0_resid32<float>(F.g, sr, si, om, F.k2, F.U1, scratch, F.T, st, nullptr);
+            });
+            c->tune_log.push_back(TuneRec{l, 13, ty, 152 * m, t});
+            if (t < best) { best = t; bty = ty; bct = 152 * m; }
+          }
+        const bool use = best < t_plain;
+        F.g.fused_down = use ? 1 : 0;
+        F.g.tile_ty[slot] = use ? bty : ty0;
+        F.g.tile_ctas[slot] = use ? bct : ct0;
+        TRY(check_launch(c, "autotune (fused pre-smoothing and residual)"));
+      }
+    }
     VLevel<R>& C = lv[l + 1];
     CU(cudaMemsetAsync(C.E, 0x3f, C.g.npts() * C.g.nb * sizeof(cx<R>), st));
     TRY(tune_slot(c, F.g, tile_slot<R>(TILE_PROLONG), l, st, [&](const Grid& g) {
@@ -1847,6 +1899,13 @@ helm_status helm_launch_shapes(const helm_ctx* c, int level, int* ty, int* ctas)
     ty[q] = c->L[level].g.tile_ty[q];
     ctas[q] = c->L[level].g.tile_ctas[q];
   }
+  return HELM_OK;
+}
+
+helm_status helm_kernel_variants(const helm_ctx* c, int level, int* flags) {
+  if (!c || !flags || level < 0 || level >= c->nlev) return HELM_EINVAL;
+  const Grid& g = c->L[level].g;
+  *flags = (g.tiled ? 1 : 0) | (g.fused_down ? 2 : 0);
   return HELM_OK;
 }
 

@@ -122,6 +122,13 @@ template <typename R>
 void launch_coarse_cycle(const CCycle<R>& cc, size_t smem_bytes, const cx<R>* b, cx<R>* e, cudaStream_t st,
                          const int* active);
 
+// FP32 pre-smoothing from zero fused with the residual, one right-hand side (stencil.cu):
+// u1 = (omega/d) b and r = b - M u1, u1 recomputed at the neighbours; same values as
+// launch_smooth0 followed by launch_resid.
+template <typename TB>
+void launch_smooth0_resid32(const Grid& g, double s_re, double s_im, double omega, const float* k2, const cx<TB>* b,
+                            z64* u1, z64* r, cudaStream_t st, const int* active);
+
 // ---- IDR(s) (idrs.cu); part holds RED_STRIDE-strided slots of complex partial sums ----
 void launch_idr_v(const IdrCtl* ic, int k, const z128* r, const z128* G, size_t n, z128* v, cudaStream_t st);
 void launch_idr_u(const IdrCtl* ic, int k, const z128* vh, z128* U, size_t n, cudaStream_t st);

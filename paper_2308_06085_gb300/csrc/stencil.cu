@@ -175,6 +175,62 @@ __global__ void __launch_bounds__(TX* TYT)
   }
 }
 
+// FP32 pre-smoothing from zero fused with the residual (one right-hand side): u1 = (omega/d) b
+// is written for the interpolation step, and r = b - M u1 is formed from u1 values recomputed at
+// the six neighbours (b and k^2 there), so neither u1 nor b is read back from memory.  Each u1
+// value is the same product as in k_smooth0, so the results equal those of the two separate
+// kernels.
+template <typename TB>
+__global__ void __launch_bounds__(TX* TY)
+    k_smooth0_resid32(Grid g, OpCoef<float> c, const float* __restrict__ k2, const cx<TB>* __restrict__ b,
+                      z64* __restrict__ u1, z64* __restrict__ r, int zchunk, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const int i = blockIdx.x * TX + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.N1 || j >= g.N2) return;
+  const int k0 = blockIdx.z * zchunk;
+  if (k0 >= g.N3) return;
+  const int k1 = min(k0 + zchunk, g.N3);
+  const bool som = g.bc == 1;
+  const size_t S = (size_t)g.N1 * g.N2;
+  const z64 z0 = mkc<float>(0.f, 0.f);
+  // u1 at node (ii, jj, kk) of the grid (the caller keeps it inside)
+  auto u1_at = [&](int ii, int jj, int kk, size_t q) {
+    const int nf = som ? (ii == 0) + (ii == g.N1 - 1) + (jj == 0) + (jj == g.N2 - 1) + (kk == 0) + (kk == g.N3 - 1) : 0;
+    const float kq = __ldg(k2 + q);
+    const z64 w = omega_over(op_diag(c, kq, nf, nf ? face_k<float>(g, q, kq) : 0.f), c.omega);
+    return cmul(w, cvt<float>(ldg(b + q)));
+  };
+  const bool hxm = i > 0, hxp = i < g.N1 - 1, hym = j > 0, hyp = j < g.N2 - 1;
+  const int nfxy = som ? (!hxm) + (!hxp) + (!hym) + (!hyp) : 0;
+  size_t p = gidx(i, j, k0, g.N1, g.N2);
+  z64 uc = u1_at(i, j, k0, p);
+  z64 um = k0 > 0 ? u1_at(i, j, k0 - 1, p - S) : z0;
+  for (int k = k0; k < k1; ++k, p += S) {
+    const bool hzp = k + 1 < g.N3;
+    const z64 up = hzp ? u1_at(i, j, k + 1, p + S) : z0;
+    int nf = nfxy;
+    z64 zm, zp;
+    if (k > 0) zm = um;
+    else if (som) { zm = up; ++nf; }
+    else zm = z0;
+    if (hzp) zp = up;
+    else if (som) { zp = um; ++nf; }
+    else zp = z0;
+    const z64 xm = hxm ? u1_at(i - 1, j, k, p - 1) : (som ? u1_at(i + 1, j, k, p + 1) : z0);
+    const z64 xp = hxp ? u1_at(i + 1, j, k, p + 1) : (som ? u1_at(i - 1, j, k, p - 1) : z0);
+    const z64 ym = hym ? u1_at(i, j - 1, k, p - g.N1) : (som ? u1_at(i, j + 1, k, p + g.N1) : z0);
+    const z64 yp = hyp ? u1_at(i, j + 1, k, p + g.N1) : (som ? u1_at(i, j - 1, k, p - g.N1) : z0);
+    const float kk = __ldg(k2 + p);
+    const z64 d = op_diag(c, kk, nf, nf ? face_k<float>(g, p, kk) : 0.f);
+    const bool real_d = c.real_shift && nf == 0;
+    u1[p] = uc;
+    r[p] = op_resid(cvt<float>(ldg(b + p)), d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
+    um = uc;
+    uc = up;
+  }
+}
+
 // Pre-smoothing from a zero initial guess: one damped-Jacobi sweep gives u1 = (omega/d) b.
 template <typename R, bool DINV, typename TB>
 __global__ void __launch_bounds__(TX* TY)
@@ -890,6 +946,18 @@ void launch_smooth0(const Grid& g, double s_re, double s_im, double omega, const
   else
     k_smooth0<R, false, TB><<<gr, blk, 0, st>>>(g, c, k2, dinv, b, out, zc, active);
 }
+
+template <typename TB>
+void launch_smooth0_resid32(const Grid& g, double s_re, double s_im, double omega, const float* k2, const cx<TB>* b,
+                            z64* u1, z64* r, cudaStream_t st, const int* active) {
+  int zc;
+  dim3 blk, gr = grid_for<float>(g, TILE_SMOOTH0, zc, blk);
+  k_smooth0_resid32<TB><<<gr, blk, 0, st>>>(g, coef_for<float>(g.h, s_re, s_im, omega), k2, b, u1, r, zc, active);
+}
+template void launch_smooth0_resid32<float>(const Grid&, double, double, double, const float*, const z64*, z64*, z64*,
+                                            cudaStream_t, const int*);
+template void launch_smooth0_resid32<double>(const Grid&, double, double, double, const float*, const z128*, z64*,
+                                             z64*, cudaStream_t, const int*);
 
 template <typename R>
 void launch_restrict(const Grid& gf, const Grid& gc, const cx<R>* r, cx<R>* out, cudaStream_t st, const int* active) {

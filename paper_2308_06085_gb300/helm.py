@@ -85,6 +85,8 @@ def lib():
     L.helm_launch_shapes.restype = i
     L.helm_tune_log.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_float), i, C.POINTER(C.c_int)]
     L.helm_tune_log.restype = i
+    L.helm_kernel_variants.argtypes = [vp, i, C.POINTER(C.c_int)]
+    L.helm_kernel_variants.restype = i
     L.helm_apply_c64_df.restype = i
     L.helm_set_shadow_space.restype = i
     L.cslp_fcycle.restype = i
@@ -255,6 +257,12 @@ class Solver:
         ty, ct = (C.c_int * 8)(), (C.c_int * 8)()
         self._check(lib().helm_launch_shapes(self._ctx, level, ty, ct))
         return [(ty[q], ct[q]) for q in range(8)]
+
+    def kernel_variants(self, level):
+        """{'tiled': bool, 'fused_down': bool} picked by the autotuner on `level`."""
+        f = C.c_int()
+        self._check(lib().helm_kernel_variants(self._ctx, level, C.byref(f)))
+        return {"tiled": bool(f.value & 1), "fused_down": bool(f.value & 2)}
 
     def tune_log(self):
         """Every launch shape the autotuner timed: (level, slot, ty, ctas, ms per launch)."""
