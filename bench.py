@@ -11,7 +11,7 @@ roofline from live CUDA-event timings inside the timed region, the end-to-end ti
 C ABI with host buffers, the FP64 CPU oracle timed on a bounded sample, clocks sampled during
 the timed region, and variants (mixed precision; n = 256) when --variants is on.
 
---impl reference times the FP64 CPU oracle (the reference for this build) on the host cores.
+--impl reference times the FP64 CPU oracle (the reference arm) on the host cores.
 """
 from __future__ import annotations
 

@@ -75,7 +75,7 @@ typedef struct {
   double beta1;     /* real part of the CSLP shift multiplier */
   double beta2;     /* CSLP complex shift; the shift is (beta1 - beta2 i) */
   double omega;     /* damped-Jacobi relaxation, 0 < omega < 2 */
-  int nu1, nu2;     /* pre/post smoothing sweeps; this build supports nu1 = nu2 = 1 */
+  int nu1, nu2;     /* pre/post smoothing sweeps; the library supports nu1 = nu2 = 1 */
   int coarsest_n;   /* >= 2; coarsen while every n_d is even and n_d/2 >= coarsest_n;
                        the coarsest grid may hold at most 4096 unknowns */
   int krylov;       /* helm_krylov: right-preconditioned GMRES(m), flexible GMRES(m),
@@ -247,7 +247,7 @@ HELM_API helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, helm_solv
  * it again replaces the space.  HELM_EINVAL for s out of range or a NULL P. */
 HELM_API helm_status helm_set_shadow_space(helm_ctx* ctx, int s, const void* P, void* stream);
 
-/* Solve A_h X_r = B_r for nrhs right-hand sides together (S9 of the build's hot path; the
+/* Solve A_h X_r = B_r for nrhs right-hand sides together (the batched form of the solve; the
  * paper solves one source at a time).  The right-hand sides run through the same
  * preconditioned flexible GMRES(m) in lockstep, in chunks of up to 32: grid vectors are
  * stored node-major with the right-hand side innermost, so every stencil, transfer and
