@@ -369,10 +369,13 @@ def end_to_end(torch, s, b, steps):
 
 def run_variants(torch, helm, inputs, args):
     out = {}
-    for name, n, prec, krylov, orth, cycle, *nog in [
-            ("wedge_n128_fp64_nographs", 128, "fp64", "gmres", args.orth, "v", "plain launches"),
+    for name, n, prec, krylov, orth, cycle, *extra in [
+            ("wedge_n128_fp64_nographs", 128, "fp64", "gmres", args.orth, "v", {"graphs": False}),
+            ("wedge_n128_fp64_gs_4fma", 128, "fp64", "gmres", args.orth, "v", {"gs_sums": False}),
             ("wedge_n128_mixed", 128, "mixed", "fgmres", args.orth, "v"),
             ("wedge_n128_mixed_orth_df", 128, "mixed", "fgmres", "df", "v"),
+            ("wedge_n128_mixed_orth_df_sweeps_unfused", 128, "mixed", "fgmres", "df", "v", {"fuse_down": 0, "fuse_up": 0}),
+            ("wedge_n128_mixed_orth_df_sweeps_fused", 128, "mixed", "fgmres", "df", "v", {"fuse_down": 2, "fuse_up": 1}),
             ("wedge_n128_fp64_orth_df", 128, "fp64", "gmres", "df", "v"),
             ("wedge_n128_fp64_fcycle", 128, "fp64", "gmres", args.orth, "f"),
             ("wedge_n128_mixed_orth_df_fcycle", 128, "mixed", "fgmres", "df", "f"),
@@ -389,7 +392,7 @@ def run_variants(torch, helm, inputs, args):
             ("mixed_n256_mixed_idr4", 256, "mixed", "idrs", args.orth, "v")]:
         w = inputs.workload("mixed" if n == 256 else "wedge", n)
         s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov=krylov, precision=prec, orth=orth,
-                        reorth=args.reorth, cycle=cycle, max_iter=8000, graphs=not nog)
+                        reorth=args.reorth, cycle=cycle, max_iter=8000, **(extra[0] if extra else {}))
         b = s.rhs_point(w["sources"])
         s.solve(b)
         ms, infos, _ = time_solves(torch, s, b, 2)
@@ -399,6 +402,7 @@ def run_variants(torch, helm, inputs, args):
         del s
         torch.cuda.empty_cache()
     out.update(run_closed_off_table1(torch, helm, inputs))
+    out.update(run_closed_off_weak(torch, helm, inputs))
     if args.variants >= 3:
         out.update(run_shift_sweep(torch, helm, inputs, args))
     if args.variants >= 2:
@@ -409,32 +413,68 @@ def run_variants(torch, helm, inputs, args):
     return out
 
 
-def run_closed_off_table1(torch, helm, inputs):
-    """The closed-off problem of Table 1 (Sec. 5.1.3): 65^3 nodes (n = 64, Dirichlet), k = 40,
-    coarsest grid 17^3 nodes (the paper's 17-node rule, coarsest_n = 16), FP64.  The paper
-    prints #Matvec 145 (left-preconditioned GMRES), 359-407 (Bi-CGSTAB), 192-211 (IDR(4)).
-    The GPU runs GMRES(200) (no restart is reached) preconditioned from the left with the
-    paper's stopping rule and from the right, and Bi-CGSTAB and IDR(4) on the true residual."""
-    import numpy as np
+def paper_golden(name):
+    rows = []
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
 
-    n, k = 64, 40.0
-    shape = inputs.unknown_shape(n, helm.DIRICHLET)
-    k2 = np.full(shape, k * k)
-    b = torch.from_numpy(inputs.closed_off_rhs(n, k)).cuda()
+
+def run_closed_off(torch, helm, inputs, n, solvers, steps):
+    """Time the closed-off problem (Sec. 2.1, k = 40, Dirichlet) in the paper's configuration:
+    coarsest grid by the 17-node rule (Sec. 4.2), FP64, GMRES(200) (no restart is reached),
+    preconditioned from the left with the paper's stopping rule or from the right, and
+    Bi-CGSTAB / IDR(4) on the true residual."""
+    w = inputs.workload("closed_off", n)
+    b = torch.from_numpy(w["rhs"]).cuda()
     out = {}
-    for krylov, side, restart, paper in (("gmres", "left", 200, [145]), ("gmres", "right", 200, [145]),
-                                         ("bicgstab", "right", 30, [359, 359, 403, 407]),
-                                         ("idrs", "right", 30, [192, 211, 192, 201])):
-        s = helm.Solver(n, 1.0 / n, k2, helm.DIRICHLET, coarsest_n=16, krylov=krylov, restart=restart, max_iter=3000,
-                        side=side)
+    for krylov, side in solvers:
+        s = helm.Solver(w["n"], w["h"], w["k2"], helm.DIRICHLET, coarsest_n=w["coarsest_n"], krylov=krylov,
+                        restart=200 if krylov == "gmres" else 30, max_iter=3000, side=side)
         s.solve(b)
-        ms, infos, _ = time_solves(torch, s, b, 2)
-        out[f"closed_off_n64_k40_{krylov}" + ("_left" if side == "left" else "")] = {"ms": ms, "iterations": infos[-1]["iterations"],
-                                              "rel_residual": infos[-1]["rel_residual"],
-                                              "paper_matvec_table1": paper, "unknowns": (n - 1) ** 3}
+        ms, infos, _ = time_solves(torch, s, b, steps)
+        it = infos[-1]["iterations"]
+        out[f"closed_off_n{n}_k40_{krylov}" + ("_left" if side == "left" else "")] = {
+            "ms": ms, "iterations": it, "ms_per_iteration": ms / max(it, 1), "rel_residual": infos[-1]["rel_residual"],
+            "unknowns": (n - 1) ** 3, "coarsest_nodes": w["coarsest_n"] + 1}
         s.close()
         del s
         torch.cuda.empty_cache()
+    return out
+
+
+def run_closed_off_table1(torch, helm, inputs):
+    """Table 1 (Sec. 5.1.3): 65^3 nodes; the paper prints #Matvec 145 (GMRES), 359-407
+    (Bi-CGSTAB) and 192-211 (IDR(4)) over four processor layouts."""
+    paper = {r[0]: [int(v) for v in r[1:]] for r in paper_golden("table1_matvec.txt")}
+    out = run_closed_off(torch, helm, inputs, 64, (("gmres", "left"), ("gmres", "right"), ("bicgstab", "right"),
+                                                  ("idrs", "right")), 2)
+    for key, name in (("gmres_left", "GMRES"), ("gmres", "GMRES"), ("bicgstab", "Bi-CGSTAB"), ("idrs", "IDR(4)")):
+        out[f"closed_off_n64_k40_{key}"]["paper_matvec_table1"] = paper[name]
+    return out
+
+
+def run_closed_off_weak(torch, helm, inputs):
+    """Table 2 (Sec. 5.2): 129^3, 193^3 and 257^3 nodes, GMRES (left) and IDR(4), beside the
+    paper's #Matvec and wall-clock times on 8, 27 and 64 CPU cores, and Table 3's seconds per
+    GMRES iteration of the paper's code at 129^3 (context: other hardware)."""
+    out = {}
+    rows = paper_golden("weak_scaling_matvec.txt")
+    per_iter = {int(r[1]): float(r[2]) for r in rows if r[0] == "per_iter"}
+    for r in rows:
+        if r[0] == "per_iter":
+            continue
+        n = int(r[0]) - 1
+        res = run_closed_off(torch, helm, inputs, n, (("gmres", "left"), ("idrs", "right")), 1)
+        res[f"closed_off_n{n}_k40_gmres_left"].update(paper_matvec_table2=int(r[2]), paper_s_table2=float(r[3]),
+                                                      paper_np=int(r[1]))
+        res[f"closed_off_n{n}_k40_idrs"].update(paper_matvec_table2=int(r[4]), paper_s_table2=float(r[5]),
+                                                paper_np=int(r[1]))
+        if n == 128:
+            res["closed_off_n128_k40_gmres_left"]["paper_s_per_iteration_table3"] = per_iter
+        out.update(res)
     return out
 
 

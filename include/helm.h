@@ -128,6 +128,24 @@ typedef struct {
                        0 (default): level by level, which measures faster on GB300 (one SM
                        cannot hide the latency of the coarse-grid product and coefficient
                        loads that many small grids spread over all SMs). */
+  int gs_sums;      /* FP64 Gram-Schmidt of GMRES / FGMRES (orth = HELM_ORTH_FP64).  1 (default):
+                       every basis vector is stored together with its element sums
+                       Re v + Im v (8 more bytes per unknown and vector), so that the inner
+                       products conj(v) w and the updates w -= h v take three FP64 FMAs per
+                       complex multiply-add instead of four (the three-multiplication form of
+                       a complex product); 0: the textbook four-FMA form.  The results differ
+                       only by rounding. */
+  int fuse_down;    /* down-sweep of the complex64 cycle (one right-hand side), per level:
+                       -1 (default): the autotuner's choice (separate kernels when autotune is
+                       0); 0: pre-smoothing, residual and restriction as three kernels; 1:
+                       pre-smoothing and residual as one kernel, then the restriction; 2: all
+                       three as one kernel (the residual stays in shared memory).  The
+                       arithmetic per point is the same in every form (bit-identical results). */
+  int fuse_up;      /* up-sweep of the complex64 cycle (one right-hand side), per level: -1
+                       (default): the autotuner's choice (separate kernels when autotune is 0);
+                       0: prolongation + correction, then post-smoothing, as two kernels; 1: one
+                       kernel (the corrected iterate stays in shared memory).  Bit-identical
+                       results either way. */
 } helm_params;
 
 /* Per-solve report (host struct). */
@@ -186,9 +204,12 @@ HELM_API helm_status cslp_vcycle(helm_ctx* ctx, helm_dtype dt, const void* r, vo
  * the default shape (8 rows, 8 CTAs per SM).  ty and ctas: host arrays of 8. */
 HELM_API helm_status helm_launch_shapes(const helm_ctx* ctx, int level, int* ty, int* ctas);
 
-/* Kernel variants the autotuner picked on `level` (library instrumentation): *flags bit 0 =
- * FP32 7-point kernels with shared-memory tiles, bit 1 = FP32 pre-smoothing and residual fused
- * into one kernel.  Both change the schedule only, not the arithmetic of a point. */
+/* Kernel variants in use on `level` (library instrumentation; the autotuner's picks, or
+ * helm_params.fuse_down): *flags bit 0 = FP32 7-point kernels with shared-memory tiles, bit 1 =
+ * FP32 pre-smoothing and residual fused into one kernel, bit 2 = the whole FP32 down-sweep
+ * (pre-smoothing, residual, restriction) as one kernel, bit 3 = the whole FP32 up-sweep
+ * (prolongation, correction, post-smoothing) as one kernel.  All change the schedule only, not
+ * the arithmetic of a point. */
 HELM_API helm_status helm_kernel_variants(const helm_ctx* ctx, int level, int* flags);
 
 /* The autotuner's measurements (library instrumentation): *count = number of timed shapes; the

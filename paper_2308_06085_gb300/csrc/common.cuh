@@ -70,6 +70,7 @@ struct alignas(16) zdf {
   float rh, ih, rl, il;
 };
 
+__device__ __forceinline__ double ldg(const double* p) { return __ldg(p); }
 __device__ __forceinline__ zdf ldg(const zdf* p) {
   const float4 v = __ldg(reinterpret_cast<const float4*>(p));
   zdf z;
@@ -168,6 +169,12 @@ struct Grid {
   // FP32, one right-hand side: pre-smoothing from zero and the residual as one kernel (the
   // pre-smoothing slot then holds that kernel's shape); set by the autotuner when faster
   int fused_down = 0;
+  // FP32, one right-hand side: the whole down-sweep (pre-smoothing, residual, restriction) as
+  // one kernel (k_down32) with down_kc coarse planes per CTA; set by the autotuner when faster
+  int down_full = 0, down_kc = 0;
+  // FP32, one right-hand side: prolongation, correction and post-smoothing as one kernel
+  // (k_up32) with up_kz fine planes per CTA; set by the autotuner when faster
+  int up_full = 0, up_kz = 0;
   __host__ __device__ size_t npts() const { return (size_t)N1 * N2 * N3; }
 };
 

@@ -62,12 +62,12 @@ template <> struct LevelBufs<float> {
 // Kernel families for the opt-in profiler (names match the kernel functions).
 enum Fam {
   F_APPLY, F_RESID, F_JACOBI, F_SMOOTH0, F_RESTRICT, F_PROLONG, F_COARSE, F_MDOT, F_REDUCE_DOTS, F_GS_UPDATE,
-  F_NORM, F_REDUCE_NORM, F_SCALE, F_GIVENS, F_SOLUPDATE, F_MISC, F_CCYCLE, F_COUNT
+  F_NORM, F_REDUCE_NORM, F_SCALE, F_GIVENS, F_SOLUPDATE, F_MISC, F_CCYCLE, F_DOWN, F_UP, F_COUNT
 };
 const char* const FAM_NAMES[F_COUNT] = {
     "k_stencil(apply)", "k_stencil(resid)", "k_stencil(jacobi)", "k_smooth0", "k_restrict", "k_prolong_add",
     "k_coarse", "k_mdot", "k_reduce_dots", "k_gs_update", "k_norm2_part", "k_reduce_norm", "k_scale_inv",
-    "k_givens", "k_xupdate/k_combine/k_axpy1/k_trisolve", "other", "k_coarse_cycle"};
+    "k_givens", "k_xupdate/k_combine/k_axpy1/k_trisolve", "other", "k_coarse_cycle", "k_down32", "k_up32"};
 
 struct TuneRec {
   int level, slot, ty, ctas;
@@ -129,6 +129,7 @@ struct helm_ctx {
   int m = 0;
   size_t n0 = 0;
   z128* V = nullptr;      // (m+1) x n0
+  double* Vs = nullptr;   // (m+1) x n0 element sums Re V + Im V of the FP64 basis (gs_sums)
   z128* Z64 = nullptr;    // m x n0, FGMRES in FP64
   z64* Z32 = nullptr;     // m x n0, mixed precision
   z128* zs = nullptr;     // n0 scratch (V-cycle output, GMRES)
@@ -358,42 +359,6 @@ void assemble_coarse(const Level& L, int bc, std::complex<double> s, const std::
       }
 }
 
-// In-place inverse by Gauss-Jordan elimination with partial pivoting.  Returns false on a
-// zero pivot.
-bool invert_dense(int n, std::vector<std::complex<double>>& A) {
-  std::vector<std::complex<double>> I((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
-  for (int col = 0; col < n; ++col) {
-    int piv = col;
-    double best = std::abs(A[(size_t)col * n + col]);
-    for (int r = col + 1; r < n; ++r) {
-      const double v = std::abs(A[(size_t)r * n + col]);
-      if (v > best) { best = v; piv = r; }
-    }
-    if (best == 0.0) return false;
-    if (piv != col)
-      for (int q = 0; q < n; ++q) {
-        std::swap(A[(size_t)col * n + q], A[(size_t)piv * n + q]);
-        std::swap(I[(size_t)col * n + q], I[(size_t)piv * n + q]);
-      }
-    const std::complex<double> inv = 1.0 / A[(size_t)col * n + col];
-    for (int q = 0; q < n; ++q) {
-      A[(size_t)col * n + q] *= inv;
-      I[(size_t)col * n + q] *= inv;
-    }
-    for (int r = 0; r < n; ++r) {
-      if (r == col) continue;
-      const std::complex<double> f = A[(size_t)r * n + col];
-      if (f == 0.0) continue;
-      for (int q = 0; q < n; ++q) {
-        A[(size_t)r * n + q] -= f * A[(size_t)col * n + q];
-        I[(size_t)r * n + q] -= f * I[(size_t)col * n + q];
-      }
-    }
-  }
-  A.swap(I);
-  return true;
-}
 
 // One V-cycle z ~= M^{-1} r in working precision R (input type TI, output type TO).
 // Buffers and grid of one V-cycle level (single or batched right-hand sides).
@@ -416,6 +381,30 @@ void down_fused_launch(const VLevel<R>& F, double sr, double si, double om, cons
                        const int* active) {
   if constexpr (std::is_same<R, float>::value)
     launch_smooth0_resid32<TB>(F.g, sr, si, om, F.k2, b, F.U1, F.T, st, active);
+}
+// Whether level F runs its whole down-sweep (pre-smoothing, residual, restriction into C.B) as
+// one kernel, and that launch.
+template <typename R>
+bool down_full(const VLevel<R>& F) {
+  return std::is_same<R, float>::value && F.g.nb == 1 && F.g.down_full;
+}
+// Whether level F runs its whole up-sweep (prolongation, correction, post-smoothing) as one
+// kernel, and that launch.
+template <typename R>
+bool up_full(const VLevel<R>& F) {
+  return std::is_same<R, float>::value && F.g.nb == 1 && F.g.up_full;
+}
+template <typename R, typename TB, typename TO>
+void up_full_launch(const VLevel<R>& F, const VLevel<R>& C, double sr, double si, double om, const cx<TB>* b,
+                    cx<TO>* out, cudaStream_t st, const int* active) {
+  if constexpr (std::is_same<R, float>::value)
+    launch_up32<TB, TO>(F.g, C.g, sr, si, om, F.k2, F.U1, C.E, b, out, F.g.up_kz, st, active);
+}
+template <typename R, typename TB>
+void down_full_launch(const VLevel<R>& F, const VLevel<R>& C, double sr, double si, double om, const cx<TB>* b,
+                      cudaStream_t st, const int* active) {
+  if constexpr (std::is_same<R, float>::value)
+    launch_down32<TB>(F.g, C.g, sr, si, om, F.k2, b, F.U1, C.B, F.g.down_kc, st, active);
 }
 
 // Levels from which the rest of a V-cycle over lv[0..L) runs in one CTA (k_coarse_cycle):
@@ -492,6 +481,12 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
     const VLevel<R>& C = lv[l + 1];
     const double n = (double)F.g.npts(), ncn = (double)C.g.npts();
     const double bi = l == 0 ? ib : cb;
+    if (down_full(F)) {
+      // pre-smoothing, residual and restriction in one kernel (FP32, one right-hand side)
+      if (l == 0) KL(F_DOWN, n * (bi + kb + cb) + ncn * cb, 60 * n, down_full_launch(F, C, sr, si, om, rin, st, active));
+      else KL(F_DOWN, n * (bi + kb + cb) + ncn * cb, 60 * n, down_full_launch(F, C, sr, si, om, F.B, st, active));
+      continue;
+    }
     if (down_fused(F)) {
       // u1 and the residual in one kernel (FP32, one right-hand side)
       if (l == 0) KL(F_SMOOTH0, n * (bi + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, rin, st, active));
@@ -519,6 +514,14 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
     const VLevel<R>& F = lv[l];
     const VLevel<R>& C = lv[l + 1];
     const double n = (double)F.g.npts(), ncn = (double)C.g.npts();
+    if (up_full(F)) {
+      // prolongation, correction and post-smoothing in one kernel (FP32, one right-hand side)
+      if (l == 0)
+        KL(F_UP, n * (cb + ib + kb + ob) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, rin, zout, st, active));
+      else
+        KL(F_UP, n * (3 * cb + kb) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, F.B, F.E, st, active));
+      continue;
+    }
     KL(F_PROLONG, n * 2 * cb + ncn * cb, 6 * n * nbv, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
     if (l == 0)
       KL(F_JACOBI, n * (cb + ib + kb + db + ob), 32 * n * nbv, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, rin, zout, st, active)));
@@ -556,6 +559,10 @@ void vcycle_from(helm_ctx* c, const VLevel<R>* lv, int L, int l, cudaStream_t st
   KL(F_RESID, n * (3 * cb + kb), 24 * n, (launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.B, F.T, st, active)));
   KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
   run_vcycle_levels<R, R, R>(c, lv + l + 1, L - l - 1, C.B, C.E, st, active);
+  if (up_full(F)) {
+    KL(F_UP, n * (3 * cb + kb) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, F.B, F.E, st, active));
+    return;
+  }
   KL(F_PROLONG, n * 2 * cb + ncn * cb, 6 * n, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
   KL(F_JACOBI, n * (3 * cb + kb + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.B, F.E, st, active)));
 }
@@ -577,15 +584,23 @@ void fcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, int l, const cx<TI>*
   const VLevel<R>& F = lv[l];
   const VLevel<R>& C = lv[l + 1];
   const double n = (double)F.g.npts() * F.g.nb, ncn = (double)C.g.npts() * C.g.nb, db = F.dinv ? 16.0 : 0.0;
-  if (down_fused(F)) {
-    KL(F_SMOOTH0, n * (ib + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, rin, st, active));
+  if (down_full(F)) {
+    KL(F_DOWN, n * (ib + kb + cb) + ncn * cb, 60 * n, down_full_launch(F, C, sr, si, om, rin, st, active));
   } else {
-    KL(F_SMOOTH0, n * (ib + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
-    KL(F_RESID, n * (cb + ib + kb + cb), 24 * n, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
+    if (down_fused(F)) {
+      KL(F_SMOOTH0, n * (ib + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, rin, st, active));
+    } else {
+      KL(F_SMOOTH0, n * (ib + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
+      KL(F_RESID, n * (cb + ib + kb + cb), 24 * n, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
+    }
+    KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
   }
-  KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
   fcycle_levels<R, R, R>(c, lv, L, l + 1, C.B, C.E, st, active);
   vcycle_from<R>(c, lv, L, l + 1, st, active);
+  if (up_full(F)) {
+    KL(F_UP, n * (cb + ib + kb + ob) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, rin, zout, st, active));
+    return;
+  }
   KL(F_PROLONG, n * 2 * cb + ncn * cb, 6 * n, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
   KL(F_JACOBI, n * (cb + ib + kb + db + ob), 32 * n, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, rin, zout, st, active)));
 }
@@ -799,6 +814,53 @@ helm_status tune_vlevels(helm_ctx* c, VLevel<R>* lv, int L, cudaStream_t st) {
     TRY(tune_slot(c, C.g, tile_slot<R>(TILE_RESTRICT), l + 1, st, [&](const Grid& g) {
       launch_restrict<R>(F.g, g, F.T, C.B, st, nullptr);
     }));
+    if constexpr (std::is_same<R, float>::value) {
+      if (F.g.nb == 1) {
+        // the whole down-sweep in one kernel against the chosen kernels (logged as slot 14,
+        // coarse planes per CTA in the shape column)
+        const float t_cur =
+            (F.g.fused_down
+                 ? time_burst(c, st, [&] {
+                     launch_smooth0_resid32<float>(F.g, sr, si, om, F.k2, F.U1, reinterpret_cast<z64*>(c->zs), F.T, st,
+                                                   nullptr);
+                   })
+                 : time_burst(c, st, [&] { launch_smooth0<R, R>(F.g, sr, si, om, F.k2, F.dinv, F.U1, F.T, st, nullptr); }) +
+                       time_burst(c, st, [&] { launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.U1, F.T, st, nullptr); })) +
+            time_burst(c, st, [&] { launch_restrict<R>(F.g, C.g, F.T, C.B, st, nullptr); });
+        float best = 1e30f;
+        int bkc = 0;
+        for (int kc : {1, 2, 4, 8, 16}) {
+          if (kc > 1 && (kc / 2) >= C.g.N3) break;
+          const float t = time_burst(c, st, [&] {
+            launch_down32<float>(F.g, C.g, sr, si, om, F.k2, F.T, reinterpret_cast<z64*>(c->zs), C.B, kc, st, nullptr);
+          });
+          c->tune_log.push_back(TuneRec{l, 14, kc, 0, t});
+          if (t < best) { best = t; bkc = kc; }
+        }
+        F.g.down_full = best < t_cur ? 1 : 0;
+        F.g.down_kc = bkc;
+        TRY(check_launch(c, "autotune (fused down-sweep)"));
+        // the whole up-sweep in one kernel against prolongation + post-smoothing (logged as
+        // slot 15, fine planes per CTA in the shape column)
+        z64* scratch = reinterpret_cast<z64*>(c->zs);
+        const float t_up =
+            time_burst(c, st, [&] { launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, nullptr); }) +
+            time_burst(c, st, [&] { launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.U1, scratch, st, nullptr); });
+        float bu = 1e30f;
+        int bkz = 0;
+        for (int kz : {4, 8, 16, 32, 64}) {
+          if (kz > 4 && kz / 2 >= F.g.N3) break;
+          const float t = time_burst(c, st, [&] {
+            launch_up32<float, float>(F.g, C.g, sr, si, om, F.k2, F.U1, C.E, F.U1, scratch, kz, st, nullptr);
+          });
+          c->tune_log.push_back(TuneRec{l, 15, kz, 0, t});
+          if (t < bu) { bu = t; bkz = kz; }
+        }
+        F.g.up_full = bu < t_up ? 1 : 0;
+        F.g.up_kz = bkz;
+        TRY(check_launch(c, "autotune (fused up-sweep)"));
+      }
+    }
   }
   return HELM_OK;
 }
@@ -844,10 +906,12 @@ helm_status autotune(helm_ctx* c, cudaStream_t st) {
     const size_t n = c->n0;
     const int nv = std::min(16, c->m);
     CU(cudaMemsetAsync(c->V, 0x3f, (size_t)(nv + 1) * n * sizeof(z128), st));
+    if (c->Vs) CU(cudaMemsetAsync(c->Vs, 0x3f, (size_t)nv * n * sizeof(double), st));
     float best = 1e30f;
     for (int v = 0; v < 2; ++v) {
       const float t = time_burst(c, st, [&] {
-        launch_mdot(c->V, n, nv, c->V + (size_t)nv * n, n, c->part, 1, st, nullptr, v);
+        if (c->Vs) launch_mdot_sums(c->V, c->Vs, n, nv, c->V + (size_t)nv * n, n, c->part, 1, st, nullptr, v);
+        else launch_mdot(c->V, n, nv, c->V + (size_t)nv * n, n, c->part, 1, st, nullptr, v);
       });
       c->tune_log.push_back(TuneRec{-1, 16 + v, nv, 0, t});
       if (t < best) { best = t; c->mdot_variant = v; }
@@ -901,6 +965,7 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
   KrylovCtl* ctl = c->ctl;
   const int* act = &ctl->active;
   const bool df = c->p.orth == HELM_ORTH_DF;
+  const bool sums = !df && c->Vs;  // FP64 Gram-Schmidt against the summed basis
   zdf* Vdf = reinterpret_cast<zdf*>(c->V);
   // the paper's left preconditioning (Sec. 3.2): GMRES on M^{-1} A x = M^{-1} b, stopping on
   // ||M^{-1}(b - A x)|| / ||M^{-1} b|| (Sec. 5); FP64 GMRES only (checked at creation)
@@ -942,6 +1007,8 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
     if (df) {
       if (mixed) KL(F_SCALE, 40.0 * n, 2.0 * n, (launch_scale_df<z128, float>(c->r, &ctl->beta, Vdf, c->vcur32, n, st, act)));
       else KL(F_SCALE, 48.0 * n, 2.0 * n, (launch_scale_df<z128, double>(c->r, &ctl->beta, Vdf, c->vcur64, n, st, act)));
+    } else if (sums) {
+      KL(F_SCALE, 40.0 * n, 3.0 * n, launch_scale_inv_sums(c->r, &ctl->beta, c->V, c->Vs, n, st, act));
     } else {
       KL(F_SCALE, 32.0 * n, 2.0 * n, launch_scale_inv(c->r, &ctl->beta, c->V, n, st, act));
     }
@@ -983,6 +1050,9 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
           if (df)
             KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd,
                nb = launch_mdot_df(Vdf, n, j + 1, wd, n, c->part, wn, st, a2, c->mdot_df_variant));
+          else if (sums)
+            KL(F_MDOT, (24.0 * nv + 16.0) * nd, 6.0 * nv * nd,
+               nb = launch_mdot_sums(c->V, c->Vs, n, j + 1, w, n, c->part, wn, st, a2, c->mdot_variant));
           else
             KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd,
                nb = launch_mdot(c->V, n, j + 1, w, n, c->part, wn, st, a2, c->mdot_variant));
@@ -991,6 +1061,9 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
                                 st, a2));
           if (df)
             KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_gs_update_df(Vdf, n, j + 1, c->hpass, wd, n, st, a2));
+          else if (sums)
+            KL(F_GS_UPDATE, (24.0 * nv + 32.0) * nd, 6.0 * nv * nd,
+               launch_gs_update_sums(c->V, c->Vs, n, j + 1, c->hpass, w, n, st, a2));
           else
             KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_gs_update(c->V, n, j + 1, c->hpass, w, n, st, a2));
         }
@@ -1007,6 +1080,8 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
           zdf* vn = Vdf + (size_t)(j + 1) * n;
           if (mixed) KL(F_SCALE, 40.0 * nd, 2.0 * nd, (launch_scale_df<zdf, float>(wd, c->hnorm, vn, c->vcur32, n, st, act)));
           else KL(F_SCALE, 48.0 * nd, 2.0 * nd, (launch_scale_df<zdf, double>(wd, c->hnorm, vn, c->vcur64, n, st, act)));
+        } else if (sums) {
+          KL(F_SCALE, 40.0 * nd, 3.0 * nd, launch_scale_inv_sums(w, c->hnorm, w, c->Vs + (size_t)(j + 1) * n, n, st, act));
         } else {
           KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_scale_inv(w, c->hnorm, w, n, st, act));
         }
@@ -1624,6 +1699,9 @@ void helm_default_params(helm_params* p) {
   p->autotune = 1;
   p->side = HELM_SIDE_RIGHT;
   p->fuse_coarse = 0;
+  p->gs_sums = 1;
+  p->fuse_down = -1;
+  p->fuse_up = -1;
 }
 
 const char* helm_last_error(const helm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
@@ -1748,14 +1826,37 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
   CU(cudaStreamSynchronize(st));
   std::vector<std::complex<double>> A;
   assemble_coarse(c->L[nl - 1], bc, std::complex<double>(c->s_re, c->s_im), k2c, A);
-  if (!invert_dense(c->nc, A)) return fail(c, HELM_ENUMERIC, "coarsest-grid operator is singular");
-  TRY(dalloc(c, &c->Minv, (size_t)c->nc * c->nc));
-  CU(cudaMemcpy(c->Minv, A.data(), A.size() * sizeof(z128), cudaMemcpyHostToDevice));
+  {
+    // inverted on the device by Gauss-Jordan elimination with partial pivoting
+    z128 *Aw = nullptr, *fcol = nullptr, *pinv = nullptr;
+    int *piv = nullptr, *sing = nullptr;
+    TRY(dalloc(c, &c->Minv, (size_t)c->nc * c->nc));
+    TRY(dalloc(c, &Aw, (size_t)c->nc * c->nc));
+    TRY(dalloc(c, &fcol, c->nc));
+    TRY(dalloc(c, &pinv, 1));
+    TRY(dalloc(c, &piv, 1));
+    TRY(dalloc(c, &sing, 1));
+    CU(cudaMemcpyAsync(Aw, A.data(), A.size() * sizeof(z128), cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(sing, 0, sizeof(int), st));
+    launch_gj_invert(Aw, c->Minv, c->nc, fcol, piv, pinv, sing, st);
+    int hsing = 0;
+    CU(cudaMemcpyAsync(&hsing, sing, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    TRY(check_launch(c, "coarsest-grid inverse"));
+    dfree(c, Aw);
+    dfree(c, fcol);
+    dfree(c, pinv);
+    dfree(c, piv);
+    dfree(c, sing);
+    if (hsing) return fail(c, HELM_ENUMERIC, "coarsest-grid operator is singular");
+  }
   // Krylov workspace
   const int m = P.restart;
   c->m = m;
   // Bi-CGSTAB keeps its eight vectors in the basis storage
   TRY(dalloc(c, &c->V, (size_t)std::max(m + 1, 8) * n0));
+  if (P.gs_sums && P.orth == HELM_ORTH_FP64 && (P.krylov == HELM_GMRES || P.krylov == HELM_FGMRES))
+    TRY(dalloc(c, &c->Vs, (size_t)(m + 1) * n0));
   if (P.precision == HELM_PREC_MIXED) TRY(dalloc(c, &c->Z32, (size_t)m * n0));
   else if (P.krylov == HELM_FGMRES) TRY(dalloc(c, &c->Z64, (size_t)m * n0));
   TRY(dalloc(c, &c->zs, n0));
@@ -1801,6 +1902,13 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
   for (int i = 0; i < c->nev; ++i) CU(cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming));
   CU(cudaStreamSynchronize(st));
   if (P.autotune) TRY(autotune(c, st));
+  if (P.fuse_down >= 0)
+    for (int l = 0; l + 1 < nl; ++l) {
+      c->L[l].g.fused_down = P.fuse_down == 1 ? 1 : 0;
+      c->L[l].g.down_full = P.fuse_down == 2 ? 1 : 0;
+    }
+  if (P.fuse_up >= 0)
+    for (int l = 0; l + 1 < nl; ++l) c->L[l].g.up_full = P.fuse_up;
   return HELM_OK;
 }
 
@@ -1834,6 +1942,9 @@ helm_status helm_create(int n1, int n2, int n3, double h, const double* k2, helm
   if (P.cycle != HELM_CYCLE_V && P.cycle != HELM_CYCLE_F) return fail(nullptr, HELM_EINVAL, "unknown cycle %d", P.cycle);
   if (P.reorth != HELM_REORTH_ALWAYS && P.reorth != HELM_REORTH_SELECTIVE)
     return fail(nullptr, HELM_EINVAL, "unknown reorth %d", P.reorth);
+  if (P.gs_sums != 0 && P.gs_sums != 1) return fail(nullptr, HELM_EINVAL, "gs_sums must be 0 or 1");
+  if (P.fuse_down < -1 || P.fuse_down > 2) return fail(nullptr, HELM_EINVAL, "fuse_down must lie in -1..2");
+  if (P.fuse_up < -1 || P.fuse_up > 1) return fail(nullptr, HELM_EINVAL, "fuse_up must lie in -1..1");
   if (P.precision == HELM_PREC_MIXED && P.krylov == HELM_GMRES) P.krylov = HELM_FGMRES;
   helm_ctx* c = new (std::nothrow) helm_ctx();
   if (!c) return fail(nullptr, HELM_ENOMEM, "host allocation failed");
@@ -1905,7 +2016,7 @@ helm_status helm_launch_shapes(const helm_ctx* c, int level, int* ty, int* ctas)
 helm_status helm_kernel_variants(const helm_ctx* c, int level, int* flags) {
   if (!c || !flags || level < 0 || level >= c->nlev) return HELM_EINVAL;
   const Grid& g = c->L[level].g;
-  *flags = (g.tiled ? 1 : 0) | (g.fused_down ? 2 : 0);
+  *flags = (g.tiled ? 1 : 0) | (g.fused_down ? 2 : 0) | (g.down_full ? 4 : 0) | (g.up_full ? 8 : 0);
   return HELM_OK;
 }
 

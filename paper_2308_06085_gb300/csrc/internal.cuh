@@ -32,6 +32,9 @@ void launch_prolong_add(const Grid& gf, const Grid& gc, const cx<R>* u1, const c
 template <typename TI, typename TO>
 void launch_coarse(int nc, const z128* Minv, const cx<TI>* b, cx<TO>* e, cudaStream_t st, const int* active,
                    int nb = 1);
+// X = A^{-1} by Gauss-Jordan elimination with partial pivoting (A, n x n row-major, is
+// overwritten); scratch fcol (n), piv, pinv; *singular is set when a pivot column is zero.
+void launch_gj_invert(z128* A, z128* X, int n, z128* fcol, int* piv, z128* pinv, int* singular, cudaStream_t st);
 void launch_dinv(const Grid& g, double s_re, double s_im, double omega, const double* k2, z128* out, cudaStream_t st);
 void launch_inject(const Grid& gf, const Grid& gc, const double* kf, double* kc, cudaStream_t st);
 void launch_to_float(const double* a, float* b, size_t n, cudaStream_t st);
@@ -48,6 +51,10 @@ constexpr int MAX_BASIS = 257;   // restart <= 256
 // writes the partial |w|^2 to slot nv.  Returns the number of blocks (partials per row).
 int launch_mdot(const z128* V, size_t ld, int nv, const z128* w, size_t n, z128* part, int with_norm,
                 cudaStream_t st, const int* active, int variant = 0);
+// The same against a basis stored with its element sums Vs[i * ld + p] = Re V + Im V (three
+// FP64 FMAs per complex multiply-add instead of four).
+int launch_mdot_sums(const z128* V, const double* Vs, size_t ld, int nv, const z128* w, size_t n, z128* part,
+                     int with_norm, cudaStream_t st, const int* active, int variant);
 // hpass[i] = sum_{blk < nb} part[i * RED_STRIDE + blk]; hacc[i] = hpass[i] (accumulate 0) or
 // += (1).  decide_j >= 0: also read |w|^2 from slot nv and set *pass2 = log[decide_j] =
 // (second Gram-Schmidt pass needed)
@@ -56,12 +63,17 @@ void launch_reduce_dots(const z128* part, int nv, int nb, z128* hpass, z128* hac
 // w -= sum_i h[i] V_i
 void launch_gs_update(const z128* V, size_t ld, int nv, const z128* h, z128* w, size_t n, cudaStream_t st,
                       const int* active);
+void launch_gs_update_sums(const z128* V, const double* Vs, size_t ld, int nv, const z128* h, z128* w, size_t n,
+                           cudaStream_t st, const int* active);
 // partial sums of |x|^2 into partr[0..nb); returns nb
 int launch_norm2_part(const z128* x, size_t n, double* partr, cudaStream_t st, const int* active);
 // *out = sqrt(sum_{b < nb} partr[b])
 void launch_reduce_norm(const double* partr, int nb, double* out, cudaStream_t st, const int* active);
 // out = in * (1 / *s)   (when *s != 0)
 void launch_scale_inv(const z128* in, const double* s, z128* out, size_t n, cudaStream_t st, const int* active);
+// out = in / *s and outs = Re out + Im out
+void launch_scale_inv_sums(const z128* in, const double* s, z128* out, double* outs, size_t n, cudaStream_t st,
+                           const int* active);
 // start a restart cycle: active = 1, g = (beta, 0, ...), iter0 recorded
 void launch_cycle_init(KrylovCtl* ctl, z128* gvec, int m, int iter0, cudaStream_t st);
 // Arnoldi step j: rotations on H(:, j) (column stored at Hcol), new rotation, g update,
@@ -125,6 +137,17 @@ void launch_coarse_cycle(const CCycle<R>& cc, size_t smem_bytes, const cx<R>* b,
 // FP32 pre-smoothing from zero fused with the residual, one right-hand side (stencil.cu):
 // u1 = (omega/d) b and r = b - M u1, u1 recomputed at the neighbours; same values as
 // launch_smooth0 followed by launch_resid.
+// The FP32 up-sweep of one level in one kernel: out = u2 + (omega/d)(b - M u2) with
+// u2 = u1 + P e (zchunk fine planes per CTA)
+template <typename TB, typename TO>
+void launch_up32(const Grid& gf, const Grid& gc, double s_re, double s_im, double omega, const float* k2,
+                 const z64* u1, const z64* e, const cx<TB>* b, cx<TO>* out, int zchunk, cudaStream_t st,
+                 const int* active);
+// The FP32 down-sweep of one level in one kernel: u1 = (omega/d) b on the fine grid and the
+// full-weighting restriction of b - M u1 into bc on the coarse grid (kchunk coarse planes per CTA)
+template <typename TB>
+void launch_down32(const Grid& gf, const Grid& gc, double s_re, double s_im, double omega, const float* k2,
+                   const cx<TB>* b, z64* u1, z64* bc, int kchunk, cudaStream_t st, const int* active);
 template <typename TB>
 void launch_smooth0_resid32(const Grid& g, double s_re, double s_im, double omega, const float* k2, const cx<TB>* b,
                             z64* u1, z64* r, cudaStream_t st, const int* active);

@@ -28,8 +28,9 @@ __device__ __forceinline__ void block_range(size_t n, size_t& p0, size_t& p1) {
 // ~50-100 points per lane.  Partials per block go to part[slot * RED_STRIDE + block].
 constexpr int KS = 4;  // slots per warp per pass over the block's points
 
-struct AccD {  // FP64 accumulator
+struct AccD {  // FP64 accumulator, four FMAs per complex multiply-add
   static constexpr bool kBalanced = false;
+  static constexpr bool kSums = false;
   double re, im;
   __device__ void zero() { re = im = 0.0; }
   __device__ void mac(const z128& v, const z128& w) { cdot_acc(v, w, re, im); }
@@ -59,6 +60,7 @@ __device__ __forceinline__ void df_shfl_reduce(float& s, float& c) {
 
 struct AccF {  // double-float accumulator, FP32 arithmetic only
   static constexpr bool kBalanced = true;
+  static constexpr bool kSums = false;
   float rs, rc, is, ic;
   __device__ void zero() { rs = rc = is = ic = 0.f; }
   __device__ void mac(const zdf& v, const zdf& w) {
@@ -83,6 +85,45 @@ struct AccF {  // double-float accumulator, FP32 arithmetic only
   }
 };
 
+// FP64 accumulator against a basis stored with its element sums s = Re v + Im v: with
+// A = sum vr wr, B = sum vi wi and C = sum s (wi - wr),
+//   conj(v) . w = (A + B) + i (C + A - B),
+// since s (wi - wr) = vr wi - vi wr - (vr wr - vi wi).  Three FMAs per element and slot; the
+// difference wi - wr is formed once per element of w and shared by all slots.
+struct AccD3 {
+  static constexpr bool kBalanced = false;
+  static constexpr bool kSums = true;
+  double a, b, c;
+  __device__ void zero() { a = b = c = 0.0; }
+  __device__ void mac3(const z128& v, double sv, const z128& w, double wd) {
+    a = fma(v.re, w.re, a);
+    b = fma(v.im, w.im, b);
+    c = fma(sv, wd, c);
+  }
+  __device__ void norm(const z128& w) {
+    a = fma(w.re, w.re, a);
+    b = fma(w.im, w.im, b);
+  }
+  __device__ void reduce_warp(double& r, double& i) {
+    r = a + b;
+    i = c + (a - b);
+    for (int o = 16; o; o >>= 1) {
+      r += __shfl_xor_sync(0xffffffffu, r, o);
+      i += __shfl_xor_sync(0xffffffffu, i, o);
+    }
+  }
+};
+
+// One slot's multiply-add: the plain accumulators read V alone, AccD3 also the sums Vs.
+template <typename ACC, typename E>
+__device__ __forceinline__ void slot_mac(ACC& acc, const E* __restrict__ V, const double* __restrict__ Vs, size_t off,
+                                         const E& w, double wd) {
+  if constexpr (ACC::kSums) acc.mac3(ldg(V + off), ldg(Vs + off), w, wd);
+  else acc.mac(ldg(V + off), w);
+}
+__device__ __forceinline__ double w_diff(const z128& w) { return w.im - w.re; }
+__device__ __forceinline__ double w_diff(const zdf&) { return 0.0; }
+
 // Warps sharing one slot: the groups of NW / wps warps take the slots round-robin, so the
 // busiest group holds ceil(nslot / groups) of them.  Take the least sharing that leaves at most
 // 1/8 of the warp-slots idle: less sharing means more points per lane between warp reductions,
@@ -102,8 +143,8 @@ __device__ __forceinline__ int share_width(int nslot) {
 // warp reads w itself (the block's warps share it through L1) and runs barrier-free.
 template <typename E, typename ACC, int TILE, int KSV = KS, bool STAGE = true>
 __global__ void __launch_bounds__(NT)
-    k_mdot(const E* __restrict__ V, size_t ld, int nv, const E* __restrict__ w, size_t n, z128* __restrict__ part,
-           int with_norm, const int* __restrict__ active) {
+    k_mdot(const E* __restrict__ V, const double* __restrict__ Vs, size_t ld, int nv, const E* __restrict__ w, size_t n,
+           z128* __restrict__ part, int with_norm, const int* __restrict__ active) {
   if (active && *active == 0) return;
   __shared__ E sw[TILE];
   __shared__ double sred[NW][2];
@@ -130,10 +171,11 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll 2
         for (int q = sub * 32 + lane; q < tn; q += 32 * wps) {
           const E wv = sw[q];
+          const double wd = ACC::kSums ? w_diff(wv) : 0.0;
 #pragma unroll
           for (int k = 0; k < KSV; ++k) {
             const int sl = sfirst + (sbase + k) * sstep;
-            if (sl < nv) acc[k].mac(ldg(V + (size_t)sl * ld + t0 + q), wv);
+            if (sl < nv) slot_mac(acc[k], V, Vs, (size_t)sl * ld + t0 + q, wv, wd);
             else if (sl == nv && with_norm) acc[k].norm(wv);
           }
         }
@@ -142,10 +184,11 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll 2
       for (size_t q = p0 + sub * 32 + lane; q < p1; q += 32 * wps) {
         const E wv = ldg(w + q);
+        const double wd = ACC::kSums ? w_diff(wv) : 0.0;
 #pragma unroll
         for (int k = 0; k < KSV; ++k) {
           const int sl = sfirst + (sbase + k) * sstep;
-          if (sl < nv) acc[k].mac(ldg(V + (size_t)sl * ld + q), wv);
+          if (sl < nv) slot_mac(acc[k], V, Vs, (size_t)sl * ld + q, wv, wd);
           else if (sl == nv && with_norm) acc[k].norm(wv);
         }
       }
@@ -244,6 +287,35 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
+// w -= sum_i h_i v_i against the summed basis: with P = sum hr vr, Q = sum hi vi and
+// R = sum (hr + hi) s,  h v = (P - Q) + i (R - P - Q) summed over i, three FMAs per element
+// and basis vector (hr + hi is formed once per vector).
+__global__ void __launch_bounds__(NT)
+    k_gs_update_sums(const z128* __restrict__ V, const double* __restrict__ Vs, size_t ld, int nv,
+                     const z128* __restrict__ h, z128* __restrict__ w, size_t n, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ double3 sh[MAX_BASIS];
+  for (int i = threadIdx.x; i < nv; i += NT) {
+    const z128 c = h[i];
+    sh[i] = make_double3(c.re, c.im, c.re + c.im);
+  }
+  __syncthreads();
+  for (size_t p = blockIdx.x * (size_t)NT + threadIdx.x; p < n; p += (size_t)gridDim.x * NT) {
+    double P = 0.0, Q = 0.0, R = 0.0;
+    for (int i = 0; i < nv; ++i) {
+      const size_t off = (size_t)i * ld + p;
+      const z128 v = ldg(V + off);
+      const double sv = ldg(Vs + off);
+      const double3 c = sh[i];
+      P = fma(c.x, v.re, P);
+      Q = fma(c.y, v.im, Q);
+      R = fma(c.z, sv, R);
+    }
+    const z128 a = w[p];
+    w[p] = mkc<double>(a.re - (P - Q), a.im - (R - (P + Q)));
+  }
+}
+
 __global__ void __launch_bounds__(NT)
     k_norm2_part(const z128* __restrict__ x, size_t n, double* __restrict__ part, const int* __restrict__ active) {
   if (active && *active == 0) return;
@@ -292,6 +364,22 @@ __global__ void __launch_bounds__(NT)
   for (size_t p = blockIdx.x * (size_t)NT + threadIdx.x; p < n; p += (size_t)gridDim.x * NT) {
     const z128 v = in[p];
     out[p] = mkc<double>(v.re * inv, v.im * inv);
+  }
+}
+
+// out = in / *s, and outs = Re out + Im out (the element sums of a summed basis vector).
+__global__ void __launch_bounds__(NT)
+    k_scale_inv_sums(const z128* __restrict__ in, const double* __restrict__ s, z128* __restrict__ out,
+                     double* __restrict__ outs, size_t n, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const double d = *s;
+  if (!(d != 0.0)) return;
+  const double inv = 1.0 / d;
+  for (size_t p = blockIdx.x * (size_t)NT + threadIdx.x; p < n; p += (size_t)gridDim.x * NT) {
+    const z128 v = in[p];
+    const z128 o = mkc<double>(v.re * inv, v.im * inv);
+    out[p] = o;
+    outs[p] = o.re + o.im;
   }
 }
 
@@ -596,17 +684,22 @@ int stream_blocks(size_t n) {
 
 }  // namespace
 
-template <bool STAGE>
-int mdot_fp64(const z128* V, size_t ld, int nv, const z128* w, size_t n, z128* part, int with_norm, cudaStream_t st,
-              const int* active) {
-  static const int nb = wave_blocks(k_mdot<z128, AccD, 4 * NT, KS, STAGE>);
-  k_mdot<z128, AccD, 4 * NT, KS, STAGE><<<nb, NT, 0, st>>>(V, ld, nv, w, n, part, with_norm, active);
+template <typename ACC, bool STAGE>
+int mdot_fp64(const z128* V, const double* Vs, size_t ld, int nv, const z128* w, size_t n, z128* part, int with_norm,
+              cudaStream_t st, const int* active) {
+  static const int nb = wave_blocks(k_mdot<z128, ACC, 4 * NT, KS, STAGE>);
+  k_mdot<z128, ACC, 4 * NT, KS, STAGE><<<nb, NT, 0, st>>>(V, Vs, ld, nv, w, n, part, with_norm, active);
   return nb;
 }
 int launch_mdot(const z128* V, size_t ld, int nv, const z128* w, size_t n, z128* part, int with_norm,
                 cudaStream_t st, const int* active, int variant) {
-  return variant == 1 ? mdot_fp64<false>(V, ld, nv, w, n, part, with_norm, st, active)
-                      : mdot_fp64<true>(V, ld, nv, w, n, part, with_norm, st, active);
+  return variant == 1 ? mdot_fp64<AccD, false>(V, nullptr, ld, nv, w, n, part, with_norm, st, active)
+                      : mdot_fp64<AccD, true>(V, nullptr, ld, nv, w, n, part, with_norm, st, active);
+}
+int launch_mdot_sums(const z128* V, const double* Vs, size_t ld, int nv, const z128* w, size_t n, z128* part,
+                     int with_norm, cudaStream_t st, const int* active, int variant) {
+  return variant == 1 ? mdot_fp64<AccD3, false>(V, Vs, ld, nv, w, n, part, with_norm, st, active)
+                      : mdot_fp64<AccD3, true>(V, Vs, ld, nv, w, n, part, with_norm, st, active);
 }
 void launch_reduce_dots(const z128* part, int nv, int nb, z128* hpass, z128* hacc, int accumulate, int decide_j,
                         int* pass2, int* log, cudaStream_t st, const int* active) {
@@ -615,6 +708,10 @@ void launch_reduce_dots(const z128* part, int nv, int nb, z128* hpass, z128* hac
 void launch_gs_update(const z128* V, size_t ld, int nv, const z128* h, z128* w, size_t n, cudaStream_t st,
                       const int* active) {
   k_gs_update<<<stream_blocks(n), NT, 0, st>>>(V, ld, nv, h, w, n, active);
+}
+void launch_gs_update_sums(const z128* V, const double* Vs, size_t ld, int nv, const z128* h, z128* w, size_t n,
+                           cudaStream_t st, const int* active) {
+  k_gs_update_sums<<<stream_blocks(n), NT, 0, st>>>(V, Vs, ld, nv, h, w, n, active);
 }
 int launch_norm2_part(const z128* x, size_t n, double* partr, cudaStream_t st, const int* active) {
   static const int nb = wave_blocks(k_norm2_part);
@@ -626,6 +723,10 @@ void launch_reduce_norm(const double* partr, int nb, double* out, cudaStream_t s
 }
 void launch_scale_inv(const z128* in, const double* s, z128* out, size_t n, cudaStream_t st, const int* active) {
   k_scale_inv<<<stream_blocks(n), NT, 0, st>>>(in, s, out, n, active);
+}
+void launch_scale_inv_sums(const z128* in, const double* s, z128* out, double* outs, size_t n, cudaStream_t st,
+                           const int* active) {
+  k_scale_inv_sums<<<stream_blocks(n), NT, 0, st>>>(in, s, out, outs, n, active);
 }
 void launch_cycle_init(KrylovCtl* ctl, z128* gvec, int m, int iter0, cudaStream_t st) {
   k_cycle_init<<<1, 256, 0, st>>>(ctl, gvec, m, iter0);
@@ -656,7 +757,7 @@ template <int KSV>
 int mdot_df_ks(const zdf* V, size_t ld, int nv, const zdf* w, size_t n, z128* part, int with_norm, cudaStream_t st,
                const int* active) {
   static const int nb = wave_blocks(k_mdot<zdf, AccF, 4 * NT, KSV>);
-  k_mdot<zdf, AccF, 4 * NT, KSV><<<nb, NT, 0, st>>>(V, ld, nv, w, n, part, with_norm, active);
+  k_mdot<zdf, AccF, 4 * NT, KSV><<<nb, NT, 0, st>>>(V, nullptr, ld, nv, w, n, part, with_norm, active);
   return nb;
 }
 int launch_mdot_df(const zdf* V, size_t ld, int nv, const zdf* w, size_t n, z128* part, int with_norm,

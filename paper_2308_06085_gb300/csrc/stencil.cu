@@ -231,6 +231,229 @@ __global__ void __launch_bounds__(TX* TY)
   }
 }
 
+// The whole down-sweep of one FP32 level (one right-hand side) in one kernel: pre-smoothing from
+// zero (u1 = (omega/d) b, Sec. 3.4.1), the residual r = b - M u1 and its full-weighting
+// restriction (Sec. 3.4.2) to the next level's right-hand side.  r never goes to memory.
+// A CTA owns DCX x DCY coarse columns and a chunk of coarse planes.  It streams the fine planes
+// in z: u1 over the fine window with a halo of two, r over the window with a halo of one, each
+// in a three-plane ring in shared memory, and after fine plane 2K + off + 1 the coarse plane K.
+// u1 is also written to memory for the fine points this CTA owns (the windows of neighbouring
+// CTAs overlap; ownership tiles the grid).  Every value goes through the same arithmetic in
+// the same order as k_smooth0 / k_stencil(resid) / k_restrict, so the results are identical.
+constexpr int DCX = 16, DCY = 8, DNT = 256;
+constexpr int DUX = 2 * DCX + 3, DUY = 2 * DCY + 3, DRX = 2 * DCX + 1, DRY = 2 * DCY + 1;
+template <typename TB>
+__global__ void __launch_bounds__(DNT)
+    k_down32(Grid gf, Grid gc, OpCoef<float> c, const float* __restrict__ k2, const cx<TB>* __restrict__ b,
+             z64* __restrict__ u1, z64* __restrict__ bco, int kchunk, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ z64 su[3][DUY][DUX];
+  __shared__ z64 sr[3][DRY][DRX];
+  const int off = gf.bc == 0 ? 1 : 0;  // the fine centre of coarse node I is 2 I + off
+  const bool som = gf.bc == 1;
+  const int N1 = gf.N1, N2 = gf.N2, N3 = gf.N3;
+  const int I0 = blockIdx.x * DCX, J0 = blockIdx.y * DCY, K0 = blockIdx.z * kchunk;
+  if (K0 >= gc.N3) return;
+  const int K1 = min(K0 + kchunk, gc.N3);
+  const int rx0 = 2 * I0 + off - 1, ry0 = 2 * J0 + off - 1, rz0 = 2 * K0 + off - 1;
+  const int ux0 = rx0 - 1, uy0 = ry0 - 1;
+  const int ox0 = I0 == 0 ? 0 : rx0, ox1 = I0 + DCX >= gc.N1 ? N1 : rx0 + 2 * DCX;
+  const int oy0 = J0 == 0 ? 0 : ry0, oy1 = J0 + DCY >= gc.N2 ? N2 : ry0 + 2 * DCY;
+  const int oz0 = K0 == 0 ? 0 : rz0, oz1 = K1 >= gc.N3 ? N3 : 2 * K1 + off - 1;
+  const int zlo = max(rz0, 0), zhi = min(2 * (K1 - 1) + off + 1, N3 - 1);
+  const z64 z0 = mkc<float>(0.f, 0.f);
+  auto fill_u = [&](int z) {
+    z64(*U)[DUX] = su[z % 3];
+    for (int t = threadIdx.x; t < DUX * DUY; t += DNT) {
+      const int ly = t / DUX, lx = t - ly * DUX;
+      const int x = ux0 + lx, y = uy0 + ly;
+      z64 v = z0;
+      if (x >= 0 && x < N1 && y >= 0 && y < N2) {
+        const size_t q = gidx(x, y, z, N1, N2);
+        const int nf = som ? (x == 0) + (x == N1 - 1) + (y == 0) + (y == N2 - 1) + (z == 0) + (z == N3 - 1) : 0;
+        const float kq = __ldg(k2 + q);
+        const z64 w = omega_over(op_diag(c, kq, nf, nf ? face_k<float>(gf, q, kq) : 0.f), c.omega);
+        v = cmul(w, cvt<float>(ldg(b + q)));
+        if (x >= ox0 && x < ox1 && y >= oy0 && y < oy1 && z >= oz0 && z < oz1) u1[q] = v;
+      }
+      U[ly][lx] = v;
+    }
+  };
+  auto fill_r = [&](int z) {
+    const z64(*Um)[DUX] = su[(z + 2) % 3];
+    const z64(*Uc)[DUX] = su[z % 3];
+    const z64(*Up)[DUX] = su[(z + 1) % 3];
+    z64(*Rz)[DRX] = sr[z % 3];
+    const bool hzm = z > 0, hzp = z + 1 < N3;
+    for (int t = threadIdx.x; t < DRX * DRY; t += DNT) {
+      const int ly = t / DRX, lx = t - ly * DRX;
+      const int x = rx0 + lx, y = ry0 + ly;
+      z64 v = z0;
+      if (x >= 0 && x < N1 && y >= 0 && y < N2) {
+        const int li = lx + 1, lj = ly + 1;
+        const bool hxm = x > 0, hxp = x < N1 - 1, hym = y > 0, hyp = y < N2 - 1;
+        int nf = som ? (!hxm) + (!hxp) + (!hym) + (!hyp) : 0;
+        const z64 uc = Uc[lj][li];
+        z64 zm, zp;
+        if (hzm) zm = Um[lj][li];
+        else if (som) { zm = Up[lj][li]; ++nf; }
+        else zm = z0;
+        if (hzp) zp = Up[lj][li];
+        else if (som) { zp = Um[lj][li]; ++nf; }
+        else zp = z0;
+        const z64 xm = hxm ? Uc[lj][li - 1] : (som ? Uc[lj][li + 1] : z0);
+        const z64 xp = hxp ? Uc[lj][li + 1] : (som ? Uc[lj][li - 1] : z0);
+        const z64 ym = hym ? Uc[lj - 1][li] : (som ? Uc[lj + 1][li] : z0);
+        const z64 yp = hyp ? Uc[lj + 1][li] : (som ? Uc[lj - 1][li] : z0);
+        const size_t q = gidx(x, y, z, N1, N2);
+        const float kk = __ldg(k2 + q);
+        const z64 d = op_diag(c, kk, nf, nf ? face_k<float>(gf, q, kk) : 0.f);
+        const bool real_d = c.real_shift && nf == 0;
+        v = op_resid(cvt<float>(ldg(b + q)), d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
+      }
+      Rz[ly][lx] = v;
+    }
+  };
+  auto restrict_plane = [&](int K) {
+    const int fk = 2 * K + off;
+    for (int t = threadIdx.x; t < DCX * DCY; t += DNT) {
+      const int ly = t / DCX, lx = t - ly * DCX;
+      const int I = I0 + lx, J = J0 + ly;
+      if (I >= gc.N1 || J >= gc.N2) continue;
+      const int fi = 2 * I + off, fj = 2 * J + off;
+      float are = 0.f, aim = 0.f;
+      for (int dz = -1; dz <= 1; ++dz) {
+        const int z = fk + dz;
+        if (z < 0 || z >= N3) continue;
+        const float wz = dz ? 1.f : 2.f;
+        for (int dy = -1; dy <= 1; ++dy) {
+          const int y = fj + dy;
+          if (y < 0 || y >= N2) continue;
+          const float wyz = wz * (dy ? 1.f : 2.f);
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int x = fi + dx;
+            if (x < 0 || x >= N1) continue;
+            const float w = wyz * (dx ? 1.f : 2.f);
+            const z64 v = sr[z % 3][y - ry0][x - rx0];
+            are = fmaf(w, v.re, are);
+            aim = fmaf(w, v.im, aim);
+          }
+        }
+      }
+      bco[gidx(I, J, K, gc.N1, gc.N2)] = mkc<float>(are * (float)(1.0 / 64.0), aim * (float)(1.0 / 64.0));
+    }
+  };
+  if (zlo > 0) fill_u(zlo - 1);
+  fill_u(zlo);
+  int K = K0;
+  for (int z = zlo; z <= zhi; ++z) {
+    if (z + 1 < N3) fill_u(z + 1);
+    __syncthreads();
+    fill_r(z);
+    __syncthreads();
+    // coarse plane K needs fine r planes 2K + off - 1 .. 2K + off + 1 (those inside the grid)
+    while (K < K1 && min(2 * K + off + 1, N3 - 1) == z) restrict_plane(K++);
+  }
+}
+
+// The whole up-sweep of one FP32 level (one right-hand side) in one kernel: u2 = u1 + P e
+// (trilinear interpolation, Sec. 3.4.3) and the post-smoothing u3 = u2 + (omega/d)(b - M u2)
+// (Sec. 3.4.1).  u2 never goes to memory: a CTA of 32 x UTY fine columns computes it over its
+// window with a halo of one into a three-plane ring in shared memory while it streams its
+// z-chunk.  Same arithmetic per point, in the same order, as k_prolong_add and
+// k_stencil(jacobi), so the results are identical.
+constexpr int UTY = 8, UWX = TX + 2, UWY = UTY + 2;
+template <typename TB, typename TO>
+__global__ void __launch_bounds__(TX* UTY)
+    k_up32(Grid gf, Grid gc, OpCoef<float> c, const float* __restrict__ k2, const z64* __restrict__ u1,
+           const z64* __restrict__ e, const cx<TB>* __restrict__ b, cx<TO>* __restrict__ out, int zchunk,
+           const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ z64 su[3][UWY][UWX];
+  const int N1 = gf.N1, N2 = gf.N2, N3 = gf.N3;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * UTY;
+  const int k0 = blockIdx.z * zchunk;
+  if (k0 >= N3) return;
+  const int k1 = min(k0 + zchunk, N3);
+  const int off = gf.bc == 0 ? 1 : 0;
+  const bool som = gf.bc == 1;
+  const z64 z0 = mkc<float>(0.f, 0.f);
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  auto fill = [&](int z) {
+    z64(*U)[UWX] = su[z % 3];
+    const int fk = z + off;
+    const int cz0 = (fk >> 1) - off, cz1 = ((fk + 1) >> 1) - off;
+    const int nz = cz0 == cz1 ? 1 : 2;
+    for (int t = tid; t < UWX * UWY; t += TX * UTY) {
+      const int ly = t / UWX, lx = t - ly * UWX;
+      const int x = x0 - 1 + lx, y = y0 - 1 + ly;
+      z64 v = z0;
+      if (x >= 0 && x < N1 && y >= 0 && y < N2) {
+        const int fi = x + off, fj = y + off;
+        const int cxs[2] = {(fi >> 1) - off, ((fi + 1) >> 1) - off};
+        const int cys[2] = {(fj >> 1) - off, ((fj + 1) >> 1) - off};
+        const int czs[2] = {cz0, cz1};
+        const int nx = cxs[0] == cxs[1] ? 1 : 2, ny = cys[0] == cys[1] ? 1 : 2;
+        float are = 0.f, aim = 0.f;
+        for (int cq = 0; cq < nz; ++cq) {
+          if (czs[cq] < 0 || czs[cq] >= gc.N3) continue;
+          for (int bq = 0; bq < ny; ++bq) {
+            if (cys[bq] < 0 || cys[bq] >= gc.N2) continue;
+            for (int a = 0; a < nx; ++a) {
+              if (cxs[a] < 0 || cxs[a] >= gc.N1) continue;
+              const z64 ev = ldg(e + gidx(cxs[a], cys[bq], czs[cq], gc.N1, gc.N2));
+              are += ev.re;
+              aim += ev.im;
+            }
+          }
+        }
+        const float sc = 1.f / (float)(nx * ny * nz);
+        const z64 base = ldg(u1 + gidx(x, y, z, N1, N2));
+        v = mkc<float>(fmaf(are, sc, base.re), fmaf(aim, sc, base.im));
+      }
+      U[ly][lx] = v;
+    }
+  };
+  const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
+  const int li = threadIdx.x + 1, lj = threadIdx.y + 1;
+  const bool inside = i < N1 && j < N2;
+  const bool hxm = i > 0, hxp = i < N1 - 1, hym = j > 0, hyp = j < N2 - 1;
+  const int nfxy = som ? (!hxm) + (!hxp) + (!hym) + (!hyp) : 0;
+  if (k0 > 0) fill(k0 - 1);
+  fill(k0);
+  for (int k = k0; k < k1; ++k) {
+    const bool hzp = k + 1 < N3;
+    if (hzp) fill(k + 1);
+    __syncthreads();
+    if (inside) {
+      const z64(*Um)[UWX] = su[(k + 2) % 3];
+      const z64(*Uc)[UWX] = su[k % 3];
+      const z64(*Up)[UWX] = su[(k + 1) % 3];
+      int nf = nfxy;
+      const z64 uc = Uc[lj][li];
+      z64 zm, zp;
+      if (k > 0) zm = Um[lj][li];
+      else if (som) { zm = Up[lj][li]; ++nf; }
+      else zm = z0;
+      if (hzp) zp = Up[lj][li];
+      else if (som) { zp = Um[lj][li]; ++nf; }
+      else zp = z0;
+      const z64 xm = hxm ? Uc[lj][li - 1] : (som ? Uc[lj][li + 1] : z0);
+      const z64 xp = hxp ? Uc[lj][li + 1] : (som ? Uc[lj][li - 1] : z0);
+      const z64 ym = hym ? Uc[lj - 1][li] : (som ? Uc[lj + 1][li] : z0);
+      const z64 yp = hyp ? Uc[lj + 1][li] : (som ? Uc[lj - 1][li] : z0);
+      const size_t p = gidx(i, j, k, N1, N2);
+      const float kk = __ldg(k2 + p);
+      const z64 d = op_diag(c, kk, nf, nf ? face_k<float>(gf, p, kk) : 0.f);
+      const bool real_d = c.real_shift && nf == 0;
+      const z64 res = op_resid(cvt<float>(ldg(b + p)), d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
+      const z64 w = omega_over(d, c.omega);
+      out[p] = cvt<TO>(cfma(w, res, uc));
+    }
+    __syncthreads();
+  }
+}
+
 // Pre-smoothing from a zero initial guess: one damped-Jacobi sweep gives u1 = (omega/d) b.
 template <typename R, bool DINV, typename TB>
 __global__ void __launch_bounds__(TX* TY)
@@ -396,6 +619,98 @@ __global__ void k_check_k2(const double* __restrict__ a, size_t n, int* __restri
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
     local += !(isfinite(a[p]) && a[p] > 0.0);
   if (local) atomicAdd(bad, local);
+}
+
+// ---- coarsest-grid inverse (set-up only): Gauss-Jordan elimination with partial pivoting ----
+// A (n x n, row-major) is reduced to the identity while X, started as the identity, becomes
+// A^{-1}.  Column col takes three launches: the pivot search (the largest |A[r][col]|, r >= col,
+// the smallest r on ties) which also saves the column's multipliers as they stand after the row
+// swap; the swap and scaling of the pivot row; the elimination of every other row with a
+// nonzero multiplier.
+__global__ void k_gj_identity(z128* __restrict__ X, int n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)n * n; t += (size_t)gridDim.x * blockDim.x)
+    X[t] = mkc<double>((t / n) == (t % n) ? 1.0 : 0.0, 0.0);
+}
+
+constexpr int GJ_THREADS = 1024;
+__global__ void __launch_bounds__(GJ_THREADS)
+    k_gj_pivot(const z128* __restrict__ A, int n, int col, z128* __restrict__ fcol, int* __restrict__ piv,
+               z128* __restrict__ pinv, int* __restrict__ singular) {
+  __shared__ double sbest[GJ_THREADS / 32];
+  __shared__ int sidx[GJ_THREADS / 32];
+  __shared__ int spiv;
+  double best = -1.0;
+  int idx = n;
+  for (int r = col + threadIdx.x; r < n; r += GJ_THREADS) {
+    const z128 a = A[(size_t)r * n + col];
+    const double m = a.re * a.re + a.im * a.im;
+    if (m > best) { best = m; idx = r; }  // rows visited in increasing order: ties keep the first
+  }
+  for (int o = 16; o; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sbest[threadIdx.x >> 5] = best;
+    sidx[threadIdx.x >> 5] = idx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    best = sbest[0];
+    idx = sidx[0];
+    for (int w = 1; w < GJ_THREADS / 32; ++w)
+      if (sbest[w] > best || (sbest[w] == best && sidx[w] < idx)) { best = sbest[w]; idx = sidx[w]; }
+    if (!(best > 0.0)) {  // singular (or NaN): finish harmlessly, the host reports it
+      *singular = 1;
+      idx = col;
+      *pinv = mkc<double>(0.0, 0.0);
+    } else {
+      const z128 p = A[(size_t)idx * n + col];
+      const double inv = 1.0 / (p.re * p.re + p.im * p.im);
+      *pinv = mkc<double>(p.re * inv, -p.im * inv);
+    }
+    *piv = idx;
+    spiv = idx;
+  }
+  __syncthreads();
+  const int pv = spiv;
+  for (int r = threadIdx.x; r < n; r += GJ_THREADS) {
+    const int src = r == col ? pv : (r == pv ? col : r);
+    fcol[r] = r == col ? mkc<double>(0.0, 0.0) : A[(size_t)src * n + col];
+  }
+}
+
+__global__ void k_gj_swap_scale(z128* __restrict__ A, z128* __restrict__ X, int n, int col, const int* __restrict__ piv,
+                                const z128* __restrict__ pinv) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 2 * n || q < col) return;  // columns of A left of col are finished
+  z128* M = q < n ? A : X;
+  const int c = q < n ? q : q - n;
+  const int pv = *piv;
+  const z128 pi = *pinv;
+  const z128 a = M[(size_t)col * n + c], b = M[(size_t)pv * n + c];
+  M[(size_t)pv * n + c] = a;
+  M[(size_t)col * n + c] = mkc<double>(b.re * pi.re - b.im * pi.im, b.re * pi.im + b.im * pi.re);
+}
+
+__global__ void k_gj_eliminate(z128* __restrict__ A, z128* __restrict__ X, int n, int col,
+                               const z128* __restrict__ fcol) {
+  const int r = blockIdx.y;
+  const z128 f = fcol[r];
+  if (f.re == 0.0 && f.im == 0.0) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 2 * n || q < col) return;  // columns of A left of col are finished
+  z128* M = q < n ? A : X;
+  const int c = q < n ? q : q - n;
+  const z128 p = M[(size_t)col * n + c];
+  if (p.re == 0.0 && p.im == 0.0) return;
+  z128 v = M[(size_t)r * n + c];
+  v.re = fma(-f.re, p.re, v.re);
+  v.re = fma(f.im, p.im, v.re);
+  v.im = fma(-f.re, p.im, v.im);
+  v.im = fma(-f.im, p.re, v.im);
+  M[(size_t)r * n + c] = v;
 }
 
 // Exact coarsest-grid solve as a dense FP64 product with the precomputed inverse:
@@ -959,6 +1274,36 @@ template void launch_smooth0_resid32<float>(const Grid&, double, double, double,
 template void launch_smooth0_resid32<double>(const Grid&, double, double, double, const float*, const z128*, z64*,
                                              z64*, cudaStream_t, const int*);
 
+template <typename TB>
+void launch_down32(const Grid& gf, const Grid& gc, double s_re, double s_im, double omega, const float* k2,
+                   const cx<TB>* b, z64* u1, z64* bc, int kchunk, cudaStream_t st, const int* active) {
+  const int kc = kchunk > 0 ? kchunk : 4;
+  const dim3 gr((gc.N1 + DCX - 1) / DCX, (gc.N2 + DCY - 1) / DCY, (gc.N3 + kc - 1) / kc);
+  k_down32<TB><<<gr, DNT, 0, st>>>(gf, gc, coef_for<float>(gf.h, s_re, s_im, omega), k2, b, u1, bc, kc, active);
+}
+template void launch_down32<float>(const Grid&, const Grid&, double, double, double, const float*, const z64*, z64*,
+                                   z64*, int, cudaStream_t, const int*);
+template void launch_down32<double>(const Grid&, const Grid&, double, double, double, const float*, const z128*,
+                                    z64*, z64*, int, cudaStream_t, const int*);
+
+template <typename TB, typename TO>
+void launch_up32(const Grid& gf, const Grid& gc, double s_re, double s_im, double omega, const float* k2,
+                 const z64* u1, const z64* e, const cx<TB>* b, cx<TO>* out, int zchunk, cudaStream_t st,
+                 const int* active) {
+  const int kz = zchunk > 0 ? zchunk : 16;
+  const dim3 gr((gf.N1 + TX - 1) / TX, (gf.N2 + UTY - 1) / UTY, (gf.N3 + kz - 1) / kz);
+  k_up32<TB, TO><<<gr, dim3(TX, UTY), 0, st>>>(gf, gc, coef_for<float>(gf.h, s_re, s_im, omega), k2, u1, e, b, out,
+                                               kz, active);
+}
+template void launch_up32<float, float>(const Grid&, const Grid&, double, double, double, const float*, const z64*,
+                                        const z64*, const z64*, z64*, int, cudaStream_t, const int*);
+template void launch_up32<double, float>(const Grid&, const Grid&, double, double, double, const float*, const z64*,
+                                         const z64*, const z128*, z64*, int, cudaStream_t, const int*);
+template void launch_up32<float, double>(const Grid&, const Grid&, double, double, double, const float*, const z64*,
+                                         const z64*, const z64*, z128*, int, cudaStream_t, const int*);
+template void launch_up32<double, double>(const Grid&, const Grid&, double, double, double, const float*, const z64*,
+                                          const z64*, const z128*, z128*, int, cudaStream_t, const int*);
+
 template <typename R>
 void launch_restrict(const Grid& gf, const Grid& gc, const cx<R>* r, cx<R>* out, cudaStream_t st, const int* active) {
   int zc;
@@ -981,6 +1326,16 @@ void launch_coarse(int nc, const z128* Minv, const cx<TI>* b, cx<TO>* e, cudaStr
     k_coarse<TI, TO><<<(nc + wpb - 1) / wpb, wpb * 32, 0, st>>>(nc, Minv, b, e, active);
   } else {
     k_coarse_b<TI, TO><<<(nc * nb + 255) / 256, 256, 0, st>>>(nc, nb, Minv, b, e, active);
+  }
+}
+
+void launch_gj_invert(z128* A, z128* X, int n, z128* fcol, int* piv, z128* pinv, int* singular, cudaStream_t st) {
+  k_gj_identity<<<1216, 256, 0, st>>>(X, n);
+  const int bx = (2 * n + 255) / 256;
+  for (int col = 0; col < n; ++col) {
+    k_gj_pivot<<<1, GJ_THREADS, 0, st>>>(A, n, col, fcol, piv, pinv, singular);
+    k_gj_swap_scale<<<bx, 256, 0, st>>>(A, X, n, col, piv, pinv);
+    k_gj_eliminate<<<dim3(bx, n), 256, 0, st>>>(A, X, n, col, fcol);
   }
 }
 

@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int), ("orth", C.c_int),
                 ("reorth", C.c_int), ("cycle", C.c_int), ("idr_kappa", C.c_double),
                 ("graphs", C.c_int), ("autotune", C.c_int), ("side", C.c_int),
-                ("fuse_coarse", C.c_int)]
+                ("fuse_coarse", C.c_int), ("gs_sums", C.c_int), ("fuse_down", C.c_int), ("fuse_up", C.c_int)]
 
 
 class KernelStat(C.Structure):
@@ -155,7 +155,7 @@ class Solver:
 
     def __init__(self, n, h, k2, bc=SOMMERFELD, *, beta1=1.0, beta2=-0.5, omega=0.8, coarsest_n=4,
                  krylov="gmres", restart=30, tol=1e-6, max_iter=2000, precision="fp64", orth=None,
-                 reorth=None, cycle="v", idr_s=4, idr_kappa=0.7, shadow=None, graphs=True, autotune=True, side="right", fuse_coarse=False, device=None):
+                 reorth=None, cycle="v", idr_s=4, idr_kappa=0.7, shadow=None, graphs=True, autotune=True, side="right", fuse_coarse=False, gs_sums=True, fuse_down=-1, fuse_up=-1, device=None):
         n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(int(x) for x in n)
         self.n = (n1, n2, n3)
         self.h = float(h)
@@ -175,6 +175,9 @@ class Solver:
         p.autotune = int(bool(autotune))
         p.side = {"right": 0, "left": 1}[side]
         p.fuse_coarse = int(bool(fuse_coarse))
+        p.gs_sums = int(bool(gs_sums))
+        p.fuse_down = int(fuse_down)
+        p.fuse_up = int(fuse_up)
         p.restart, p.tol, p.max_iter = restart, tol, max_iter
         p.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
         if orth is not None:
@@ -259,10 +262,13 @@ class Solver:
         return [(ty[q], ct[q]) for q in range(8)]
 
     def kernel_variants(self, level):
-        """{'tiled': bool, 'fused_down': bool} picked by the autotuner on `level`."""
+        """{'tiled', 'fused_down', 'down_full', 'up_full'} in use on `level`: the shared-memory
+        tiled FP32 stencils, pre-smoothing + residual as one kernel, the whole down-sweep as one,
+        the whole up-sweep as one."""
         f = C.c_int()
         self._check(lib().helm_kernel_variants(self._ctx, level, C.byref(f)))
-        return {"tiled": bool(f.value & 1), "fused_down": bool(f.value & 2)}
+        return {"tiled": bool(f.value & 1), "fused_down": bool(f.value & 2), "down_full": bool(f.value & 4),
+                "up_full": bool(f.value & 8)}
 
     def tune_log(self):
         """Every launch shape the autotuner timed: (level, slot, ty, ctas, ms per launch)."""

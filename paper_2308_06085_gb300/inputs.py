@@ -159,7 +159,7 @@ def random_k2(shape, seed, kmin=5.0, kmax=40.0):
 
 
 # ---------------------------------------------------------------------------------------
-# The five workloads.  `n` may be overridden to scale a workload down for parity tests
+# The workloads.  `n` may be overridden to scale a workload down for parity tests
 # while keeping its structure (model, boundary, source placement, max k*h).
 # ---------------------------------------------------------------------------------------
 def workload(name, n=None):
@@ -185,4 +185,21 @@ def workload(name, n=None):
         return dict(name=name, n=(n, n, n), h=1.0 / n, bc=SOMMERFELD, k2=k2_from_velocity(c, omega),
                     omega=omega, velocity=c, sources=source_grid(n, 2, 4, 0.1),
                     receiver_plane=receiver_plane(n, 0.9), precision="mixed", restart=30)
+    if name == "closed_off":  # Sec. 2.1 at k = 40 (Tables 1-3), Dirichlet u = 1, no point source
+        n = 64 if n is None else n
+        k = 40.0
+        return dict(name=name, n=(n, n, n), h=1.0 / n, bc=DIRICHLET, k2=np.full(unknown_shape(n, DIRICHLET), k * k),
+                    rhs=closed_off_rhs(n, k), coarsest_n=coarsest_by_node_rule(n), precision="fp64")
     raise ValueError(name)
+
+
+def coarsest_by_node_rule(n, nodes=17):
+    """Coarsest-grid interval count (the solver's `coarsest_n`) under the stopping rule of
+    Sec. 4.2: coarsen by two until some direction has at most `nodes` grid points.  n is the
+    interval count, or a tuple of them for a box, where the shortest direction decides:
+    65 -> 17, 129 -> 17, 193 -> 13, 257 -> 17 nodes, and 641 x 641 x 193 -> 41 x 41 x 13 as the
+    paper states for the salt grid (Sec. 5.1.2)."""
+    m = min(n) if isinstance(n, (tuple, list)) else n
+    while m + 1 > nodes and m % 2 == 0:
+        m //= 2
+    return m

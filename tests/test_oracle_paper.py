@@ -70,11 +70,22 @@ def test_table1_bicgstab(closed_off):
 
 @pytest.mark.slow
 def test_table1_gmres_with_the_papers_coarse_solver():
-    """The paper solves the 17^3 coarsest grid by full GMRES to 1e-11 (Sec. 5) where this
-    build solves it exactly; with the paper's coarse solver the count stays at Table 1's."""
+    """The paper solves the 17^3 coarsest grid by full GMRES to 1e-11 (Sec. 5) where the
+    default oracle and the library solve it exactly; with the paper's coarse solver the count stays at Table 1's."""
     n, k = 64, 40.0
     shape = I.unknown_shape(n, oracle.DIRICHLET)
     o = oracle.Solver(n, 1.0 / n, oracle.DIRICHLET, np.full(shape, k * k), coarsest_n=16, coarse_tol=1e-11)
     r = o.gmres(oracle.rhs_closed_off(n, k), restart=400, tol=1e-6, max_iter=400, left=True)
     assert r["status"] == 0
     assert abs(r["iters"] - table1()["GMRES"][0]) <= 2, r["iters"]
+
+
+def test_seventeen_node_rule():
+    """Sec. 4.2's coarsening stop, on the grids the paper names: the closed-off cubes of
+    Tables 1-2 and the salt grid, whose coarsest grid the paper gives as 41 x 41 x 13 nodes
+    (Sec. 5.1.2).  With coarsest_n = m, a direction of n intervals halves while the shortest
+    one stays >= m, so the salt grid's 640-interval sides end at 640 / (192 / m) intervals."""
+    assert [I.coarsest_by_node_rule(n) for n in (64, 128, 192, 256)] == [16, 16, 12, 16]
+    m = I.coarsest_by_node_rule((640, 640, 192))
+    halvings = int(np.log2(192 // m))
+    assert (640 >> halvings) + 1 == 41 and (192 >> halvings) + 1 == 13

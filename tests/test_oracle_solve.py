@@ -50,6 +50,27 @@ def test_closed_off_second_order():
     assert 3.6 < r1 < 4.4 and 3.8 < r2 < 4.2, errs
 
 
+def test_closed_off_discrete_closed_form():
+    """S = sin(pi x1) sin(2 pi x2) sin(4 pi x3) is an eigenvector of the 7-point Dirichlet
+    Laplacian (eigenvalue lam_h = sum over m in (1, 2, 4) of (4 / h^2) sin^2(m pi h / 2)) and
+    the boundary value 1 is annihilated by it, so the closed-off problem's discrete solution is
+    u_h = 1 + a S, a = (21 pi^2 - k^2) / (lam_h - k^2), here indefinite (k^2 = 400 lies above
+    the smallest eigenvalue, about 3 pi^2, and above lam_h, so a < 0).  The preconditioned solve must reach it; a wrong sign or scale of the boundary
+    data, of k^2 or of the right-hand side moves the solution off u_h."""
+    n, k = 32, 20.0
+    h = 1.0 / n
+    b = oracle.rhs_closed_off(n, k)
+    o = oracle.Solver(n, h, D, np.full(I.unknown_shape(n, D), k * k), coarsest_n=4)
+    res = o.gmres(b, restart=100, tol=1e-12, max_iter=1000)
+    assert res["status"] == 0
+    c = np.arange(1, n) * h
+    S = np.sin(4 * np.pi * c)[:, None, None] * np.sin(2 * np.pi * c)[None, :, None] * np.sin(np.pi * c)[None, None, :]
+    lam = sum(4.0 / h ** 2 * np.sin(m * np.pi * h / 2) ** 2 for m in (1, 2, 4))
+    assert k * k > lam > 3 * np.pi ** 2
+    u_h = 1.0 + (21 * np.pi ** 2 - k * k) / (lam - k * k) * S
+    assert np.abs(res["x"] - u_h).max() <= 1e-9
+
+
 def test_reciprocity():
     """A = D^-1 S with S symmetric and D = 1 at interior nodes, so the discrete Green's
     function is reciprocal between interior nodes: G(s -> r) = G(r -> s)."""
