@@ -178,7 +178,8 @@ def workload_config(n, precision="fp64", cycle="v"):
             "n": n, "unknowns": (n + 1) ** 3, "krylov": "GMRES(30)" if precision == "fp64" else "FGMRES(30)",
             "precision": "complex128" if precision == "fp64" else "complex64 cycle / complex128 outer",
             "beta": [1.0, -0.5], "omega": 0.8,
-            "l2": "working set > L2: the Krylov basis alone is 31 x 34 MB = 1.06 GB, so every step streams from HBM"}
+            "l2": f"working set > L2: the Krylov basis alone is 31 x {16 * (n + 1) ** 3 / 1e6:.0f} MB = "
+                  f"{31 * 16 * (n + 1) ** 3 / 1e9:.2f} GB, so every step streams from HBM"}
 
 
 # ------------------------------------------------------------------------------------------

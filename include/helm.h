@@ -212,6 +212,16 @@ HELM_API helm_status helm_launch_shapes(const helm_ctx* ctx, int level, int* ty,
  * the arithmetic of a point. */
 HELM_API helm_status helm_kernel_variants(const helm_ctx* ctx, int level, int* flags);
 
+/* The variant of helm_solve's Gram-Schmidt inner-product kernel (one right-hand side; library
+ * instrumentation): with set = 0,
+ * *variant receives the one in use; with set = 1 it replaces it (the autotuner's choice) for the
+ * context's arithmetic (helm_params.orth).  FP64: 0 = w staged in shared memory, 1 = each warp
+ * reads w itself.  Double-float: 0, 1, 2 = 4, 2, 8 basis vectors per warp pass.  The variants of
+ * one arithmetic share one grid and sum each inner product over the same points in the same
+ * order, so the results are identical; only the speed differs.  HELM_EINVAL outside 0..1 (FP64)
+ * or 0..2 (double-float). */
+HELM_API helm_status helm_dot_variant(helm_ctx* ctx, int set, int* variant);
+
 /* The autotuner's measurements (library instrumentation): *count = number of timed shapes; the
  * first min(cap, count) are written as rec[4 i .. 4 i + 3] = (level, slot, ty, ctas) and ms[i] =
  * the best of three timings of three back-to-back launches, per launch.  rec / ms may be NULL. */

@@ -2020,6 +2020,20 @@ helm_status helm_kernel_variants(const helm_ctx* c, int level, int* flags) {
   return HELM_OK;
 }
 
+helm_status helm_dot_variant(helm_ctx* c, int set, int* variant) {
+  if (!c || !variant) return HELM_EINVAL;
+  const bool df = c->p.orth == HELM_ORTH_DF;
+  int& v = df ? c->mdot_df_variant : c->mdot_variant;
+  if (!set) {
+    *variant = v;
+    return HELM_OK;
+  }
+  if (*variant < 0 || *variant > (df ? 2 : 1)) return fail(c, HELM_EINVAL, "inner-product variant out of range");
+  v = *variant;
+  clear_graphs(c);  // captured steps hold the old kernels
+  return HELM_OK;
+}
+
 helm_status helm_tune_log(const helm_ctx* c, int* rec, float* ms, int cap, int* count) {
   if (!c || !count) return HELM_EINVAL;
   *count = (int)c->tune_log.size();

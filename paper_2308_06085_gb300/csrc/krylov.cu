@@ -137,8 +137,8 @@ __device__ __forceinline__ int share_width(int nslot) {
   return NW;
 }
 
-// TILE points of w per shared-memory tile (16 KB): few barriers per point keep loads in
-// flight.
+// TILE points of w per shared-memory tile (16 KB, and 8 KB more for wi - wr with the summed
+// basis): few barriers per point keep loads in flight.
 // STAGE: w passes through shared memory tile by tile (two barriers per tile); without it each
 // warp reads w itself (the block's warps share it through L1) and runs barrier-free.
 template <typename E, typename ACC, int TILE, int KSV = KS, bool STAGE = true>
@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(NT)
            z128* __restrict__ part, int with_norm, const int* __restrict__ active) {
   if (active && *active == 0) return;
   __shared__ E sw[TILE];
+  __shared__ double swd[ACC::kSums ? TILE : 1];  // wi - wr of the staged points (summed basis)
   __shared__ double sred[NW][2];
   size_t p0, p1;
   block_range(n, p0, p1);
@@ -166,12 +167,16 @@ __global__ void __launch_bounds__(NT)
       for (size_t t0 = p0; t0 < p1; t0 += TILE) {
         const int tn = (int)min((size_t)TILE, p1 - t0);
         __syncthreads();
-        for (int q = threadIdx.x; q < tn; q += NT) sw[q] = ldg(w + t0 + q);
+        for (int q = threadIdx.x; q < tn; q += NT) {
+          const E wv = ldg(w + t0 + q);
+          sw[q] = wv;
+          if (ACC::kSums) swd[q] = w_diff(wv);  // once per point, not once per warp
+        }
         __syncthreads();
 #pragma unroll 2
         for (int q = sub * 32 + lane; q < tn; q += 32 * wps) {
           const E wv = sw[q];
-          const double wd = ACC::kSums ? w_diff(wv) : 0.0;
+          const double wd = ACC::kSums ? swd[q] : 0.0;
 #pragma unroll
           for (int k = 0; k < KSV; ++k) {
             const int sl = sfirst + (sbase + k) * sstep;
@@ -676,6 +681,18 @@ int wave_blocks(K kern) {
   return nb < RED_STRIDE ? nb : RED_STRIDE;
 }
 
+// A wave of the least resident of two kernels at NT threads (capped at RED_STRIDE).
+template <typename K1, typename K2>
+int common_wave(K1 a, K2 b) {
+  int dev = 0, sms = 0, pa = 0, pb = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pa, a, NT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, b, NT, 0);
+  const int per = std::max(1, std::min(pa, pb));
+  return std::min(sms * per, RED_STRIDE);
+}
+
 int stream_blocks(size_t n) {
   size_t b = (n + NT - 1) / NT;
   const size_t cap = 152 * 8;
@@ -684,22 +701,36 @@ int stream_blocks(size_t n) {
 
 }  // namespace
 
+// The variants of one inner-product family share one grid, so the points fall into the same
+// block ranges whichever variant runs and the partial sums (hence the results) are identical: a
+// wave of the family's least-resident variant.
+template <typename ACC>
+int mdot_fp64_grid() {
+  static const int nb = common_wave(k_mdot<z128, ACC, 4 * NT, KS, true>, k_mdot<z128, ACC, 4 * NT, KS, false>);
+  return nb;
+}
 template <typename ACC, bool STAGE>
 int mdot_fp64(const z128* V, const double* Vs, size_t ld, int nv, const z128* w, size_t n, z128* part, int with_norm,
               cudaStream_t st, const int* active) {
-  static const int nb = wave_blocks(k_mdot<z128, ACC, 4 * NT, KS, STAGE>);
+  const int nb = mdot_fp64_grid<ACC>();
   k_mdot<z128, ACC, 4 * NT, KS, STAGE><<<nb, NT, 0, st>>>(V, Vs, ld, nv, w, n, part, with_norm, active);
   return nb;
 }
+// variant 0: w staged in shared memory; 1: each warp reads w itself.  Same sums (same grid, same
+// points per lane in the same order).
+template <typename ACC>
+int mdot_variant(const z128* V, const double* Vs, size_t ld, int nv, const z128* w, size_t n, z128* part,
+                 int with_norm, cudaStream_t st, const int* active, int variant) {
+  return variant == 1 ? mdot_fp64<ACC, false>(V, Vs, ld, nv, w, n, part, with_norm, st, active)
+                      : mdot_fp64<ACC, true>(V, Vs, ld, nv, w, n, part, with_norm, st, active);
+}
 int launch_mdot(const z128* V, size_t ld, int nv, const z128* w, size_t n, z128* part, int with_norm,
                 cudaStream_t st, const int* active, int variant) {
-  return variant == 1 ? mdot_fp64<AccD, false>(V, nullptr, ld, nv, w, n, part, with_norm, st, active)
-                      : mdot_fp64<AccD, true>(V, nullptr, ld, nv, w, n, part, with_norm, st, active);
+  return mdot_variant<AccD>(V, nullptr, ld, nv, w, n, part, with_norm, st, active, variant);
 }
 int launch_mdot_sums(const z128* V, const double* Vs, size_t ld, int nv, const z128* w, size_t n, z128* part,
                      int with_norm, cudaStream_t st, const int* active, int variant) {
-  return variant == 1 ? mdot_fp64<AccD3, false>(V, Vs, ld, nv, w, n, part, with_norm, st, active)
-                      : mdot_fp64<AccD3, true>(V, Vs, ld, nv, w, n, part, with_norm, st, active);
+  return mdot_variant<AccD3>(V, Vs, ld, nv, w, n, part, with_norm, st, active, variant);
 }
 void launch_reduce_dots(const z128* part, int nv, int nb, z128* hpass, z128* hacc, int accumulate, int decide_j,
                         int* pass2, int* log, cudaStream_t st, const int* active) {
@@ -753,10 +784,16 @@ void launch_combine(const KrylovCtl* ctl, const z128* V, size_t ld, const z128* 
                     cudaStream_t st) {
   k_combine<<<stream_blocks(n), NT, 0, st>>>(ctl, V, ld, y, w, n);
 }
+// One grid for the double-float variants (a wave of the 2- and 4-slot kernels; the 8-slot one,
+// with more registers, runs it in more than one wave).
+int mdot_df_grid() {
+  static const int nb = common_wave(k_mdot<zdf, AccF, 4 * NT, 2>, k_mdot<zdf, AccF, 4 * NT, 4>);
+  return nb;
+}
 template <int KSV>
 int mdot_df_ks(const zdf* V, size_t ld, int nv, const zdf* w, size_t n, z128* part, int with_norm, cudaStream_t st,
                const int* active) {
-  static const int nb = wave_blocks(k_mdot<zdf, AccF, 4 * NT, KSV>);
+  const int nb = mdot_df_grid();
   k_mdot<zdf, AccF, 4 * NT, KSV><<<nb, NT, 0, st>>>(V, nullptr, ld, nv, w, n, part, with_norm, active);
   return nb;
 }

@@ -55,9 +55,28 @@ __global__ void __launch_bounds__(TX* TY)
   size_t e = p * nb + r;                  // element index
   cx<R> uc = ld(e);
   cx<R> um = (k0 > 0) ? ld(e - Se) : zero_c<R>();
+  // FP32 (memory-bound): the next trip's z neighbour, k^2 and b are loaded one trip ahead, so
+  // each thread keeps two planes' loads in flight
+  constexpr bool PF = std::is_same<R, float>::value;
+  cx<R> upf = (PF && k0 + 1 < g.N3) ? ld(e + Se) : zero_c<R>();
+  R kpf = PF ? __ldg(k2 + p) : (R)0;
+  cx<R> bpf = (PF && MODE != 0) ? cvt<R>(ldg(b + e)) : zero_c<R>();
   for (int k = k0; k < k1; ++k, p += S, e += Se) {
     const bool hzp = k + 1 < g.N3;
-    cx<R> up = hzp ? ld(e + Se) : zero_c<R>();
+    cx<R> up, bv = zero_c<R>();
+    R kk;
+    if constexpr (PF) {
+      up = upf;
+      kk = kpf;
+      bv = bpf;
+      if (k + 1 < k1) {
+        upf = k + 2 < g.N3 ? ld(e + 2 * Se) : zero_c<R>();
+        kpf = __ldg(k2 + p + S);
+        if (MODE != 0) bpf = cvt<R>(ldg(b + e + Se));
+      }
+    } else {
+      up = hzp ? ld(e + Se) : zero_c<R>();
+    }
     int nf = nfxy;
     cx<R> zm, zp;
     if (k > 0) zm = um;
@@ -70,7 +89,10 @@ __global__ void __launch_bounds__(TX* TY)
     cx<R> xp = hxp ? ld(e + Xe) : (som ? ld(e - Xe) : zero_c<R>());
     cx<R> ym = hym ? ld(e - Ye) : (som ? ld(e + Ye) : zero_c<R>());
     cx<R> yp = hyp ? ld(e + Ye) : (som ? ld(e - Ye) : zero_c<R>());
-    const R kk = __ldg(k2 + p);
+    if constexpr (!PF) {
+      kk = __ldg(k2 + p);
+      if (MODE != 0) bv = cvt<R>(ldg(b + e));
+    }
     const cx<R> d = op_diag(c, kk, nf, nf ? face_k<R>(g, p, kk) : (R)0);
     const bool real_d = c.real_shift && nf == 0;
     if (MODE == 0) {
@@ -80,7 +102,7 @@ __global__ void __launch_bounds__(TX* TY)
       else
         out[e] = cvt<TO>(v);
     } else {
-      const cx<R> res = op_resid(cvt<R>(ldg(b + e)), d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
+      const cx<R> res = op_resid(bv, d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
       if (MODE == 1) {
         out[e] = cvt<TO>(res);
       } else {
@@ -473,16 +495,32 @@ __global__ void __launch_bounds__(TX* TY)
   const size_t S = (size_t)g.N1 * g.N2;
   size_t p = gidx(i, j, k0, g.N1, g.N2);
   size_t e = p * nb + r;
+  // FP32: b and k^2 of the next trip are loaded one trip ahead (two planes of loads in flight)
+  constexpr bool PF = !DINV && std::is_same<R, float>::value;
+  R kpf = PF && k0 < k1 ? __ldg(k2 + p) : (R)0;
+  cx<R> bpf = PF && k0 < k1 ? cvt<R>(ldg(b + e)) : zero_c<R>();
   for (int k = k0; k < k1; ++k, p += S, e += S * nb) {
-    cx<R> w;
+    cx<R> w, bv;
     if (DINV) {
       w = ldg(dinv + p);
+      bv = cvt<R>(ldg(b + e));
     } else {
       const int nf = nfxy + (som ? (k == 0) + (k == g.N3 - 1) : 0);
-      const R kk = __ldg(k2 + p);
+      R kk;
+      if constexpr (PF) {
+        kk = kpf;
+        bv = bpf;
+        if (k + 1 < k1) {
+          kpf = __ldg(k2 + p + S);
+          bpf = cvt<R>(ldg(b + e + S * nb));
+        }
+      } else {
+        kk = __ldg(k2 + p);
+        bv = cvt<R>(ldg(b + e));
+      }
       w = omega_over(op_diag(c, kk, nf, nf ? face_k<R>(g, p, kk) : (R)0), c.omega);
     }
-    out[e] = cmul(w, cvt<R>(ldg(b + e)));
+    out[e] = cmul(w, bv);
   }
 }
 

@@ -85,6 +85,8 @@ def lib():
     L.helm_launch_shapes.restype = i
     L.helm_tune_log.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_float), i, C.POINTER(C.c_int)]
     L.helm_tune_log.restype = i
+    L.helm_dot_variant.argtypes = [vp, i, C.POINTER(C.c_int)]
+    L.helm_dot_variant.restype = i
     L.helm_kernel_variants.argtypes = [vp, i, C.POINTER(C.c_int)]
     L.helm_kernel_variants.restype = i
     L.helm_apply_c64_df.restype = i
@@ -260,6 +262,12 @@ class Solver:
         ty, ct = (C.c_int * 8)(), (C.c_int * 8)()
         self._check(lib().helm_launch_shapes(self._ctx, level, ty, ct))
         return [(ty[q], ct[q]) for q in range(8)]
+
+    def dot_variant(self, variant=None):
+        """The Gram-Schmidt inner-product kernel variant in use; with `variant`, replace it."""
+        v = C.c_int(-1 if variant is None else int(variant))
+        self._check(lib().helm_dot_variant(self._ctx, 0 if variant is None else 1, C.byref(v)))
+        return v.value
 
     def kernel_variants(self, level):
         """{'tiled', 'fused_down', 'down_full', 'up_full'} in use on `level`: the shared-memory

@@ -143,3 +143,38 @@ def test_sweep_forms_are_bit_exact(helm, name, n, bc):
     for o in outs[1:]:
         assert torch.equal(o[0], outs[0][0]) and torch.equal(o[1], outs[0][1])
         assert o[3] == outs[0][3] and torch.equal(o[2], outs[0][2])
+
+
+@pytest.mark.parametrize("orth,sums", [("fp64", True), ("fp64", False), ("df", True)])
+def test_dot_variants_are_bit_exact(helm, orth, sums):
+    """Every Gram-Schmidt inner-product kernel variant the autotuner chooses from (w staged or
+    not, 2, 4 or 8 basis vectors per warp pass) sums each inner product over the same points in
+    the same order: solves agree bit for bit whichever variant runs."""
+    w = I.workload("wedge", 32)
+    s = helm.Solver(w["n"], w["h"], w["k2"], S, krylov="gmres", orth=orth, gs_sums=sums, restart=20)
+    b = s.rhs_point(w["sources"])
+    out = []
+    nvar = 3 if orth == "df" else 2
+    for v in range(nvar):
+        assert s.dot_variant(v) == v
+        x, info = s.solve(b)
+        out.append((x.clone(), info["iterations"]))
+    for x, it in out[1:]:
+        assert it == out[0][1] and torch.equal(x, out[0][0])
+    with pytest.raises(helm.HelmError):
+        s.dot_variant(nvar)
+
+
+def test_autotuned_batched_double_float_is_bit_exact(helm):
+    """The batched double-float inner products: whichever slots-per-pass variant and launch
+    shapes the autotuner picks for a width, the batched solve equals the untuned one bit for bit."""
+    w = I.workload("wedge", 32)
+    kw = dict(krylov="fgmres", precision="mixed", orth="df", restart=12)
+    a = helm.Solver(w["n"], w["h"], w["k2"], S, autotune=False, **kw)
+    t = helm.Solver(w["n"], w["h"], w["k2"], S, autotune=True, **kw)
+    src = [(8 + 4 * i, 8 + 4 * j, 1) for i in range(3) for j in range(3)]
+    B = torch.stack([a.rhs_point([p]) for p in src])
+    Xa, ia = a.solve_batched(B)
+    Xt, it = t.solve_batched(B)
+    assert [q["iterations"] for q in ia] == [q["iterations"] for q in it]
+    assert torch.equal(Xa, Xt)

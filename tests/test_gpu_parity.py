@@ -418,9 +418,12 @@ def test_left_preconditioned_gmres_vs_oracle(helm, bc):
     x, info = s.solve(b)
     ro = o.gmres(b.cpu().numpy(), restart=30, tol=1e-6, left=True)
     assert info["status"] == 0 and ro["status"] == 0
-    # the final residuals are ~1e-6 of the start: rounding-order differences show at the percent level
-    assert info["rel_residual"] <= 1e-6 and abs(info["rel_residual"] - ro["relres"]) <= 0.02 * ro["relres"]
+    assert info["rel_residual"] <= 1e-6 and ro["relres"] <= 1e-6
     assert abs(info["iterations"] - ro["iters"]) <= 1, (info, ro["iters"])
+    # with equal counts both sides stop on the same iterate up to rounding; when the last
+    # estimate sits at the tolerance one side may take one more step (the +-1 above)
+    if info["iterations"] == ro["iters"]:
+        assert abs(info["rel_residual"] - ro["relres"]) <= 0.02 * ro["relres"]
     assert rel(x.cpu().numpy(), ro["x"]) <= 1e-5
     with pytest.raises(helm.HelmError):
         helm.Solver(w["n"], w["h"], w["k2"], bc, krylov="fgmres", side="left")
