@@ -784,10 +784,11 @@ void launch_combine(const KrylovCtl* ctl, const z128* V, size_t ld, const z128* 
                     cudaStream_t st) {
   k_combine<<<stream_blocks(n), NT, 0, st>>>(ctl, V, ld, y, w, n);
 }
-// One grid for the double-float variants (a wave of the 2- and 4-slot kernels; the 8-slot one,
-// with more registers, runs it in more than one wave).
+// One grid for the double-float variants: a wave of the most resident (2-slot) kernel, the one
+// the autotuner measures fastest; the 4- and 8-slot kernels, with more registers, run it in more
+// than one wave.
 int mdot_df_grid() {
-  static const int nb = common_wave(k_mdot<zdf, AccF, 4 * NT, 2>, k_mdot<zdf, AccF, 4 * NT, 4>);
+  static const int nb = wave_blocks(k_mdot<zdf, AccF, 4 * NT, 2>);
   return nb;
 }
 template <int KSV>

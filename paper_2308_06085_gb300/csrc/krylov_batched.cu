@@ -594,11 +594,11 @@ int launch_bmdot(const z128* V, size_t ld, int nv, const z128* w, size_t ne, int
   k_bmdot<z128, BAccD><<<nblk, NT, 0, st>>>(V, ld, nv, w, ne, nb, part, with_norm, active);
   return nblk;
 }
-// The double-float variants share one grid (a wave of the less resident of the 2- and 4-slot
-// kernels; the 8-slot one runs it in more than one wave), so the points fall into the same block
-// ranges whichever variant the autotuner picks and the results are identical.
+// The double-float variants share one grid, a wave of the most resident (2-slot) kernel (the 4-
+// and 8-slot ones run it in more than one wave), so the points fall into the same block ranges
+// whichever variant the autotuner picks and the results are identical.
 int bmdot_df_grid() {
-  static const int nblk = std::min(wave_blocks(k_bmdot<zdf, BAccF, 2>, 0), wave_blocks(k_bmdot<zdf, BAccF, 4>, 0));
+  static const int nblk = wave_blocks(k_bmdot<zdf, BAccF, 2>, 0);
   return nblk;
 }
 template <int KSV>
