@@ -114,8 +114,11 @@ typedef struct {
   int autotune;     /* 1 (default): helm_create times every stencil, smoothing and transfer
                        kernel of every level over launch shapes (rows of x-lines per CTA x CTA
                        count) and keeps the fastest, and helm_solve_batched does the same for
-                       its width on first use; 0: the fixed default shape.  Results do not
-                       depend on the shape (no reductions in these kernels). */
+                       its width on first use, and picks the Gram-Schmidt inner-product
+                       kernel variant and the FP32 kernel forms (see fuse_down, fuse_up); 0:
+                       the fixed default shape and forms.  Results do not depend on any of these
+                       choices (the grid kernels have no reductions; the inner-product variants
+                       share one grid). */
   int side;         /* helm_side: right preconditioning (default; every solver), or the paper's
                        left-preconditioned GMRES (Sec. 3.2) with its stopping rule
                        ||M^{-1}(b - A x)|| / ||M^{-1} b|| <= tol (Sec. 5), for which

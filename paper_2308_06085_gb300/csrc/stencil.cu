@@ -1,11 +1,13 @@
 // stencil.cu -- matrix-free grid kernels of libhelm: the 7-point Helmholtz / CSLP operator
 // (Sec. 2.4, Sec. 3.5 Algorithm 2), damped Jacobi (Sec. 3.4.1), full-weighting restriction
 // (Sec. 3.4.2), trilinear interpolation (Sec. 3.4.3), k^2 injection for the DCG coarse
-// operators (Sec. 3.4.4) and the exact coarsest-grid solve.
+// operators (Sec. 3.4.4), the exact coarsest-grid solve and the set-up inverse behind it.
 //
-// Every grid kernel maps a 32 x 8 tile of (x, y) columns to a 256-thread block and streams
-// along z: the z-1 / z / z+1 values of a thread's own column stay in registers (2.5D
-// streaming), the in-plane neighbours come through the read-only L1 path.
+// The streaming grid kernels map a 32 x rows tile of (x, y) columns to a block and stream along
+// z: the z-1 / z / z+1 values of a thread's own column stay in registers (2.5D streaming), the
+// in-plane neighbours come through the read-only L1 path; in FP32 the next plane's loads are
+// issued one trip ahead.  The fused FP32 sweep kernels (k_down32, k_up32) instead keep
+// three-plane rings of their tile and halo in shared memory.
 #include "internal.cuh"
 
 #include <type_traits>
