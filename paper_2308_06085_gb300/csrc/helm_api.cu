@@ -1051,7 +1051,9 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
             KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd,
                nb = launch_mdot_df(Vdf, n, j + 1, wd, n, c->part, wn, st, a2, c->mdot_df_variant));
           else if (sums)
-            KL(F_MDOT, (24.0 * nv + 16.0) * nd, 6.0 * nv * nd,
+            // algorithmic flops: 8 per basis vector and unknown (a complex multiply-add), of
+            // which the summed form executes 6; bytes: what its layout must move
+            KL(F_MDOT, (24.0 * nv + 16.0) * nd, 8.0 * nv * nd,
                nb = launch_mdot_sums(c->V, c->Vs, n, j + 1, w, n, c->part, wn, st, a2, c->mdot_variant));
           else
             KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd,
@@ -1062,7 +1064,7 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
           if (df)
             KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_gs_update_df(Vdf, n, j + 1, c->hpass, wd, n, st, a2));
           else if (sums)
-            KL(F_GS_UPDATE, (24.0 * nv + 32.0) * nd, 6.0 * nv * nd,
+            KL(F_GS_UPDATE, (24.0 * nv + 32.0) * nd, 8.0 * nv * nd,
                launch_gs_update_sums(c->V, c->Vs, n, j + 1, c->hpass, w, n, st, a2));
           else
             KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_gs_update(c->V, n, j + 1, c->hpass, w, n, st, a2));
