@@ -368,14 +368,19 @@ HELM_API helm_status helm_profile_read(helm_ctx* ctx, helm_kernel_stat* stats, i
  * with that device current; make that first call before capturing a stream into a graph.
  * Every call on a device shares the one array and overwrites all of its live part, so
  * nothing in it needs to start at zero, but calls that overlap on the GPU (other streams,
- * other threads) race on it: order them. */
+ * other threads) race on it: order them.
+ * A CUDA error already pending on the calling thread when the call starts is left in place
+ * (not cleared) and the call returns HELM_ECUDA without launching anything. */
 #define HELM_NOALLOC_MAX_POINTS 262144
 HELM_API helm_status helm_vcycle_down_noalloc(int n1, int n2, int n3, double h, const double* k2, helm_bc bc,
                                               double beta1, double beta2, double omega, const void* b, void* out,
                                               void* stream);
 
-/* Message for the last failing call on ctx (or for the last failing helm_create when
- * ctx is NULL).  The string is owned by the library. */
+/* Message for the last failing call on ctx, or, when ctx is NULL, for the last failing
+ * context-free call (helm_create, helm_vcycle_down_noalloc) made on the calling host thread:
+ * that message is kept per thread, so threads never see or overwrite each other's.  The
+ * string is owned by the library and stays valid until the next failing call of the same
+ * kind (on ctx, or on this thread). */
 HELM_API const char* helm_last_error(const helm_ctx* ctx);
 
 #ifdef __cplusplus

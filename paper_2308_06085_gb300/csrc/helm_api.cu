@@ -25,7 +25,10 @@ constexpr int MAX_COARSE = 4096;  // unknowns of the dense coarsest solve
 constexpr int TYT_TILED = 8;      // rows of the tiled FP32 stencil CTAs (stencil.cu)
 constexpr int FLAG_LAG = 2;       // Arnoldi steps enqueued ahead of the host's flag check
 
-std::string g_create_error;
+// Message of the last failing context-free call (helm_create, helm_vcycle_down_noalloc) on
+// this host thread, read by helm_last_error(NULL).  One slot per thread: concurrent failing
+// calls on different threads never share the string.
+thread_local std::string g_create_error;
 
 struct Level {
   int n1, n2, n3;

@@ -62,6 +62,16 @@ extern "C" helm_status helm_vcycle_down_noalloc(int n1, int n2, int n3, double h
     helm_set_global_error(msg);
     return HELM_EINVAL;
   }
+  // An error left on this thread by earlier, unrelated CUDA work is the caller's: report it
+  // without clearing it, so that the check after the launches below sees only this call's.
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess) {
+    char msg[200];
+    snprintf(msg, sizeof(msg), "helm_vcycle_down_noalloc: a CUDA error was already pending: %s",
+             cudaGetErrorString(pending));
+    helm_set_global_error(msg);
+    return HELM_ECUDA;
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();

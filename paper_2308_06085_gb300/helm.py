@@ -142,7 +142,26 @@ def vcycle_down_noalloc(n, h, k2, b, bc=SOMMERFELD, beta1=1.0, beta2=-0.5, omega
     fine unknowns; b: complex128 CUDA tensor; returns the coarse right-hand side (the output
     tensor is the caller's allocation)."""
     n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(int(x) for x in n)
+    if bc not in (DIRICHLET, SOMMERFELD):
+        raise ValueError(f"unknown boundary condition {bc}")
     d = -1 if bc == DIRICHLET else 1
+    fine = (n3 + d) * (n2 + d) * (n1 + d)
+    # the library reads fine-grid vectors through raw pointers: check type, device, layout and
+    # size here, before anything is launched
+    args = (("k2", k2, torch.float64), ("b", b, torch.complex128))
+    for name, t, dt in args:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if t.dtype != dt:
+            raise TypeError(f"{name} must be {dt}, got {t.dtype}")
+    for name, t, _ in args:
+        if t.numel() != fine:
+            raise ValueError(f"{name} has {t.numel()} elements; the fine grid has {fine} unknowns")
+    for name, t, _ in args:
+        if t.device.type != "cuda" or t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must be on the current CUDA device, got {t.device}")
+    k2 = k2.reshape(-1).contiguous()
+    b = b.reshape(-1).contiguous()
     cshape = (n3 // 2 + d, n2 // 2 + d, n1 // 2 + d)
     out = torch.empty(cshape, dtype=torch.complex128, device=b.device)
     st = lib().helm_vcycle_down_noalloc(n1, n2, n3, float(h), _ptr(k2), bc, beta1, beta2, omega, _ptr(b), _ptr(out),

@@ -92,3 +92,28 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(helm, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         helm.lib()
+
+
+def test_noalloc_binding_rejects_bad_tensors_before_any_launch():
+    """The binding of the allocation-free entry point checks dtype, size and device of k^2 and
+    b on the host, so a wrong tensor never reaches the kernels as a raw pointer."""
+    import torch
+
+    from paper_2308_06085_gb300 import helm
+
+    n, bc = (8, 8, 8), helm.SOMMERFELD
+    fine = 9 ** 3
+    k2 = torch.ones(fine, dtype=torch.float64)
+    b = torch.zeros(fine, dtype=torch.complex128)
+    with pytest.raises(TypeError):  # complex64 b would be read as complex128: twice its bytes
+        helm.vcycle_down_noalloc(n, 0.125, k2, b.to(torch.complex64), bc=bc)
+    with pytest.raises(TypeError):
+        helm.vcycle_down_noalloc(n, 0.125, k2.float(), b, bc=bc)
+    with pytest.raises(ValueError):  # one unknown short
+        helm.vcycle_down_noalloc(n, 0.125, k2[:-1], b, bc=bc)
+    with pytest.raises(ValueError):  # the Dirichlet grid of the same n has 7^3 unknowns
+        helm.vcycle_down_noalloc(n, 0.125, k2, b, bc=helm.DIRICHLET)
+    with pytest.raises(ValueError):  # host tensors are not device pointers
+        helm.vcycle_down_noalloc(n, 0.125, k2, b, bc=bc)
+    with pytest.raises(ValueError):
+        helm.vcycle_down_noalloc(n, 0.125, k2, b, bc=7)
