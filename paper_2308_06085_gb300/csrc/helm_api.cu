@@ -65,12 +65,17 @@ template <> struct LevelBufs<float> {
 // Kernel families for the opt-in profiler (names match the kernel functions).
 enum Fam {
   F_APPLY, F_RESID, F_JACOBI, F_SMOOTH0, F_RESTRICT, F_PROLONG, F_COARSE, F_MDOT, F_REDUCE_DOTS, F_GS_UPDATE,
-  F_NORM, F_REDUCE_NORM, F_SCALE, F_GIVENS, F_SOLUPDATE, F_MISC, F_CCYCLE, F_DOWN, F_UP, F_COUNT
+  F_NORM, F_REDUCE_NORM, F_SCALE, F_GIVENS, F_SOLUPDATE, F_MISC, F_CCYCLE, F_DOWN, F_UP,
+  // the same multigrid kernels on the finest level, where the bytes are (kept apart so that
+  // their roofline can be read off directly)
+  F_SMOOTH0_F, F_RESID_F, F_RESTRICT_F, F_PROLONG_F, F_JACOBI_F, F_DOWN_F, F_UP_F, F_COUNT
 };
 const char* const FAM_NAMES[F_COUNT] = {
     "k_stencil(apply)", "k_stencil(resid)", "k_stencil(jacobi)", "k_smooth0", "k_restrict", "k_prolong_add",
     "k_coarse", "k_mdot", "k_reduce_dots", "k_gs_update", "k_norm2_part", "k_reduce_norm", "k_scale_inv",
-    "k_givens", "k_xupdate/k_combine/k_axpy1/k_trisolve", "other", "k_coarse_cycle", "k_down32", "k_up32"};
+    "k_givens", "k_xupdate/k_combine/k_axpy1/k_trisolve", "other", "k_coarse_cycle", "k_down32", "k_up32",
+    "k_smooth0 (finest)", "k_stencil(resid) (finest)", "k_restrict (finest)", "k_prolong_add (finest)",
+    "k_stencil(jacobi) (finest)", "k_down32 (finest)", "k_up32 (finest)"};
 
 struct TuneRec {
   int level, slot, ty, ctas;
@@ -328,6 +333,23 @@ void prof_flush(helm_ctx* c, int jend) {
     prof_post(c, st, e0_, fam, (double)(bytes), (double)(flops)); \
   } while (0)
 
+// Profiler family of a multigrid kernel on grid g: its finest-level family when g is the
+// finest grid (any batch width).
+int vfam(const helm_ctx* c, const Grid& g, int fam) {
+  const Grid& g0 = c->L[0].g;
+  if (g.N1 != g0.N1 || g.N2 != g0.N2 || g.N3 != g0.N3) return fam;
+  switch (fam) {
+    case F_SMOOTH0: return F_SMOOTH0_F;
+    case F_RESID: return F_RESID_F;
+    case F_RESTRICT: return F_RESTRICT_F;
+    case F_PROLONG: return F_PROLONG_F;
+    case F_JACOBI: return F_JACOBI_F;
+    case F_DOWN: return F_DOWN_F;
+    case F_UP: return F_UP_F;
+    default: return fam;
+  }
+}
+
 // Dense coarsest operator M_L (row-major), entries as in the grid kernels: diagonal
 // 6/h^2 - s k^2 - i (2 k / h) per Sommerfeld face, -1/h^2 per in-grid neighbour, and a
 // neighbour beyond a Sommerfeld face folded onto the opposite node (ghost elimination).
@@ -486,22 +508,22 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
     const double bi = l == 0 ? ib : cb;
     if (down_full(F)) {
       // pre-smoothing, residual and restriction in one kernel (FP32, one right-hand side)
-      if (l == 0) KL(F_DOWN, n * (bi + kb + cb) + ncn * cb, 60 * n, down_full_launch(F, C, sr, si, om, rin, st, active));
-      else KL(F_DOWN, n * (bi + kb + cb) + ncn * cb, 60 * n, down_full_launch(F, C, sr, si, om, F.B, st, active));
+      if (l == 0) KL(vfam(c, F.g, F_DOWN), n * (bi + kb + cb) + ncn * cb, 60 * n, down_full_launch(F, C, sr, si, om, rin, st, active));
+      else KL(vfam(c, F.g, F_DOWN), n * (bi + kb + cb) + ncn * cb, 60 * n, down_full_launch(F, C, sr, si, om, F.B, st, active));
       continue;
     }
     if (down_fused(F)) {
       // u1 and the residual in one kernel (FP32, one right-hand side)
-      if (l == 0) KL(F_SMOOTH0, n * (bi + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, rin, st, active));
-      else KL(F_SMOOTH0, n * (bi + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, F.B, st, active));
+      if (l == 0) KL(vfam(c, F.g, F_SMOOTH0), n * (bi + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, rin, st, active));
+      else KL(vfam(c, F.g, F_SMOOTH0), n * (bi + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, F.B, st, active));
     } else if (l == 0) {
-      KL(F_SMOOTH0, n * (bi + (db ? db : kb) + cb), 6 * n * nbv, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
-      KL(F_RESID, n * (cb + bi + kb + cb), 24 * n * nbv, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
+      KL(vfam(c, F.g, F_SMOOTH0), n * (bi + (db ? db : kb) + cb), 6 * n * nbv, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
+      KL(vfam(c, F.g, F_RESID), n * (cb + bi + kb + cb), 24 * n * nbv, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
     } else {
-      KL(F_SMOOTH0, n * (bi + (db ? db : kb) + cb), 6 * n * nbv, (launch_smooth0<R, R>(F.g, sr, si, om, F.k2, F.dinv, F.B, F.U1, st, active)));
-      KL(F_RESID, n * (cb + bi + kb + cb), 24 * n * nbv, (launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.B, F.T, st, active)));
+      KL(vfam(c, F.g, F_SMOOTH0), n * (bi + (db ? db : kb) + cb), 6 * n * nbv, (launch_smooth0<R, R>(F.g, sr, si, om, F.k2, F.dinv, F.B, F.U1, st, active)));
+      KL(vfam(c, F.g, F_RESID), n * (cb + bi + kb + cb), 24 * n * nbv, (launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.B, F.T, st, active)));
     }
-    KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn * nbv, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
+    KL(vfam(c, F.g, F_RESTRICT), n * cb + ncn * cb, 54 * ncn * nbv, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
   }
   if (lf < L) {
     // the sub-cycle lv[lf].B -> lv[lf].E in one CTA
@@ -520,16 +542,16 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
     if (up_full(F)) {
       // prolongation, correction and post-smoothing in one kernel (FP32, one right-hand side)
       if (l == 0)
-        KL(F_UP, n * (cb + ib + kb + ob) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, rin, zout, st, active));
+        KL(vfam(c, F.g, F_UP), n * (cb + ib + kb + ob) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, rin, zout, st, active));
       else
-        KL(F_UP, n * (3 * cb + kb) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, F.B, F.E, st, active));
+        KL(vfam(c, F.g, F_UP), n * (3 * cb + kb) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, F.B, F.E, st, active));
       continue;
     }
-    KL(F_PROLONG, n * 2 * cb + ncn * cb, 6 * n * nbv, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
+    KL(vfam(c, F.g, F_PROLONG), n * 2 * cb + ncn * cb, 6 * n * nbv, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
     if (l == 0)
-      KL(F_JACOBI, n * (cb + ib + kb + db + ob), 32 * n * nbv, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, rin, zout, st, active)));
+      KL(vfam(c, F.g, F_JACOBI), n * (cb + ib + kb + db + ob), 32 * n * nbv, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, rin, zout, st, active)));
     else
-      KL(F_JACOBI, n * (3 * cb + kb + db), 32 * n * nbv, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.B, F.E, st, active)));
+      KL(vfam(c, F.g, F_JACOBI), n * (3 * cb + kb + db), 32 * n * nbv, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.B, F.E, st, active)));
   }
 }
 
@@ -558,16 +580,16 @@ void vcycle_from(helm_ctx* c, const VLevel<R>* lv, int L, int l, cudaStream_t st
   }
   const VLevel<R>& C = lv[l + 1];
   const double n = (double)F.g.npts() * F.g.nb, ncn = (double)C.g.npts() * C.g.nb;
-  KL(F_JACOBI, n * (3 * cb + kb + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.E, F.B, F.U1, st, active)));
-  KL(F_RESID, n * (3 * cb + kb), 24 * n, (launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.B, F.T, st, active)));
-  KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
+  KL(vfam(c, F.g, F_JACOBI), n * (3 * cb + kb + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.E, F.B, F.U1, st, active)));
+  KL(vfam(c, F.g, F_RESID), n * (3 * cb + kb), 24 * n, (launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.B, F.T, st, active)));
+  KL(vfam(c, F.g, F_RESTRICT), n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
   run_vcycle_levels<R, R, R>(c, lv + l + 1, L - l - 1, C.B, C.E, st, active);
   if (up_full(F)) {
-    KL(F_UP, n * (3 * cb + kb) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, F.B, F.E, st, active));
+    KL(vfam(c, F.g, F_UP), n * (3 * cb + kb) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, F.B, F.E, st, active));
     return;
   }
-  KL(F_PROLONG, n * 2 * cb + ncn * cb, 6 * n, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
-  KL(F_JACOBI, n * (3 * cb + kb + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.B, F.E, st, active)));
+  KL(vfam(c, F.g, F_PROLONG), n * 2 * cb + ncn * cb, 6 * n, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
+  KL(vfam(c, F.g, F_JACOBI), n * (3 * cb + kb + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.B, F.E, st, active)));
 }
 
 // F-cycle (Sec. 3.4.5) from level l down: pre-smoothing from zero, residual, restriction; the
@@ -588,24 +610,24 @@ void fcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, int l, const cx<TI>*
   const VLevel<R>& C = lv[l + 1];
   const double n = (double)F.g.npts() * F.g.nb, ncn = (double)C.g.npts() * C.g.nb, db = F.dinv ? 16.0 : 0.0;
   if (down_full(F)) {
-    KL(F_DOWN, n * (ib + kb + cb) + ncn * cb, 60 * n, down_full_launch(F, C, sr, si, om, rin, st, active));
+    KL(vfam(c, F.g, F_DOWN), n * (ib + kb + cb) + ncn * cb, 60 * n, down_full_launch(F, C, sr, si, om, rin, st, active));
   } else {
     if (down_fused(F)) {
-      KL(F_SMOOTH0, n * (ib + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, rin, st, active));
+      KL(vfam(c, F.g, F_SMOOTH0), n * (ib + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, rin, st, active));
     } else {
-      KL(F_SMOOTH0, n * (ib + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
-      KL(F_RESID, n * (cb + ib + kb + cb), 24 * n, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
+      KL(vfam(c, F.g, F_SMOOTH0), n * (ib + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
+      KL(vfam(c, F.g, F_RESID), n * (cb + ib + kb + cb), 24 * n, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
     }
-    KL(F_RESTRICT, n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
+    KL(vfam(c, F.g, F_RESTRICT), n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
   }
   fcycle_levels<R, R, R>(c, lv, L, l + 1, C.B, C.E, st, active);
   vcycle_from<R>(c, lv, L, l + 1, st, active);
   if (up_full(F)) {
-    KL(F_UP, n * (cb + ib + kb + ob) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, rin, zout, st, active));
+    KL(vfam(c, F.g, F_UP), n * (cb + ib + kb + ob) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, rin, zout, st, active));
     return;
   }
-  KL(F_PROLONG, n * 2 * cb + ncn * cb, 6 * n, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
-  KL(F_JACOBI, n * (cb + ib + kb + db + ob), 32 * n, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, rin, zout, st, active)));
+  KL(vfam(c, F.g, F_PROLONG), n * 2 * cb + ncn * cb, 6 * n, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
+  KL(vfam(c, F.g, F_JACOBI), n * (cb + ib + kb + db + ob), 32 * n, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, rin, zout, st, active)));
 }
 
 template <typename R, typename TI, typename TO>

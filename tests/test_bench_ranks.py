@@ -48,7 +48,7 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     monkeypatch.setenv("RANK", "1")
     called = []
-    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: called.append(1))
+    monkeypatch.setattr(bench, "oracle_samples", lambda *a, **k: called.append(1))
     args = types.SimpleNamespace(n=128, warmup=3, steps=5, gpus=2)
     assert bench.run_reference(args) == 0
     assert not called and capsys.readouterr().out == ""
