@@ -77,6 +77,7 @@ def parse(argv=None):
                          "capture with --profile-from-start off (see profiles/)")
     ap.add_argument("--write-traffic", metavar="CSV", default=None,
                     help="record the DRAM bytes of an ncu --csv capture of --ncu-region into profiles/ncu_traffic.json")
+    ap.add_argument("--traffic-out", default=None, help="where --write-traffic writes (default profiles/ncu_traffic.json)")
     return ap.parse_args(argv)
 
 
@@ -574,7 +575,7 @@ def ncu_region(torch, helm, inputs, kind):
     Krylov basis so that the device holds a few GB:
       gs       : 8 Arnoldi steps of FP64 GMRES with a second Gram-Schmidt pass on every step
                  and plain launches (k_mdot / k_gs_update with 1..8 basis vectors);
-      vcycle64 : one FP64 V-cycle (cslp_vcycle, complex128);
+      vcycle64 : one FP64 V-cycle (cslp_vcycle, complex128), then one product with A;
       vcycle32 : one Arnoldi step of the mixed solve (its complex64 V-cycle; the FP32 kernels are
                  told apart from the FP64 outer ones by their template arguments).
     The library's profiler runs over the same launches; its per-family launch counts and
@@ -585,11 +586,15 @@ def ncu_region(torch, helm, inputs, kind):
                         graphs=False)
         b = s.rhs_point(w["sources"])
         run = lambda: s.solve(b)  # noqa: E731
-    elif kind == "vcycle64":
+    elif kind == "vcycle64":  # one FP64 V-cycle, then one product with A
         s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, restart=2, max_iter=1)
         r = torch.from_numpy(inputs.random_vector(s.shape, 7)).cuda()
         z = torch.empty_like(r)
-        run = lambda: s.vcycle(r, out=z)  # noqa: E731
+        v = torch.empty_like(r)
+
+        def run():
+            s.vcycle(r, out=z)
+            s.apply(z, out=v)
     else:  # one Arnoldi step of the mixed solve: its complex64 V-cycle reads the complex128 v_j
         s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, krylov="fgmres", precision="mixed", restart=2,
                         max_iter=1, graphs=False)
@@ -676,14 +681,14 @@ SOURCES = {"gs": ["paper_2308_06085_gb300/csrc/krylov.cu", "paper_2308_06085_gb3
            "vcycle32": ["paper_2308_06085_gb300/csrc/stencil.cu", "paper_2308_06085_gb300/csrc/common.cuh"]}
 
 
-def write_traffic(csv_path, kind, cmd=""):
+def write_traffic(csv_path, kind, cmd="", out_path=None):
     """Record, per kernel family of the region, the DRAM bytes ncu measured over the captured
     launches against the algorithmic bytes the library counted for them, with hashes of the
     sources as they were when captured (run in the same call as the capture)."""
     region = json.load(open(os.path.join(REGION_OUT, f"ncu_region_{kind}.json")))
     launches = read_ncu_csv(csv_path)
     fams = region["families"]
-    out_path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    out_path = out_path or os.path.join(ROOT, "profiles", "ncu_traffic.json")
     rec = json.load(open(out_path)) if os.path.exists(out_path) else {}
     rec["note"] = ("per kernel family: DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of ncu-captured "
                    "launches over the algorithmic bytes the library's profiler counted for the same launches; an "
@@ -704,12 +709,17 @@ def write_traffic(csv_path, kind, cmd=""):
             use = lst
             if not alg or fams[fam]["launches"] != len(lst):
                 continue
-        else:  # the finest level: first launch of a down-sweep kernel, last of an up-sweep kernel
+        elif fam + " (finest)" in fams:  # finest level: first launch of a down-sweep kernel, last of an up-sweep one
             use = [lst[0] if fam in DOWN_FAMILIES else lst[-1]]
-            f = fams.get(fam + " (finest)")
-            if not f or f["launches"] != 1:
+            f = fams[fam + " (finest)"]
+            if f["launches"] != 1:
                 continue
             name, alg = fam + " (finest)" + suffix, f["bytes"]
+        else:  # a kernel launched once in the region (the product with A)
+            f = fams.get(fam)
+            if not f or f["launches"] != len(lst):
+                continue
+            use, name, alg = lst, fam + suffix, f["bytes"]
         dram = sum(u["dram"] for u in use)
         kernels[name] = {"dram_over_algorithmic": dram / alg, "dram_bytes": dram, "algorithmic_bytes": alg,
                          "launches": len(use), "duration_us": sum(u["ns"] or 0 for u in use) / 1e3,
@@ -937,7 +947,7 @@ def run_adjoint_variant(torch, helm, inputs):
 def main(argv=None):
     args = parse(argv)
     if args.write_traffic:
-        return write_traffic(args.write_traffic, args.ncu_region, " ".join(sys.argv))
+        return write_traffic(args.write_traffic, args.ncu_region, " ".join(sys.argv), args.traffic_out)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -138,17 +138,19 @@ typedef struct {
                        complex multiply-add instead of four (the three-multiplication form of
                        a complex product); 0: the textbook four-FMA form.  The results differ
                        only by rounding. */
-  int fuse_down;    /* down-sweep of the complex64 cycle (one right-hand side), per level:
+  int fuse_down;    /* down-sweep of the multigrid cycle (one right-hand side), per level:
                        -1 (default): the autotuner's choice (separate kernels when autotune is
-                       0); 0: pre-smoothing, residual and restriction as three kernels; 1:
-                       pre-smoothing and residual as one kernel, then the restriction; 2: all
-                       three as one kernel (the residual stays in shared memory).  The
+                       0); 0: pre-smoothing, residual and restriction as three kernels; 1
+                       (complex64 only): pre-smoothing and residual as one kernel, then the
+                       restriction; 2 (complex64 only): all three as one kernel; 3
+                       (complex64 and complex128): the pre-smoothing, then the residual and its
+                       restriction as one kernel (the residual stays in shared memory).  The
                        arithmetic per point is the same in every form (bit-identical results). */
-  int fuse_up;      /* up-sweep of the complex64 cycle (one right-hand side), per level: -1
-                       (default): the autotuner's choice (separate kernels when autotune is 0);
-                       0: prolongation + correction, then post-smoothing, as two kernels; 1: one
-                       kernel (the corrected iterate stays in shared memory).  Bit-identical
-                       results either way. */
+  int fuse_up;      /* up-sweep of the multigrid cycle (one right-hand side; complex64 and
+                       complex128), per level: -1 (default): the autotuner's choice (separate
+                       kernels when autotune is 0); 0: prolongation + correction, then
+                       post-smoothing, as two kernels; 1: one kernel (the corrected iterate
+                       stays in shared memory).  Bit-identical results either way. */
 } helm_params;
 
 /* Per-solve report (host struct). */
@@ -210,9 +212,9 @@ HELM_API helm_status helm_launch_shapes(const helm_ctx* ctx, int level, int* ty,
 /* Kernel variants in use on `level` (library instrumentation; the autotuner's picks, or
  * helm_params.fuse_down): *flags bit 0 = FP32 7-point kernels with shared-memory tiles, bit 1 =
  * FP32 pre-smoothing and residual fused into one kernel, bit 2 = the whole FP32 down-sweep
- * (pre-smoothing, residual, restriction) as one kernel, bit 3 = the whole FP32 up-sweep
- * (prolongation, correction, post-smoothing) as one kernel.  All change the schedule only, not
- * the arithmetic of a point. */
+ * (pre-smoothing, residual, restriction) as one kernel, bit 3 = the whole up-sweep
+ * (prolongation, correction, post-smoothing) as one kernel, bit 4 = the residual and its
+ * restriction as one kernel.  All change the schedule only, not the arithmetic of a point. */
 HELM_API helm_status helm_kernel_variants(const helm_ctx* ctx, int level, int* flags);
 
 /* The variant of helm_solve's Gram-Schmidt inner-product kernel (one right-hand side; library

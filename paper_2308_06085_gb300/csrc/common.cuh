@@ -172,9 +172,13 @@ struct Grid {
   // FP32, one right-hand side: the whole down-sweep (pre-smoothing, residual, restriction) as
   // one kernel (k_down32) with down_kc coarse planes per CTA; set by the autotuner when faster
   int down_full = 0, down_kc = 0;
-  // FP32, one right-hand side: prolongation, correction and post-smoothing as one kernel
-  // (k_up32) with up_kz fine planes per CTA; set by the autotuner when faster
+  // one right-hand side (FP32 or FP64): prolongation, correction and post-smoothing as one
+  // kernel (k_up) with up_kz fine planes per CTA; set by the autotuner when faster
   int up_full = 0, up_kz = 0;
+  // one right-hand side (FP32 or FP64): the residual and its restriction as one kernel (k_rr)
+  // with rr_kc coarse planes per CTA, after the pre-smoothing kernel; set by the autotuner when
+  // faster
+  int rr_full = 0, rr_kc = 0;
   __host__ __device__ size_t npts() const { return (size_t)N1 * N2 * N3; }
 };
 

@@ -37,7 +37,7 @@ struct Level {
   float* k2f = nullptr;    // FP32 copy
   double* sk = nullptr;    // sqrt(k^2), FP64 (face terms)
   float* skf = nullptr;    // sqrt(k^2), FP32
-  z128* dinv = nullptr;    // omega / diag(M), FP64 path
+  z128* dinv = nullptr;    // FP64 path: omega / diag(M) at [0, npts), diag(M) at [npts, 2 npts)
   // V-cycle work vectors: B = right-hand side (levels >= 1), U1 = pre-smoothed iterate,
   // T = residual / corrected iterate, E = result (levels >= 1)
   z128 *B64 = nullptr, *U164 = nullptr, *T64 = nullptr, *E64 = nullptr;
@@ -65,17 +65,17 @@ template <> struct LevelBufs<float> {
 // Kernel families for the opt-in profiler (names match the kernel functions).
 enum Fam {
   F_APPLY, F_RESID, F_JACOBI, F_SMOOTH0, F_RESTRICT, F_PROLONG, F_COARSE, F_MDOT, F_REDUCE_DOTS, F_GS_UPDATE,
-  F_NORM, F_REDUCE_NORM, F_SCALE, F_GIVENS, F_SOLUPDATE, F_MISC, F_CCYCLE, F_DOWN, F_UP,
+  F_NORM, F_REDUCE_NORM, F_SCALE, F_GIVENS, F_SOLUPDATE, F_MISC, F_CCYCLE, F_DOWN, F_UP, F_RR,
   // the same multigrid kernels on the finest level, where the bytes are (kept apart so that
   // their roofline can be read off directly)
-  F_SMOOTH0_F, F_RESID_F, F_RESTRICT_F, F_PROLONG_F, F_JACOBI_F, F_DOWN_F, F_UP_F, F_COUNT
+  F_SMOOTH0_F, F_RESID_F, F_RESTRICT_F, F_PROLONG_F, F_JACOBI_F, F_DOWN_F, F_UP_F, F_RR_F, F_COUNT
 };
 const char* const FAM_NAMES[F_COUNT] = {
     "k_stencil(apply)", "k_stencil(resid)", "k_stencil(jacobi)", "k_smooth0", "k_restrict", "k_prolong_add",
     "k_coarse", "k_mdot", "k_reduce_dots", "k_gs_update", "k_norm2_part", "k_reduce_norm", "k_scale_inv",
-    "k_givens", "k_xupdate/k_combine/k_axpy1/k_trisolve", "other", "k_coarse_cycle", "k_down32", "k_up32",
+    "k_givens", "k_xupdate/k_combine/k_axpy1/k_trisolve", "other", "k_coarse_cycle", "k_down32", "k_up", "k_rr",
     "k_smooth0 (finest)", "k_stencil(resid) (finest)", "k_restrict (finest)", "k_prolong_add (finest)",
-    "k_stencil(jacobi) (finest)", "k_down32 (finest)", "k_up32 (finest)"};
+    "k_stencil(jacobi) (finest)", "k_down32 (finest)", "k_up (finest)", "k_rr (finest)"};
 
 struct TuneRec {
   int level, slot, ty, ctas;
@@ -346,6 +346,7 @@ int vfam(const helm_ctx* c, const Grid& g, int fam) {
     case F_JACOBI: return F_JACOBI_F;
     case F_DOWN: return F_DOWN_F;
     case F_UP: return F_UP_F;
+    case F_RR: return F_RR_F;
     default: return fam;
   }
 }
@@ -414,16 +415,28 @@ bool down_full(const VLevel<R>& F) {
   return std::is_same<R, float>::value && F.g.nb == 1 && F.g.down_full;
 }
 // Whether level F runs its whole up-sweep (prolongation, correction, post-smoothing) as one
-// kernel, and that launch.
+// kernel, and that launch (FP32, or FP64 with complex128 input and output).
 template <typename R>
 bool up_full(const VLevel<R>& F) {
-  return std::is_same<R, float>::value && F.g.nb == 1 && F.g.up_full;
+  return F.g.nb == 1 && F.g.up_full;
 }
 template <typename R, typename TB, typename TO>
 void up_full_launch(const VLevel<R>& F, const VLevel<R>& C, double sr, double si, double om, const cx<TB>* b,
                     cx<TO>* out, cudaStream_t st, const int* active) {
-  if constexpr (std::is_same<R, float>::value)
-    launch_up32<TB, TO>(F.g, C.g, sr, si, om, F.k2, F.U1, C.E, b, out, F.g.up_kz, st, active);
+  if constexpr (std::is_same<R, float>::value || (std::is_same<TB, double>::value && std::is_same<TO, double>::value))
+    launch_up<R, TB, TO>(F.g, C.g, sr, si, om, F.k2, F.dinv, F.U1, C.E, b, out, F.g.up_kz, st, active);
+}
+// Whether level F runs its residual and restriction (into C.B) as one kernel after the
+// pre-smoothing, and that launch.
+template <typename R>
+bool rr_full(const VLevel<R>& F) {
+  return F.g.nb == 1 && F.g.rr_full;
+}
+template <typename R, typename TB>
+void rr_launch(const VLevel<R>& F, const VLevel<R>& C, double sr, double si, const cx<TB>* b, cudaStream_t st,
+               const int* active) {
+  if constexpr (std::is_same<R, float>::value || std::is_same<TB, double>::value)
+    launch_rr<R, TB>(F.g, C.g, sr, si, F.k2, F.dinv, F.U1, b, C.B, F.g.rr_kc, st, active);
 }
 template <typename R, typename TB>
 void down_full_launch(const VLevel<R>& F, const VLevel<R>& C, double sr, double si, double om, const cx<TB>* b,
@@ -489,6 +502,7 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
   const double cb = 2.0 * sizeof(R) * nbv;  // bytes of one node's complex values
   const double kb = sizeof(R), ib = 2.0 * sizeof(TI) * nbv, ob = 2.0 * sizeof(TO) * nbv;
   const double db = lv[0].dinv ? 16.0 : 0.0;  // omega/d array (FP64 path)
+  const double kd = db ? 16.0 : kb;            // the diagonal: FP64 table of d, or k^2
   const double nc = c->nc;
   if (L == 1) {
     KL(F_COARSE, nc * nc * 16 + nc * (ib + ob), 8 * nc * nc * nbv,
@@ -512,18 +526,22 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
       else KL(vfam(c, F.g, F_DOWN), n * (bi + kb + cb) + ncn * cb, 60 * n, down_full_launch(F, C, sr, si, om, F.B, st, active));
       continue;
     }
-    if (down_fused(F)) {
+    // the residual and its restriction as one kernel after the pre-smoothing (one right-hand side)
+    const bool rr = rr_full(F);
+    if (down_fused(F) && !rr) {
       // u1 and the residual in one kernel (FP32, one right-hand side)
       if (l == 0) KL(vfam(c, F.g, F_SMOOTH0), n * (bi + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, rin, st, active));
       else KL(vfam(c, F.g, F_SMOOTH0), n * (bi + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, F.B, st, active));
     } else if (l == 0) {
       KL(vfam(c, F.g, F_SMOOTH0), n * (bi + (db ? db : kb) + cb), 6 * n * nbv, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
-      KL(vfam(c, F.g, F_RESID), n * (cb + bi + kb + cb), 24 * n * nbv, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
+      if (rr) KL(vfam(c, F.g, F_RR), n * (cb + bi + kd) + ncn * cb, 24 * n + 54 * ncn, rr_launch(F, C, sr, si, rin, st, active));
+      else KL(vfam(c, F.g, F_RESID), n * (cb + bi + kd + cb), 24 * n * nbv, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active, F.dinv)));
     } else {
       KL(vfam(c, F.g, F_SMOOTH0), n * (bi + (db ? db : kb) + cb), 6 * n * nbv, (launch_smooth0<R, R>(F.g, sr, si, om, F.k2, F.dinv, F.B, F.U1, st, active)));
-      KL(vfam(c, F.g, F_RESID), n * (cb + bi + kb + cb), 24 * n * nbv, (launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.B, F.T, st, active)));
+      if (rr) KL(vfam(c, F.g, F_RR), n * (cb + bi + kd) + ncn * cb, 24 * n + 54 * ncn, rr_launch(F, C, sr, si, F.B, st, active));
+      else KL(vfam(c, F.g, F_RESID), n * (cb + bi + kd + cb), 24 * n * nbv, (launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.B, F.T, st, active, F.dinv)));
     }
-    KL(vfam(c, F.g, F_RESTRICT), n * cb + ncn * cb, 54 * ncn * nbv, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
+    if (!rr) KL(vfam(c, F.g, F_RESTRICT), n * cb + ncn * cb, 54 * ncn * nbv, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
   }
   if (lf < L) {
     // the sub-cycle lv[lf].B -> lv[lf].E in one CTA
@@ -540,18 +558,18 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
     const VLevel<R>& C = lv[l + 1];
     const double n = (double)F.g.npts(), ncn = (double)C.g.npts();
     if (up_full(F)) {
-      // prolongation, correction and post-smoothing in one kernel (FP32, one right-hand side)
+      // prolongation, correction and post-smoothing in one kernel (one right-hand side)
       if (l == 0)
-        KL(vfam(c, F.g, F_UP), n * (cb + ib + kb + ob) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, rin, zout, st, active));
+        KL(vfam(c, F.g, F_UP), n * (cb + ib + (db ? kd + db : kb) + ob) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, rin, zout, st, active));
       else
-        KL(vfam(c, F.g, F_UP), n * (3 * cb + kb) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, F.B, F.E, st, active));
+        KL(vfam(c, F.g, F_UP), n * (3 * cb + (db ? kd + db : kb)) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, F.B, F.E, st, active));
       continue;
     }
     KL(vfam(c, F.g, F_PROLONG), n * 2 * cb + ncn * cb, 6 * n * nbv, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
     if (l == 0)
-      KL(vfam(c, F.g, F_JACOBI), n * (cb + ib + kb + db + ob), 32 * n * nbv, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, rin, zout, st, active)));
+      KL(vfam(c, F.g, F_JACOBI), n * (cb + ib + kd + db + ob), 32 * n * nbv, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, rin, zout, st, active)));
     else
-      KL(vfam(c, F.g, F_JACOBI), n * (3 * cb + kb + db), 32 * n * nbv, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.B, F.E, st, active)));
+      KL(vfam(c, F.g, F_JACOBI), n * (3 * cb + kd + db), 32 * n * nbv, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.B, F.E, st, active)));
   }
 }
 
@@ -573,23 +591,27 @@ template <typename R>
 void vcycle_from(helm_ctx* c, const VLevel<R>* lv, int L, int l, cudaStream_t st, const int* active) {
   const double sr = c->s_re, si = c->s_im, om = c->p.omega;
   const VLevel<R>& F = lv[l];
-  const double nc = c->nc, cb = 2.0 * sizeof(R), kb = sizeof(R), db = F.dinv ? 16.0 : 0.0;
+  const double nc = c->nc, cb = 2.0 * sizeof(R), kb = sizeof(R), db = F.dinv ? 16.0 : 0.0, kd = db ? 16.0 : kb;
   if (l == L - 1) {
     KL(F_COARSE, nc * nc * 16 + nc * 2 * cb, 8 * nc * nc, (launch_coarse<R, R>(c->nc, c->Minv, F.B, F.E, st, active, F.g.nb)));
     return;
   }
   const VLevel<R>& C = lv[l + 1];
   const double n = (double)F.g.npts() * F.g.nb, ncn = (double)C.g.npts() * C.g.nb;
-  KL(vfam(c, F.g, F_JACOBI), n * (3 * cb + kb + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.E, F.B, F.U1, st, active)));
-  KL(vfam(c, F.g, F_RESID), n * (3 * cb + kb), 24 * n, (launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.B, F.T, st, active)));
-  KL(vfam(c, F.g, F_RESTRICT), n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
+  KL(vfam(c, F.g, F_JACOBI), n * (3 * cb + kd + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.E, F.B, F.U1, st, active)));
+  if (rr_full(F)) {
+    KL(vfam(c, F.g, F_RR), n * (2 * cb + kd) + ncn * cb, 24 * n + 54 * ncn, rr_launch(F, C, sr, si, F.B, st, active));
+  } else {
+    KL(vfam(c, F.g, F_RESID), n * (3 * cb + kd), 24 * n, (launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.B, F.T, st, active, F.dinv)));
+    KL(vfam(c, F.g, F_RESTRICT), n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
+  }
   run_vcycle_levels<R, R, R>(c, lv + l + 1, L - l - 1, C.B, C.E, st, active);
   if (up_full(F)) {
-    KL(vfam(c, F.g, F_UP), n * (3 * cb + kb) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, F.B, F.E, st, active));
+    KL(vfam(c, F.g, F_UP), n * (3 * cb + (db ? kd + db : kb)) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, F.B, F.E, st, active));
     return;
   }
   KL(vfam(c, F.g, F_PROLONG), n * 2 * cb + ncn * cb, 6 * n, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
-  KL(vfam(c, F.g, F_JACOBI), n * (3 * cb + kb + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.B, F.E, st, active)));
+  KL(vfam(c, F.g, F_JACOBI), n * (3 * cb + kd + db), 32 * n, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.B, F.E, st, active)));
 }
 
 // F-cycle (Sec. 3.4.5) from level l down: pre-smoothing from zero, residual, restriction; the
@@ -609,25 +631,29 @@ void fcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, int l, const cx<TI>*
   const VLevel<R>& F = lv[l];
   const VLevel<R>& C = lv[l + 1];
   const double n = (double)F.g.npts() * F.g.nb, ncn = (double)C.g.npts() * C.g.nb, db = F.dinv ? 16.0 : 0.0;
+  const double kd = db ? 16.0 : kb;
   if (down_full(F)) {
     KL(vfam(c, F.g, F_DOWN), n * (ib + kb + cb) + ncn * cb, 60 * n, down_full_launch(F, C, sr, si, om, rin, st, active));
+  } else if (rr_full(F)) {
+    KL(vfam(c, F.g, F_SMOOTH0), n * (ib + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
+    KL(vfam(c, F.g, F_RR), n * (cb + ib + kd) + ncn * cb, 24 * n + 54 * ncn, rr_launch(F, C, sr, si, rin, st, active));
   } else {
     if (down_fused(F)) {
       KL(vfam(c, F.g, F_SMOOTH0), n * (ib + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, rin, st, active));
     } else {
       KL(vfam(c, F.g, F_SMOOTH0), n * (ib + (db ? db : kb) + cb), 6 * n, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
-      KL(vfam(c, F.g, F_RESID), n * (cb + ib + kb + cb), 24 * n, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active)));
+      KL(vfam(c, F.g, F_RESID), n * (cb + ib + kd + cb), 24 * n, (launch_resid<R, R, TI, R>(F.g, sr, si, F.k2, F.U1, rin, F.T, st, active, F.dinv)));
     }
     KL(vfam(c, F.g, F_RESTRICT), n * cb + ncn * cb, 54 * ncn, (launch_restrict<R>(F.g, C.g, F.T, C.B, st, active)));
   }
   fcycle_levels<R, R, R>(c, lv, L, l + 1, C.B, C.E, st, active);
   vcycle_from<R>(c, lv, L, l + 1, st, active);
   if (up_full(F)) {
-    KL(vfam(c, F.g, F_UP), n * (cb + ib + kb + ob) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, rin, zout, st, active));
+    KL(vfam(c, F.g, F_UP), n * (cb + ib + (db ? kd + db : kb) + ob) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, rin, zout, st, active));
     return;
   }
   KL(vfam(c, F.g, F_PROLONG), n * 2 * cb + ncn * cb, 6 * n, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
-  KL(vfam(c, F.g, F_JACOBI), n * (cb + ib + kb + db + ob), 32 * n, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, rin, zout, st, active)));
+  KL(vfam(c, F.g, F_JACOBI), n * (cb + ib + kd + db + ob), 32 * n, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, rin, zout, st, active)));
 }
 
 template <typename R, typename TI, typename TO>
@@ -810,7 +836,7 @@ helm_status tune_vlevels(helm_ctx* c, VLevel<R>* lv, int L, cudaStream_t st) {
         z64* scratch = reinterpret_cast<z64*>(c->zs);
         const float t_plain =
             time_burst(c, st, [&] { launch_smooth0<R, R>(F.g, sr, si, om, F.k2, F.dinv, F.U1, F.T, st, nullptr); }) +
-            time_burst(c, st, [&] { launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.U1, F.T, st, nullptr); });
+            time_burst(c, st, [&] { launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.U1, F.T, st, nullptr, F.dinv); });
         const int ty0 = F.g.tile_ty[slot], ct0 = F.g.tile_ctas[slot];
         float best = 1e30f;
         int bty = 0, bct = 0;
@@ -839,53 +865,91 @@ helm_status tune_vlevels(helm_ctx* c, VLevel<R>* lv, int L, cudaStream_t st) {
     TRY(tune_slot(c, C.g, tile_slot<R>(TILE_RESTRICT), l + 1, st, [&](const Grid& g) {
       launch_restrict<R>(F.g, g, F.T, C.B, st, nullptr);
     }));
-    if constexpr (std::is_same<R, float>::value) {
-      if (F.g.nb == 1) {
-        // the whole down-sweep in one kernel against the chosen kernels (logged as slot 14,
-        // coarse planes per CTA in the shape column)
-        const float t_cur =
-            (F.g.fused_down
-                 ? time_burst(c, st, [&] {
+    if (F.g.nb != 1) continue;
+    // scratch for the forms' outputs: the context's complex128 work vector holds a grid vector
+    // of any level in either precision
+    cx<R>* scratch = reinterpret_cast<cx<R>*>(c->zs);
+    // the residual and its restriction as one kernel against the chosen pair (logged as slot 16,
+    // coarse planes per CTA in the shape column); with it the pre-smoothing runs on its own
+    {
+      const float t_pair =
+          (F.g.fused_down
+               ? time_burst(c, st, [&] {
+                   if constexpr (std::is_same<R, float>::value)
                      launch_smooth0_resid32<float>(F.g, sr, si, om, F.k2, F.U1, reinterpret_cast<z64*>(c->zs), F.T, st,
                                                    nullptr);
-                   })
-                 : time_burst(c, st, [&] { launch_smooth0<R, R>(F.g, sr, si, om, F.k2, F.dinv, F.U1, F.T, st, nullptr); }) +
-                       time_burst(c, st, [&] { launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.U1, F.T, st, nullptr); })) +
-            time_burst(c, st, [&] { launch_restrict<R>(F.g, C.g, F.T, C.B, st, nullptr); });
-        float best = 1e30f;
-        int bkc = 0;
-        for (int kc : {1, 2, 4, 8, 16}) {
-          if (kc > 1 && (kc / 2) >= C.g.N3) break;
-          const float t = time_burst(c, st, [&] {
-            launch_down32<float>(F.g, C.g, sr, si, om, F.k2, F.T, reinterpret_cast<z64*>(c->zs), C.B, kc, st, nullptr);
-          });
-          c->tune_log.push_back(TuneRec{l, 14, kc, 0, t});
-          if (t < best) { best = t; bkc = kc; }
-        }
-        F.g.down_full = best < t_cur ? 1 : 0;
-        F.g.down_kc = bkc;
-        TRY(check_launch(c, "autotune (fused down-sweep)"));
-        // the whole up-sweep in one kernel against prolongation + post-smoothing (logged as
-        // slot 15, fine planes per CTA in the shape column)
-        z64* scratch = reinterpret_cast<z64*>(c->zs);
-        const float t_up =
-            time_burst(c, st, [&] { launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, nullptr); }) +
-            time_burst(c, st, [&] { launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.U1, scratch, st, nullptr); });
-        float bu = 1e30f;
-        int bkz = 0;
-        for (int kz : {4, 8, 16, 32, 64}) {
-          if (kz > 4 && kz / 2 >= F.g.N3) break;
-          const float t = time_burst(c, st, [&] {
-            launch_up32<float, float>(F.g, C.g, sr, si, om, F.k2, F.U1, C.E, F.U1, scratch, kz, st, nullptr);
-          });
-          c->tune_log.push_back(TuneRec{l, 15, kz, 0, t});
-          if (t < bu) { bu = t; bkz = kz; }
-        }
-        F.g.up_full = bu < t_up ? 1 : 0;
-        F.g.up_kz = bkz;
-        TRY(check_launch(c, "autotune (fused up-sweep)"));
+                 })
+               : time_burst(c, st, [&] { launch_smooth0<R, R>(F.g, sr, si, om, F.k2, F.dinv, F.U1, F.T, st, nullptr); }) +
+                     time_burst(c, st, [&] { launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.U1, F.T, st, nullptr, F.dinv); })) +
+          time_burst(c, st, [&] { launch_restrict<R>(F.g, C.g, F.T, C.B, st, nullptr); });
+      const float t_s0 =
+          time_burst(c, st, [&] { launch_smooth0<R, R>(F.g, sr, si, om, F.k2, F.dinv, F.U1, F.T, st, nullptr); });
+      float best = 1e30f;
+      int bkc = 0;
+      for (int kc : {1, 2, 4, 8, 16}) {
+        if (kc > 1 && (kc / 2) >= C.g.N3) break;
+        const float t = time_burst(c, st, [&] {
+          launch_rr<R, R>(F.g, C.g, sr, si, F.k2, F.dinv, F.U1, F.U1, C.B, kc, st, nullptr);
+        });
+        c->tune_log.push_back(TuneRec{l, 16, kc, 0, t});
+        if (t < best) { best = t; bkc = kc; }
       }
+      F.g.rr_full = t_s0 + best < t_pair ? 1 : 0;
+      F.g.rr_kc = bkc;
+      if (F.g.rr_full) F.g.fused_down = 0;
+      TRY(check_launch(c, "autotune (residual with restriction)"));
     }
+    if constexpr (std::is_same<R, float>::value) {
+      // the whole down-sweep in one kernel against the chosen kernels (logged as slot 14,
+      // coarse planes per CTA in the shape column)
+      const float t_cur =
+          (F.g.fused_down
+               ? time_burst(c, st, [&] {
+                   launch_smooth0_resid32<float>(F.g, sr, si, om, F.k2, F.U1, reinterpret_cast<z64*>(c->zs), F.T, st,
+                                                 nullptr);
+                 })
+               : time_burst(c, st, [&] { launch_smooth0<R, R>(F.g, sr, si, om, F.k2, F.dinv, F.U1, F.T, st, nullptr); })) +
+          (F.g.rr_full
+               ? time_burst(c, st, [&] {
+                   launch_rr<R, R>(F.g, C.g, sr, si, F.k2, F.dinv, F.U1, F.U1, C.B, F.g.rr_kc, st, nullptr);
+                 })
+               : (F.g.fused_down ? 0.f
+                                 : time_burst(c, st, [&] {
+                                     launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.U1, F.T, st, nullptr);
+                                   })) +
+                     time_burst(c, st, [&] { launch_restrict<R>(F.g, C.g, F.T, C.B, st, nullptr); }));
+      float best = 1e30f;
+      int bkc = 0;
+      for (int kc : {1, 2, 4, 8, 16}) {
+        if (kc > 1 && (kc / 2) >= C.g.N3) break;
+        const float t = time_burst(c, st, [&] {
+          launch_down32<float>(F.g, C.g, sr, si, om, F.k2, F.T, reinterpret_cast<z64*>(c->zs), C.B, kc, st, nullptr);
+        });
+        c->tune_log.push_back(TuneRec{l, 14, kc, 0, t});
+        if (t < best) { best = t; bkc = kc; }
+      }
+      F.g.down_full = best < t_cur ? 1 : 0;
+      F.g.down_kc = bkc;
+      TRY(check_launch(c, "autotune (fused down-sweep)"));
+    }
+    // the whole up-sweep in one kernel against prolongation + post-smoothing (logged as slot 15,
+    // fine planes per CTA in the shape column)
+    const float t_up =
+        time_burst(c, st, [&] { launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, nullptr); }) +
+        time_burst(c, st, [&] { launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.U1, scratch, st, nullptr); });
+    float bu = 1e30f;
+    int bkz = 0;
+    for (int kz : {4, 8, 16, 32, 64}) {
+      if (kz > 4 && kz / 2 >= F.g.N3) break;
+      const float t = time_burst(c, st, [&] {
+        launch_up<R, R, R>(F.g, C.g, sr, si, om, F.k2, F.dinv, F.U1, C.E, F.U1, scratch, kz, st, nullptr);
+      });
+      c->tune_log.push_back(TuneRec{l, 15, kz, 0, t});
+      if (t < bu) { bu = t; bkz = kz; }
+    }
+    F.g.up_full = bu < t_up ? 1 : 0;
+    F.g.up_kz = bkz;
+    TRY(check_launch(c, "autotune (fused up-sweep)"));
   }
   return HELM_OK;
 }
@@ -1195,10 +1259,17 @@ void stage_impl(helm_ctx* c, int l, int stage, const cx<R>* b, const cx<R>* e, c
     return;
   }
   Level& C = c->L[l + 1];
+  // the kernel forms the context's V-cycle uses on this level (their results are identical)
   launch_smooth0<R, R>(F.g, sr, si, om, B::k2(F), B::dinv(F), b, B::U1(F), st, nullptr);
   if (stage == 0) {
-    launch_resid<R, R, R, R>(F.g, sr, si, B::k2(F), B::U1(F), b, B::T(F), st, nullptr);
-    launch_restrict<R>(F.g, C.g, B::T(F), out, st, nullptr);
+    if (F.g.rr_full) {
+      launch_rr<R, R>(F.g, C.g, sr, si, B::k2(F), B::dinv(F), B::U1(F), b, out, F.g.rr_kc, st, nullptr);
+    } else {
+      launch_resid<R, R, R, R>(F.g, sr, si, B::k2(F), B::U1(F), b, B::T(F), st, nullptr, B::dinv(F));
+      launch_restrict<R>(F.g, C.g, B::T(F), out, st, nullptr);
+    }
+  } else if (F.g.up_full) {
+    launch_up<R, R, R>(F.g, C.g, sr, si, om, B::k2(F), B::dinv(F), B::U1(F), e, b, out, F.g.up_kz, st, nullptr);
   } else {
     launch_prolong_add<R>(F.g, C.g, B::U1(F), e, B::T(F), st, nullptr);
     launch_jacobi<R, R, R>(F.g, sr, si, om, B::k2(F), B::dinv(F), B::T(F), b, out, st, nullptr);
@@ -1815,7 +1886,7 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
     TRY(dalloc(c, &L.skf, np));
     L.g.sqk = L.sk;
     L.g.sqkf = L.skf;
-    TRY(dalloc(c, &L.dinv, np));
+    TRY(dalloc(c, &L.dinv, 2 * np));
     TRY(dalloc(c, &L.U164, np));
     TRY(dalloc(c, &L.T64, np));
     TRY(dalloc(c, &L.U132, np));
@@ -1933,6 +2004,7 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
     for (int l = 0; l + 1 < nl; ++l) {
       c->L[l].g.fused_down = P.fuse_down == 1 ? 1 : 0;
       c->L[l].g.down_full = P.fuse_down == 2 ? 1 : 0;
+      c->L[l].g.rr_full = P.fuse_down == 3 ? 1 : 0;
     }
   if (P.fuse_up >= 0)
     for (int l = 0; l + 1 < nl; ++l) c->L[l].g.up_full = P.fuse_up;
@@ -1970,7 +2042,7 @@ helm_status helm_create(int n1, int n2, int n3, double h, const double* k2, helm
   if (P.reorth != HELM_REORTH_ALWAYS && P.reorth != HELM_REORTH_SELECTIVE)
     return fail(nullptr, HELM_EINVAL, "unknown reorth %d", P.reorth);
   if (P.gs_sums != 0 && P.gs_sums != 1) return fail(nullptr, HELM_EINVAL, "gs_sums must be 0 or 1");
-  if (P.fuse_down < -1 || P.fuse_down > 2) return fail(nullptr, HELM_EINVAL, "fuse_down must lie in -1..2");
+  if (P.fuse_down < -1 || P.fuse_down > 3) return fail(nullptr, HELM_EINVAL, "fuse_down must lie in -1..3");
   if (P.fuse_up < -1 || P.fuse_up > 1) return fail(nullptr, HELM_EINVAL, "fuse_up must lie in -1..1");
   if (P.precision == HELM_PREC_MIXED && P.krylov == HELM_GMRES) P.krylov = HELM_FGMRES;
   helm_ctx* c = new (std::nothrow) helm_ctx();
@@ -2043,7 +2115,8 @@ helm_status helm_launch_shapes(const helm_ctx* c, int level, int* ty, int* ctas)
 helm_status helm_kernel_variants(const helm_ctx* c, int level, int* flags) {
   if (!c || !flags || level < 0 || level >= c->nlev) return HELM_EINVAL;
   const Grid& g = c->L[level].g;
-  *flags = (g.tiled ? 1 : 0) | (g.fused_down ? 2 : 0) | (g.down_full ? 4 : 0) | (g.up_full ? 8 : 0);
+  *flags = (g.tiled ? 1 : 0) | (g.fused_down ? 2 : 0) | (g.down_full ? 4 : 0) | (g.up_full ? 8 : 0) |
+           (g.rr_full ? 16 : 0);
   return HELM_OK;
 }
 

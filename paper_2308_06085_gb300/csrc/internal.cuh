@@ -14,9 +14,11 @@ void launch_apply(const Grid& g, double s_re, double s_im, const R* k2, const cx
 template <typename TU>
 void launch_apply_split(const Grid& g, double s_re, double s_im, const double* k2, const cx<TU>* u, zdf* v,
                         cudaStream_t st, const int* active);
+// out = b - M u; with dtab (an FP64 level's coefficient table: omega/d, then d) the diagonal of
+// M is read from the table instead of computed from k^2 (same values)
 template <typename R, typename TU, typename TB, typename TO>
 void launch_resid(const Grid& g, double s_re, double s_im, const R* k2, const cx<TU>* u, const cx<TB>* b, cx<TO>* out,
-                  cudaStream_t st, const int* active);
+                  cudaStream_t st, const int* active, const cx<R>* dtab = nullptr);
 template <typename R, typename TB, typename TO>
 void launch_jacobi(const Grid& g, double s_re, double s_im, double omega, const R* k2, const cx<R>* dinv,
                    const cx<R>* u, const cx<TB>* b, cx<TO>* out, cudaStream_t st, const int* active);
@@ -35,6 +37,7 @@ void launch_coarse(int nc, const z128* Minv, const cx<TI>* b, cx<TO>* e, cudaStr
 // X = A^{-1} by Gauss-Jordan elimination with partial pivoting (A, n x n row-major, is
 // overwritten); scratch fcol (n), piv, pinv; *singular is set when a pivot column is zero.
 void launch_gj_invert(z128* A, z128* X, int n, z128* fcol, int* piv, z128* pinv, int* singular, cudaStream_t st);
+// FP64 level coefficient table: out[p] = omega / diag(M)_p, out[npts + p] = diag(M)_p
 void launch_dinv(const Grid& g, double s_re, double s_im, double omega, const double* k2, z128* out, cudaStream_t st);
 void launch_inject(const Grid& gf, const Grid& gc, const double* kf, double* kc, cudaStream_t st);
 void launch_to_float(const double* a, float* b, size_t n, cudaStream_t st);
@@ -137,12 +140,18 @@ void launch_coarse_cycle(const CCycle<R>& cc, size_t smem_bytes, const cx<R>* b,
 // FP32 pre-smoothing from zero fused with the residual, one right-hand side (stencil.cu):
 // u1 = (omega/d) b and r = b - M u1, u1 recomputed at the neighbours; same values as
 // launch_smooth0 followed by launch_resid.
-// The FP32 up-sweep of one level in one kernel: out = u2 + (omega/d)(b - M u2) with
-// u2 = u1 + P e (zchunk fine planes per CTA)
-template <typename TB, typename TO>
-void launch_up32(const Grid& gf, const Grid& gc, double s_re, double s_im, double omega, const float* k2,
-                 const z64* u1, const z64* e, const cx<TB>* b, cx<TO>* out, int zchunk, cudaStream_t st,
-                 const int* active);
+// The up-sweep of one level in one kernel (one right-hand side): out = u2 + (omega/d)(b - M u2)
+// with u2 = u1 + P e (zchunk fine planes per CTA); dinv: an FP64 level's coefficient table
+template <typename R, typename TB, typename TO>
+void launch_up(const Grid& gf, const Grid& gc, double s_re, double s_im, double omega, const R* k2, const cx<R>* dinv,
+               const cx<R>* u1, const cx<R>* e, const cx<TB>* b, cx<TO>* out, int zchunk, cudaStream_t st,
+               const int* active);
+// The residual b - M u1 of one level and its full-weighting restriction into bc in one kernel
+// (one right-hand side, kchunk coarse planes per CTA); same values as launch_resid followed by
+// launch_restrict.  dtab: an FP64 level's coefficient table.
+template <typename R, typename TB>
+void launch_rr(const Grid& gf, const Grid& gc, double s_re, double s_im, const R* k2, const cx<R>* dtab,
+               const cx<R>* u1, const cx<TB>* b, cx<R>* bc, int kchunk, cudaStream_t st, const int* active);
 // The FP32 down-sweep of one level in one kernel: u1 = (omega/d) b on the fine grid and the
 // full-weighting restriction of b - M u1 into bc on the coarse grid (kchunk coarse planes per CTA)
 template <typename TB>

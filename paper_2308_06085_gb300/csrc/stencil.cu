@@ -6,7 +6,7 @@
 // The streaming grid kernels map a 32 x rows tile of (x, y) columns to a block and stream along
 // z: the z-1 / z / z+1 values of a thread's own column stay in registers (2.5D streaming), the
 // in-plane neighbours come through the read-only L1 path; in FP32 the next plane's loads are
-// issued one trip ahead.  The fused FP32 sweep kernels (k_down32, k_up32) instead keep
+// issued one trip ahead.  The fused sweep kernels (k_down32, k_up, k_rr) instead keep
 // three-plane rings of their tile and halo in shared memory.
 #include "internal.cuh"
 
@@ -23,13 +23,45 @@ __device__ __forceinline__ cx<T> zero_c() {
   return mkc<T>((T)0, (T)0);
 }
 
+// Full weighting (Sec. 3.4.2) in one fixed order that every restriction kernel shares, so that
+// the separate and the fused forms give identical results: per fine plane dz in {-1, 0, 1}
+// around the fine centre, the in-plane sum p_dz = sum over dy, dx of w_y w_x r (w = 2 at the
+// centre line, 1 beside it; one FMA chain, dy outer, dx inner, fine points outside the grid
+// skipped), then b_H = ((p_-1 + 2 p_0) + p_+1) / 64 with p = 0 for planes outside the grid.
+template <typename R, typename Get>
+__device__ __forceinline__ cx<R> fw_plane(int fi, int fj, int N1, int N2, Get&& get) {
+  R are = 0, aim = 0;
+  for (int dy = -1; dy <= 1; ++dy) {
+    const int y = fj + dy;
+    if (y < 0 || y >= N2) continue;
+    const R wy = dy ? (R)1 : (R)2;
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int x = fi + dx;
+      if (x < 0 || x >= N1) continue;
+      const R w = wy * (dx ? (R)1 : (R)2);
+      const cx<R> v = get(x, y);
+      are = fma(w, v.re, are);
+      aim = fma(w, v.im, aim);
+    }
+  }
+  return mkc<R>(are, aim);
+}
+template <typename R>
+__device__ __forceinline__ cx<R> fw_combine(cx<R> pm, cx<R> p0, cx<R> pp) {
+  R re = fma((R)2, p0.re, pm.re), im = fma((R)2, p0.im, pm.im);
+  re = re + pp.re;
+  im = im + pp.im;
+  return mkc<R>(re * (R)(1.0 / 64.0), im * (R)(1.0 / 64.0));
+}
+
 // One stencil kernel for three uses (MODE):
 //   APPLY  : out = Op u
 //   RESID  : out = b - Op u
 //   JACOBI : out = u + (omega / d) (b - Op u)
-// with Op = -Lap_h - s k^2 (s in OpCoef).  DINV: read omega/d from a precomputed array
-// (FP64 path, where a complex division costs more than the 16-byte read) instead of
-// computing it.  With g.nb right-hand sides per node, a thread owns one (node column, rhs)
+// with Op = -Lap_h - s k^2 (s in OpCoef).  DINV (FP64 multigrid levels): read the diagonal d
+// of M and omega/d from the level's coefficient table (omega/d at [0, npts), d at [npts,
+// 2 npts)) instead of computing them from k^2: on this GPU FP64 instructions, not bytes, bound
+// these kernels, and the table holds the very values op_diag and the division would give.  With g.nb right-hand sides per node, a thread owns one (node column, rhs)
 // pair; for nb = 32 a warp covers the 32 right-hand sides of one node with one 256-byte
 // (complex64) row and reads k^2 once.
 template <typename R, int MODE, bool DINV, typename TU, typename TB, typename TO, bool SPLIT = false>
@@ -92,10 +124,10 @@ __global__ void __launch_bounds__(TX* TY)
     cx<R> ym = hym ? ld(e - Ye) : (som ? ld(e + Ye) : zero_c<R>());
     cx<R> yp = hyp ? ld(e + Ye) : (som ? ld(e - Ye) : zero_c<R>());
     if constexpr (!PF) {
-      kk = __ldg(k2 + p);
+      if (!DINV) kk = __ldg(k2 + p);
       if (MODE != 0) bv = cvt<R>(ldg(b + e));
     }
-    const cx<R> d = op_diag(c, kk, nf, nf ? face_k<R>(g, p, kk) : (R)0);
+    const cx<R> d = DINV ? ldg(dinv + g.npts() + p) : op_diag(c, kk, nf, nf ? face_k<R>(g, p, kk) : (R)0);
     const bool real_d = c.real_shift && nf == 0;
     if (MODE == 0) {
       const cx<R> v = op_apply(d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
@@ -345,26 +377,15 @@ __global__ void __launch_bounds__(DNT)
       const int I = I0 + lx, J = J0 + ly;
       if (I >= gc.N1 || J >= gc.N2) continue;
       const int fi = 2 * I + off, fj = 2 * J + off;
-      float are = 0.f, aim = 0.f;
+      z64 p[3];
       for (int dz = -1; dz <= 1; ++dz) {
         const int z = fk + dz;
+        p[dz + 1] = z0;
         if (z < 0 || z >= N3) continue;
-        const float wz = dz ? 1.f : 2.f;
-        for (int dy = -1; dy <= 1; ++dy) {
-          const int y = fj + dy;
-          if (y < 0 || y >= N2) continue;
-          const float wyz = wz * (dy ? 1.f : 2.f);
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int x = fi + dx;
-            if (x < 0 || x >= N1) continue;
-            const float w = wyz * (dx ? 1.f : 2.f);
-            const z64 v = sr[z % 3][y - ry0][x - rx0];
-            are = fmaf(w, v.re, are);
-            aim = fmaf(w, v.im, aim);
-          }
-        }
+        const z64(*Rz)[DRX] = sr[z % 3];
+        p[dz + 1] = fw_plane<float>(fi, fj, N1, N2, [&](int x, int y) { return Rz[y - ry0][x - rx0]; });
       }
-      bco[gidx(I, J, K, gc.N1, gc.N2)] = mkc<float>(are * (float)(1.0 / 64.0), aim * (float)(1.0 / 64.0));
+      bco[gidx(I, J, K, gc.N1, gc.N2)] = fw_combine(p[0], p[1], p[2]);
     }
   };
   if (zlo > 0) fill_u(zlo - 1);
@@ -380,20 +401,21 @@ __global__ void __launch_bounds__(DNT)
   }
 }
 
-// The whole up-sweep of one FP32 level (one right-hand side) in one kernel: u2 = u1 + P e
+// The whole up-sweep of one level (one right-hand side) in one kernel: u2 = u1 + P e
 // (trilinear interpolation, Sec. 3.4.3) and the post-smoothing u3 = u2 + (omega/d)(b - M u2)
 // (Sec. 3.4.1).  u2 never goes to memory: a CTA of 32 x UTY fine columns computes it over its
 // window with a halo of one into a three-plane ring in shared memory while it streams its
 // z-chunk.  Same arithmetic per point, in the same order, as k_prolong_add and
-// k_stencil(jacobi), so the results are identical.
+// k_stencil(jacobi) (DINV: the FP64 level's table of omega/d and d), so the results are
+// identical.
 constexpr int UTY = 8, UWX = TX + 2, UWY = UTY + 2;
-template <typename TB, typename TO>
+template <typename R, bool DINV, typename TB, typename TO>
 __global__ void __launch_bounds__(TX* UTY)
-    k_up32(Grid gf, Grid gc, OpCoef<float> c, const float* __restrict__ k2, const z64* __restrict__ u1,
-           const z64* __restrict__ e, const cx<TB>* __restrict__ b, cx<TO>* __restrict__ out, int zchunk,
-           const int* __restrict__ active) {
+    k_up(Grid gf, Grid gc, OpCoef<R> c, const R* __restrict__ k2, const cx<R>* __restrict__ dinv,
+         const cx<R>* __restrict__ u1, const cx<R>* __restrict__ e, const cx<TB>* __restrict__ b,
+         cx<TO>* __restrict__ out, int zchunk, const int* __restrict__ active) {
   if (active && *active == 0) return;
-  __shared__ z64 su[3][UWY][UWX];
+  __shared__ cx<R> su[3][UWY][UWX];
   const int N1 = gf.N1, N2 = gf.N2, N3 = gf.N3;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * UTY;
   const int k0 = blockIdx.z * zchunk;
@@ -401,39 +423,40 @@ __global__ void __launch_bounds__(TX* UTY)
   const int k1 = min(k0 + zchunk, N3);
   const int off = gf.bc == 0 ? 1 : 0;
   const bool som = gf.bc == 1;
-  const z64 z0 = mkc<float>(0.f, 0.f);
+  const size_t NP = gf.npts();
+  const cx<R> z0 = zero_c<R>();
   const int tid = threadIdx.y * TX + threadIdx.x;
   auto fill = [&](int z) {
-    z64(*U)[UWX] = su[z % 3];
+    cx<R>(*U)[UWX] = su[z % 3];
     const int fk = z + off;
     const int cz0 = (fk >> 1) - off, cz1 = ((fk + 1) >> 1) - off;
     const int nz = cz0 == cz1 ? 1 : 2;
     for (int t = tid; t < UWX * UWY; t += TX * UTY) {
       const int ly = t / UWX, lx = t - ly * UWX;
       const int x = x0 - 1 + lx, y = y0 - 1 + ly;
-      z64 v = z0;
+      cx<R> v = z0;
       if (x >= 0 && x < N1 && y >= 0 && y < N2) {
         const int fi = x + off, fj = y + off;
         const int cxs[2] = {(fi >> 1) - off, ((fi + 1) >> 1) - off};
         const int cys[2] = {(fj >> 1) - off, ((fj + 1) >> 1) - off};
         const int czs[2] = {cz0, cz1};
         const int nx = cxs[0] == cxs[1] ? 1 : 2, ny = cys[0] == cys[1] ? 1 : 2;
-        float are = 0.f, aim = 0.f;
+        R are = 0, aim = 0;
         for (int cq = 0; cq < nz; ++cq) {
           if (czs[cq] < 0 || czs[cq] >= gc.N3) continue;
           for (int bq = 0; bq < ny; ++bq) {
             if (cys[bq] < 0 || cys[bq] >= gc.N2) continue;
             for (int a = 0; a < nx; ++a) {
               if (cxs[a] < 0 || cxs[a] >= gc.N1) continue;
-              const z64 ev = ldg(e + gidx(cxs[a], cys[bq], czs[cq], gc.N1, gc.N2));
+              const cx<R> ev = ldg(e + gidx(cxs[a], cys[bq], czs[cq], gc.N1, gc.N2));
               are += ev.re;
               aim += ev.im;
             }
           }
         }
-        const float sc = 1.f / (float)(nx * ny * nz);
-        const z64 base = ldg(u1 + gidx(x, y, z, N1, N2));
-        v = mkc<float>(fmaf(are, sc, base.re), fmaf(aim, sc, base.im));
+        const R sc = (R)1 / (R)(nx * ny * nz);
+        const cx<R> base = ldg(u1 + gidx(x, y, z, N1, N2));
+        v = mkc<R>(fma(are, sc, base.re), fma(aim, sc, base.im));
       }
       U[ly][lx] = v;
     }
@@ -450,31 +473,140 @@ __global__ void __launch_bounds__(TX* UTY)
     if (hzp) fill(k + 1);
     __syncthreads();
     if (inside) {
-      const z64(*Um)[UWX] = su[(k + 2) % 3];
-      const z64(*Uc)[UWX] = su[k % 3];
-      const z64(*Up)[UWX] = su[(k + 1) % 3];
+      const cx<R>(*Um)[UWX] = su[(k + 2) % 3];
+      const cx<R>(*Uc)[UWX] = su[k % 3];
+      const cx<R>(*Up)[UWX] = su[(k + 1) % 3];
       int nf = nfxy;
-      const z64 uc = Uc[lj][li];
-      z64 zm, zp;
+      const cx<R> uc = Uc[lj][li];
+      cx<R> zm, zp;
       if (k > 0) zm = Um[lj][li];
       else if (som) { zm = Up[lj][li]; ++nf; }
       else zm = z0;
       if (hzp) zp = Up[lj][li];
       else if (som) { zp = Um[lj][li]; ++nf; }
       else zp = z0;
-      const z64 xm = hxm ? Uc[lj][li - 1] : (som ? Uc[lj][li + 1] : z0);
-      const z64 xp = hxp ? Uc[lj][li + 1] : (som ? Uc[lj][li - 1] : z0);
-      const z64 ym = hym ? Uc[lj - 1][li] : (som ? Uc[lj + 1][li] : z0);
-      const z64 yp = hyp ? Uc[lj + 1][li] : (som ? Uc[lj - 1][li] : z0);
+      const cx<R> xm = hxm ? Uc[lj][li - 1] : (som ? Uc[lj][li + 1] : z0);
+      const cx<R> xp = hxp ? Uc[lj][li + 1] : (som ? Uc[lj][li - 1] : z0);
+      const cx<R> ym = hym ? Uc[lj - 1][li] : (som ? Uc[lj + 1][li] : z0);
+      const cx<R> yp = hyp ? Uc[lj + 1][li] : (som ? Uc[lj - 1][li] : z0);
       const size_t p = gidx(i, j, k, N1, N2);
-      const float kk = __ldg(k2 + p);
-      const z64 d = op_diag(c, kk, nf, nf ? face_k<float>(gf, p, kk) : 0.f);
+      cx<R> d, w;
+      if constexpr (DINV) {
+        d = ldg(dinv + NP + p);
+        w = ldg(dinv + p);
+      } else {
+        const R kk = __ldg(k2 + p);
+        d = op_diag(c, kk, nf, nf ? face_k<R>(gf, p, kk) : (R)0);
+        w = omega_over(d, c.omega);
+      }
       const bool real_d = c.real_shift && nf == 0;
-      const z64 res = op_resid(cvt<float>(ldg(b + p)), d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
-      const z64 w = omega_over(d, c.omega);
+      const cx<R> res = op_resid(cvt<R>(ldg(b + p)), d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
       out[p] = cvt<TO>(cfma(w, res, uc));
     }
     __syncthreads();
+  }
+}
+
+// Residual and restriction of one level in one kernel (one right-hand side): r = b - M u1 on
+// the fine grid and its full-weighting restriction (Sec. 3.4.2) to the next level's right-hand
+// side.  r stays in a three-plane ring in shared memory and never goes to memory.  A CTA of
+// RWX x RWY threads owns RCX x RCY coarse columns and a chunk of coarse planes; each thread
+// computes r on one fine column of the CTA's window (the fine points of those coarse columns
+// with a halo of one) while it streams the fine planes in z, u1 of its own column in registers
+// and the in-plane neighbours through the read-only path, exactly as k_stencil(resid).  After
+// fine plane 2K + off + 1, coarse plane K is restricted by three threads per coarse point, one
+// fine plane each (fw_plane), combined by a shuffle (fw_combine) as k_restrict does, so the
+// results equal those of the two separate kernels.  DINV: the FP64 level's table of d.
+constexpr int RCX = 16, RCY = 8, RWX = 2 * RCX + 1, RWY = 2 * RCY + 1, RNT = RWX * RWY;
+template <typename R, bool DINV, typename TB>
+__global__ void __launch_bounds__(RNT, 2)
+    k_rr(Grid gf, Grid gc, OpCoef<R> c, const R* __restrict__ k2, const cx<R>* __restrict__ dtab,
+         const cx<R>* __restrict__ u1, const cx<TB>* __restrict__ b, cx<R>* __restrict__ bco, int kchunk,
+         const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ cx<R> sr[3][RWY][RWX];
+  const int off = gf.bc == 0 ? 1 : 0;
+  const bool som = gf.bc == 1;
+  const int N1 = gf.N1, N2 = gf.N2, N3 = gf.N3;
+  const int I0 = blockIdx.x * RCX, J0 = blockIdx.y * RCY, K0 = blockIdx.z * kchunk;
+  if (K0 >= gc.N3) return;  // the whole CTA
+  const int K1 = min(K0 + kchunk, gc.N3);
+  const int t = threadIdx.x;
+  const int ly = t / RWX, lx = t - ly * RWX;
+  const int rx0 = 2 * I0 + off - 1, ry0 = 2 * J0 + off - 1;
+  const int x = rx0 + lx, y = ry0 + ly;
+  const bool inside = x >= 0 && x < N1 && y >= 0 && y < N2;
+  const int zlo = max(2 * K0 + off - 1, 0), zhi = min(2 * (K1 - 1) + off + 1, N3 - 1);
+  const size_t S = (size_t)N1 * N2;
+  const size_t NP = gf.npts();
+  const bool hxm = x > 0, hxp = x < N1 - 1, hym = y > 0, hyp = y < N2 - 1;
+  const int nfxy = som ? (!hxm) + (!hxp) + (!hym) + (!hyp) : 0;
+  const cx<R> z0 = zero_c<R>();
+  size_t p = inside ? gidx(x, y, zlo, N1, N2) : 0;
+  cx<R> uc = inside ? ldg(u1 + p) : z0;
+  cx<R> um = (inside && zlo > 0) ? ldg(u1 + p - S) : z0;
+  // restriction duty: coarse point q = t / 4 of the tile, fine plane part - 1 around its centre
+  // (lanes 4q .. 4q + 3 share a warp; the fourth lane only waits)
+  constexpr int RQ = 4 * RCX * RCY;
+  const int q = t >> 2, part = t & 3;
+  const int qI = I0 + (q % RCX), qJ = J0 + (q / RCX);
+  const bool rduty = t < RQ && qI < gc.N1 && qJ < gc.N2;
+  int K = K0;
+  for (int z = zlo; z <= zhi; ++z) {
+    cx<R> v = z0;
+    if (inside) {
+      const bool hzp = z + 1 < N3;
+      const cx<R> up = hzp ? ldg(u1 + p + S) : z0;
+      int nf = nfxy;
+      cx<R> zm, zp;
+      if (z > 0) zm = um;
+      else if (som) { zm = up; ++nf; }
+      else zm = z0;
+      if (hzp) zp = up;
+      else if (som) { zp = um; ++nf; }
+      else zp = z0;
+      const cx<R> xm = hxm ? ldg(u1 + p - 1) : (som ? ldg(u1 + p + 1) : z0);
+      const cx<R> xp = hxp ? ldg(u1 + p + 1) : (som ? ldg(u1 + p - 1) : z0);
+      const cx<R> ym = hym ? ldg(u1 + p - N1) : (som ? ldg(u1 + p + N1) : z0);
+      const cx<R> yp = hyp ? ldg(u1 + p + N1) : (som ? ldg(u1 + p - N1) : z0);
+      cx<R> d;
+      if constexpr (DINV) {
+        d = ldg(dtab + NP + p);
+      } else {
+        const R kk = __ldg(k2 + p);
+        d = op_diag(c, kk, nf, nf ? face_k<R>(gf, p, kk) : (R)0);
+      }
+      const bool real_d = c.real_shift && nf == 0;
+      v = op_resid(cvt<R>(ldg(b + p)), d, real_d, uc, c.ih2, xm, xp, ym, yp, zm, zp);
+      um = uc;
+      uc = up;
+      p += S;
+    }
+    sr[z % 3][ly][lx] = v;
+    __syncthreads();
+    // coarse plane K needs fine planes 2K + off - 1 .. 2K + off + 1 (those inside the grid)
+    bool did = false;
+    while (K < K1 && min(2 * K + off + 1, N3 - 1) == z) {
+      if (t < RQ) {
+        const int zz = 2 * K + off + part - 1;
+        cx<R> pv = z0;
+        if (rduty && part < 3 && zz >= 0 && zz < N3) {
+          const cx<R>(*Rz)[RWX] = sr[zz % 3];
+          pv = fw_plane<R>(2 * qI + off, 2 * qJ + off, N1, N2,
+                           [&](int xx, int yy) { return Rz[yy - ry0][xx - rx0]; });
+        }
+        const int lane0 = (threadIdx.x & 31) & ~3;
+        const cx<R> pm = mkc<R>(__shfl_sync(0xffffffffu, pv.re, lane0), __shfl_sync(0xffffffffu, pv.im, lane0));
+        const cx<R> p0 =
+            mkc<R>(__shfl_sync(0xffffffffu, pv.re, lane0 + 1), __shfl_sync(0xffffffffu, pv.im, lane0 + 1));
+        const cx<R> pp =
+            mkc<R>(__shfl_sync(0xffffffffu, pv.re, lane0 + 2), __shfl_sync(0xffffffffu, pv.im, lane0 + 2));
+        if (rduty && part == 0) bco[gidx(qI, qJ, K, gc.N1, gc.N2)] = fw_combine(pm, p0, pp);
+      }
+      ++K;
+      did = true;
+    }
+    if (did) __syncthreads();  // the next plane overwrites the oldest ring slot
   }
 }
 
@@ -526,7 +658,8 @@ __global__ void __launch_bounds__(TX* TY)
   }
 }
 
-// omega / diag(M) at every node (FP64 path; computed once per level at set-up).
+// The coefficient table of an FP64 level (computed once at set-up): omega / diag(M) at every
+// node in out[0, npts), diag(M) itself in out[npts, 2 npts).
 __global__ void k_dinv(Grid g, OpCoef<double> c, const double* __restrict__ k2, z128* __restrict__ out) {
   const size_t n = g.npts();
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
@@ -535,9 +668,10 @@ __global__ void k_dinv(Grid g, OpCoef<double> c, const double* __restrict__ k2, 
     const int k = (int)(p / ((size_t)g.N1 * g.N2));
     const int nf = g.bc == 1 ? (i == 0) + (i == g.N1 - 1) + (j == 0) + (j == g.N2 - 1) + (k == 0) + (k == g.N3 - 1) : 0;
     const z128 d = op_diag(c, k2[p], nf, sqrt(k2[p]));
-    // omega / d as omega conj(d) / |d|^2 in FP64 (set-up only)
+    // omega / d as omega conj(d) / |d|^2 in FP64 (set-up only), then d itself
     const double m2 = d.re * d.re + d.im * d.im;
     out[p] = mkc<double>(c.omega * d.re / m2, -c.omega * d.im / m2);
+    out[n + p] = d;
   }
 }
 
@@ -560,26 +694,15 @@ __global__ void __launch_bounds__(TX* TY)
   const int fi = 2 * (I + off) - off, fj = 2 * (J + off) - off;
   for (int K = K0; K < K1; ++K) {
     const int fk = 2 * (K + off) - off;
-    R are = 0, aim = 0;
+    cx<R> p[3];
     for (int dz = -1; dz <= 1; ++dz) {
       const int z = fk + dz;
+      p[dz + 1] = zero_c<R>();
       if (z < 0 || z >= gf.N3) continue;
-      const R wz = dz ? (R)1 : (R)2;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int y = fj + dy;
-        if (y < 0 || y >= gf.N2) continue;
-        const R wyz = wz * (dy ? (R)1 : (R)2);
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int x = fi + dx;
-          if (x < 0 || x >= gf.N1) continue;
-          const R w = wyz * (dx ? (R)1 : (R)2);
-          const cx<R> v = ldg(r + gidx(x, y, z, gf.N1, gf.N2) * nb + q);
-          are = fma(w, v.re, are);
-          aim = fma(w, v.im, aim);
-        }
-      }
+      p[dz + 1] = fw_plane<R>(fi, fj, gf.N1, gf.N2,
+                              [&](int x, int y) { return ldg(r + gidx(x, y, z, gf.N1, gf.N2) * nb + q); });
     }
-    out[gidx(I, J, K, gc.N1, gc.N2) * nb + q] = mkc<R>(are * (R)(1.0 / 64.0), aim * (R)(1.0 / 64.0));
+    out[gidx(I, J, K, gc.N1, gc.N2) * nb + q] = fw_combine(p[0], p[1], p[2]);
   }
 }
 
@@ -1053,26 +1176,14 @@ __global__ void __launch_bounds__(CC_THREADS)
       int I, J, K;
       cc_ijk<R>(gc, Q, I, J, K);
       const int fi = 2 * (I + off) - off, fj = 2 * (J + off) - off, fk = 2 * (K + off) - off;
-      R are = 0, aim = 0;
+      cx<R> pz[3];
       for (int dz = -1; dz <= 1; ++dz) {
         const int z = fk + dz;
+        pz[dz + 1] = mkc<R>((R)0, (R)0);
         if (z < 0 || z >= g.N3) continue;
-        const R wz = dz ? (R)1 : (R)2;
-        for (int dy = -1; dy <= 1; ++dy) {
-          const int y = fj + dy;
-          if (y < 0 || y >= g.N2) continue;
-          const R wyz = wz * (dy ? (R)1 : (R)2);
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int x = fi + dx;
-            if (x < 0 || x >= g.N1) continue;
-            const R wgt = wyz * (dx ? (R)1 : (R)2);
-            const cx<R> v = r[(z * g.N2 + y) * g.N1 + x];
-            are = fma(wgt, v.re, are);
-            aim = fma(wgt, v.im, aim);
-          }
-        }
+        pz[dz + 1] = fw_plane<R>(fi, fj, g.N1, g.N2, [&](int x, int y) { return r[(z * g.N2 + y) * g.N1 + x]; });
       }
-      sm[C.off_b + Q] = mkc<R>(are * (R)(1.0 / 64.0), aim * (R)(1.0 / 64.0));
+      sm[C.off_b + Q] = fw_combine(pz[0], pz[1], pz[2]);
     }
     __syncthreads();
   }
@@ -1256,8 +1367,14 @@ template void launch_apply_split<float>(const Grid&, double, double, const doubl
 
 template <typename R, typename TU, typename TB, typename TO>
 void launch_resid(const Grid& g, double s_re, double s_im, const R* k2, const cx<TU>* u, const cx<TB>* b,
-                  cx<TO>* out, cudaStream_t st, const int* active) {
+                  cx<TO>* out, cudaStream_t st, const int* active, const cx<R>* dtab) {
   int zc;
+  if (dtab) {
+    dim3 blk, gr = grid_for<R>(g, TILE_STENCIL, zc, blk);
+    k_stencil<R, 1, true, TU, TB, TO><<<gr, blk, 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, dtab, u, b, out,
+                                                           zc, active);
+    return;
+  }
   if constexpr (std::is_same<R, float>::value) {
     if (g.nb == 1 && g.tiled) {
       const dim3 gr = grid_tiled(g, zc);
@@ -1326,23 +1443,52 @@ template void launch_down32<float>(const Grid&, const Grid&, double, double, dou
 template void launch_down32<double>(const Grid&, const Grid&, double, double, double, const float*, const z128*,
                                     z64*, z64*, int, cudaStream_t, const int*);
 
-template <typename TB, typename TO>
-void launch_up32(const Grid& gf, const Grid& gc, double s_re, double s_im, double omega, const float* k2,
-                 const z64* u1, const z64* e, const cx<TB>* b, cx<TO>* out, int zchunk, cudaStream_t st,
-                 const int* active) {
+template <typename R, typename TB, typename TO>
+void launch_up(const Grid& gf, const Grid& gc, double s_re, double s_im, double omega, const R* k2, const cx<R>* dinv,
+               const cx<R>* u1, const cx<R>* e, const cx<TB>* b, cx<TO>* out, int zchunk, cudaStream_t st,
+               const int* active) {
   const int kz = zchunk > 0 ? zchunk : 16;
   const dim3 gr((gf.N1 + TX - 1) / TX, (gf.N2 + UTY - 1) / UTY, (gf.N3 + kz - 1) / kz);
-  k_up32<TB, TO><<<gr, dim3(TX, UTY), 0, st>>>(gf, gc, coef_for<float>(gf.h, s_re, s_im, omega), k2, u1, e, b, out,
-                                               kz, active);
+  const OpCoef<R> c = coef_for<R>(gf.h, s_re, s_im, omega);
+  if constexpr (std::is_same<R, double>::value) {
+    if (dinv) {  // FP64 levels carry the coefficient table
+      k_up<R, true, TB, TO><<<gr, dim3(TX, UTY), 0, st>>>(gf, gc, c, k2, dinv, u1, e, b, out, kz, active);
+      return;
+    }
+  }
+  k_up<R, false, TB, TO><<<gr, dim3(TX, UTY), 0, st>>>(gf, gc, c, k2, dinv, u1, e, b, out, kz, active);
 }
-template void launch_up32<float, float>(const Grid&, const Grid&, double, double, double, const float*, const z64*,
-                                        const z64*, const z64*, z64*, int, cudaStream_t, const int*);
-template void launch_up32<double, float>(const Grid&, const Grid&, double, double, double, const float*, const z64*,
-                                         const z64*, const z128*, z64*, int, cudaStream_t, const int*);
-template void launch_up32<float, double>(const Grid&, const Grid&, double, double, double, const float*, const z64*,
-                                         const z64*, const z64*, z128*, int, cudaStream_t, const int*);
-template void launch_up32<double, double>(const Grid&, const Grid&, double, double, double, const float*, const z64*,
-                                          const z64*, const z128*, z128*, int, cudaStream_t, const int*);
+#define UP_INST(R, TB, TO)                                                                                        \
+  template void launch_up<R, TB, TO>(const Grid&, const Grid&, double, double, double, const R*, const cx<R>*,   \
+                                     const cx<R>*, const cx<R>*, const cx<TB>*, cx<TO>*, int, cudaStream_t,      \
+                                     const int*);
+UP_INST(float, float, float)
+UP_INST(float, double, float)
+UP_INST(float, float, double)
+UP_INST(float, double, double)
+UP_INST(double, double, double)
+#undef UP_INST
+
+template <typename R, typename TB>
+void launch_rr(const Grid& gf, const Grid& gc, double s_re, double s_im, const R* k2, const cx<R>* dtab,
+               const cx<R>* u1, const cx<TB>* b, cx<R>* bc, int kchunk, cudaStream_t st, const int* active) {
+  const int kc = kchunk > 0 ? kchunk : 4;
+  const dim3 gr((gc.N1 + RCX - 1) / RCX, (gc.N2 + RCY - 1) / RCY, (gc.N3 + kc - 1) / kc);
+  const OpCoef<R> c = coef_for<R>(gf.h, s_re, s_im, 0.0);
+  if constexpr (std::is_same<R, double>::value) {
+    if (dtab) {  // FP64 levels carry the coefficient table
+      k_rr<R, true, TB><<<gr, RNT, 0, st>>>(gf, gc, c, k2, dtab, u1, b, bc, kc, active);
+      return;
+    }
+  }
+  k_rr<R, false, TB><<<gr, RNT, 0, st>>>(gf, gc, c, k2, dtab, u1, b, bc, kc, active);
+}
+template void launch_rr<float, float>(const Grid&, const Grid&, double, double, const float*, const z64*, const z64*,
+                                      const z64*, z64*, int, cudaStream_t, const int*);
+template void launch_rr<float, double>(const Grid&, const Grid&, double, double, const float*, const z64*,
+                                       const z64*, const z128*, z64*, int, cudaStream_t, const int*);
+template void launch_rr<double, double>(const Grid&, const Grid&, double, double, const double*, const z128*,
+                                        const z128*, const z128*, z128*, int, cudaStream_t, const int*);
 
 template <typename R>
 void launch_restrict(const Grid& gf, const Grid& gc, const cx<R>* r, cx<R>* out, cudaStream_t st, const int* active) {
@@ -1433,10 +1579,10 @@ HELM_INST_R(float)
 template void launch_apply<double, double, double>(const Grid&, double, double, const double*, const z128*, z128*, cudaStream_t, const int*);
 template void launch_apply<double, float, double>(const Grid&, double, double, const double*, const z64*, z128*, cudaStream_t, const int*);
 template void launch_apply<float, float, float>(const Grid&, double, double, const float*, const z64*, z64*, cudaStream_t, const int*);
-template void launch_resid<double, double, double, double>(const Grid&, double, double, const double*, const z128*, const z128*, z128*, cudaStream_t, const int*);
-template void launch_resid<double, double, double, float>(const Grid&, double, double, const double*, const z128*, const z128*, z64*, cudaStream_t, const int*);
-template void launch_resid<float, float, float, float>(const Grid&, double, double, const float*, const z64*, const z64*, z64*, cudaStream_t, const int*);
-template void launch_resid<float, float, double, float>(const Grid&, double, double, const float*, const z64*, const z128*, z64*, cudaStream_t, const int*);
+template void launch_resid<double, double, double, double>(const Grid&, double, double, const double*, const z128*, const z128*, z128*, cudaStream_t, const int*, const z128*);
+template void launch_resid<double, double, double, float>(const Grid&, double, double, const double*, const z128*, const z128*, z64*, cudaStream_t, const int*, const z128*);
+template void launch_resid<float, float, float, float>(const Grid&, double, double, const float*, const z64*, const z64*, z64*, cudaStream_t, const int*, const z64*);
+template void launch_resid<float, float, double, float>(const Grid&, double, double, const float*, const z64*, const z128*, z64*, cudaStream_t, const int*, const z64*);
 template void launch_jacobi<double, double, double>(const Grid&, double, double, double, const double*, const z128*, const z128*, const z128*, z128*, cudaStream_t, const int*);
 template void launch_jacobi<float, float, float>(const Grid&, double, double, double, const float*, const z64*, const z64*, const z64*, z64*, cudaStream_t, const int*);
 template void launch_jacobi<float, double, float>(const Grid&, double, double, double, const float*, const z64*, const z64*, const z128*, z64*, cudaStream_t, const int*);

@@ -289,13 +289,13 @@ class Solver:
         return v.value
 
     def kernel_variants(self, level):
-        """{'tiled', 'fused_down', 'down_full', 'up_full'} in use on `level`: the shared-memory
-        tiled FP32 stencils, pre-smoothing + residual as one kernel, the whole down-sweep as one,
-        the whole up-sweep as one."""
+        """{'tiled', 'fused_down', 'down_full', 'up_full', 'rr'} in use on `level`: the
+        shared-memory tiled FP32 stencils, pre-smoothing + residual as one kernel, the whole
+        down-sweep as one, the whole up-sweep as one, residual + restriction as one."""
         f = C.c_int()
         self._check(lib().helm_kernel_variants(self._ctx, level, C.byref(f)))
         return {"tiled": bool(f.value & 1), "fused_down": bool(f.value & 2), "down_full": bool(f.value & 4),
-                "up_full": bool(f.value & 8)}
+                "up_full": bool(f.value & 8), "rr": bool(f.value & 16)}
 
     def tune_log(self):
         """Every launch shape the autotuner timed: (level, slot, ty, ctas, ms per launch)."""

@@ -74,7 +74,7 @@ def test_bad_parameters_rejected(libhelm):
     for field, val, msg in [("nu1", 2, "nu1"), ("restart", 0, "restart"), ("coarsest_n", 1, "coarsest_n"),
                             ("omega", 0.0, "omega"), ("tol", 0.0, "tol"), ("precision", 7, "precision"),
                             ("gs_sums", 2, "gs_sums"), ("side", 3, "side"), ("cycle", 2, "cycle"),
-                            ("fuse_down", 3, "fuse_down"), ("fuse_up", 2, "fuse_up")]:
+                            ("fuse_down", 4, "fuse_down"), ("fuse_up", 2, "fuse_up")]:
         p = helm.Params()
         libhelm.helm_default_params(C.byref(p))
         setattr(p, field, val)

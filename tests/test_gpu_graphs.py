@@ -117,24 +117,55 @@ def test_autotuned_shapes_are_bit_exact(helm, n):
                                        ("wedge64", 64, S)])
 def test_sweep_forms_are_bit_exact(helm, name, n, bc):
     """The complex64 down-sweep as three kernels, as pre-smoothing + residual then restriction,
-    or as one kernel that keeps the residual in shared memory (fuse_down 0 / 1 / 2), and the
-    up-sweep as two kernels or one (fuse_up 0 / 1), also with the autotuner's planes per CTA,
-    compute every point with the same arithmetic: V-cycles, F-cycles and mixed-precision solves
-    agree bit for bit."""
+    as one kernel that keeps the residual in shared memory, or as pre-smoothing then residual +
+    restriction in one kernel (fuse_down 0 / 1 / 2 / 3), and the up-sweep as two kernels or one
+    (fuse_up 0 / 1), also with the autotuner's planes per CTA, compute every point with the same
+    arithmetic: V-cycles, F-cycles and mixed-precision solves agree bit for bit."""
     h = 1.0 / (n if np.isscalar(n) else max(n))
     if name.startswith("wedge"):
         k2 = I.workload("wedge", n)["k2"]
     else:
         k2 = I.random_k2(I.unknown_shape(n, bc), seed=sum(map(ord, name)), kmin=2.0, kmax=0.6 / h)
     outs = []
-    for fuse, up, tune in ((0, 0, False), (1, 0, False), (2, 1, False), (2, 1, True), (0, 1, True)):
+    for fuse, up, tune in ((0, 0, False), (1, 0, False), (2, 1, False), (3, 1, False), (3, 0, False), (2, 1, True),
+                           (0, 1, True)):
         s = helm.Solver(n, h, k2, bc, krylov="fgmres", precision="mixed", coarsest_n=2, fuse_down=fuse, fuse_up=up,
                         autotune=tune)
         for lev in range(s.nlevels - 1):
             v = s.kernel_variants(lev)
             assert v["down_full"] == (fuse == 2) and v["fused_down"] == (fuse == 1), (lev, v)
-            assert v["up_full"] == (up == 1), (lev, v)
+            assert v["rr"] == (fuse == 3) and v["up_full"] == (up == 1), (lev, v)
         r = torch.from_numpy(I.random_vector(s.shape, 21).astype(np.complex64)).cuda()
+        src = [tuple(m // 2 for m in ((n, n, n) if np.isscalar(n) else n))]
+        b = s.rhs_point(src)
+        x, info = s.solve(b)
+        outs.append((s.vcycle(r), s.fcycle(r), x, info["iterations"]))
+        s.close()
+    for o in outs[1:]:
+        assert torch.equal(o[0], outs[0][0]) and torch.equal(o[1], outs[0][1])
+        assert o[3] == outs[0][3] and torch.equal(o[2], outs[0][2])
+
+
+@pytest.mark.parametrize("name,n,bc", [("wedge32", 32, S), ("som_ragged", (40, 20, 12), S), ("dir_ragged", (40, 20, 12), 0),
+                                       ("som_noncubic", (24, 8, 16), S)])
+def test_fp64_sweep_forms_are_bit_exact(helm, name, n, bc):
+    """The FP64 cycle's down-sweep as three kernels or as pre-smoothing then residual +
+    restriction in one kernel (fuse_down 0 / 3), its up-sweep as two kernels or one (fuse_up
+    0 / 1), and the autotuner's choice among them: V-cycles, F-cycles and FP64 solves agree bit
+    for bit (the fused kernels read the same coefficient table and sum in the same order)."""
+    h = 1.0 / (n if np.isscalar(n) else max(n))
+    if name.startswith("wedge"):
+        k2 = I.workload("wedge", n)["k2"]
+    else:
+        k2 = I.random_k2(I.unknown_shape(n, bc), seed=sum(map(ord, name)), kmin=2.0, kmax=0.6 / h)
+    outs = []
+    for fuse, up, tune in ((0, 0, False), (3, 1, False), (3, 0, False), (0, 1, False), (-1, -1, True)):
+        s = helm.Solver(n, h, k2, bc, krylov="gmres", coarsest_n=2, fuse_down=fuse, fuse_up=up, autotune=tune)
+        if not tune:
+            for lev in range(s.nlevels - 1):
+                v = s.kernel_variants(lev)
+                assert v["rr"] == (fuse == 3) and v["up_full"] == (up == 1), (lev, v)
+        r = torch.from_numpy(I.random_vector(s.shape, 22)).cuda()
         src = [tuple(m // 2 for m in ((n, n, n) if np.isscalar(n) else n))]
         b = s.rhs_point(src)
         x, info = s.solve(b)
