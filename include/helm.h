@@ -378,9 +378,18 @@ HELM_API helm_status helm_vcycle_down_noalloc(int n1, int n2, int n3, double h, 
                                               double beta1, double beta2, double omega, const void* b, void* out,
                                               void* stream);
 
+/* The FP32 -> FP64 conversion the FP64 kernels use on complex64 data (library instrumentation;
+ * the paper has no counterpart).  It is written with integer instructions from the IEEE-754
+ * layouts, since a converting instruction issues on this GPU's FP64 pipe, and must give the
+ * hardware conversion's bits: out64[i] = (double)in32[i].  Both arrays are device buffers of n
+ * elements owned by the caller; stream-ordered.  HELM_EINVAL for a NULL pointer (message in
+ * helm_last_error(NULL)). */
+HELM_API helm_status helm_convert_check(const float* in32, double* out64, size_t n, void* stream);
+
 /* Message for the last failing call on ctx, or, when ctx is NULL, for the last failing
- * context-free call (helm_create, helm_vcycle_down_noalloc) made on the calling host thread:
- * that message is kept per thread, so threads never see or overwrite each other's.  The
+ * context-free call (helm_create, helm_vcycle_down_noalloc, helm_convert_check) made on the
+ * calling host thread: that message is kept per thread, so threads never see or overwrite
+ * each other's.  The
  * string is owned by the library and stays valid until the next failing call of the same
  * kind (on ctx, or on this thread). */
 HELM_API const char* helm_last_error(const helm_ctx* ctx);

@@ -23,10 +23,32 @@ __host__ __device__ __forceinline__ cx<R> mkc(R a, R b) {
   z.im = b;
   return z;
 }
+// FP32 -> FP64 conversion by the IEEE-754 bit layouts, in integer instructions.  On this GPU a
+// converting instruction issues on the FP64 pipe, the one that bounds every FP64 kernel; the
+// FP64 A-product on complex64 data (the mixed-precision Krylov method) spent a third of its time
+// converting.  For zeros and normal numbers this gives the hardware conversion's bits: the
+// exponent is rebiased by 1023 - 127 = 896 and the mantissa moved up 29 bits.  The rare other
+// inputs (subnormals, infinities, NaNs) take the converting instruction in a separate call.
+// (The opposite direction stays on the converting instruction: the FP32 kernels that read
+// complex128 data are memory-bound, and an integer rounding measured slower there.)
+static __device__ __noinline__ double f32_to_f64_hw(float f) { return (double)f; }
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned mag = u & 0x7fffffffu;
+  if (mag != 0u && mag - 0x00800000u >= 0x7f000000u) return f32_to_f64_hw(f);
+  const unsigned hi = (u & 0x80000000u) | (mag ? (mag >> 3) + 0x38000000u : 0u);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 template <typename To, typename From>
 __device__ __forceinline__ cx<To> cvt(cx<From> a) {
   return mkc<To>((To)a.re, (To)a.im);
 }
+template <>
+__device__ __forceinline__ cx<double> cvt<double, float>(cx<float> a) {
+  return mkc<double>(f32_to_f64(a.re), f32_to_f64(a.im));
+}
+
 template <typename R>
 __device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) { return mkc<R>(a.re + b.re, a.im + b.im); }
 template <typename R>

@@ -109,6 +109,7 @@ struct BatchWS {
   int tty[6][MAX_LEVELS][8] = {}, tct[6][MAX_LEVELS][8] = {};
   int g0ty[6][8] = {}, g0ct[6][8] = {};
   z128 *V = nullptr, *Z64 = nullptr, *w = nullptr, *r = nullptr, *Bt = nullptr, *Xt = nullptr;
+  double* Vs = nullptr;     // (m+1) x ne element sums Re V + Im V (FP64 Gram-Schmidt, gs_sums)
   z64* Z32 = nullptr;
   zdf* wdf = nullptr;       // Arnoldi vector, double-float Gram-Schmidt
   z128* vcur64 = nullptr;   // V-cycle input copy of v_j (double-float basis, FP64 V-cycle)
@@ -1288,6 +1289,7 @@ helm_status batch_alloc(helm_ctx* c, int nb) {
   const int m = c->m;
   const bool mixed = c->p.precision == HELM_PREC_MIXED;
   TRY(dalloc(c, &W.V, (size_t)(m + 1) * ne));
+  if (c->p.orth == HELM_ORTH_FP64 && c->p.gs_sums) TRY(dalloc(c, &W.Vs, (size_t)(m + 1) * ne));
   if (mixed) TRY(dalloc(c, &W.Z32, (size_t)m * ne));
   else TRY(dalloc(c, &W.Z64, (size_t)m * ne));
   TRY(dalloc(c, &W.r, ne));
@@ -1446,7 +1448,8 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
       if (mixed) KL(F_SCALE, 40.0 * nd, 2.0 * nd, (launch_bscale_df<z128, float>(W.r, W.h.beta, Vdf, W.vcur32, ne, nb, st, any)));
       else KL(F_SCALE, 48.0 * nd, 2.0 * nd, (launch_bscale_df<z128, double>(W.r, W.h.beta, Vdf, W.vcur64, ne, nb, st, any)));
     } else {
-      KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_bscale_inv(W.r, W.h.beta, W.V, ne, nb, st, any));
+      KL(F_SCALE, (W.Vs ? 40.0 : 32.0) * nd, (W.Vs ? 3.0 : 2.0) * nd,
+         launch_bscale_inv(W.r, W.h.beta, W.V, W.Vs, ne, nb, st, any));
     }
     for (int j = 0; j < m; ++j) {
       c->cur_j = j;
@@ -1480,15 +1483,22 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
           if (df)
             KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd,
                nbk = launch_bmdot_df(Vdf, ne, j + 1, W.wdf, ne, nb, W.part, wn, st, a2, bvar));
+          else if (W.Vs)
+            // algorithmic flops: 8 per basis vector and element (a complex multiply-add), of which
+            // the summed form executes 6; bytes: what its layout must move
+            KL(F_MDOT, (24.0 * nv + 16.0) * nd, 8.0 * nv * nd,
+               nbk = launch_bmdot(W.V, W.Vs, ne, j + 1, w, ne, nb, W.part, wn, st, a2));
           else
-            KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd, nbk = launch_bmdot(W.V, ne, j + 1, w, ne, nb, W.part, wn, st, a2));
+            KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd,
+               nbk = launch_bmdot(W.V, nullptr, ne, j + 1, w, ne, nb, W.part, wn, st, a2));
           KL(F_REDUCE_DOTS, 16.0 * nv * nb * nbk, 2.0 * nv * nb * nbk,
              launch_breduce_dots(W.part, j + 1, nb, nbk, W.hpass, W.hacc, pass, wn ? j : -1, W.h.act, &ctl->pass2,
                                  c->reorth_log, W.sw2, st, a2));
           if (df)
             KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_bgs_update_df(Vdf, ne, j + 1, nb, W.hpass, W.wdf, ne, st, a2));
           else
-            KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_bgs_update(W.V, ne, j + 1, nb, W.hpass, w, ne, st, a2));
+            KL(F_GS_UPDATE, (W.Vs ? 24.0 * nv + 32.0 : 16.0 * (nv + 2)) * nd, 8.0 * nv * nd,
+               launch_bgs_update(W.V, W.Vs, ne, j + 1, nb, W.hpass, w, ne, st, a2));
         }
         c->cur_cond = 0;
         int nbn = 0;
@@ -1503,7 +1513,8 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
           if (mixed) KL(F_SCALE, 40.0 * nd, 2.0 * nd, (launch_bscale_df<zdf, float>(W.wdf, W.hnorm, vn, W.vcur32, ne, nb, st, any)));
           else KL(F_SCALE, 48.0 * nd, 2.0 * nd, (launch_bscale_df<zdf, double>(W.wdf, W.hnorm, vn, W.vcur64, ne, nb, st, any)));
         } else {
-          KL(F_SCALE, 32.0 * nd, 2.0 * nd, launch_bscale_inv(w, W.hnorm, w, ne, nb, st, any));
+          KL(F_SCALE, (W.Vs ? 40.0 : 32.0) * nd, (W.Vs ? 3.0 : 2.0) * nd,
+             launch_bscale_inv(w, W.hnorm, w, W.Vs ? W.Vs + (size_t)(j + 1) * ne : nullptr, ne, nb, st, any));
         }
       };
       // one graph per Arnoldi column and batch width (the workspace and the tuned shapes of
@@ -1803,6 +1814,21 @@ void helm_default_params(helm_params* p) {
 }
 
 const char* helm_last_error(const helm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+helm_status helm_convert_check(const float* in32, double* out64, size_t n, void* stream) {
+  if (n == 0) return HELM_OK;
+  if (!in32 || !out64) {
+    helm_set_global_error("helm_convert_check: NULL pointer");
+    return HELM_EINVAL;
+  }
+  launch_convert_check(in32, out64, n, (cudaStream_t)stream);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    helm_set_global_error(cudaGetErrorString(e));
+    return HELM_ECUDA;
+  }
+  return HELM_OK;
+}
 
 helm_status helm_profile(helm_ctx* c, int enable) {
   if (!c) return HELM_EINVAL;

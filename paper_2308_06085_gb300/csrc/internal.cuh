@@ -41,6 +41,8 @@ void launch_gj_invert(z128* A, z128* X, int n, z128* fcol, int* piv, z128* pinv,
 void launch_dinv(const Grid& g, double s_re, double s_im, double omega, const double* k2, z128* out, cudaStream_t st);
 void launch_inject(const Grid& gf, const Grid& gc, const double* kf, double* kc, cudaStream_t st);
 void launch_to_float(const double* a, float* b, size_t n, cudaStream_t st);
+// out64 = the kernels' FP32 -> FP64 conversion of in32
+void launch_convert_check(const float* in32, double* out64, size_t n, cudaStream_t st);
 // sk = sqrt(k2) in FP64, skf = sqrtf(float(k2)) in FP32 (the face terms' k)
 void launch_sqrt_table(const double* k2, double* sk, float* skf, size_t n, cudaStream_t st);
 void launch_check_k2(const double* a, size_t n, int* bad, cudaStream_t st);
@@ -189,14 +191,17 @@ void launch_bicg_init(BicgCtl* bc, const z128* part, int nb, const z128* r, z128
 // ---- batched FGMRES kernels (krylov_batched.cu); vectors node-major, rhs innermost ----
 int launch_bnorm2_part(const z128* x, size_t ne, int nb, double* part, cudaStream_t st, const int* active);
 void launch_breduce_norm(const double* part, int nb, int nblk, double* out, cudaStream_t st, const int* active);
-int launch_bmdot(const z128* V, size_t ld, int nv, const z128* w, size_t ne, int nb, z128* part, int with_norm,
-                 cudaStream_t st, const int* active);
+// Vs: the element sums Re V + Im V of a summed basis (three FP64 FMAs per complex
+// multiply-add), or NULL for the textbook four-FMA form
+int launch_bmdot(const z128* V, const double* Vs, size_t ld, int nv, const z128* w, size_t ne, int nb, z128* part,
+                 int with_norm, cudaStream_t st, const int* active);
 void launch_breduce_dots(const z128* part, int nv, int nb, int nblk, z128* hpass, z128* hacc, int accumulate,
                          int decide_j, const int* act, int* pass2, int* log, double* sw2, cudaStream_t st,
                          const int* active);
-void launch_bgs_update(const z128* V, size_t ld, int nv, int nb, const z128* h, z128* w, size_t ne, cudaStream_t st,
-                       const int* active);
-void launch_bscale_inv(const z128* in, const double* s, z128* out, size_t ne, int nb, cudaStream_t st,
+void launch_bgs_update(const z128* V, const double* Vs, size_t ld, int nv, int nb, const z128* h, z128* w, size_t ne,
+                       cudaStream_t st, const int* active);
+// out = in / s[r]; with outs, also the element sums Re out + Im out
+void launch_bscale_inv(const z128* in, const double* s, z128* out, double* outs, size_t ne, int nb, cudaStream_t st,
                        const int* active);
 // double-float Gram-Schmidt variants (basis and Arnoldi vector as zdf)
 int launch_bnorm2_part_df(const zdf* x, size_t ne, int nb, double* part, cudaStream_t st, const int* active);

@@ -50,6 +50,7 @@ __device__ __forceinline__ void df_group_sum(float& s, float& c, int nb) {
 // Accumulators of one lane: FP64 (z128 vectors) or double-float (zdf vectors, FP32 pipes).
 struct BAccD {
   static constexpr bool kBalanced = false;
+  static constexpr bool kSums = false;
   double re, im;
   __device__ void zero() { re = im = 0.0; }
   __device__ void mac(const z128& v, const z128& w) { cdot_acc(v, w, re, im); }
@@ -62,8 +63,31 @@ struct BAccD {
     i = lane_group_sum(im, nb);
   }
 };
+// FP64 accumulator against a basis stored with its element sums s = Re v + Im v (three FMAs
+// per complex multiply-add): A = sum vr wr, B = sum vi wi, C = sum s (wi - wr) give
+// conj(v) . w = (A + B) + i (C + A - B).
+struct BAccD3 {
+  static constexpr bool kBalanced = false;
+  static constexpr bool kSums = true;
+  double a, b, c;
+  __device__ void zero() { a = b = c = 0.0; }
+  __device__ void mac3(const z128& v, double sv, const z128& w, double wd) {
+    a = fma(v.re, w.re, a);
+    b = fma(v.im, w.im, b);
+    c = fma(sv, wd, c);
+  }
+  __device__ void norm(const z128& w) {
+    a = fma(w.re, w.re, a);
+    b = fma(w.im, w.im, b);
+  }
+  __device__ void group(int nb, double& r, double& i) {
+    r = lane_group_sum(a + b, nb);
+    i = lane_group_sum(c + (a - b), nb);
+  }
+};
 struct BAccF {
   static constexpr bool kBalanced = true;
+  static constexpr bool kSums = false;
   float rs, rc, is, ic;
   __device__ void zero() { rs = rc = is = ic = 0.f; }
   __device__ void mac(const zdf& v, const zdf& w) {
@@ -135,12 +159,22 @@ __device__ __forceinline__ int bshare_width(int nslot) {
   return NW;
 }
 
+template <typename ACC, typename E>
+__device__ __forceinline__ void bslot_mac(ACC& acc, const E* __restrict__ V, const double* __restrict__ Vs, size_t off,
+                                          const E& w, double wd) {
+  if constexpr (ACC::kSums) acc.mac3(ldg(V + off), ldg(Vs + off), w, wd);
+  else acc.mac(ldg(V + off), w);
+}
+__device__ __forceinline__ double bw_diff(const z128& w) { return w.im - w.re; }
+__device__ __forceinline__ double bw_diff(const zdf&) { return 0.0; }
+
 template <typename E, typename ACC, int KSV = KS>
 __global__ void __launch_bounds__(NT)
-    k_bmdot(const E* __restrict__ V, size_t ld, int nv, const E* __restrict__ w, size_t ne, int nb,
-            z128* __restrict__ part, int with_norm, const int* __restrict__ active) {
+    k_bmdot(const E* __restrict__ V, const double* __restrict__ Vs, size_t ld, int nv, const E* __restrict__ w,
+            size_t ne, int nb, z128* __restrict__ part, int with_norm, const int* __restrict__ active) {
   if (active && *active == 0) return;
   __shared__ E sw[TILE];
+  __shared__ double swd[ACC::kSums ? TILE : 1];  // wi - wr of the staged points (summed basis)
   __shared__ double sred[NW][32][2];
   size_t e0, e1;
   block_range_e(ne, nb, e0, e1);
@@ -156,14 +190,19 @@ __global__ void __launch_bounds__(NT)
     for (size_t t0 = e0; t0 < e1; t0 += TILE) {
       const int tn = (int)min((size_t)TILE, e1 - t0);
       __syncthreads();
-      for (int q = threadIdx.x; q < tn; q += NT) sw[q] = ldg(w + t0 + q);
+      for (int q = threadIdx.x; q < tn; q += NT) {
+        const E wv = ldg(w + t0 + q);
+        sw[q] = wv;
+        if (ACC::kSums) swd[q] = bw_diff(wv);  // once per point, not once per warp
+      }
       __syncthreads();
       for (int q = sub * 32 + lane; q < tn; q += 32 * wps) {
         const E wv = sw[q];
+        const double wd = ACC::kSums ? swd[q] : 0.0;
 #pragma unroll
         for (int k = 0; k < KSV; ++k) {
           const int sl = sfirst + (sbase + k) * sstep;
-          if (sl < nv) acc[k].mac(ldg(V + (size_t)sl * ld + t0 + q), wv);
+          if (sl < nv) bslot_mac(acc[k], V, Vs, (size_t)sl * ld + t0 + q, wv, wd);
           else if (sl == nv && with_norm) acc[k].norm(wv);
         }
       }
@@ -274,6 +313,54 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
+// w[e] -= sum_i h[i][r] V_i[e] against the summed basis: with P = sum hr vr, Q = sum hi vi and
+// R = sum (hr + hi) s, h v = (P - Q) + i (R - P - Q), three FMAs per element and vector
+__global__ void __launch_bounds__(NT)
+    k_bgs_update_sums(const z128* __restrict__ V, const double* __restrict__ Vs, size_t ld, int nv, int nb,
+                      const z128* __restrict__ h, z128* __restrict__ w, size_t ne, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  extern __shared__ double3 shs[];
+  for (int i = threadIdx.x; i < nv * nb; i += NT) {
+    const z128 c = h[i];
+    shs[i] = make_double3(c.re, c.im, c.re + c.im);
+  }
+  __syncthreads();
+  const size_t stride = (size_t)gridDim.x * NT;
+  const int r = (int)((blockIdx.x * (size_t)NT + threadIdx.x) & (size_t)(nb - 1));  // fixed per thread
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
+    double P = 0.0, Q = 0.0, R = 0.0;
+    for (int i = 0; i < nv; ++i) {
+      const size_t off = (size_t)i * ld + e;
+      const z128 v = ldg(V + off);
+      const double sv = ldg(Vs + off);
+      const double3 c = shs[i * nb + r];
+      P = fma(c.x, v.re, P);
+      Q = fma(c.y, v.im, Q);
+      R = fma(c.z, sv, R);
+    }
+    const z128 a = w[e];
+    w[e] = mkc<double>(a.re - (P - Q), a.im - (R - (P + Q)));
+  }
+}
+
+// out[e] = in[e] * (1 / s[r]) where s[r] > 0, else 0, and outs[e] = Re out + Im out (the element
+// sums of a summed basis vector)
+__global__ void __launch_bounds__(NT)
+    k_bscale_inv_sums(const z128* __restrict__ in, const double* __restrict__ s, z128* __restrict__ out,
+                      double* __restrict__ outs, size_t ne, int nb, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const size_t stride = (size_t)gridDim.x * NT;
+  const double d = s[(blockIdx.x * (size_t)NT + threadIdx.x) & (size_t)(nb - 1)];  // fixed per thread
+  // one division per thread (an FP64 division costs many FP64 issue slots), as k_scale_inv does
+  const double inv = d > 0.0 ? 1.0 / d : 0.0;
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
+    const z128 v = in[e];
+    const z128 o = mkc<double>(v.re * inv, v.im * inv);
+    out[e] = o;
+    outs[e] = o.re + o.im;
+  }
+}
+
 // double-float: w[e] -= sum_i h[i][r] V_i[e], all on the FP32 pipes
 __global__ void __launch_bounds__(NT)
     k_bgs_update_df(const zdf* __restrict__ V, size_t ld, int nv, int nb, const z128* __restrict__ h,
@@ -350,16 +437,18 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
-// out[e] = in[e] / s[r] where s[r] > 0, else 0
+// out[e] = in[e] * (1 / s[r]) where s[r] > 0, else 0
 __global__ void __launch_bounds__(NT)
     k_bscale_inv(const z128* __restrict__ in, const double* __restrict__ s, z128* __restrict__ out, size_t ne, int nb,
                  const int* __restrict__ active) {
   if (active && *active == 0) return;
   const size_t stride = (size_t)gridDim.x * NT;
   const double d = s[(blockIdx.x * (size_t)NT + threadIdx.x) & (size_t)(nb - 1)];  // fixed per thread
+  // one division per thread (an FP64 division costs many FP64 issue slots), as k_scale_inv does
+  const double inv = d > 0.0 ? 1.0 / d : 0.0;
   for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
     const z128 v = in[e];
-    out[e] = d > 0.0 ? mkc<double>(v.re / d, v.im / d) : mkc<double>(0.0, 0.0);
+    out[e] = mkc<double>(v.re * inv, v.im * inv);
   }
 }
 
@@ -588,10 +677,15 @@ int launch_bnorm2_part_df(const zdf* x, size_t ne, int nb, double* part, cudaStr
 void launch_breduce_norm(const double* part, int nb, int nblk, double* out, cudaStream_t st, const int* active) {
   k_breduce_norm<<<1, NT, 0, st>>>(part, nb, nblk, out, active);
 }
-int launch_bmdot(const z128* V, size_t ld, int nv, const z128* w, size_t ne, int nb, z128* part, int with_norm,
-                 cudaStream_t st, const int* active) {
+int launch_bmdot(const z128* V, const double* Vs, size_t ld, int nv, const z128* w, size_t ne, int nb, z128* part,
+                 int with_norm, cudaStream_t st, const int* active) {
+  if (Vs) {  // the summed basis
+    static const int nblk3 = wave_blocks(k_bmdot<z128, BAccD3>, 0);
+    k_bmdot<z128, BAccD3><<<nblk3, NT, 0, st>>>(V, Vs, ld, nv, w, ne, nb, part, with_norm, active);
+    return nblk3;
+  }
   static const int nblk = wave_blocks(k_bmdot<z128, BAccD>, 0);
-  k_bmdot<z128, BAccD><<<nblk, NT, 0, st>>>(V, ld, nv, w, ne, nb, part, with_norm, active);
+  k_bmdot<z128, BAccD><<<nblk, NT, 0, st>>>(V, nullptr, ld, nv, w, ne, nb, part, with_norm, active);
   return nblk;
 }
 // The double-float variants share one grid, a wave of the most resident (2-slot) kernel (the 4-
@@ -605,7 +699,7 @@ template <int KSV>
 int bmdot_df_ks(const zdf* V, size_t ld, int nv, const zdf* w, size_t ne, int nb, z128* part, int with_norm,
                 cudaStream_t st, const int* active) {
   const int nblk = bmdot_df_grid();
-  k_bmdot<zdf, BAccF, KSV><<<nblk, NT, 0, st>>>(V, ld, nv, w, ne, nb, part, with_norm, active);
+  k_bmdot<zdf, BAccF, KSV><<<nblk, NT, 0, st>>>(V, nullptr, ld, nv, w, ne, nb, part, with_norm, active);
   return nblk;
 }
 int launch_bmdot_df(const zdf* V, size_t ld, int nv, const zdf* w, size_t ne, int nb, z128* part, int with_norm,
@@ -637,13 +731,19 @@ void launch_breduce_dots(const z128* part, int nv, int nb, int nblk, z128* hpass
                                                       active);
   if (decide_j >= 0) k_bdecide<<<1, 32, 0, st>>>(hpass, sw2, nv, nb, decide_j, act, pass2, log, active);
 }
-void launch_bgs_update(const z128* V, size_t ld, int nv, int nb, const z128* h, z128* w, size_t ne, cudaStream_t st,
-                       const int* active) {
-  k_bgs_update<<<stream_blocks(ne), NT, sizeof(z128) * nv * nb, st>>>(V, ld, nv, nb, h, w, ne, active);
+void launch_bgs_update(const z128* V, const double* Vs, size_t ld, int nv, int nb, const z128* h, z128* w, size_t ne,
+                       cudaStream_t st, const int* active) {
+  if (Vs)
+    k_bgs_update_sums<<<stream_blocks(ne), NT, sizeof(double3) * nv * nb, st>>>(V, Vs, ld, nv, nb, h, w, ne, active);
+  else
+    k_bgs_update<<<stream_blocks(ne), NT, sizeof(z128) * nv * nb, st>>>(V, ld, nv, nb, h, w, ne, active);
 }
-void launch_bscale_inv(const z128* in, const double* s, z128* out, size_t ne, int nb, cudaStream_t st,
+void launch_bscale_inv(const z128* in, const double* s, z128* out, double* outs, size_t ne, int nb, cudaStream_t st,
                        const int* active) {
-  k_bscale_inv<<<stream_blocks(ne), NT, 0, st>>>(in, s, out, ne, nb, active);
+  if (outs)
+    k_bscale_inv_sums<<<stream_blocks(ne), NT, 0, st>>>(in, s, out, outs, ne, nb, active);
+  else
+    k_bscale_inv<<<stream_blocks(ne), NT, 0, st>>>(in, s, out, ne, nb, active);
 }
 void launch_bcycle_init(BatchCtl* bc, int nb, int m, double tol, cudaStream_t st) {
   k_bcycle_init<<<1, 32, 0, st>>>(bc, nb, m, tol);

@@ -61,10 +61,15 @@ __device__ __forceinline__ cx<R> fw_combine(cx<R> pm, cx<R> p0, cx<R> pp) {
 // with Op = -Lap_h - s k^2 (s in OpCoef).  DINV (FP64 multigrid levels): read the diagonal d
 // of M and omega/d from the level's coefficient table (omega/d at [0, npts), d at [npts,
 // 2 npts)) instead of computing them from k^2: on this GPU FP64 instructions, not bytes, bound
-// these kernels, and the table holds the very values op_diag and the division would give.  With g.nb right-hand sides per node, a thread owns one (node column, rhs)
-// pair; for nb = 32 a warp covers the 32 right-hand sides of one node with one 256-byte
-// (complex64) row and reads k^2 once.
-template <typename R, int MODE, bool DINV, typename TU, typename TB, typename TO, bool SPLIT = false>
+// these kernels, and the table holds the very values op_diag and the division would give.
+// REALA (the operator A, real shift s = 1, APPLY or RESID): the diagonal is real away from the
+// Sommerfeld faces, so the two products with its imaginary part are issued only at face nodes
+// (same operations in the same order as the general path, so the same results).  With g.nb
+// right-hand sides per node, a thread owns one (node column, rhs) pair; for nb = 32 a warp
+// covers the 32 right-hand sides of one node with one 256-byte (complex64) row and reads k^2
+// once.
+template <typename R, int MODE, bool DINV, typename TU, typename TB, typename TO, bool SPLIT = false,
+          bool REALA = false>
 __global__ void __launch_bounds__(TX* TY)
     k_stencil(Grid g, OpCoef<R> c, const R* __restrict__ k2, const cx<R>* __restrict__ dinv,
               const cx<TU>* __restrict__ u, const cx<TB>* __restrict__ b, cx<TO>* __restrict__ out,
@@ -126,6 +131,29 @@ __global__ void __launch_bounds__(TX* TY)
     if constexpr (!PF) {
       if (!DINV) kk = __ldg(k2 + p);
       if (MODE != 0) bv = cvt<R>(ldg(b + e));
+    }
+    if constexpr (REALA && MODE != 2) {
+      // real diagonal 6/h^2 - k^2; a face node adds -i (2k/h) nf (op_diag's face term)
+      const cx<R> dr = mkc<R>(fma(-c.s_re, kk, c.six_ih2), (R)0);
+      cx<R> v = MODE == 0 ? op_apply(dr, true, uc, c.ih2, xm, xp, ym, yp, zm, zp)
+                          : op_resid(bv, dr, true, uc, c.ih2, xm, xp, ym, yp, zm, zp);
+      if (nf) {
+        const R dim = fma(-(R)nf * c.two_over_h, face_k<R>(g, p, kk), (R)0);
+        if (MODE == 0) {
+          v.re = fma(-dim, uc.im, v.re);
+          v.im = fma(dim, uc.re, v.im);
+        } else {
+          v.re = fma(dim, uc.im, v.re);
+          v.im = fma(-dim, uc.re, v.im);
+        }
+      }
+      if (MODE == 0 && SPLIT)
+        reinterpret_cast<zdf*>(out)[e] = df_from(cvt<double>(v));
+      else
+        out[e] = cvt<TO>(v);
+      um = uc;
+      uc = up;
+      continue;
     }
     const cx<R> d = DINV ? ldg(dinv + g.npts() + p) : op_diag(c, kk, nf, nf ? face_k<R>(g, p, kk) : (R)0);
     const bool real_d = c.real_shift && nf == 0;
@@ -771,6 +799,13 @@ __global__ void k_sqrt_table(const double* __restrict__ k2, double* __restrict__
   }
 }
 
+// The kernels' FP32 -> FP64 conversion (f32_to_f64) applied elementwise, for checks against
+// the hardware conversion.
+__global__ void k_convert_check(const float* __restrict__ in32, double* __restrict__ out64, size_t n) {
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+    out64[p] = f32_to_f64(in32[p]);
+}
+
 __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n) {
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
     b[p] = (float)a[p];
@@ -1325,8 +1360,12 @@ void launch_apply(const Grid& g, double s_re, double s_im, const R* k2, const cx
     }
   }
   dim3 blk, gr = grid_for<R>(g, TILE_STENCIL, zc, blk);
-  k_stencil<R, 0, false, TU, TU, TO><<<gr, blk, 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr, u,
-                                                                   nullptr, v, zc, active);
+  if (s_im == 0.0 && std::is_same<R, double>::value)  // the operator A: real diagonal off the faces
+    k_stencil<R, 0, false, TU, TU, TO, false, true><<<gr, blk, 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2,
+                                                                        nullptr, u, nullptr, v, zc, active);
+  else
+    k_stencil<R, 0, false, TU, TU, TO><<<gr, blk, 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr, u,
+                                                           nullptr, v, zc, active);
 }
 
 static float2 df_const(double x) {
@@ -1357,8 +1396,12 @@ void launch_apply_split(const Grid& g, double s_re, double s_im, const double* k
                         cudaStream_t st, const int* active) {
   int zc;
   dim3 blk, gr = grid_for<double>(g, TILE_STENCIL, zc, blk);
-  k_stencil<double, 0, false, TU, TU, double, true><<<gr, blk, 0, st>>>(
-      g, coef_for<double>(g.h, s_re, s_im, 0.0), k2, nullptr, u, nullptr, reinterpret_cast<z128*>(v), zc, active);
+  if (s_im == 0.0)
+    k_stencil<double, 0, false, TU, TU, double, true, true><<<gr, blk, 0, st>>>(
+        g, coef_for<double>(g.h, s_re, s_im, 0.0), k2, nullptr, u, nullptr, reinterpret_cast<z128*>(v), zc, active);
+  else
+    k_stencil<double, 0, false, TU, TU, double, true><<<gr, blk, 0, st>>>(
+        g, coef_for<double>(g.h, s_re, s_im, 0.0), k2, nullptr, u, nullptr, reinterpret_cast<z128*>(v), zc, active);
 }
 template void launch_apply_split<double>(const Grid&, double, double, const double*, const z128*, zdf*, cudaStream_t,
                                          const int*);
@@ -1384,8 +1427,12 @@ void launch_resid(const Grid& g, double s_re, double s_im, const R* k2, const cx
     }
   }
   dim3 blk, gr = grid_for<R>(g, TILE_STENCIL, zc, blk);
-  k_stencil<R, 1, false, TU, TB, TO><<<gr, blk, 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr,
-                                                                   u, b, out, zc, active);
+  if (s_im == 0.0 && std::is_same<R, double>::value)  // the operator A: real diagonal off the faces
+    k_stencil<R, 1, false, TU, TB, TO, false, true><<<gr, blk, 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2,
+                                                                        nullptr, u, b, out, zc, active);
+  else
+    k_stencil<R, 1, false, TU, TB, TO><<<gr, blk, 0, st>>>(g, coef_for<R>(g.h, s_re, s_im, 0.0), k2, nullptr, u, b,
+                                                           out, zc, active);
 }
 
 template <typename R, typename TB, typename TO>
@@ -1539,6 +1586,10 @@ void launch_sqrt_table(const double* k2, double* sk, float* skf, size_t n, cudaS
 
 void launch_to_float(const double* a, float* b, size_t n, cudaStream_t st) {
   k_to_float<<<1216, 256, 0, st>>>(a, b, n);
+}
+
+void launch_convert_check(const float* in32, double* out64, size_t n, cudaStream_t st) {
+  k_convert_check<<<1216, 256, 0, st>>>(in32, out64, n);
 }
 
 void launch_check_k2(const double* a, size_t n, int* bad, cudaStream_t st) {

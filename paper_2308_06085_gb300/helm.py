@@ -107,6 +107,8 @@ def lib():
         getattr(L, f).restype = i
     L.helm_vcycle_down_noalloc.argtypes = [i, i, i, d, vp, i, d, d, d, vp, vp, vp]
     L.helm_vcycle_down_noalloc.restype = i
+    L.helm_convert_check.argtypes = [vp, vp, C.c_size_t, vp]
+    L.helm_convert_check.restype = i
     L.helm_last_error.argtypes = [vp]
     L.helm_last_error.restype = C.c_char_p
     for f in ("helm_create", "helm_destroy", "helm_levels", "helm_level_dims", "helm_apply", "cslp_vcycle",
@@ -131,6 +133,19 @@ def _ptr(t):
 
 
 _DT = {torch.complex128: C128, torch.complex64: C64}
+
+
+def convert_check(x32):
+    """The kernels' own FP32 -> FP64 conversion (integer instructions) applied to a float32 CUDA
+    tensor; returns float64."""
+    x32 = x32.reshape(-1).contiguous()
+    if x32.dtype != torch.float32:
+        raise TypeError("convert_check takes a float32 tensor")
+    o64 = torch.empty(x32.shape, dtype=torch.float64, device=x32.device)
+    st = lib().helm_convert_check(_ptr(x32), _ptr(o64), x32.numel(), _stream())
+    if st != OK:
+        raise HelmError(st, lib().helm_last_error(None).decode())
+    return o64
 
 
 NOALLOC_MAX_POINTS = 262144

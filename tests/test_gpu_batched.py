@@ -104,3 +104,30 @@ def test_batched_fcycle_matches_single(helm):
         assert infos[r]["status"] == 0 and infos[r]["rel_residual"] <= 1e-6, infos[r]
         assert abs(infos[r]["iterations"] - i1["iterations"]) <= 1, (r, infos[r], i1)
         assert rel(X[r].cpu().numpy(), x1.cpu().numpy()) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_summed_basis_matches_textbook(helm, precision):
+    """Batched FP64 Gram-Schmidt against the summed basis (three FMAs per complex multiply-add,
+    the default) and in the textbook four-FMA form: the same solves to 1e-10, so #Matvec within
+    +-1 and solutions within 1e-8 for every right-hand side; the default also against the oracle."""
+    w = I.workload("batched", 16)
+    src = sources(16, 6)
+    out = []
+    for sums in (True, False):
+        s = helm.Solver(w["n"], w["h"], w["k2"], S, krylov="fgmres", precision=precision, gs_sums=sums, tol=1e-10,
+                        max_iter=4000)
+        B = torch.stack([s.rhs_point([p]) for p in src])
+        X, infos = s.solve_batched(B)
+        assert all(i["status"] == 0 and i["rel_residual"] <= 1e-10 for i in infos)
+        out.append((X.cpu().numpy(), [i["iterations"] for i in infos], B.cpu().numpy()))
+        s.close()
+    (xa, ia, B), (xb, ib, _) = out
+    for r in range(len(src)):
+        assert abs(ia[r] - ib[r]) <= 1, (r, ia, ib)
+        assert rel(xa[r], xb[r]) <= 1e-8
+    if precision == "fp64":
+        o = oracle.Solver(w["n"], w["h"], S, w["k2"])
+        for r in range(2):
+            ro = o.gmres(B[r], restart=30, tol=1e-10, max_iter=4000, flexible=True)
+            assert abs(ia[r] - ro["iters"]) <= 1 and rel(xa[r], ro["x"]) <= 1e-8
