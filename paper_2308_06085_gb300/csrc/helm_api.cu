@@ -84,7 +84,8 @@ struct TuneRec {
 
 struct ProfRec {
   int fam, j, e0, e1;
-  int cond;  // 1: second Gram-Schmidt pass, which ran only if the step's log entry is set
+  int cond;  // 1: second Gram-Schmidt pass, which ran only if the step's log entry is set; 2: the
+             // same, with bytes and flops per right-hand side times the logged count
   double bytes, flops;
 };
 
@@ -110,6 +111,7 @@ struct BatchWS {
   int g0ty[6][8] = {}, g0ct[6][8] = {};
   z128 *V = nullptr, *Z64 = nullptr, *w = nullptr, *r = nullptr, *Bt = nullptr, *Xt = nullptr;
   double* Vs = nullptr;     // (m+1) x ne element sums Re V + Im V (FP64 Gram-Schmidt, gs_sums)
+  int* need = nullptr;      // per right-hand side: the current step takes the second Gram-Schmidt pass
   z64* Z32 = nullptr;
   zdf* wdf = nullptr;       // Arnoldi vector, double-float Gram-Schmidt
   z128* vcur64 = nullptr;   // V-cycle input copy of v_j (double-float basis, FP64 V-cycle)
@@ -316,9 +318,11 @@ void prof_flush(helm_ctx* c, int jend) {
     if (r.cond && r.j >= 0 && !c->hreorth_log[r.j]) continue;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, P.pool[r.e0], P.pool[r.e1]) != cudaSuccess) { cudaGetLastError(); continue; }
+    // cond 2: bytes and flops were given per right-hand side; the log holds how many took part
+    const double f = r.cond == 2 && r.j >= 0 ? (double)c->hreorth_log[r.j] : 1.0;
     P.ms[r.fam] += ms;
-    P.bytes[r.fam] += r.bytes;
-    P.flops[r.fam] += r.flops;
+    P.bytes[r.fam] += r.bytes * f;
+    P.flops[r.fam] += r.flops * f;
     P.cnt[r.fam] += 1;
   }
   P.recs.clear();
@@ -1307,6 +1311,8 @@ helm_status batch_alloc(helm_ctx* c, int nb) {
   TRY(dalloc(c, &W.hnorm, nb));
   TRY(dalloc(c, &W.sw2, nb));
   TRY(dalloc(c, &W.log, m));
+  TRY(dalloc(c, &W.need, nb));
+  CU(cudaMemset(W.need, 0, sizeof(int) * nb));
   BatchCtl& h = W.h;
   h.any = 0; h.pass2 = 0; h.max_iter = c->p.max_iter; h.pad = 0;
   TRY(dalloc(c, &h.act, nb)); TRY(dalloc(c, &h.jend, nb)); TRY(dalloc(c, &h.flag, nb));
@@ -1480,7 +1486,14 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
           c->cur_cond = (pass == 1 && sel) ? 1 : 0;
           const int wn = (pass == 0 && sel) ? 1 : 0;
           int nbk = 0;
-          if (df)
+          // FP64 second pass with the selective test: only the right-hand sides that need it
+          // (profiled per right-hand side and scaled by the logged count)
+          const bool per_rhs = pass == 1 && sel && !df;
+          if (per_rhs) c->cur_cond = 2;
+          if (per_rhs)
+            KL(F_MDOT, ((W.Vs ? 24.0 * nv + 16.0 : 16.0 * (nv + 1)) * nd) / nb, 8.0 * nv * nd / nb,
+               nbk = launch_bmdot_sel(W.V, W.Vs, ne, j + 1, w, ne, nb, W.need, W.part, st, a2));
+          else if (df)
             KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd,
                nbk = launch_bmdot_df(Vdf, ne, j + 1, W.wdf, ne, nb, W.part, wn, st, a2, bvar));
           else if (W.Vs)
@@ -1491,10 +1504,15 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
           else
             KL(F_MDOT, 16.0 * (nv + 1) * nd, 8.0 * nv * nd,
                nbk = launch_bmdot(W.V, nullptr, ne, j + 1, w, ne, nb, W.part, wn, st, a2));
+          if (per_rhs) c->cur_cond = 1;
           KL(F_REDUCE_DOTS, 16.0 * nv * nb * nbk, 2.0 * nv * nb * nbk,
              launch_breduce_dots(W.part, j + 1, nb, nbk, W.hpass, W.hacc, pass, wn ? j : -1, W.h.act, &ctl->pass2,
-                                 c->reorth_log, W.sw2, st, a2));
-          if (df)
+                                 c->reorth_log, W.sw2, W.need, st, a2));
+          if (per_rhs) c->cur_cond = 2;
+          if (per_rhs)
+            KL(F_GS_UPDATE, ((W.Vs ? 24.0 * nv + 32.0 : 16.0 * (nv + 2)) * nd) / nb, 8.0 * nv * nd / nb,
+               launch_bgs_update_sel(W.V, W.Vs, ne, j + 1, nb, W.hpass, w, ne, W.need, st, a2));
+          else if (df)
             KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_bgs_update_df(Vdf, ne, j + 1, nb, W.hpass, W.wdf, ne, st, a2));
           else
             KL(F_GS_UPDATE, (W.Vs ? 24.0 * nv + 32.0 : 16.0 * (nv + 2)) * nd, 8.0 * nv * nd,

@@ -195,9 +195,18 @@ void launch_breduce_norm(const double* part, int nb, int nblk, double* out, cuda
 // multiply-add), or NULL for the textbook four-FMA form
 int launch_bmdot(const z128* V, const double* Vs, size_t ld, int nv, const z128* w, size_t ne, int nb, z128* part,
                  int with_norm, cudaStream_t st, const int* active);
+// decide_j >= 0: the second-pass test per right-hand side (need[r]); *pass2 = any, log[decide_j] =
+// how many
 void launch_breduce_dots(const z128* part, int nv, int nb, int nblk, z128* hpass, z128* hacc, int accumulate,
-                         int decide_j, const int* act, int* pass2, int* log, double* sw2, cudaStream_t st,
+                         int decide_j, const int* act, int* pass2, int* log, double* sw2, int* need, cudaStream_t st,
                          const int* active);
+// the second Gram-Schmidt pass for the right-hand sides with need[r] only (FP64; Vs: summed
+// basis or NULL): inner products into part (k_bmdot's layout and grid; zeros for the others),
+// and the update
+int launch_bmdot_sel(const z128* V, const double* Vs, size_t ld, int nv, const z128* w, size_t ne, int nb,
+                     const int* need, z128* part, cudaStream_t st, const int* active);
+void launch_bgs_update_sel(const z128* V, const double* Vs, size_t ld, int nv, int nb, const z128* h, z128* w,
+                           size_t ne, const int* need, cudaStream_t st, const int* active);
 void launch_bgs_update(const z128* V, const double* Vs, size_t ld, int nv, int nb, const z128* h, z128* w, size_t ne,
                        cudaStream_t st, const int* active);
 // out = in / s[r]; with outs, also the element sums Re out + Im out

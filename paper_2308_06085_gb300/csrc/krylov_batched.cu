@@ -62,6 +62,10 @@ struct BAccD {
     r = lane_group_sum(re, nb);
     i = lane_group_sum(im, nb);
   }
+  __device__ void value(double& r, double& i) const {
+    r = re;
+    i = im;
+  }
 };
 // FP64 accumulator against a basis stored with its element sums s = Re v + Im v (three FMAs
 // per complex multiply-add): A = sum vr wr, B = sum vi wi, C = sum s (wi - wr) give
@@ -83,6 +87,10 @@ struct BAccD3 {
   __device__ void group(int nb, double& r, double& i) {
     r = lane_group_sum(a + b, nb);
     i = lane_group_sum(c + (a - b), nb);
+  }
+  __device__ void value(double& r, double& i) const {
+    r = a + b;
+    i = c + (a - b);
   }
 };
 struct BAccF {
@@ -270,22 +278,166 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
-// The Daniel-Gragg-Kaufman-Stewart test over the active right-hand sides: a second pass when
-// the first one removed more than half of |w|^2 for any of them.
+// The Daniel-Gragg-Kaufman-Stewart test per active right-hand side: r takes a second pass when
+// its first one removed more than half of |w_r|^2 (need[r]); the pass runs when any r needs it,
+// and log[decide_j] holds how many do.
 __global__ void k_bdecide(const z128* __restrict__ hpass, const double* __restrict__ sw2, int nv, int nb,
                           int decide_j, const int* __restrict__ act, int* __restrict__ pass2, int* __restrict__ log,
-                          const int* __restrict__ active) {
+                          int* __restrict__ need, const int* __restrict__ active) {
   if (active && *active == 0) return;
   if (threadIdx.x != 0) return;
-  int again = 0;
+  int count = 0;
   for (int r = 0; r < nb; ++r) {
-    if (!act[r]) continue;
-    double h2 = 0.0;
-    for (int i = 0; i < nv; ++i) h2 += hpass[i * nb + r].re * hpass[i * nb + r].re + hpass[i * nb + r].im * hpass[i * nb + r].im;
-    again |= !(sw2[r] - h2 >= 0.5 * sw2[r]);
+    int nr = 0;
+    if (act[r]) {
+      double h2 = 0.0;
+      for (int i = 0; i < nv; ++i) h2 += hpass[i * nb + r].re * hpass[i * nb + r].re + hpass[i * nb + r].im * hpass[i * nb + r].im;
+      nr = !(sw2[r] - h2 >= 0.5 * sw2[r]);
+    }
+    need[r] = nr;
+    count += nr;
   }
-  *pass2 = again;
-  log[decide_j] = again;
+  *pass2 = count > 0;
+  log[decide_j] = count;
+}
+
+// The list of right-hand sides that need the second pass, in increasing order, in shared memory.
+__device__ __forceinline__ int need_list(const int* __restrict__ need, int nb, int* list) {
+  __shared__ int cnt;
+  if (threadIdx.x < 32) {
+    const int f = (int)threadIdx.x < nb ? need[threadIdx.x] != 0 : 0;
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (f) list[__popc(m & ((1u << threadIdx.x) - 1u))] = threadIdx.x;
+    if (threadIdx.x == 0) cnt = __popc(m);
+  }
+  __syncthreads();
+  return cnt;
+}
+
+// Second Gram-Schmidt pass for the right-hand sides in need[] only (FP64, summed basis or
+// textbook accumulator).  The partials keep k_bmdot's layout and block ranges, so
+// k_breduce_dots sums them unchanged; the rows of the other right-hand sides get zeros.  The
+// work is packed: with K selected right-hand sides, thread t of the block takes the pairs
+// (node, selected right-hand side t % K) for t < (NT / K) K, so every active lane works on a
+// selected right-hand side, and a warp reads a few contiguous rows of nb values; the per-thread
+// sums are then added over the threads of each right-hand side in a fixed order.
+template <typename ACC>
+__global__ void __launch_bounds__(NT)
+    k_bmdot_sel(const z128* __restrict__ V, const double* __restrict__ Vs, size_t ld, int nv,
+                const z128* __restrict__ w, size_t ne, int nb, const int* __restrict__ need, z128* __restrict__ part,
+                const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ int list[32];
+  __shared__ double sred[KS][NT][2];
+  const int cnt = need_list(need, nb, list);
+  size_t e0, e1;
+  block_range_e(ne, nb, e0, e1);
+  const size_t q0 = e0 / nb, q1 = e1 / nb;  // node range of this block (chunks are multiples of nb)
+  double* partd = reinterpret_cast<double*>(part);
+  // zeros for the rows of the right-hand sides without a second pass
+  for (int t = threadIdx.x; t < nv * nb; t += NT) {
+    const int r = t % nb;
+    bool sel = false;
+    for (int k = 0; k < cnt; ++k) sel |= list[k] == r;
+    if (!sel) {
+      partd[2 * ((size_t)t * RED_STRIDE + blockIdx.x)] = 0.0;
+      partd[2 * ((size_t)t * RED_STRIDE + blockIdx.x) + 1] = 0.0;
+    }
+  }
+  if (cnt == 0) return;
+  const int per = NT / cnt;            // nodes per block sweep
+  const int tk = threadIdx.x % cnt;    // this thread's selected right-hand side
+  const int tq = threadIdx.x / cnt;    // this thread's node offset in a sweep
+  const bool on = tq < per;
+  const int r = list[tk];
+  for (int sbase = 0; sbase < nv; sbase += KS) {
+    ACC acc[KS];
+#pragma unroll
+    for (int s = 0; s < KS; ++s) acc[s].zero();
+    if (on)
+      for (size_t q = q0 + tq; q < q1; q += per) {
+        const size_t e = q * nb + r;
+        const z128 wv = ldg(w + e);
+        const double wd = bw_diff(wv);
+#pragma unroll
+        for (int s = 0; s < KS; ++s)
+          if (sbase + s < nv) bslot_mac(acc[s], V, Vs, (size_t)(sbase + s) * ld + e, wv, wd);
+      }
+#pragma unroll
+    for (int s = 0; s < KS; ++s) {
+      double re, im;
+      acc[s].value(re, im);  // this thread's own sum (no lane exchange)
+      sred[s][threadIdx.x][0] = on ? re : 0.0;
+      sred[s][threadIdx.x][1] = on ? im : 0.0;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < KS * cnt; t += NT) {
+      const int s = t / cnt, k = t % cnt;
+      if (sbase + s < nv) {
+        double tr = 0.0, ti = 0.0;
+        for (int u = k; u < per * cnt; u += cnt) {
+          tr += sred[s][u][0];
+          ti += sred[s][u][1];
+        }
+        const size_t row = (size_t)(sbase + s) * nb + list[k];
+        partd[2 * (row * RED_STRIDE + blockIdx.x)] = tr;
+        partd[2 * (row * RED_STRIDE + blockIdx.x) + 1] = ti;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// w[e] -= sum_i h[i][r] V_i[e] for the right-hand sides in need[] only (the others' h is zero),
+// packed as in k_bmdot_sel: thread t of the grid takes (node, selected right-hand side t % K)
+template <bool SUMS>
+__global__ void __launch_bounds__(NT)
+    k_bgs_update_sel(const z128* __restrict__ V, const double* __restrict__ Vs, size_t ld, int nv, int nb,
+                     const z128* __restrict__ h, z128* __restrict__ w, size_t ne, const int* __restrict__ need,
+                     const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  __shared__ int list[32];
+  extern __shared__ double3 shq[];
+  const int cnt = need_list(need, nb, list);
+  if (cnt == 0) return;
+  for (int t = threadIdx.x; t < nv * cnt; t += NT) {
+    const z128 c = h[(t / cnt) * nb + list[t % cnt]];
+    shq[t] = make_double3(c.re, c.im, c.re + c.im);
+  }
+  __syncthreads();
+  const int per = NT / cnt;
+  const int tk = threadIdx.x % cnt, tq = threadIdx.x / cnt;
+  if (tq >= per) return;
+  const int r = list[tk];
+  const size_t nq = ne / nb;
+  for (size_t q = blockIdx.x * (size_t)per + tq; q < nq; q += (size_t)gridDim.x * per) {
+    const size_t e = q * nb + r;
+    const z128 a = w[e];
+    if (SUMS) {
+      double P = 0.0, Q = 0.0, R = 0.0;
+      for (int i = 0; i < nv; ++i) {
+        const size_t off = (size_t)i * ld + e;
+        const z128 v = ldg(V + off);
+        const double sv = ldg(Vs + off);
+        const double3 c = shq[i * cnt + tk];
+        P = fma(c.x, v.re, P);
+        Q = fma(c.y, v.im, Q);
+        R = fma(c.z, sv, R);
+      }
+      w[e] = mkc<double>(a.re - (P - Q), a.im - (R - (P + Q)));
+    } else {
+      z128 acc = a;
+      for (int i = 0; i < nv; ++i) {
+        const z128 v = ldg(V + (size_t)i * ld + e);
+        const double3 c = shq[i * cnt + tk];
+        acc.re = fma(-c.x, v.re, acc.re);
+        acc.re = fma(c.y, v.im, acc.re);
+        acc.im = fma(-c.x, v.im, acc.im);
+        acc.im = fma(-c.y, v.re, acc.im);
+      }
+      w[e] = acc;
+    }
+  }
 }
 
 // w[e] -= sum_i h[i][r] V_i[e]
@@ -724,12 +876,32 @@ template void launch_bscale_df<z128, float>(const z128*, const double*, zdf*, z6
 template void launch_bscale_df<zdf, double>(const zdf*, const double*, zdf*, z128*, size_t, int, cudaStream_t, const int*);
 template void launch_bscale_df<zdf, float>(const zdf*, const double*, zdf*, z64*, size_t, int, cudaStream_t, const int*);
 void launch_breduce_dots(const z128* part, int nv, int nb, int nblk, z128* hpass, z128* hacc, int accumulate,
-                         int decide_j, const int* act, int* pass2, int* log, double* sw2, cudaStream_t st,
+                         int decide_j, const int* act, int* pass2, int* log, double* sw2, int* need, cudaStream_t st,
                          const int* active) {
   const int rows = (decide_j >= 0 ? nv + 1 : nv) * nb;
   k_breduce_dots<<<(rows + NW - 1) / NW, NT, 0, st>>>(part, nv, nb, nblk, hpass, hacc, accumulate, decide_j, sw2,
                                                       active);
-  if (decide_j >= 0) k_bdecide<<<1, 32, 0, st>>>(hpass, sw2, nv, nb, decide_j, act, pass2, log, active);
+  if (decide_j >= 0) k_bdecide<<<1, 32, 0, st>>>(hpass, sw2, nv, nb, decide_j, act, pass2, log, need, active);
+}
+int launch_bmdot_sel(const z128* V, const double* Vs, size_t ld, int nv, const z128* w, size_t ne, int nb,
+                     const int* need, z128* part, cudaStream_t st, const int* active) {
+  // the grid of the first pass's kernel, so that the block ranges and partial slots match
+  if (Vs) {
+    static const int nblk3 = wave_blocks(k_bmdot<z128, BAccD3>, 0);
+    k_bmdot_sel<BAccD3><<<nblk3, NT, 0, st>>>(V, Vs, ld, nv, w, ne, nb, need, part, active);
+    return nblk3;
+  }
+  static const int nblk = wave_blocks(k_bmdot<z128, BAccD>, 0);
+  k_bmdot_sel<BAccD><<<nblk, NT, 0, st>>>(V, nullptr, ld, nv, w, ne, nb, need, part, active);
+  return nblk;
+}
+void launch_bgs_update_sel(const z128* V, const double* Vs, size_t ld, int nv, int nb, const z128* h, z128* w,
+                           size_t ne, const int* need, cudaStream_t st, const int* active) {
+  const size_t smem = sizeof(double3) * nv * nb;
+  if (Vs)
+    k_bgs_update_sel<true><<<stream_blocks(ne / nb), NT, smem, st>>>(V, Vs, ld, nv, nb, h, w, ne, need, active);
+  else
+    k_bgs_update_sel<false><<<stream_blocks(ne / nb), NT, smem, st>>>(V, nullptr, ld, nv, nb, h, w, ne, need, active);
 }
 void launch_bgs_update(const z128* V, const double* Vs, size_t ld, int nv, int nb, const z128* h, z128* w, size_t ne,
                        cudaStream_t st, const int* active) {
