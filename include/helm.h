@@ -309,6 +309,15 @@ HELM_API helm_status helm_solve_batched(helm_ctx* ctx, int nrhs, const void* B, 
 HELM_API helm_status helm_solve_adjoint(helm_ctx* ctx, const void* g, void* lambda, helm_solve_info* info,
                                         void* stream);
 
+/* The adjoint solve of helm_solve_adjoint for nrhs right-hand sides at once, through the
+ * lockstep batched solver of helm_solve_batched (the D-scaling and conjugation are applied in
+ * its node-major batched layout).
+ *   G, Lambda : device c128, nrhs consecutive grid vectors (Lambda overwritten; zero start)
+ *   infos     : optional host array of nrhs reports
+ * Waits for completion.  Errors as helm_solve_batched. */
+HELM_API helm_status helm_solve_adjoint_batched(helm_ctx* ctx, int nrhs, const void* G, void* Lambda,
+                                                helm_solve_info* infos, void* stream);
+
 /* Accumulate the adjoint-state gradient with respect to k^2 at every node:
  *   grad_k2[p] += -Re( conj(lambda_p) * dA_pp/dk^2_p * u_p ),  dA_pp/dk^2_p = -1 - i nf_p / (h k_p)
  * (nf_p = Sommerfeld faces at p).  u: the forward solution, lambda: the adjoint solution for
@@ -324,8 +333,11 @@ HELM_API helm_status helm_grad_k2(helm_ctx* ctx, const void* u, const void* lamb
  *   d_obs     : device c128, nsrc x nrec (row per source)
  *   grad_k2   : device FP64, N1*N2*N3, overwritten;  loss : host double
  *   info      : optional host report (iterations summed over all solves, worst residual)
- * The forward wavefield of one source is held on the device until its adjoint step (one
- * source at a time).  Waits for completion.  HELM_ENOCONV if any solve hit max_iter. */
+ * With GMRES / FGMRES (right preconditioning) and nsrc > 1 every forward solve runs in
+ * helm_solve_batched's lockstep batches, then every adjoint solve the same way, so the
+ * context holds nsrc forward wavefields, receiver residuals and adjoint states (3 nsrc grid
+ * vectors, allocated on first use); otherwise one source at a time, holding one wavefield.
+ * Waits for completion.  HELM_ENOCONV if any solve hit max_iter. */
 HELM_API helm_status helm_adjoint_grad(helm_ctx* ctx, int nsrc, const int* src_nodes, int nrec, const int* rec_idx,
                                        const void* d_obs, double* grad_k2, double* loss, helm_solve_info* info,
                                        void* stream);

@@ -23,21 +23,24 @@ __device__ __forceinline__ int faces_at(const Grid& g, size_t p) {
   return (i == 0) + (i == g.N1 - 1) + (j == 0) + (j == g.N2 - 1) + (k == 0) + (k == g.N3 - 1);
 }
 
-__global__ void __launch_bounds__(NT) k_adjoint_rhs(Grid g, const z128* __restrict__ in, z128* __restrict__ q) {
-  const size_t n = g.npts();
-  for (size_t p = blockIdx.x * (size_t)NT + threadIdx.x; p < n; p += (size_t)gridDim.x * NT) {
-    const double s = (double)(1 << faces_at(g, p));  // D^-1, an exact power of two
-    const z128 v = in[p];
-    q[p] = mkc<double>(s * v.re, -s * v.im);
+// q = D^-1 conj(in) elementwise; g.nb values per node (node-major, right-hand side innermost).
+// in and q may be the same buffer (each element is read, then written, by one thread).
+__global__ void __launch_bounds__(NT) k_adjoint_rhs(Grid g, const z128* in, z128* q) {
+  const size_t n = g.npts() * g.nb;
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT) {
+    const double s = (double)(1 << faces_at(g, e / g.nb));  // D^-1, an exact power of two
+    const z128 v = in[e];
+    q[e] = mkc<double>(s * v.re, -s * v.im);
   }
 }
 
+// x = conj(D x) elementwise, g.nb values per node
 __global__ void __launch_bounds__(NT) k_adjoint_finish(Grid g, z128* __restrict__ x) {
-  const size_t n = g.npts();
-  for (size_t p = blockIdx.x * (size_t)NT + threadIdx.x; p < n; p += (size_t)gridDim.x * NT) {
-    const double s = 1.0 / (double)(1 << faces_at(g, p));  // D, exact
-    const z128 v = x[p];
-    x[p] = mkc<double>(s * v.re, -s * v.im);
+  const size_t n = g.npts() * g.nb;
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < n; e += (size_t)gridDim.x * NT) {
+    const double s = 1.0 / (double)(1 << faces_at(g, e / g.nb));  // D, exact
+    const z128 v = x[e];
+    x[e] = mkc<double>(s * v.re, -s * v.im);
   }
 }
 
@@ -89,10 +92,10 @@ int blocks_for(size_t n) {
 }  // namespace
 
 void launch_adjoint_rhs(const Grid& g, const z128* in, z128* q, cudaStream_t st) {
-  k_adjoint_rhs<<<blocks_for(g.npts()), NT, 0, st>>>(g, in, q);
+  k_adjoint_rhs<<<blocks_for(g.npts() * g.nb), NT, 0, st>>>(g, in, q);
 }
 void launch_adjoint_finish(const Grid& g, z128* x, cudaStream_t st) {
-  k_adjoint_finish<<<blocks_for(g.npts()), NT, 0, st>>>(g, x);
+  k_adjoint_finish<<<blocks_for(g.npts() * g.nb), NT, 0, st>>>(g, x);
 }
 void launch_grad_k2(const Grid& g, const double* k2, const z128* u, const z128* lam, double* grad, cudaStream_t st) {
   k_grad_k2<<<blocks_for(g.npts()), NT, 0, st>>>(g, k2, u, lam, grad);

@@ -180,6 +180,9 @@ struct helm_ctx {
   long long reorth_steps = 0, arnoldi_steps = 0;
   // adjoint-state gradient buffers (allocated on first use)
   z128 *adj_u = nullptr, *adj_g = nullptr, *adj_l = nullptr;
+  // batched adjoint gradient: wavefields, receiver residuals and adjoint states of every source
+  z128 *adj_U = nullptr, *adj_G = nullptr, *adj_L = nullptr;
+  int adj_cap = 0;
   double* adj_part = nullptr;
   double* adj_norm = nullptr;
   int* adj_rec = nullptr;
@@ -1803,6 +1806,65 @@ helm_status krylov_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* 
 // Message slot of helm_last_error(NULL), shared with the context-free entry point.
 void helm_set_global_error(const char* msg) { g_create_error = msg; }
 
+namespace {
+
+// nrhs solves with A (or, adjoint, with A^H from a zero start) in chunks of <= 32 lockstep
+// right-hand sides; B, X device, nrhs vectors each.  The adjoint goes through the forward solver:
+// A nu = D^-1 conj(g), lambda = conj(D nu), applied in the batched layout.
+helm_status solve_batched_core(helm_ctx* c, int nrhs, const z128* B, z128* X, helm_solve_info* infos, cudaStream_t st,
+                               bool adjoint) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t n = c->n0;
+  helm_status worst = HELM_OK;
+  for (int start = 0; start < nrhs; start += 32) {
+    const int cnt = std::min(32, nrhs - start);
+    int nb = 1;
+    while (nb < cnt) nb <<= 1;
+    TRY(batch_alloc(c, nb));
+    BatchWS& W = c->bw;
+    Grid gb = c->L[0].g;
+    gb.nb = nb;
+    launch_to_batch(B + (size_t)start * n, W.Bt, n, nb, cnt, st);
+    if (adjoint) {
+      launch_adjoint_rhs(gb, W.Bt, W.Bt, st);
+      CU(cudaMemsetAsync(W.Xt, 0, n * nb * sizeof(z128), st));
+    } else {
+      launch_to_batch(X + (size_t)start * n, W.Xt, n, nb, cnt, st);
+    }
+    TRY(check_launch(c, "batch transpose"));
+    TRY(gmres_batched(c, nb, st));
+    if (adjoint) launch_adjoint_finish(gb, W.Xt, st);
+    launch_from_batch(W.Xt, X + (size_t)start * n, n, nb, cnt, st);
+    std::vector<int> it(nb);
+    std::vector<double> bn(nb), be(nb);
+    CU(cudaMemcpyAsync(it.data(), W.h.iters, sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(bn.data(), W.h.bnorm, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(be.data(), W.h.beta, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int r = 0; r < cnt; ++r) {
+      const double rr = bn[r] > 0.0 ? be[r] / bn[r] : 0.0;
+      helm_status sr = HELM_OK;
+      if (!(rr == rr) || rr == HUGE_VAL) sr = HELM_ENUMERIC;
+      else if (rr > c->p.tol) sr = HELM_ENOCONV;
+      if (sr != HELM_OK && worst != HELM_ENUMERIC) worst = sr;
+      if (infos) {
+        helm_solve_info& I = infos[start + r];
+        I.iterations = it[r];
+        I.restarts = 0;
+        I.rel_residual = rr;
+        I.status = (int)sr;
+        I.ms_total = ms;
+      }
+    }
+  }
+  if (worst == HELM_ENOCONV) fail(c, worst, "some right-hand sides reached max_iter (%d)", c->p.max_iter);
+  if (worst == HELM_ENUMERIC) fail(c, worst, "non-finite residual in a batched solve");
+  return worst;
+}
+
+}  // namespace
+
 extern "C" {
 
 void helm_default_params(helm_params* p) {
@@ -2312,7 +2374,45 @@ helm_status helm_adjoint_grad(helm_ctx* c, int nsrc, const int* src_nodes, int n
   int iters = 0, restarts = 0;
   helm_status worst = HELM_OK;
   double worst_rr = 0.0;
-  for (int s = 0; s < nsrc; ++s) {
+  const bool batched =
+      nsrc > 1 && (c->p.krylov == HELM_GMRES || c->p.krylov == HELM_FGMRES) && c->p.side == HELM_SIDE_RIGHT;
+  if (batched) {
+    // every source's forward solve in lockstep batches (helm_solve_batched), then every
+    // adjoint solve the same way: nsrc wavefields, right-hand sides and adjoint states
+    if (nsrc > c->adj_cap) {
+      TRY(dalloc(c, &c->adj_U, (size_t)nsrc * n));
+      TRY(dalloc(c, &c->adj_G, (size_t)nsrc * n));
+      TRY(dalloc(c, &c->adj_L, (size_t)nsrc * n));
+      c->adj_cap = nsrc;
+    }
+    for (int s = 0; s < nsrc; ++s) TRY(helm_rhs_point(c, 1, src_nodes + 3 * s, c->adj_G + (size_t)s * n, st));
+    CU(cudaMemsetAsync(c->adj_U, 0, (size_t)nsrc * n * sizeof(z128), st));
+    std::vector<helm_solve_info> fi(nsrc), ai(nsrc);
+    helm_status fs = solve_batched_core(c, nsrc, c->adj_G, c->adj_U, fi.data(), st, false);
+    if (fs == HELM_ENUMERIC || fs == HELM_ECUDA || fs == HELM_ENOMEM) return fs;
+    CU(cudaMemsetAsync(c->adj_G, 0, (size_t)nsrc * n * sizeof(z128), st));
+    for (int s = 0; s < nsrc; ++s) {
+      const int nb = launch_receiver_residual(nrec, c->adj_rec, c->adj_U + (size_t)s * n,
+                                              (const z128*)d_obs + (size_t)s * nrec, c->adj_G + (size_t)s * n,
+                                              c->adj_part, st);
+      launch_reduce_norm(c->adj_part, nb, c->adj_norm, st, nullptr);
+      double rn = 0.0;
+      CU(cudaMemcpyAsync(&rn, c->adj_norm, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      total += 0.5 * rn * rn;
+    }
+    helm_status as = solve_batched_core(c, nsrc, c->adj_G, c->adj_L, ai.data(), st, true);
+    if (as == HELM_ENUMERIC || as == HELM_ECUDA || as == HELM_ENOMEM) return as;
+    for (int s = 0; s < nsrc; ++s) {
+      launch_grad_k2(F.g, F.k2, c->adj_U + (size_t)s * n, c->adj_L + (size_t)s * n, grad_k2, st);
+      iters += fi[s].iterations + ai[s].iterations;
+      worst_rr = std::max(worst_rr, std::max(fi[s].rel_residual, ai[s].rel_residual));
+    }
+    TRY(check_launch(c, "helm_adjoint_grad"));
+    if (fs != HELM_OK) worst = fs;
+    if (as != HELM_OK) worst = as;
+  }
+  for (int s = 0; s < nsrc && !batched; ++s) {
     TRY(helm_rhs_point(c, 1, src_nodes + 3 * s, c->bs, st));
     CU(cudaMemsetAsync(c->adj_u, 0, n * sizeof(z128), st));
     helm_solve_info fi;
@@ -2353,51 +2453,20 @@ helm_status helm_adjoint_grad(helm_ctx* c, int nsrc, const int* src_nodes, int n
   return worst;
 }
 
+
 helm_status helm_solve_batched(helm_ctx* c, int nrhs, const void* B, void* X, helm_solve_info* infos, void* stream) {
   if (!c) return HELM_EINVAL;
   if (nrhs < 1 || !B || !X || B == X) return fail(c, HELM_EINVAL, "bad nrhs or NULL / aliased B, X");
   if (!is_device_ptr(B) || !is_device_ptr(X)) return fail(c, HELM_EINVAL, "B and X must be device pointers");
-  const auto t0 = std::chrono::steady_clock::now();
-  cudaStream_t st = (cudaStream_t)stream;
-  const size_t n = c->n0;
-  helm_status worst = HELM_OK;
-  for (int start = 0; start < nrhs; start += 32) {
-    const int cnt = std::min(32, nrhs - start);
-    int nb = 1;
-    while (nb < cnt) nb <<= 1;
-    TRY(batch_alloc(c, nb));
-    BatchWS& W = c->bw;
-    launch_to_batch((const z128*)B + (size_t)start * n, W.Bt, n, nb, cnt, st);
-    launch_to_batch((const z128*)X + (size_t)start * n, W.Xt, n, nb, cnt, st);
-    TRY(check_launch(c, "batch transpose"));
-    TRY(gmres_batched(c, nb, st));
-    launch_from_batch(W.Xt, (z128*)X + (size_t)start * n, n, nb, cnt, st);
-    std::vector<int> it(nb);
-    std::vector<double> bn(nb), be(nb);
-    CU(cudaMemcpyAsync(it.data(), W.h.iters, sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
-    CU(cudaMemcpyAsync(bn.data(), W.h.bnorm, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
-    CU(cudaMemcpyAsync(be.data(), W.h.beta, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    for (int r = 0; r < cnt; ++r) {
-      const double rr = bn[r] > 0.0 ? be[r] / bn[r] : 0.0;
-      helm_status sr = HELM_OK;
-      if (!(rr == rr) || rr == HUGE_VAL) sr = HELM_ENUMERIC;
-      else if (rr > c->p.tol) sr = HELM_ENOCONV;
-      if (sr != HELM_OK && worst != HELM_ENUMERIC) worst = sr;
-      if (infos) {
-        helm_solve_info& I = infos[start + r];
-        I.iterations = it[r];
-        I.restarts = 0;
-        I.rel_residual = rr;
-        I.status = (int)sr;
-        I.ms_total = ms;
-      }
-    }
-  }
-  if (worst == HELM_ENOCONV) fail(c, worst, "some right-hand sides reached max_iter (%d)", c->p.max_iter);
-  if (worst == HELM_ENUMERIC) fail(c, worst, "non-finite residual in a batched solve");
-  return worst;
+  return solve_batched_core(c, nrhs, (const z128*)B, (z128*)X, infos, (cudaStream_t)stream, false);
+}
+
+helm_status helm_solve_adjoint_batched(helm_ctx* c, int nrhs, const void* G, void* Lambda, helm_solve_info* infos,
+                                       void* stream) {
+  if (!c) return HELM_EINVAL;
+  if (nrhs < 1 || !G || !Lambda || G == Lambda) return fail(c, HELM_EINVAL, "bad nrhs or NULL / aliased G, Lambda");
+  if (!is_device_ptr(G) || !is_device_ptr(Lambda)) return fail(c, HELM_EINVAL, "G and Lambda must be device pointers");
+  return solve_batched_core(c, nrhs, (const z128*)G, (z128*)Lambda, infos, (cudaStream_t)stream, true);
 }
 
 helm_status helm_set_shadow_space(helm_ctx* c, int s, const void* P, void* stream) {

@@ -232,9 +232,10 @@ void launch_to_batch(const z128* src, z128* dst, size_t n, int nb, int nrhs, cud
 void launch_from_batch(const z128* src, z128* dst, size_t n, int nb, int nrhs, cudaStream_t st);
 
 // ---- adjoint-state gradient (adjoint.cu) ----
-// q = D^-1 conj(in), D = diag(2^-faces) (Sommerfeld) or I (Dirichlet)
+// q = D^-1 conj(in), D = diag(2^-faces) (Sommerfeld) or I (Dirichlet); g.nb values per node
+// (the batched layout); in == q allowed
 void launch_adjoint_rhs(const Grid& g, const z128* in, z128* q, cudaStream_t st);
-// x = conj(D x)
+// x = conj(D x), g.nb values per node
 void launch_adjoint_finish(const Grid& g, z128* x, cudaStream_t st);
 // grad += -Re(conj(lam) (-1 - i nf / (h k)) u)
 void launch_grad_k2(const Grid& g, const double* k2, const z128* u, const z128* lam, double* grad, cudaStream_t st);

@@ -100,6 +100,8 @@ def lib():
     L.helm_solve_batched.argtypes = [vp, i, vp, vp, C.POINTER(SolveInfo), vp]
     L.helm_solve_batched.restype = i
     L.helm_solve_adjoint.argtypes = [vp, vp, vp, C.POINTER(SolveInfo), vp]
+    L.helm_solve_adjoint_batched.argtypes = [vp, i, vp, vp, C.POINTER(SolveInfo), vp]
+    L.helm_solve_adjoint_batched.restype = i
     L.helm_grad_k2.argtypes = [vp, vp, vp, vp, vp]
     L.helm_adjoint_grad.argtypes = [vp, i, C.POINTER(i), i, C.POINTER(i), vp, vp, C.POINTER(d), C.POINTER(SolveInfo),
                                     vp]
@@ -405,6 +407,20 @@ class Solver:
             self._check(st)
         return lam, info.as_dict()
 
+    def solve_adjoint_batched(self, G):
+        """Lambda with A^H Lambda_r = G_r for every r at once (complex128 CUDA, shaped
+        (nrhs, N3, N2, N1)); returns (Lambda, infos)."""
+        G = G.reshape((-1,) + self.shape).contiguous()
+        if G.dtype != torch.complex128 or G.device.type != "cuda":
+            raise TypeError("G must be a complex128 CUDA tensor")
+        nrhs = G.shape[0]
+        L = torch.empty_like(G)
+        infos = (SolveInfo * nrhs)()
+        st = lib().helm_solve_adjoint_batched(self._ctx, nrhs, _ptr(G), _ptr(L), infos, _stream())
+        if st not in (OK, ENOCONV):
+            self._check(st)
+        return L, [infos[r].as_dict() for r in range(nrhs)]
+
     def grad_k2(self, u, lam, grad=None):
         """grad += -Re(conj(lambda) dA/dk^2 u) at every node (float64 tensor shaped like u)."""
         u = self._vec(u, dtype=torch.complex128)
@@ -454,35 +470,59 @@ class Solver:
 class HelmholtzSolve(torch.autograd.Function):
     """x = A(k^2)^{-1} b as a differentiable torch op.
 
-    forward builds a context for k^2 and solves; backward solves the adjoint system
-    A^H lambda = dL/d conj(x) with the same preconditioned solver and returns
-    dL/dk^2 = -Re(conj(lambda) dA/dk^2 x) and dL/d conj(b) = lambda.  With recompute=True the
-    forward wavefield is not kept and backward solves for it again (checkpointing when
-    memory is short)."""
+    b is one right-hand side shaped like the grid, or several sources shaped (nsrc,) + grid
+    (solved together by helm_solve_batched).  forward builds a context for k^2 and solves;
+    backward solves the adjoint systems A^H lambda = dL/d conj(x) with the same preconditioned
+    solver (helm_solve_adjoint_batched for several sources) and returns
+    dL/dk^2 = -sum_s Re(conj(lambda_s) dA/dk^2 x_s) and dL/d conj(b) = lambda.
+
+    recompute: True drops the forward wavefields and solves for them again in backward
+    (checkpointing); False keeps them; None (default) keeps them when they take at most a
+    quarter of the device memory that is free after the forward solve (cudaMemGetInfo), so
+    that the adjoint solves still have room, and recomputes otherwise."""
 
     @staticmethod
-    def forward(ctx, k2, b, n, h, bc, opts=None, recompute=False):
+    def forward(ctx, k2, b, n, h, bc, opts=None, recompute=None):
         opts = dict(opts or {})
         s = Solver(n, h, k2.detach(), bc, **opts)
-        bb = b.detach().reshape(s.shape).contiguous()
-        x, info = s.solve(bb)
-        if info["status"] not in (OK,):
-            raise HelmError(info["status"], "forward solve did not converge")
+        batched = b.dim() == 4
+        bb = b.detach().reshape(((-1,) if batched else ()) + s.shape).contiguous()
+        if batched:
+            x, infos = s.solve_batched(bb)
+        else:
+            x, info = s.solve(bb)
+            infos = [info]
+        if any(i["status"] != OK for i in infos):
+            raise HelmError(max(i["status"] for i in infos), "forward solve did not converge")
+        if recompute is None:
+            free, _ = torch.cuda.mem_get_info(x.device)
+            recompute = x.numel() * x.element_size() > free // 4
         ctx.solver = s
-        ctx.recompute = recompute
-        ctx.save_for_backward(bb if recompute else x)
+        ctx.batched = batched
+        ctx.recompute = bool(recompute)
+        ctx.save_for_backward(bb if ctx.recompute else x)
         return x
 
     @staticmethod
     def backward(ctx, gx):
         s = ctx.solver
         (saved,) = ctx.saved_tensors
-        x = s.solve(saved)[0] if ctx.recompute else saved
-        lam, info = s.solve_adjoint(gx.reshape(s.shape).contiguous())
-        gk2 = s.grad_k2(x, lam)
+        if ctx.recompute:
+            x = s.solve_batched(saved)[0] if ctx.batched else s.solve(saved)[0]
+        else:
+            x = saved
+        g = gx.reshape(x.shape).contiguous()
+        if ctx.batched:
+            lam, _ = s.solve_adjoint_batched(g)
+            gk2 = torch.zeros(s.shape, dtype=torch.float64, device=x.device)
+            for r in range(x.shape[0]):
+                s.grad_k2(x[r], lam[r], gk2)
+        else:
+            lam, _ = s.solve_adjoint(g)
+            gk2 = s.grad_k2(x, lam)
         return gk2, lam, None, None, None, None, None
 
 
-def helmholtz_solve(k2, b, n, h, bc=SOMMERFELD, opts=None, recompute=False):
+def helmholtz_solve(k2, b, n, h, bc=SOMMERFELD, opts=None, recompute=None):
     """Differentiable x = A(k^2)^{-1} b (see HelmholtzSolve)."""
     return HelmholtzSolve.apply(k2, b, n, h, bc, opts, recompute)
