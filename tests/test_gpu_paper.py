@@ -95,8 +95,11 @@ def test_table1_counts(helm):
     assert abs(g - ro["iters"]) <= 0.1 * ro["iters"], (g, ro["iters"])
     assert 0.9 * min(t["IDR(4)"]) <= g <= 1.1 * max(t["IDR(4)"]), g
 
-    # Bi-CGSTAB's count moves most with rounding order (Sec. 5.1.3: 359-407 over layouts); the
-    # coarsest inverse alone, eliminated in another order, moves the GPU's count by 5%
+    # Bi-CGSTAB's count moves most with rounding order (Sec. 5.1.3: 359-407 over layouts) and with
+    # the coarsest-grid solve: the library solves it exactly, where the paper runs GMRES to 1e-11,
+    # and the oracle measures 321 products exactly against 347 with the paper's coarse solver
+    # (test_oracle_paper); the coarsest inverse alone, eliminated in another order, moves the
+    # GPU's count by 5%.  Hence the lower bound of 0.8 of the paper's smallest count.
     g = gpu_count(helm, w, "bicgstab")
     ro = o.bicgstab(w["rhs"], tol=1e-6, max_iter=2000)
     assert abs(g - ro["iters"]) <= 0.1 * ro["iters"], (g, ro["iters"])

@@ -80,6 +80,22 @@ def test_table1_gmres_with_the_papers_coarse_solver():
     assert abs(r["iters"] - table1()["GMRES"][0]) <= 2, r["iters"]
 
 
+@pytest.mark.slow
+def test_table1_bicgstab_with_the_papers_coarse_solver():
+    """Bi-CGSTAB's count depends on the coarsest-grid solve: with the exact solve the oracle
+    takes 321 products with A, 11% under the paper's 359 on one process (Table 1), while with
+    the paper's own coarse solver, full GMRES to 1e-11 (Sec. 5), it takes 347, inside the spread
+    the paper prints over its processor layouts (359-407) widened by 5%.  GMRES, whose count is
+    insensitive to this (previous test), and IDR(4) agree either way."""
+    n, k = 64, 40.0
+    shape = I.unknown_shape(n, oracle.DIRICHLET)
+    o = oracle.Solver(n, 1.0 / n, oracle.DIRICHLET, np.full(shape, k * k), coarsest_n=16, coarse_tol=1e-11)
+    r = o.bicgstab(oracle.rhs_closed_off(n, k), tol=1e-6, max_iter=2000)
+    t = table1()["Bi-CGSTAB"]
+    assert r["status"] == 0
+    assert 0.95 * min(t) <= r["iters"] <= 1.05 * max(t), r["iters"]
+
+
 def test_seventeen_node_rule():
     """Sec. 4.2's coarsening stop, on the grids the paper names: the closed-off cubes of
     Tables 1-2 and the salt grid, whose coarsest grid the paper gives as 41 x 41 x 13 nodes
