@@ -97,9 +97,11 @@ __global__ void __launch_bounds__(TX* TY)
   // FP32 (memory-bound): the next trip's z neighbour, k^2 and b are loaded one trip ahead, so
   // each thread keeps two planes' loads in flight
   constexpr bool PF = std::is_same<R, float>::value;
+  // the prefetched b stays in its stored precision until it is used: a conversion right after
+  // the load would wait for the load and undo the prefetch
   cx<R> upf = (PF && k0 + 1 < g.N3) ? ld(e + Se) : zero_c<R>();
   R kpf = PF ? __ldg(k2 + p) : (R)0;
-  cx<R> bpf = (PF && MODE != 0) ? cvt<R>(ldg(b + e)) : zero_c<R>();
+  cx<TB> bpf = (PF && MODE != 0) ? ldg(b + e) : zero_c<TB>();
   for (int k = k0; k < k1; ++k, p += S, e += Se) {
     const bool hzp = k + 1 < g.N3;
     cx<R> up, bv = zero_c<R>();
@@ -107,11 +109,11 @@ __global__ void __launch_bounds__(TX* TY)
     if constexpr (PF) {
       up = upf;
       kk = kpf;
-      bv = bpf;
+      bv = cvt<R>(bpf);
       if (k + 1 < k1) {
         upf = k + 2 < g.N3 ? ld(e + 2 * Se) : zero_c<R>();
         kpf = __ldg(k2 + p + S);
-        if (MODE != 0) bpf = cvt<R>(ldg(b + e + Se));
+        if (MODE != 0) bpf = ldg(b + e + Se);
       }
     } else {
       up = hzp ? ld(e + Se) : zero_c<R>();
@@ -660,7 +662,7 @@ __global__ void __launch_bounds__(TX* TY)
   // FP32: b and k^2 of the next trip are loaded one trip ahead (two planes of loads in flight)
   constexpr bool PF = !DINV && std::is_same<R, float>::value;
   R kpf = PF && k0 < k1 ? __ldg(k2 + p) : (R)0;
-  cx<R> bpf = PF && k0 < k1 ? cvt<R>(ldg(b + e)) : zero_c<R>();
+  cx<TB> bpf = PF && k0 < k1 ? ldg(b + e) : zero_c<TB>();  // converted when used (see k_stencil)
   for (int k = k0; k < k1; ++k, p += S, e += S * nb) {
     cx<R> w, bv;
     if (DINV) {
@@ -671,10 +673,10 @@ __global__ void __launch_bounds__(TX* TY)
       R kk;
       if constexpr (PF) {
         kk = kpf;
-        bv = bpf;
+        bv = cvt<R>(bpf);
         if (k + 1 < k1) {
           kpf = __ldg(k2 + p + S);
-          bpf = cvt<R>(ldg(b + e + S * nb));
+          bpf = ldg(b + e + S * nb);
         }
       } else {
         kk = __ldg(k2 + p);
