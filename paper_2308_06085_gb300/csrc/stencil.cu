@@ -24,34 +24,68 @@ __device__ __forceinline__ cx<T> zero_c() {
 }
 
 // Full weighting (Sec. 3.4.2) in one fixed order that every restriction kernel shares, so that
-// the separate and the fused forms give identical results: per fine plane dz in {-1, 0, 1}
-// around the fine centre, the in-plane sum p_dz = sum over dy, dx of w_y w_x r (w = 2 at the
-// centre line, 1 beside it; one FMA chain, dy outer, dx inner, fine points outside the grid
-// skipped), then b_H = ((p_-1 + 2 p_0) + p_+1) / 64 with p = 0 for planes outside the grid.
+// the separate and the fused forms give identical results.  The weights (8, 4, 2, 1) / 64 are
+// the product of (1, 2, 1) / 4 along each axis, applied x first: per fine line
+// fx = 2 r_0 + (r_-1 + r_+1), per fine plane p = 2 fx_0 + (fx_-1 + fx_+1), and
+// b_H = (2 p_0 + (p_-1 + p_+1)) / 64, each as one FMA after one addition; fine values outside
+// the grid count as 0.
+template <typename R>
+__device__ __forceinline__ cx<R> fw3(cx<R> m, cx<R> c, cx<R> p) {
+  return mkc<R>(fma((R)2, c.re, m.re + p.re), fma((R)2, c.im, m.im + p.im));
+}
 template <typename R, typename Get>
 __device__ __forceinline__ cx<R> fw_plane(int fi, int fj, int N1, int N2, Get&& get) {
-  R are = 0, aim = 0;
+  cx<R> fx[3];
   for (int dy = -1; dy <= 1; ++dy) {
     const int y = fj + dy;
-    if (y < 0 || y >= N2) continue;
-    const R wy = dy ? (R)1 : (R)2;
+    cx<R> v[3];
     for (int dx = -1; dx <= 1; ++dx) {
       const int x = fi + dx;
-      if (x < 0 || x >= N1) continue;
-      const R w = wy * (dx ? (R)1 : (R)2);
-      const cx<R> v = get(x, y);
-      are = fma(w, v.re, are);
-      aim = fma(w, v.im, aim);
+      v[dx + 1] = (y >= 0 && y < N2 && x >= 0 && x < N1) ? get(x, y) : mkc<R>((R)0, (R)0);
     }
+    fx[dy + 1] = fw3(v[0], v[1], v[2]);
   }
-  return mkc<R>(are, aim);
+  return fw3(fx[0], fx[1], fx[2]);
 }
 template <typename R>
 __device__ __forceinline__ cx<R> fw_combine(cx<R> pm, cx<R> p0, cx<R> pp) {
-  R re = fma((R)2, p0.re, pm.re), im = fma((R)2, p0.im, pm.im);
-  re = re + pp.re;
-  im = im + pp.im;
-  return mkc<R>(re * (R)(1.0 / 64.0), im * (R)(1.0 / 64.0));
+  const cx<R> t = fw3(pm, p0, pp);
+  return mkc<R>(t.re * (R)(1.0 / 64.0), t.im * (R)(1.0 / 64.0));
+}
+
+// Trilinear interpolation (Sec. 3.4.3) in one fixed order shared by every prolongation kernel.
+// A fine node at an odd node index along an axis lies between the coarse nodes either side, at
+// an even index on one; coarse parents outside the unknown set (Dirichlet boundary) count as 0,
+// and the divisor counts every parent.  The parents are summed y first, then z, then x:
+// ty(X, Z) = e(X, y0, Z) [+ e(X, y1, Z)], tz(X) = ty(X, z0) [+ ty(X, z1)],
+// t = tz(x0) [+ tz(x1)], and u2 = u1 + t / (nx ny nz) as one FMA per component.
+template <typename R>
+__device__ __forceinline__ R tl_scale(int cnt) {  // 1 / cnt for cnt in {1, 2, 4, 8}, without a division
+  return cnt == 1 ? (R)1 : cnt == 2 ? (R)0.5 : cnt == 4 ? (R)0.25 : (R)0.125;
+}
+template <typename R, typename Get>
+__device__ __forceinline__ cx<R> tl_value(int fi, int fj, int fk, int off, const Grid& gc, cx<R> base, Get&& get) {
+  const int xs[2] = {(fi >> 1) - off, ((fi + 1) >> 1) - off};
+  const int ys[2] = {(fj >> 1) - off, ((fj + 1) >> 1) - off};
+  const int zs[2] = {(fk >> 1) - off, ((fk + 1) >> 1) - off};
+  const int nx = xs[0] == xs[1] ? 1 : 2, ny = ys[0] == ys[1] ? 1 : 2, nz = zs[0] == zs[1] ? 1 : 2;
+  auto val = [&](int X, int Y, int Z) {
+    return (X >= 0 && X < gc.N1 && Y >= 0 && Y < gc.N2 && Z >= 0 && Z < gc.N3) ? get(X, Y, Z) : mkc<R>((R)0, (R)0);
+  };
+  auto ty = [&](int X, int Z) {
+    cx<R> v = val(X, ys[0], Z);
+    if (ny == 2) v = cadd(v, val(X, ys[1], Z));
+    return v;
+  };
+  auto tz = [&](int X) {
+    cx<R> v = ty(X, zs[0]);
+    if (nz == 2) v = cadd(v, ty(X, zs[1]));
+    return v;
+  };
+  cx<R> t = tz(xs[0]);
+  if (nx == 2) t = cadd(t, tz(xs[1]));
+  const R sc = tl_scale<R>(nx * ny * nz);
+  return mkc<R>(fma(t.re, sc, base.re), fma(t.im, sc, base.im));
 }
 
 // One stencil kernel for three uses (MODE):
@@ -458,36 +492,13 @@ __global__ void __launch_bounds__(TX* UTY)
   const int tid = threadIdx.y * TX + threadIdx.x;
   auto fill = [&](int z) {
     cx<R>(*U)[UWX] = su[z % 3];
-    const int fk = z + off;
-    const int cz0 = (fk >> 1) - off, cz1 = ((fk + 1) >> 1) - off;
-    const int nz = cz0 == cz1 ? 1 : 2;
     for (int t = tid; t < UWX * UWY; t += TX * UTY) {
       const int ly = t / UWX, lx = t - ly * UWX;
       const int x = x0 - 1 + lx, y = y0 - 1 + ly;
       cx<R> v = z0;
-      if (x >= 0 && x < N1 && y >= 0 && y < N2) {
-        const int fi = x + off, fj = y + off;
-        const int cxs[2] = {(fi >> 1) - off, ((fi + 1) >> 1) - off};
-        const int cys[2] = {(fj >> 1) - off, ((fj + 1) >> 1) - off};
-        const int czs[2] = {cz0, cz1};
-        const int nx = cxs[0] == cxs[1] ? 1 : 2, ny = cys[0] == cys[1] ? 1 : 2;
-        R are = 0, aim = 0;
-        for (int cq = 0; cq < nz; ++cq) {
-          if (czs[cq] < 0 || czs[cq] >= gc.N3) continue;
-          for (int bq = 0; bq < ny; ++bq) {
-            if (cys[bq] < 0 || cys[bq] >= gc.N2) continue;
-            for (int a = 0; a < nx; ++a) {
-              if (cxs[a] < 0 || cxs[a] >= gc.N1) continue;
-              const cx<R> ev = ldg(e + gidx(cxs[a], cys[bq], czs[cq], gc.N1, gc.N2));
-              are += ev.re;
-              aim += ev.im;
-            }
-          }
-        }
-        const R sc = (R)1 / (R)(nx * ny * nz);
-        const cx<R> base = ldg(u1 + gidx(x, y, z, N1, N2));
-        v = mkc<R>(fma(are, sc, base.re), fma(aim, sc, base.im));
-      }
+      if (x >= 0 && x < N1 && y >= 0 && y < N2)
+        v = tl_value<R>(x + off, y + off, z + off, off, gc, ldg(u1 + gidx(x, y, z, N1, N2)),
+                        [&](int X, int Y, int Z) { return ldg(e + gidx(X, Y, Z, gc.N1, gc.N2)); });
       U[ly][lx] = v;
     }
   };
@@ -736,6 +747,54 @@ __global__ void __launch_bounds__(TX* TY)
   }
 }
 
+// Full weighting for one right-hand side with the x-neighbourhood shared along a warp: lane l
+// owns coarse x index X = X0 + l, loads the fine values at 2X + off and 2X + off + 1 of each fine
+// line it needs and takes the one at 2X + off - 1 from the lane before (lane 0 loads it).  A
+// thread streams the coarse planes of its chunk and carries the in-plane sum of the shared fine
+// plane 2Z + off + 1 into the next coarse plane, so each fine plane is filtered once per coarse
+// column.  Same sums in the same order as fw_plane / fw_combine, so the results equal
+// k_restrict's.
+constexpr int RTY = 8;
+template <typename R>
+__global__ void __launch_bounds__(TX* RTY)
+    k_restrict2(Grid gf, Grid gc, const cx<R>* __restrict__ r, cx<R>* __restrict__ out, int zchunk,
+                const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const int off = gf.bc == 0 ? 1 : 0;
+  const int lane = threadIdx.x;
+  const int X = blockIdx.x * TX + lane, Y = blockIdx.y * blockDim.y + threadIdx.y;
+  const bool own = X < gc.N1 && Y < gc.N2;
+  const int fi = 2 * X + off, fj = 2 * Y + off;
+  const cx<R> z0 = zero_c<R>();
+  // fine value, 0 outside the grid; lanes without a coarse point load nothing (their values are
+  // only ever passed to lanes that have none either)
+  auto at = [&](int x, int y, int z) {
+    return own && x >= 0 && x < gf.N1 && y >= 0 && y < gf.N2 && z >= 0 && z < gf.N3 ? ldg(r + gidx(x, y, z, gf.N1, gf.N2))
+                                                                                   : z0;
+  };
+  // the in-plane sum p of fine plane z for this lane's coarse column
+  auto plane = [&](int z) {
+    cx<R> fx[3];
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int y = fj + dy;
+      const cx<R> c = at(fi, y, z), pnext = at(fi + 1, y, z);
+      cx<R> m = mkc<R>(__shfl_up_sync(0xffffffffu, pnext.re, 1), __shfl_up_sync(0xffffffffu, pnext.im, 1));
+      if (lane == 0) m = at(fi - 1, y, z);
+      fx[dy + 1] = fw3(m, c, pnext);
+    }
+    return fw3(fx[0], fx[1], fx[2]);
+  };
+  const int K0 = blockIdx.z * zchunk, K1 = min(K0 + zchunk, gc.N3);
+  if (K0 >= K1) return;  // the whole CTA
+  cx<R> pm = plane(2 * K0 + off - 1);
+  for (int K = K0; K < K1; ++K) {
+    const int fk = 2 * K + off;
+    const cx<R> p0 = plane(fk), pp = plane(fk + 1);
+    if (own) out[gidx(X, Y, K, gc.N1, gc.N2)] = fw_combine(pm, p0, pp);
+    pm = pp;
+  }
+}
+
 // Trilinear interpolation (Sec. 3.4.3) added to u1: out = u1 + I_H^h e.  A fine node at
 // an odd node index along an axis averages the two coarse nodes either side; coarse
 // values outside the unknown set (Dirichlet boundary) are 0.
@@ -752,32 +811,74 @@ __global__ void __launch_bounds__(TX* TY)
   const int k0 = blockIdx.z * zchunk;
   const int k1 = min(k0 + zchunk, gf.N3);
   const int off = gf.bc == 0 ? 1 : 0;
-  int cx_[2], cy_[2];
-  const int fi = i + off, fj = j + off;
-  cx_[0] = (fi >> 1) - off; cx_[1] = ((fi + 1) >> 1) - off;
-  cy_[0] = (fj >> 1) - off; cy_[1] = ((fj + 1) >> 1) - off;
-  const int nx = (cx_[0] == cx_[1]) ? 1 : 2, ny = (cy_[0] == cy_[1]) ? 1 : 2;
   for (int k = k0; k < k1; ++k) {
-    const int fk = k + off;
-    int cz_[2] = {(fk >> 1) - off, ((fk + 1) >> 1) - off};
-    const int nz = (cz_[0] == cz_[1]) ? 1 : 2;
-    R are = 0, aim = 0;
-    for (int c = 0; c < nz; ++c) {
-      if (cz_[c] < 0 || cz_[c] >= gc.N3) continue;
-      for (int bq = 0; bq < ny; ++bq) {
-        if (cy_[bq] < 0 || cy_[bq] >= gc.N2) continue;
-        for (int a = 0; a < nx; ++a) {
-          if (cx_[a] < 0 || cx_[a] >= gc.N1) continue;
-          const cx<R> v = ldg(e + gidx(cx_[a], cy_[bq], cz_[c], gc.N1, gc.N2) * nb + q);
-          are += v.re;
-          aim += v.im;
-        }
-      }
-    }
-    const R s = (R)1 / (R)(nx * ny * nz);
     const size_t p = gidx(i, j, k, gf.N1, gf.N2) * nb + q;
-    const cx<R> base = ldg(u1 + p);
-    out[p] = mkc<R>(fma(are, s, base.re), fma(aim, s, base.im));
+    out[p] = tl_value<R>(i + off, j + off, k + off, off, gc, ldg(u1 + p),
+                         [&](int X, int Y, int Z) { return ldg(e + gidx(X, Y, Z, gc.N1, gc.N2) * nb + q); });
+  }
+}
+
+// Trilinear interpolation added to u1 for one right-hand side with two fine points per lane
+// along x: lane l owns coarse x node c = c0 + l and the fine nodes 2c and 2c + 1; the odd one
+// needs tz of node c + 1, taken from the next lane by a shuffle (the last lane of a warp only
+// supplies it, so warps step 31 coarse nodes).  A thread streams the coarse z nodes of its
+// chunk: each coarse plane's y-sum ty is formed once and serves the fine planes 2Z - 1 (with the
+// previous plane's) and 2Z.  Coarse loads are coalesced and no lane branches on parity.  Same
+// sums in the same order as tl_value, so the results equal k_prolong_add's.
+constexpr int PTY = 8;
+template <typename R>
+__global__ void __launch_bounds__(TX* PTY)
+    k_prolong2(Grid gf, Grid gc, const cx<R>* __restrict__ u1, const cx<R>* __restrict__ e,
+               cx<R>* __restrict__ out, int zchunk, const int* __restrict__ active) {
+  if (active && *active == 0) return;
+  const int off = gf.bc == 0 ? 1 : 0;
+  const int lane = threadIdx.x;
+  const int cn = blockIdx.x * (TX - 1) + lane;         // coarse x node
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;  // fine y index
+  const bool rowok = j < gf.N2;
+  const int X = cn - off;
+  const bool xok = X >= 0 && X < gc.N1;
+  const int fj = j + off, y0 = (fj >> 1) - off, y1 = ((fj + 1) >> 1) - off;
+  const int ny = y0 == y1 ? 1 : 2;
+  const bool y0ok = rowok && xok && y0 >= 0 && y0 < gc.N2, y1ok = rowok && xok && y1 >= 0 && y1 < gc.N2;
+  const int ie = 2 * cn - off, io = ie + 1;  // fine x indices of nodes 2c, 2c + 1
+  const bool eok = rowok && ie >= 0 && ie < gf.N1;
+  const bool ook = rowok && lane < TX - 1 && io >= 0 && io < gf.N1;
+  const cx<R> z0 = zero_c<R>();
+  auto ty = [&](int Zn) {  // y-sum at coarse z node Zn (0 outside the grid)
+    const int Z = Zn - off;
+    const bool zok = Z >= 0 && Z < gc.N3;
+    cx<R> v = (y0ok && zok) ? ldg(e + gidx(X, y0, Z, gc.N1, gc.N2)) : z0;
+    if (ny == 2) v = cadd(v, (y1ok && zok) ? ldg(e + gidx(X, y1, Z, gc.N1, gc.N2)) : z0);
+    return v;
+  };
+  // one fine plane (node fz, fine index k = fz - off) from this lane's tz
+  auto emit = [&](int fz, cx<R> tz, int nz) {
+    const cx<R> tr = mkc<R>(__shfl_down_sync(0xffffffffu, tz.re, 1), __shfl_down_sync(0xffffffffu, tz.im, 1));
+    const int k = fz - off;
+    if (k < 0 || k >= gf.N3) return;
+    if (eok) {
+      const size_t p = gidx(ie, j, k, gf.N1, gf.N2);
+      const cx<R> b = ldg(u1 + p);
+      const R sc = tl_scale<R>(ny * nz);
+      out[p] = mkc<R>(fma(tz.re, sc, b.re), fma(tz.im, sc, b.im));
+    }
+    if (ook) {
+      const size_t p = gidx(io, j, k, gf.N1, gf.N2);
+      const cx<R> b = ldg(u1 + p);
+      const cx<R> t = cadd(tz, tr);
+      const R sc = tl_scale<R>(2 * ny * nz);
+      out[p] = mkc<R>(fma(t.re, sc, b.re), fma(t.im, sc, b.im));
+    }
+  };
+  const int nzn = gc.N3 + 2 * off;  // coarse z nodes, the Dirichlet boundary nodes included
+  const int zn0 = blockIdx.z * zchunk, zn1 = min(zn0 + zchunk, nzn);
+  cx<R> prev = zn0 > 0 ? ty(zn0 - 1) : z0;
+  for (int Zn = zn0; Zn < zn1; ++Zn) {
+    const cx<R> cur = ty(Zn);
+    if (Zn > 0) emit(2 * Zn - 1, cadd(prev, cur), 2);
+    emit(2 * Zn, cur, 1);
+    prev = cur;
   }
 }
 
@@ -1259,27 +1360,8 @@ __global__ void __launch_bounds__(CC_THREADS)
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
       int i, j, k;
       cc_ijk<R>(gf, q, i, j, k);
-      const int fi = i + off, fj = j + off, fk = k + off;
-      const int cx_[2] = {(fi >> 1) - off, ((fi + 1) >> 1) - off};
-      const int cy_[2] = {(fj >> 1) - off, ((fj + 1) >> 1) - off};
-      const int cz_[2] = {(fk >> 1) - off, ((fk + 1) >> 1) - off};
-      const int nx = (cx_[0] == cx_[1]) ? 1 : 2, ny = (cy_[0] == cy_[1]) ? 1 : 2, nz = (cz_[0] == cz_[1]) ? 1 : 2;
-      R are = 0, aim = 0;
-      for (int c = 0; c < nz; ++c) {
-        if (cz_[c] < 0 || cz_[c] >= gc.N3) continue;
-        for (int bq = 0; bq < ny; ++bq) {
-          if (cy_[bq] < 0 || cy_[bq] >= gc.N2) continue;
-          for (int a = 0; a < nx; ++a) {
-            if (cx_[a] < 0 || cx_[a] >= gc.N1) continue;
-            const cx<R> v = e[(cz_[c] * gc.N2 + cy_[bq]) * gc.N1 + cx_[a]];
-            are += v.re;
-            aim += v.im;
-          }
-        }
-      }
-      const R s = (R)1 / (R)(nx * ny * nz);
-      const cx<R> base = sm[F.off_u + q];
-      sm[F.off_t + q] = mkc<R>(fma(are, s, base.re), fma(aim, s, base.im));
+      sm[F.off_t + q] = tl_value<R>(i + off, j + off, k + off, off, gc, sm[F.off_u + q],
+                                    [&](int X, int Y, int Z) { return e[(Z * gc.N2 + Y) * gc.N1 + X]; });
     }
     __syncthreads();
     cc_stencil<R, 2>(F, cc_coef(cc, gf.h), sm, smr, F.off_t, sm + F.off_u);
@@ -1543,13 +1625,29 @@ template <typename R>
 void launch_restrict(const Grid& gf, const Grid& gc, const cx<R>* r, cx<R>* out, cudaStream_t st, const int* active) {
   int zc;
   dim3 blk, gr = grid_for<R>(gc, TILE_RESTRICT, zc, blk);
-  k_restrict<R><<<gr, blk, 0, st>>>(gf, gc, r, out, zc, active);
+  if (gc.nb == 1)  // lanes along x share the fine neighbourhood; same shape rules as k_restrict
+    k_restrict2<R><<<gr, blk, 0, st>>>(gf, gc, r, out, zc, active);
+  else
+    k_restrict<R><<<gr, blk, 0, st>>>(gf, gc, r, out, zc, active);
 }
 
 template <typename R>
 void launch_prolong_add(const Grid& gf, const Grid& gc, const cx<R>* u1, const cx<R>* e, cx<R>* out, cudaStream_t st,
                         const int* active) {
   int zc;
+  if (gf.nb == 1) {  // two fine points per lane; the tuned shape sets rows per CTA and the z-chunk
+    const int slot = tile_slot<R>(TILE_PROLONG);
+    const int ty = gf.tile_ty[slot] > 0 ? gf.tile_ty[slot] : PTY;
+    const int target = gf.tile_ctas[slot] > 0 ? gf.tile_ctas[slot] : 152 * 8;
+    const int off = gf.bc == 0 ? 1 : 0;
+    const int bx = (gc.N1 + 2 * off + TX - 2) / (TX - 1), by = (gf.N2 + ty - 1) / ty, nzn = gc.N3 + 2 * off;
+    int zsplit = target / (bx * by);
+    if (zsplit < 1) zsplit = 1;
+    if (zsplit > nzn) zsplit = nzn;
+    zc = (nzn + zsplit - 1) / zsplit;
+    k_prolong2<R><<<dim3(bx, by, (nzn + zc - 1) / zc), dim3(TX, ty), 0, st>>>(gf, gc, u1, e, out, zc, active);
+    return;
+  }
   dim3 blk, gr = grid_for<R>(gf, TILE_PROLONG, zc, blk);
   k_prolong_add<R><<<gr, blk, 0, st>>>(gf, gc, u1, e, out, zc, active);
 }
