@@ -312,7 +312,8 @@ def peaks():
 
 def kernel_rows(fams, steps):
     total = sum(f["ms"] for f in fams)
-    return [{"name": f["name"], "launches": f["launches"], "ms_per_step": f["ms"] / steps,
+    return [{"name": f["name"], "launches": f["launches"], "launches_per_step": f["launches"] / steps,
+             "ms_per_step": f["ms"] / steps,
              "share": f["ms"] / total if total else None,
              "gbs": f["bytes"] / (f["ms"] * 1e-3) / 1e9 if f["ms"] else None,
              "fp64_tflops": f["flops"] / (f["ms"] * 1e-3) / 1e12 if f["ms"] else None}
@@ -637,9 +638,11 @@ def _family_of(kernel):
         args = [a.strip() for a in targs.split(",")]
         return {"0": "k_stencil(apply)", "1": "k_stencil(resid)", "2": "k_stencil(jacobi)"}.get(
             args[1] if len(args) > 1 else "")
-    if base in ("k_mdot", "k_gs_update", "k_gs_update_sums", "k_smooth0", "k_restrict", "k_prolong_add",
-                "k_smooth0_resid32", "k_down32", "k_up32", "k_down64", "k_up64"):
-        return {"k_gs_update_sums": "k_gs_update", "k_smooth0_resid32": "k_smooth0"}.get(base, base)
+    alias = {"k_gs_update_sums": "k_gs_update", "k_smooth0_resid32": "k_smooth0", "k_restrict2": "k_restrict",
+             "k_prolong2": "k_prolong_add"}
+    if base in ("k_mdot", "k_gs_update", "k_smooth0", "k_restrict", "k_prolong_add", "k_down32", "k_up", "k_rr") or \
+            base in alias:
+        return alias.get(base, base)
     return None
 
 
@@ -649,7 +652,7 @@ def _template_real(kernel):
     return m.group(1) if m else ""
 
 
-DOWN_FAMILIES = ("k_smooth0", "k_stencil(resid)", "k_restrict", "k_down32", "k_down64")
+DOWN_FAMILIES = ("k_smooth0", "k_stencil(resid)", "k_restrict", "k_down32", "k_rr")
 
 
 def read_ncu_csv(path):
@@ -681,7 +684,15 @@ SOURCES = {"gs": ["paper_2308_06085_gb300/csrc/krylov.cu", "paper_2308_06085_gb3
            "vcycle32": ["paper_2308_06085_gb300/csrc/stencil.cu", "paper_2308_06085_gb300/csrc/common.cuh"]}
 
 
-def write_traffic(csv_path, kind, cmd="", out_path=None):
+NCU_TRAFFIC_CMD = ("ncu --profile-from-start off --metrics dram__bytes_read.sum,dram__bytes_write.sum,"
+                   "gpu__time_duration.sum --clock-control none -k '{k}' --csv --log-file traffic_{kind}.csv "
+                   "python bench.py --ncu-region {kind}")
+NCU_KERNELS = {"gs": "regex:k_mdot|k_gs_update",
+               "vcycle64": "regex:k_smooth0|k_stencil|k_restrict|k_prolong|k_rr|k_up|k_down",
+               "vcycle32": "regex:k_smooth0|k_stencil|k_restrict|k_prolong|k_rr|k_up|k_down"}
+
+
+def write_traffic(csv_path, kind, out_path=None):
     """Record, per kernel family of the region, the DRAM bytes ncu measured over the captured
     launches against the algorithmic bytes the library counted for them, with hashes of the
     sources as they were when captured (run in the same call as the capture)."""
@@ -725,9 +736,10 @@ def write_traffic(csv_path, kind, cmd="", out_path=None):
                          "launches": len(use), "duration_us": sum(u["ns"] or 0 for u in use) / 1e3,
                          "source_files": hashes,
                          "capture": f"region {kind} on {region['workload']}: {len(use)} launch(es) of "
-                                    f"{use[0]['kernel'][:80]}"}
+                                    f"{use[0]['kernel'][:80]}",
+                         "command": NCU_TRAFFIC_CMD.format(k=NCU_KERNELS[kind], kind=kind)}
         print(f"{name}: dram/algorithmic = {dram / alg:.3f} over {len(use)} launch(es)")
-    rec["command"] = cmd or rec.get("command", "")
+    rec.pop("command", None)
     with open(out_path, "w") as f:
         json.dump(rec, f, indent=1)
     return 0
@@ -947,7 +959,7 @@ def run_adjoint_variant(torch, helm, inputs):
 def main(argv=None):
     args = parse(argv)
     if args.write_traffic:
-        return write_traffic(args.write_traffic, args.ncu_region, " ".join(sys.argv), args.traffic_out)
+        return write_traffic(args.write_traffic, args.ncu_region, args.traffic_out)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -65,7 +65,7 @@ def test_write_traffic_from_an_ncu_csv(tmp_path, monkeypatch):
     (tmp_path / "cap.csv").write_text(CSV)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "REGION_OUT", str(tmp_path / "gpurun_out"))
-    bench.write_traffic(str(tmp_path / "cap.csv"), "vcycle64", "cmd")
+    bench.write_traffic(str(tmp_path / "cap.csv"), "vcycle64")
     rec = json.loads((tmp_path / "profiles" / "ncu_traffic.json").read_text())["kernels"]
     assert rec["k_smooth0 (finest)"]["dram_bytes"] == pytest.approx(8e8)
     assert rec["k_smooth0 (finest)"]["dram_over_algorithmic"] == pytest.approx(0.8)
@@ -80,6 +80,9 @@ def test_kernel_families_from_ncu_names():
     assert bench._family_of("k_gs_update_sums(const cx<double>*)") == "k_gs_update"
     assert bench._family_of("k_mdot<cx<double>, AccD3>(int)") == "k_mdot"
     assert bench._template_real("k_stencil<double, 0, false>(x)") == "double"
+    assert bench._family_of("void k_restrict2<float>(Grid, Grid)") == "k_restrict"
+    assert bench._family_of("void k_prolong2<double>(Grid, Grid)") == "k_prolong_add"
+    assert bench._family_of("void k_rr<double, true, double>(Grid)") == "k_rr"
     assert bench._family_of("k_givens(int)") is None
 
 
