@@ -51,7 +51,8 @@ typedef enum {
   HELM_EINVAL = 1,   /* bad argument: sizes, pointers, enum values, unsupported option */
   HELM_ENOMEM = 2,   /* device or host allocation failed */
   HELM_ECUDA = 3,    /* a CUDA runtime call failed (message in helm_last_error) */
-  HELM_ENOCONV = 4,  /* max_iter reached before tol; x holds the last iterate */
+  HELM_ENOCONV = 4,  /* max_iter reached, or Bi-CGSTAB stagnated (stall_window), before tol; x holds
+                        the last iterate */
   HELM_ETIMEOUT = 5, /* reserved: a bounded device wait gave up */
   HELM_ENUMERIC = 6  /* NaN/Inf residual or Krylov breakdown; x holds the last finite iterate */
 } helm_status;
@@ -151,6 +152,14 @@ typedef struct {
                        kernels when autotune is 0); 0: prolongation + correction, then
                        post-smoothing, as two kernels; 1: one kernel (the corrected iterate
                        stays in shared memory).  Bit-identical results either way. */
+  int stall_window; /* Bi-CGSTAB only, >= 0: stop with HELM_ENOCONV (message in helm_last_error)
+                       when the recursive residual has not fallen below half of its last mark
+                       within this many products with A, or when three restarts from the
+                       explicit residual in a row do not halve it.  0: never (run to max_iter).
+                       Default 1000.  With precision = HELM_PREC_MIXED the complex64 cycle is a
+                       preconditioner that changes with its input's rounding, which Bi-CGSTAB's
+                       recurrences do not allow for; it can stagnate there (FGMRES and IDR(s)
+                       converge). */
 } helm_params;
 
 /* Per-solve report (host struct). */
@@ -270,8 +279,9 @@ HELM_API helm_status helm_rhs_point(helm_ctx* ctx, int nsrc, const int* nodes, v
  *   b and x may both be device pointers, or both host pointers (pageable or pinned); host
  *   buffers are copied through the context's device buffers on `stream`.
  *   info : optional host struct, filled on return
- * Waits for the solve.  Returns HELM_OK, HELM_ENOCONV (max_iter hit; x is the last
- * iterate) or HELM_ENUMERIC (breakdown to NaN/Inf). */
+ * Waits for the solve.  Returns HELM_OK, HELM_ENOCONV (max_iter hit, or Bi-CGSTAB stagnated;
+ * x is the last iterate; helm_last_error(ctx) says which) or HELM_ENUMERIC (breakdown to
+ * NaN/Inf). */
 HELM_API helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_info* info,
                        void* stream);
 

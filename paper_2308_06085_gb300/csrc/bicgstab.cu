@@ -89,9 +89,10 @@ __global__ void __launch_bounds__(NT)
 // stage 1: alpha = rho / (rh . v)
 // stage 2: |s| -> half-step test
 // stage 3: omega = (t . s) / (t . t)
-// stage 4: |r|, rho_next -> convergence test
+// stage 4: |r|, rho_next -> convergence test; stagnation when the residual has not halved within
+//          `stall` products with A (stall > 0)
 __global__ void k_bicg_scalar(BicgCtl* bc, const z128* __restrict__ part, int nb, int stage, double tol, int max_iter,
-                              double* hist, int hist_len) {
+                              int stall, double* hist, int hist_len) {
   if (blockIdx.x != 0) return;
   if (bc->active == 0) return;
   const bool lead = threadIdx.x == 0;
@@ -159,6 +160,12 @@ __global__ void k_bicg_scalar(BicgCtl* bc, const z128* __restrict__ part, int nb
       bc->active = 0;
     } else if (bc->half || bc->iters >= max_iter) {
       bc->active = 0;
+    } else if (rn < 0.5 * bc->mark) {
+      bc->mark = rn;
+      bc->mark_it = bc->iters;
+    } else if (stall > 0 && bc->iters - bc->mark_it >= stall) {
+      bc->flag = 3;
+      bc->active = 0;
     }
     if (bc->active == 0) bc->cont = 0;
   }
@@ -178,6 +185,8 @@ __global__ void k_bicg_init(BicgCtl* bc, const z128* __restrict__ part, int nb, 
     bc->rho = mkc<double>(rr, 0.0);
     bc->rho_prev = bc->alpha = bc->omega = mkc<double>(1.0, 0.0);
     bc->relres = sqrt(rr) / bc->bnorm;
+    bc->mark = bc->relres;
+    bc->mark_it = bc->iters;
     bc->half = 0;
     bc->flag = 0;
     bc->active = 1;
@@ -207,9 +216,9 @@ int launch_bicg_xr(z128* x, z128* r, const z128* ph, const z128* sh, const z128*
   k_bicg_xr<<<nb, NT, 0, st>>>(x, r, ph, sh, s, t, rh, bc, n, part);
   return nb;
 }
-void launch_bicg_scalar(BicgCtl* bc, const z128* part, int nb, int stage, double tol, int max_iter, double* hist,
-                        int hist_len, cudaStream_t st) {
-  k_bicg_scalar<<<1, 32, 0, st>>>(bc, part, nb, stage, tol, max_iter, hist, hist_len);
+void launch_bicg_scalar(BicgCtl* bc, const z128* part, int nb, int stage, double tol, int max_iter, int stall,
+                        double* hist, int hist_len, cudaStream_t st) {
+  k_bicg_scalar<<<1, 32, 0, st>>>(bc, part, nb, stage, tol, max_iter, stall, hist, hist_len);
 }
 void launch_bicg_init(BicgCtl* bc, const z128* part, int nb, const z128* r, z128* rh, z128* p, z128* v, size_t n,
                       cudaStream_t st) {

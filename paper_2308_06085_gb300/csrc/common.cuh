@@ -333,11 +333,12 @@ __device__ __forceinline__ cx<float> omega_over<float>(cx<float> d, float omega)
 struct BicgCtl {
   int active;  // 1 while the iteration continues
   int cont;    // 1 while the current step goes on past its half step
-  int flag;    // 1 converged, 2 breakdown
+  int flag;    // 1 converged, 2 breakdown, 3 stagnation
   int half;    // the half step met tol (or the #Matvec cap)
   int iters;   // #Matvec
-  int pad;
+  int mark_it; // #Matvec when the residual last fell below half of mark
   double bnorm, relres;
+  double mark; // residual at mark_it
   cx<double> rho, rho_prev, alpha, omega, beta;
 };
 

@@ -1580,6 +1580,7 @@ helm_status bicgstab_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info
   const bool mixed = c->p.precision == HELM_PREC_MIXED;
   const double tol = c->p.tol;
   const int maxit = c->p.max_iter;
+  const int stall = c->p.stall_window;
   BicgCtl* bc = c->bicg;
   z128 *r = c->V, *rh = c->V + n, *p = c->V + 2 * n, *v = c->V + 3 * n, *ph = c->V + 4 * n, *s = c->V + 5 * n,
        *sh = c->V + 6 * n, *t = c->V + 7 * n;
@@ -1596,9 +1597,9 @@ helm_status bicgstab_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info
     if (info) { info->iterations = 0; info->restarts = 0; info->rel_residual = 0.0; }
     return HELM_OK;
   }
-  int restarts = 0;
+  int restarts = 0, flat = 0;
   helm_status status = HELM_OK;
-  double relres = 0.0;
+  double relres = 0.0, best = 0.0;
   for (;;) {
     KL(F_RESID, 56.0 * nd, 24.0 * nd, (launch_resid<double, double, double, double>(F.g, 1.0, 0.0, F.k2, x, b, r, st, c->one)));
     int nb = 0;
@@ -1613,22 +1614,22 @@ helm_status bicgstab_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info
     for (int step = 0;; ++step) {
       c->cur_j = -1;
       auto enq = [&](cudaStream_t st) {
-        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 0, tol, maxit, c->hist, c->hist_len, st));
+        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 0, tol, maxit, stall, c->hist, c->hist_len, st));
         KL(F_GS_UPDATE, 48.0 * nd, 8.0 * nd, launch_bicg_p(r, p, v, bc, n, st));
         if (mixed) run_cycle<float, double, double>(c, p, ph, st, act);
         else run_cycle<double, double, double>(c, p, ph, st, act);
         KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, ph, v, st, act)));
         KL(F_MDOT, 32.0 * nd, 8.0 * nd, nb = launch_dots2(rh, v, nullptr, nullptr, n, c->part, st, act));
-        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 1, tol, maxit, c->hist, c->hist_len, st));
+        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 1, tol, maxit, stall, c->hist, c->hist_len, st));
         KL(F_GS_UPDATE, 48.0 * nd, 8.0 * nd, nb = launch_bicg_s(r, v, s, bc, n, c->part, st));
-        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 2, tol, maxit, c->hist, c->hist_len, st));
+        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 2, tol, maxit, stall, c->hist, c->hist_len, st));
         if (mixed) run_cycle<float, double, double>(c, s, sh, st, cont);
         else run_cycle<double, double, double>(c, s, sh, st, cont);
         KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, sh, t, st, cont)));
         KL(F_MDOT, 48.0 * nd, 12.0 * nd, nb = launch_dots2(t, s, t, t, n, c->part, st, cont));
-        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 3, tol, maxit, c->hist, c->hist_len, st));
+        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 3, tol, maxit, stall, c->hist, c->hist_len, st));
         KL(F_GS_UPDATE, 112.0 * nd, 20.0 * nd, nb = launch_bicg_xr(x, r, ph, sh, s, t, rh, bc, n, c->part, st));
-        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 4, tol, maxit, c->hist, c->hist_len, st));
+        KL(F_GIVENS, 0, 0, launch_bicg_scalar(bc, c->part, nb, 4, tol, maxit, stall, c->hist, c->hist_len, st));
       };
       TRY(graph_step(c, G_BICG, 0, x, st, enq));
       TRY(check_launch(c, "Bi-CGSTAB step"));
@@ -1653,8 +1654,23 @@ helm_status bicgstab_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info
     relres = rn / h.bnorm;
     if (relres <= tol) { status = HELM_OK; break; }
     if (h.flag == 2 || !(relres == relres)) { status = HELM_ENUMERIC; break; }
+    if (h.flag == 3) {
+      status = fail(c, HELM_ENOCONV, "Bi-CGSTAB stagnated: the residual did not halve within stall_window "
+                                          "products with A (with precision = mixed the complex64 cycle is not a "
+                                          "fixed preconditioner; FGMRES or IDR(s) converge there)");
+      break;
+    }
     if (h.iters >= maxit) { status = HELM_ENOCONV; break; }
-    ++restarts;  // the recursion met tol but the explicit residual did not: restart from it
+    // the recursion met tol but the explicit residual did not: restart from it, unless three
+    // restarts in a row have not halved the best explicit residual
+    flat = (restarts > 0 && relres > 0.5 * best) ? flat + 1 : 0;
+    best = restarts > 0 ? fmin(best, relres) : relres;
+    if (stall > 0 && flat >= 3) {
+      status = fail(c, HELM_ENOCONV, "Bi-CGSTAB stagnated: three restarts from the explicit residual did not "
+                                          "halve it (the recursive residual drifts from the true one)");
+      break;
+    }
+    ++restarts;
   }
   CU(cudaMemcpyAsync(c->hbicg, bc, sizeof(BicgCtl), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
@@ -1891,6 +1907,7 @@ void helm_default_params(helm_params* p) {
   p->gs_sums = 1;
   p->fuse_down = -1;
   p->fuse_up = -1;
+  p->stall_window = 1000;
 }
 
 const char* helm_last_error(const helm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
@@ -2150,6 +2167,7 @@ helm_status helm_create(int n1, int n2, int n3, double h, const double* k2, helm
   if (P.gs_sums != 0 && P.gs_sums != 1) return fail(nullptr, HELM_EINVAL, "gs_sums must be 0 or 1");
   if (P.fuse_down < -1 || P.fuse_down > 3) return fail(nullptr, HELM_EINVAL, "fuse_down must lie in -1..3");
   if (P.fuse_up < -1 || P.fuse_up > 1) return fail(nullptr, HELM_EINVAL, "fuse_up must lie in -1..1");
+  if (P.stall_window < 0) return fail(nullptr, HELM_EINVAL, "stall_window must be >= 0");
   if (P.precision == HELM_PREC_MIXED && P.krylov == HELM_GMRES) P.krylov = HELM_FGMRES;
   helm_ctx* c = new (std::nothrow) helm_ctx();
   if (!c) return fail(nullptr, HELM_ENOMEM, "host allocation failed");
@@ -2515,6 +2533,7 @@ helm_status helm_solve(helm_ctx* c, const void* b, void* x, helm_solve_info* inf
   }
   helm_solve_info tmp;
   helm_solve_info* inf = info ? info : &tmp;
+  c->err.clear();
   helm_status s = krylov_device(c, bd, xd, inf, st);
   if (!bdev && (s == HELM_OK || s == HELM_ENOCONV || s == HELM_ENUMERIC)) {
     CU(cudaMemcpyAsync(x, c->xs, bytes, cudaMemcpyDeviceToHost, st));
@@ -2522,7 +2541,8 @@ helm_status helm_solve(helm_ctx* c, const void* b, void* x, helm_solve_info* inf
   }
   inf->status = (int)s;
   inf->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  if (s == HELM_ENOCONV) fail(c, s, "max_iter (%d) reached at relative residual %.3e", c->p.max_iter, inf->rel_residual);
+  if (s == HELM_ENOCONV && c->err.empty())
+    fail(c, s, "max_iter (%d) reached at relative residual %.3e", c->p.max_iter, inf->rel_residual);
   if (s == HELM_ENUMERIC) fail(c, s, "non-finite residual or Krylov breakdown");
   return s;
 }

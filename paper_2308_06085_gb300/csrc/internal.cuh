@@ -183,8 +183,8 @@ void launch_bicg_p(const z128* r, z128* p, const z128* v, const BicgCtl* bc, siz
 int launch_bicg_s(const z128* r, const z128* v, z128* s, const BicgCtl* bc, size_t n, z128* part, cudaStream_t st);
 int launch_bicg_xr(z128* x, z128* r, const z128* ph, const z128* sh, const z128* s, const z128* t, const z128* rh,
                    const BicgCtl* bc, size_t n, z128* part, cudaStream_t st);
-void launch_bicg_scalar(BicgCtl* bc, const z128* part, int nb, int stage, double tol, int max_iter, double* hist,
-                        int hist_len, cudaStream_t st);
+void launch_bicg_scalar(BicgCtl* bc, const z128* part, int nb, int stage, double tol, int max_iter, int stall,
+                        double* hist, int hist_len, cudaStream_t st);
 void launch_bicg_init(BicgCtl* bc, const z128* part, int nb, const z128* r, z128* rh, z128* p, z128* v, size_t n,
                       cudaStream_t st);
 

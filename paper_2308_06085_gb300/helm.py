@@ -42,7 +42,8 @@ class Params(C.Structure):
                 ("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int), ("orth", C.c_int),
                 ("reorth", C.c_int), ("cycle", C.c_int), ("idr_kappa", C.c_double),
                 ("graphs", C.c_int), ("autotune", C.c_int), ("side", C.c_int),
-                ("fuse_coarse", C.c_int), ("gs_sums", C.c_int), ("fuse_down", C.c_int), ("fuse_up", C.c_int)]
+                ("fuse_coarse", C.c_int), ("gs_sums", C.c_int), ("fuse_down", C.c_int), ("fuse_up", C.c_int),
+                ("stall_window", C.c_int)]
 
 
 class KernelStat(C.Structure):
@@ -193,7 +194,8 @@ class Solver:
 
     def __init__(self, n, h, k2, bc=SOMMERFELD, *, beta1=1.0, beta2=-0.5, omega=0.8, coarsest_n=4,
                  krylov="gmres", restart=30, tol=1e-6, max_iter=2000, precision="fp64", orth=None,
-                 reorth=None, cycle="v", idr_s=4, idr_kappa=0.7, shadow=None, graphs=True, autotune=True, side="right", fuse_coarse=False, gs_sums=True, fuse_down=-1, fuse_up=-1, device=None):
+                 reorth=None, cycle="v", idr_s=4, idr_kappa=0.7, shadow=None, graphs=True, autotune=True, side="right", fuse_coarse=False, gs_sums=True, fuse_down=-1, fuse_up=-1, stall_window=1000,
+                 device=None):
         n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(int(x) for x in n)
         self.n = (n1, n2, n3)
         self.h = float(h)
@@ -216,6 +218,7 @@ class Solver:
         p.gs_sums = int(bool(gs_sums))
         p.fuse_down = int(fuse_down)
         p.fuse_up = int(fuse_up)
+        p.stall_window = int(stall_window)
         p.restart, p.tol, p.max_iter = restart, tol, max_iter
         p.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
         if orth is not None:
@@ -464,7 +467,10 @@ class Solver:
         st = lib().helm_solve(self._ctx, _ptr(b), _ptr(x), C.byref(info), _stream())
         if st not in (OK, ENOCONV):
             self._check(st)
-        return x, info.as_dict()
+        out = info.as_dict()
+        if st == ENOCONV:
+            out["message"] = lib().helm_last_error(self._ctx).decode()
+        return x, out
 
 
 class HelmholtzSolve(torch.autograd.Function):

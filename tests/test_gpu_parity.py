@@ -478,3 +478,25 @@ def test_full_size_batched_sources(helm):
         ax = oracle.apply(X[r].cpu().numpy(), w["k2"], w["h"], S)
         rr = np.linalg.norm(bn - ax) / np.linalg.norm(bn)
         assert rr <= 1.01e-6, (r, rr)
+
+
+def test_bicgstab_stall_window(helm):
+    """Bi-CGSTAB's stagnation guard.  A window of 2 products asks the residual to halve on every
+    step (two products).  In the oracle's Bi-CGSTAB on the n = 32 wedge the second step takes
+    the true residual only from 3.4e-2 to 2.0e-2 (56 products in all to 1e-6), so the guarded
+    solve stops after a few products with HELM_ENOCONV and says why.  With the guard off it converges, and the default window leaves the FP64 solve
+    unchanged, bit for bit."""
+    w = I.workload("wedge", 32)
+    runs = {}
+    for win in (2, 0, 1000):
+        s = helm.Solver(w["n"], w["h"], w["k2"], S, krylov="bicgstab", stall_window=win, max_iter=4000)
+        x, info = s.solve(s.rhs_point(w["sources"]))
+        runs[win] = (x.cpu().numpy(), info)
+        s.close()
+    x0, i0 = runs[0]
+    x1, i1 = runs[1000]
+    assert i0["status"] == 0 and i1["status"] == 0 and i0["iterations"] == i1["iterations"]
+    assert np.array_equal(x0, x1)
+    x2, i2 = runs[2]
+    assert i2["status"] == 4 and i2["iterations"] < i0["iterations"] and "stagnated" in i2["message"], i2
+    assert np.all(np.isfinite(x2))
