@@ -565,8 +565,8 @@ def run_ours(args):
 REGION_OUT = os.path.join(ROOT, "gpurun_out")
 REGION_KERNELS = {  # ncu -k filter for each region
     "gs": "regex:k_mdot|k_gs_update",
-    "vcycle64": "regex:k_smooth0|k_stencil|k_restrict|k_prolong|k_down|k_up",
-    "vcycle32": "regex:k_smooth0|k_stencil|k_restrict|k_prolong|k_down|k_up",
+    "vcycle64": "regex:k_smooth0|k_stencil|k_restrict|k_prolong|k_rr|k_up|k_down",
+    "vcycle32": "regex:k_smooth0|k_stencil|k_restrict|k_prolong|k_rr|k_up|k_down",
 }
 
 
@@ -687,9 +687,6 @@ SOURCES = {"gs": ["paper_2308_06085_gb300/csrc/krylov.cu", "paper_2308_06085_gb3
 NCU_TRAFFIC_CMD = ("ncu --profile-from-start off --metrics dram__bytes_read.sum,dram__bytes_write.sum,"
                    "gpu__time_duration.sum --clock-control none -k '{k}' --csv --log-file traffic_{kind}.csv "
                    "python bench.py --ncu-region {kind}")
-NCU_KERNELS = {"gs": "regex:k_mdot|k_gs_update",
-               "vcycle64": "regex:k_smooth0|k_stencil|k_restrict|k_prolong|k_rr|k_up|k_down",
-               "vcycle32": "regex:k_smooth0|k_stencil|k_restrict|k_prolong|k_rr|k_up|k_down"}
 
 
 def write_traffic(csv_path, kind, out_path=None):
@@ -737,7 +734,7 @@ def write_traffic(csv_path, kind, out_path=None):
                          "source_files": hashes,
                          "capture": f"region {kind} on {region['workload']}: {len(use)} launch(es) of "
                                     f"{use[0]['kernel'][:80]}",
-                         "command": NCU_TRAFFIC_CMD.format(k=NCU_KERNELS[kind], kind=kind)}
+                         "command": NCU_TRAFFIC_CMD.format(k=REGION_KERNELS[kind], kind=kind)}
         print(f"{name}: dram/algorithmic = {dram / alg:.3f} over {len(use)} launch(es)")
     rec.pop("command", None)
     with open(out_path, "w") as f:

@@ -522,6 +522,12 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
   size_t cc_bytes = 0;
   const int lf = plan_coarse_cycle<R>(c, lv, L, &cc, &cc_bytes);
   const int Ld = lf < L ? lf + 1 : L;  // levels run kernel by kernel, the sub-cycle's first included
+  // A complex128 input to a complex64 cycle (one right-hand side, separate kernels on the
+  // finest level) is converted once: the pre-smoothing writes b in complex64 to the level's B
+  // buffer, which the residual and the post-smoothing then read (same values, half the bytes,
+  // no FP64 -> FP32 conversion in either).
+  const bool b32 = std::is_same<R, float>::value && !std::is_same<TI, float>::value && nbv == 1 && Ld > 1 &&
+                   lv[0].B != nullptr && !down_full(lv[0]) && !down_fused(lv[0]) && !rr_full(lv[0]);
   // down: pre-smooth from zero, residual, restriction
   for (int l = 0; l < Ld - 1; ++l) {
     const VLevel<R>& F = lv[l];
@@ -540,6 +546,9 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
       // u1 and the residual in one kernel (FP32, one right-hand side)
       if (l == 0) KL(vfam(c, F.g, F_SMOOTH0), n * (bi + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, rin, st, active));
       else KL(vfam(c, F.g, F_SMOOTH0), n * (bi + kb + 2 * cb), 30 * n, down_fused_launch(F, sr, si, om, F.B, st, active));
+    } else if (l == 0 && b32) {
+      KL(vfam(c, F.g, F_SMOOTH0), n * (bi + kb + 2 * cb), 6 * n, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active, F.B)));
+      KL(vfam(c, F.g, F_RESID), n * (3 * cb + kd), 24 * n, (launch_resid<R, R, R, R>(F.g, sr, si, F.k2, F.U1, F.B, F.T, st, active, F.dinv)));
     } else if (l == 0) {
       KL(vfam(c, F.g, F_SMOOTH0), n * (bi + (db ? db : kb) + cb), 6 * n * nbv, (launch_smooth0<R, TI>(F.g, sr, si, om, F.k2, F.dinv, rin, F.U1, st, active)));
       if (rr) KL(vfam(c, F.g, F_RR), n * (cb + bi + kd) + ncn * cb, 24 * n + 54 * ncn, rr_launch(F, C, sr, si, rin, st, active));
@@ -567,14 +576,18 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
     const double n = (double)F.g.npts(), ncn = (double)C.g.npts();
     if (up_full(F)) {
       // prolongation, correction and post-smoothing in one kernel (one right-hand side)
-      if (l == 0)
+      if (l == 0 && b32)
+        KL(vfam(c, F.g, F_UP), n * (2 * cb + kb + ob) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, F.B, zout, st, active));
+      else if (l == 0)
         KL(vfam(c, F.g, F_UP), n * (cb + ib + (db ? kd + db : kb) + ob) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, rin, zout, st, active));
       else
         KL(vfam(c, F.g, F_UP), n * (3 * cb + (db ? kd + db : kb)) + ncn * cb, 40 * n, up_full_launch(F, C, sr, si, om, F.B, F.E, st, active));
       continue;
     }
     KL(vfam(c, F.g, F_PROLONG), n * 2 * cb + ncn * cb, 6 * n * nbv, (launch_prolong_add<R>(F.g, C.g, F.U1, C.E, F.T, st, active)));
-    if (l == 0)
+    if (l == 0 && b32)
+      KL(vfam(c, F.g, F_JACOBI), n * (2 * cb + kd + ob), 32 * n, (launch_jacobi<R, R, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.B, zout, st, active)));
+    else if (l == 0)
       KL(vfam(c, F.g, F_JACOBI), n * (cb + ib + kd + db + ob), 32 * n * nbv, (launch_jacobi<R, TI, TO>(F.g, sr, si, om, F.k2, F.dinv, F.T, rin, zout, st, active)));
     else
       KL(vfam(c, F.g, F_JACOBI), n * (3 * cb + kd + db), 32 * n * nbv, (launch_jacobi<R, R, R>(F.g, sr, si, om, F.k2, F.dinv, F.T, F.B, F.E, st, active)));
@@ -2019,6 +2032,8 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
       TRY(dalloc(c, &L.E64, np));
       TRY(dalloc(c, &L.B32, np));
       TRY(dalloc(c, &L.E32, np));
+    } else if (P.precision == HELM_PREC_MIXED) {
+      TRY(dalloc(c, &L.B32, np));  // the complex64 copy of a complex128 cycle input
     }
   }
   Level& L0 = c->L[0];

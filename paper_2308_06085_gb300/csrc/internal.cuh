@@ -22,9 +22,10 @@ void launch_resid(const Grid& g, double s_re, double s_im, const R* k2, const cx
 template <typename R, typename TB, typename TO>
 void launch_jacobi(const Grid& g, double s_re, double s_im, double omega, const R* k2, const cx<R>* dinv,
                    const cx<R>* u, const cx<TB>* b, cx<TO>* out, cudaStream_t st, const int* active);
+// u1 = (omega/d) b; with bout, b in working precision R is written there too
 template <typename R, typename TB>
 void launch_smooth0(const Grid& g, double s_re, double s_im, double omega, const R* k2, const cx<R>* dinv,
-                    const cx<TB>* b, cx<R>* out, cudaStream_t st, const int* active);
+                    const cx<TB>* b, cx<R>* out, cudaStream_t st, const int* active, cx<R>* bout = nullptr);
 template <typename R>
 void launch_restrict(const Grid& gf, const Grid& gc, const cx<R>* r, cx<R>* out, cudaStream_t st, const int* active);
 template <typename R>

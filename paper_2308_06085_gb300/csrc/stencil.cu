@@ -652,10 +652,12 @@ __global__ void __launch_bounds__(RNT, 2)
 }
 
 // Pre-smoothing from a zero initial guess: one damped-Jacobi sweep gives u1 = (omega/d) b.
+// bout (optional): b in working precision R, written beside u1, so that the level's later
+// kernels read it without converting b again.
 template <typename R, bool DINV, typename TB>
 __global__ void __launch_bounds__(TX* TY)
     k_smooth0(Grid g, OpCoef<R> c, const R* __restrict__ k2, const cx<R>* __restrict__ dinv,
-              const cx<TB>* __restrict__ b, cx<R>* __restrict__ out, int zchunk,
+              const cx<TB>* __restrict__ b, cx<R>* __restrict__ out, cx<R>* __restrict__ bout, int zchunk,
               const int* __restrict__ active) {
   if (active && *active == 0) return;
   const int nb = g.nb;
@@ -696,6 +698,7 @@ __global__ void __launch_bounds__(TX* TY)
       w = omega_over(op_diag(c, kk, nf, nf ? face_k<R>(g, p, kk) : (R)0), c.omega);
     }
     out[e] = cmul(w, bv);
+    if (bout) bout[e] = bv;
   }
 }
 
@@ -765,22 +768,33 @@ __global__ void __launch_bounds__(TX* RTY)
   const int X = blockIdx.x * TX + lane, Y = blockIdx.y * blockDim.y + threadIdx.y;
   const bool own = X < gc.N1 && Y < gc.N2;
   const int fi = 2 * X + off, fj = 2 * Y + off;
+  const int N1 = gf.N1, N2 = gf.N2, N3 = gf.N3;
+  const size_t S = (size_t)N1 * N2;
   const cx<R> z0 = zero_c<R>();
-  // fine value, 0 outside the grid; lanes without a coarse point load nothing (their values are
-  // only ever passed to lanes that have none either)
-  auto at = [&](int x, int y, int z) {
-    return own && x >= 0 && x < gf.N1 && y >= 0 && y < gf.N2 && z >= 0 && z < gf.N3 ? ldg(r + gidx(x, y, z, gf.N1, gf.N2))
-                                                                                   : z0;
-  };
-  // the in-plane sum p of fine plane z for this lane's coarse column
+  // the lane's three fine rows fj - 1 .. fj + 1 at x = fi: in-plane offsets and which of the
+  // loads (x = fi, fi + 1, and fi - 1 for lane 0) fall inside the grid, fixed for the whole
+  // z-stream; lanes without a coarse point load nothing (their values are only ever passed to
+  // lanes that have none either)
+  const bool cok = own && fi < N1, pok = own && fi + 1 < N1, mok = own && fi >= 1;
+  bool rok[3];
+  size_t rb[3];
+  for (int d = 0; d < 3; ++d) {
+    const int y = fj + d - 1;
+    rok[d] = y >= 0 && y < N2;
+    rb[d] = rok[d] ? (size_t)y * N1 + fi : 0;
+  }
+  // the in-plane sum p of fine plane z for this lane's coarse column (0 outside the grid)
   auto plane = [&](int z) {
+    const bool zok = z >= 0 && z < N3;
+    const cx<R>* P = r + (zok ? (size_t)z * S : 0);
     cx<R> fx[3];
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int y = fj + dy;
-      const cx<R> c = at(fi, y, z), pnext = at(fi + 1, y, z);
+    for (int d = 0; d < 3; ++d) {
+      const bool ok = zok && rok[d];
+      const cx<R> c = ok && cok ? ldg(P + rb[d]) : z0;
+      const cx<R> pnext = ok && pok ? ldg(P + rb[d] + 1) : z0;
       cx<R> m = mkc<R>(__shfl_up_sync(0xffffffffu, pnext.re, 1), __shfl_up_sync(0xffffffffu, pnext.im, 1));
-      if (lane == 0) m = at(fi - 1, y, z);
-      fx[dy + 1] = fw3(m, c, pnext);
+      if (lane == 0) m = ok && mok ? ldg(P + rb[d] - 1) : z0;
+      fx[d] = fw3(m, c, pnext);
     }
     return fw3(fx[0], fx[1], fx[2]);
   };
@@ -1540,14 +1554,14 @@ void launch_jacobi(const Grid& g, double s_re, double s_im, double omega, const 
 
 template <typename R, typename TB>
 void launch_smooth0(const Grid& g, double s_re, double s_im, double omega, const R* k2, const cx<R>* dinv,
-                    const cx<TB>* b, cx<R>* out, cudaStream_t st, const int* active) {
+                    const cx<TB>* b, cx<R>* out, cudaStream_t st, const int* active, cx<R>* bout) {
   int zc;
   dim3 blk, gr = grid_for<R>(g, TILE_SMOOTH0, zc, blk);
   OpCoef<R> c = coef_for<R>(g.h, s_re, s_im, omega);
   if (dinv)
-    k_smooth0<R, true, TB><<<gr, blk, 0, st>>>(g, c, k2, dinv, b, out, zc, active);
+    k_smooth0<R, true, TB><<<gr, blk, 0, st>>>(g, c, k2, dinv, b, out, bout, zc, active);
   else
-    k_smooth0<R, false, TB><<<gr, blk, 0, st>>>(g, c, k2, dinv, b, out, zc, active);
+    k_smooth0<R, false, TB><<<gr, blk, 0, st>>>(g, c, k2, dinv, b, out, bout, zc, active);
 }
 
 template <typename TB>
@@ -1740,9 +1754,9 @@ template void launch_jacobi<float, double, float>(const Grid&, double, double, d
 template void launch_jacobi<float, double, double>(const Grid&, double, double, double, const float*, const z64*, const z64*, const z128*, z128*, cudaStream_t, const int*);
 template void launch_jacobi<float, float, double>(const Grid&, double, double, double, const float*, const z64*, const z64*, const z64*, z128*, cudaStream_t, const int*);
 template void launch_jacobi<double, double, float>(const Grid&, double, double, double, const double*, const z128*, const z128*, const z128*, z64*, cudaStream_t, const int*);
-template void launch_smooth0<double, double>(const Grid&, double, double, double, const double*, const z128*, const z128*, z128*, cudaStream_t, const int*);
-template void launch_smooth0<float, float>(const Grid&, double, double, double, const float*, const z64*, const z64*, z64*, cudaStream_t, const int*);
-template void launch_smooth0<float, double>(const Grid&, double, double, double, const float*, const z64*, const z128*, z64*, cudaStream_t, const int*);
+template void launch_smooth0<double, double>(const Grid&, double, double, double, const double*, const z128*, const z128*, z128*, cudaStream_t, const int*, z128*);
+template void launch_smooth0<float, float>(const Grid&, double, double, double, const float*, const z64*, const z64*, z64*, cudaStream_t, const int*, z64*);
+template void launch_smooth0<float, double>(const Grid&, double, double, double, const float*, const z64*, const z128*, z64*, cudaStream_t, const int*, z64*);
 template void launch_coarse<double, double>(int, const z128*, const z128*, z128*, cudaStream_t, const int*, int);
 template void launch_coarse<float, float>(int, const z128*, const z64*, z64*, cudaStream_t, const int*, int);
 template void launch_coarse<double, float>(int, const z128*, const z128*, z64*, cudaStream_t, const int*, int);
