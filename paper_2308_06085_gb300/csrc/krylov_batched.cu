@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(NT)
         if (ACC::kSums) swd[q] = bw_diff(wv);  // once per point, not once per warp
       }
       __syncthreads();
+#pragma unroll 2
       for (int q = sub * 32 + lane; q < tn; q += 32 * wps) {
         const E wv = sw[q];
         const double wd = ACC::kSums ? swd[q] : 0.0;
@@ -479,8 +480,13 @@ __global__ void __launch_bounds__(NT)
   __syncthreads();
   const size_t stride = (size_t)gridDim.x * NT;
   const int r = (int)((blockIdx.x * (size_t)NT + threadIdx.x) & (size_t)(nb - 1));  // fixed per thread
-  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += stride) {
-    double P = 0.0, Q = 0.0, R = 0.0;
+  // two elements per trip, e and e + stride (the same right-hand side, as stride is a multiple
+  // of nb): twice the independent loads and FMA chains, one coefficient load for both; each
+  // element's sums run in the same order as with one element per trip
+  for (size_t e = blockIdx.x * (size_t)NT + threadIdx.x; e < ne; e += 2 * stride) {
+    const size_t e2 = e + stride;
+    const bool two = e2 < ne;
+    double P = 0.0, Q = 0.0, R = 0.0, P2 = 0.0, Q2 = 0.0, R2 = 0.0;
     for (int i = 0; i < nv; ++i) {
       const size_t off = (size_t)i * ld + e;
       const z128 v = ldg(V + off);
@@ -489,9 +495,20 @@ __global__ void __launch_bounds__(NT)
       P = fma(c.x, v.re, P);
       Q = fma(c.y, v.im, Q);
       R = fma(c.z, sv, R);
+      if (two) {
+        const z128 v2 = ldg(V + off + stride);
+        const double sv2 = ldg(Vs + off + stride);
+        P2 = fma(c.x, v2.re, P2);
+        Q2 = fma(c.y, v2.im, Q2);
+        R2 = fma(c.z, sv2, R2);
+      }
     }
     const z128 a = w[e];
     w[e] = mkc<double>(a.re - (P - Q), a.im - (R - (P + Q)));
+    if (two) {
+      const z128 a2 = w[e2];
+      w[e2] = mkc<double>(a2.re - (P2 - Q2), a2.im - (R2 - (P2 + Q2)));
+    }
   }
 }
 
