@@ -97,8 +97,9 @@ typedef struct {
                        products and sums use error-free FP32 transformations; vectors
                        outside the basis, norms and the Hessenberg problem stay FP64. */
   int reorth;       /* helm_reorth: classical Gram-Schmidt with a second pass on every Arnoldi
-                       step (ALWAYS), or only when the first pass removed more than half of
-                       |w|^2 (SELECTIVE, the Daniel-Gragg-Kaufman-Stewart test) */
+                       step (ALWAYS), or only when the first pass removed more than
+                       1 - reorth_keep of |w|^2 (SELECTIVE, the Daniel-Gragg-Kaufman-Stewart
+                       test) */
   int cycle;        /* helm_cycle: the preconditioner is one V-cycle (default) or one F-cycle
                        (Sec. 3.4.5: each coarse-grid error is an F-cycle on the next level followed
                        by one V-cycle there); the batched solver follows it too */
@@ -160,6 +161,14 @@ typedef struct {
                        preconditioner that changes with its input's rounding, which Bi-CGSTAB's
                        recurrences do not allow for; it can stagnate there (FGMRES and IDR(s)
                        converge). */
+  double reorth_keep; /* GMRES / FGMRES with reorth = HELM_REORTH_SELECTIVE, 0 <= keep < 1: the
+                       second classical Gram-Schmidt pass of an Arnoldi step is skipped when the
+                       first pass kept at least this fraction of |w|^2 (|w - V h|^2 estimated
+                       as |w|^2 - |h|^2): the Daniel-Gragg-Kaufman-Stewart test with
+                       eta = sqrt(keep).  One pass leaves the new basis vector orthogonal to the
+                       others to about eps / eta, so the second pass matters only under heavy
+                       cancellation.  Default 0.1 (eta = 0.32: orthogonality to about 3 eps);
+                       0.5 is the conservative eta = 1/sqrt(2). */
 } helm_params;
 
 /* Per-solve report (host struct). */

@@ -1150,7 +1150,7 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
             KL(F_APPLY, 40.0 * nd, 22.0 * nd, (launch_apply<double, double, double>(F.g, 1.0, 0.0, F.k2, zj, w, st, act)));
         }
         // classical Gram-Schmidt: first pass always; the second on every step (ALWAYS) or when
-        // the first pass's projection removed more than half of |w|^2 (SELECTIVE)
+        // the first pass's projection kept less than reorth_keep of |w|^2 (SELECTIVE)
         const bool sel = c->p.reorth == HELM_REORTH_SELECTIVE;
         for (int pass = 0; pass < 2; ++pass) {
           const int* a2 = (pass == 1 && sel) ? &ctl->pass2 : act;
@@ -1170,7 +1170,7 @@ helm_status gmres_device(helm_ctx* c, const z128* b, z128* x, helm_solve_info* i
                nb = launch_mdot(c->V, n, j + 1, w, n, c->part, wn, st, a2, c->mdot_variant));
           KL(F_REDUCE_DOTS, 16.0 * nv * nb, 2.0 * nv * nb,
              launch_reduce_dots(c->part, j + 1, nb, c->hpass, c->hacc, pass, wn ? j : -1, &ctl->pass2, c->reorth_log,
-                                st, a2));
+                                st, a2, c->p.reorth_keep));
           if (df)
             KL(F_GS_UPDATE, 16.0 * (nv + 2) * nd, 8.0 * nv * nd, launch_gs_update_df(Vdf, n, j + 1, c->hpass, wd, n, st, a2));
           else if (sums)
@@ -1523,7 +1523,7 @@ helm_status gmres_batched(helm_ctx* c, int nb, cudaStream_t st) {
           if (per_rhs) c->cur_cond = 1;
           KL(F_REDUCE_DOTS, 16.0 * nv * nb * nbk, 2.0 * nv * nb * nbk,
              launch_breduce_dots(W.part, j + 1, nb, nbk, W.hpass, W.hacc, pass, wn ? j : -1, W.h.act, &ctl->pass2,
-                                 c->reorth_log, W.sw2, W.need, st, a2));
+                                 c->reorth_log, W.sw2, W.need, st, a2, c->p.reorth_keep));
           if (per_rhs) c->cur_cond = 2;
           if (per_rhs)
             KL(F_GS_UPDATE, ((W.Vs ? 24.0 * nv + 32.0 : 16.0 * (nv + 2)) * nd) / nb, 8.0 * nv * nd / nb,
@@ -1921,6 +1921,7 @@ void helm_default_params(helm_params* p) {
   p->fuse_down = -1;
   p->fuse_up = -1;
   p->stall_window = 1000;
+  p->reorth_keep = 0.1;
 }
 
 const char* helm_last_error(const helm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
@@ -2183,6 +2184,7 @@ helm_status helm_create(int n1, int n2, int n3, double h, const double* k2, helm
   if (P.fuse_down < -1 || P.fuse_down > 3) return fail(nullptr, HELM_EINVAL, "fuse_down must lie in -1..3");
   if (P.fuse_up < -1 || P.fuse_up > 1) return fail(nullptr, HELM_EINVAL, "fuse_up must lie in -1..1");
   if (P.stall_window < 0) return fail(nullptr, HELM_EINVAL, "stall_window must be >= 0");
+  if (!(P.reorth_keep >= 0.0 && P.reorth_keep < 1.0)) return fail(nullptr, HELM_EINVAL, "reorth_keep must lie in [0, 1)");
   if (P.precision == HELM_PREC_MIXED && P.krylov == HELM_GMRES) P.krylov = HELM_FGMRES;
   helm_ctx* c = new (std::nothrow) helm_ctx();
   if (!c) return fail(nullptr, HELM_ENOMEM, "host allocation failed");

@@ -63,9 +63,9 @@ int launch_mdot_sums(const z128* V, const double* Vs, size_t ld, int nv, const z
                      int with_norm, cudaStream_t st, const int* active, int variant);
 // hpass[i] = sum_{blk < nb} part[i * RED_STRIDE + blk]; hacc[i] = hpass[i] (accumulate 0) or
 // += (1).  decide_j >= 0: also read |w|^2 from slot nv and set *pass2 = log[decide_j] =
-// (second Gram-Schmidt pass needed)
+// (second Gram-Schmidt pass needed: the first kept less than `keep` of |w|^2)
 void launch_reduce_dots(const z128* part, int nv, int nb, z128* hpass, z128* hacc, int accumulate, int decide_j,
-                        int* pass2, int* log, cudaStream_t st, const int* active);
+                        int* pass2, int* log, cudaStream_t st, const int* active, double keep);
 // w -= sum_i h[i] V_i
 void launch_gs_update(const z128* V, size_t ld, int nv, const z128* h, z128* w, size_t n, cudaStream_t st,
                       const int* active);
@@ -200,7 +200,7 @@ int launch_bmdot(const z128* V, const double* Vs, size_t ld, int nv, const z128*
 // how many
 void launch_breduce_dots(const z128* part, int nv, int nb, int nblk, z128* hpass, z128* hacc, int accumulate,
                          int decide_j, const int* act, int* pass2, int* log, double* sw2, int* need, cudaStream_t st,
-                         const int* active);
+                         const int* active, double keep);
 // the second Gram-Schmidt pass for the right-hand sides with need[r] only (FP64; Vs: summed
 // basis or NULL): inner products into part (k_bmdot's layout and grid; zeros for the others),
 // and the update

@@ -224,13 +224,13 @@ __global__ void __launch_bounds__(NT)
 
 // One warp per basis vector: lanes sum the nb partials in a fixed order.
 // decide_j >= 0 (first pass): slot nv holds partial |w|^2; the block then applies the
-// Daniel-Gragg-Kaufman-Stewart test -- a second pass is needed when the projection removed
-// more than half of |w|^2 (|w - V h|^2 = |w|^2 - |h|^2 < |w|^2 / 2) -- and records the
+// Daniel-Gragg-Kaufman-Stewart test -- a second pass is needed when the projection kept less
+// than `keep` of |w|^2 (|w - V h|^2 = |w|^2 - |h|^2 < keep |w|^2) -- and records the
 // decision in *pass2 and log[decide_j].
 __global__ void __launch_bounds__(NT)
     k_reduce_dots(const z128* __restrict__ part, int nv, int nb, z128* __restrict__ hpass, z128* __restrict__ hacc,
                   int accumulate, int decide_j, int* __restrict__ pass2, int* __restrict__ log,
-                  const int* __restrict__ active) {
+                  const int* __restrict__ active, double keep) {
   if (active && *active == 0) return;
   __shared__ double sw2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(NT)
   if (threadIdx.x == 0) {
     double h2 = 0.0;
     for (int i = 0; i < nv; ++i) h2 += hpass[i].re * hpass[i].re + hpass[i].im * hpass[i].im;
-    const int again = !(sw2 - h2 >= 0.5 * sw2);  // NaN also takes the second pass
+    const int again = !(sw2 - h2 >= keep * sw2);  // NaN also takes the second pass
     *pass2 = again;
     log[decide_j] = again;
   }
@@ -733,8 +733,8 @@ int launch_mdot_sums(const z128* V, const double* Vs, size_t ld, int nv, const z
   return mdot_variant<AccD3>(V, Vs, ld, nv, w, n, part, with_norm, st, active, variant);
 }
 void launch_reduce_dots(const z128* part, int nv, int nb, z128* hpass, z128* hacc, int accumulate, int decide_j,
-                        int* pass2, int* log, cudaStream_t st, const int* active) {
-  k_reduce_dots<<<1, NT, 0, st>>>(part, nv, nb, hpass, hacc, accumulate, decide_j, pass2, log, active);
+                        int* pass2, int* log, cudaStream_t st, const int* active, double keep) {
+  k_reduce_dots<<<1, NT, 0, st>>>(part, nv, nb, hpass, hacc, accumulate, decide_j, pass2, log, active, keep);
 }
 void launch_gs_update(const z128* V, size_t ld, int nv, const z128* h, z128* w, size_t n, cudaStream_t st,
                       const int* active) {

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(NT)
 
 // hpass[i * nb + r] = sum of the partials of (slot i, rhs r); hacc stores or accumulates.
 // decide_j >= 0: a second Gram-Schmidt pass is taken when, for any active right-hand side,
-// the projection removed more than half of |w_r|^2.
+// the projection kept less than `keep` of |w_r|^2 (k_bdecide).
 __global__ void __launch_bounds__(NT)
     k_breduce_dots(const z128* __restrict__ part, int nv, int nb, int nblk, z128* __restrict__ hpass,
                    z128* __restrict__ hacc, int accumulate, int decide_j, double* __restrict__ sw2,
@@ -280,11 +280,11 @@ __global__ void __launch_bounds__(NT)
 }
 
 // The Daniel-Gragg-Kaufman-Stewart test per active right-hand side: r takes a second pass when
-// its first one removed more than half of |w_r|^2 (need[r]); the pass runs when any r needs it,
+// its first one kept less than `keep` of |w_r|^2 (need[r]); the pass runs when any r needs it,
 // and log[decide_j] holds how many do.
 __global__ void k_bdecide(const z128* __restrict__ hpass, const double* __restrict__ sw2, int nv, int nb,
                           int decide_j, const int* __restrict__ act, int* __restrict__ pass2, int* __restrict__ log,
-                          int* __restrict__ need, const int* __restrict__ active) {
+                          int* __restrict__ need, const int* __restrict__ active, double keep) {
   if (active && *active == 0) return;
   if (threadIdx.x != 0) return;
   int count = 0;
@@ -293,7 +293,7 @@ __global__ void k_bdecide(const z128* __restrict__ hpass, const double* __restri
     if (act[r]) {
       double h2 = 0.0;
       for (int i = 0; i < nv; ++i) h2 += hpass[i * nb + r].re * hpass[i * nb + r].re + hpass[i * nb + r].im * hpass[i * nb + r].im;
-      nr = !(sw2[r] - h2 >= 0.5 * sw2[r]);
+      nr = !(sw2[r] - h2 >= keep * sw2[r]);
     }
     need[r] = nr;
     count += nr;
@@ -894,11 +894,11 @@ template void launch_bscale_df<zdf, double>(const zdf*, const double*, zdf*, z12
 template void launch_bscale_df<zdf, float>(const zdf*, const double*, zdf*, z64*, size_t, int, cudaStream_t, const int*);
 void launch_breduce_dots(const z128* part, int nv, int nb, int nblk, z128* hpass, z128* hacc, int accumulate,
                          int decide_j, const int* act, int* pass2, int* log, double* sw2, int* need, cudaStream_t st,
-                         const int* active) {
+                         const int* active, double keep) {
   const int rows = (decide_j >= 0 ? nv + 1 : nv) * nb;
   k_breduce_dots<<<(rows + NW - 1) / NW, NT, 0, st>>>(part, nv, nb, nblk, hpass, hacc, accumulate, decide_j, sw2,
                                                       active);
-  if (decide_j >= 0) k_bdecide<<<1, 32, 0, st>>>(hpass, sw2, nv, nb, decide_j, act, pass2, log, need, active);
+  if (decide_j >= 0) k_bdecide<<<1, 32, 0, st>>>(hpass, sw2, nv, nb, decide_j, act, pass2, log, need, active, keep);
 }
 int launch_bmdot_sel(const z128* V, const double* Vs, size_t ld, int nv, const z128* w, size_t ne, int nb,
                      const int* need, z128* part, cudaStream_t st, const int* active) {
