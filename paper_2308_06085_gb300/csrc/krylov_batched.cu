@@ -177,7 +177,7 @@ __device__ __forceinline__ double bw_diff(const z128& w) { return w.im - w.re; }
 __device__ __forceinline__ double bw_diff(const zdf&) { return 0.0; }
 
 template <typename E, typename ACC, int KSV = KS>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 4)
     k_bmdot(const E* __restrict__ V, const double* __restrict__ Vs, size_t ld, int nv, const E* __restrict__ w,
             size_t ne, int nb, z128* __restrict__ part, int with_norm, const int* __restrict__ active) {
   if (active && *active == 0) return;
