@@ -169,6 +169,14 @@ typedef struct {
                        others to about eps / eta, so the second pass matters only under heavy
                        cancellation.  Default 0.1 (eta = 0.32: orthogonality to about 3 eps);
                        0.5 is the conservative eta = 1/sqrt(2). */
+  double coarse_tol; /* coarsest-grid solve of every cycle.  0 (default): the dense inverse of
+                       M on the coarsest grid, computed once at helm_create (exact to
+                       rounding).  0 < tol < 1: the paper's own choice (Sec. 5), full GMRES on
+                       the coarsest grid from a zero guess until its relative residual is
+                       <= tol (the paper uses 1e-11), at most 256 steps, run by one
+                       thread-block cluster; one right-hand side at a time (the batched solver
+                       keeps the dense inverse).  Needs a coarsest grid of at most 4096 unknowns
+                       and (257 x that count + 65792) x 16 bytes of device memory. */
 } helm_params;
 
 /* Per-solve report (host struct). */

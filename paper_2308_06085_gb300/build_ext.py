@@ -11,7 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libhelm.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["stencil.cu", "krylov.cu", "krylov_batched.cu", "bicgstab.cu", "idrs.cu", "adjoint.cu", "helm_api.cu", "noalloc.cu"]
+SOURCES = ["stencil.cu", "krylov.cu", "krylov_batched.cu", "bicgstab.cu", "idrs.cu", "adjoint.cu", "helm_api.cu", "noalloc.cu",
+           "coarse_gmres.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

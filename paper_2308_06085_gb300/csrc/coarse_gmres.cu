@@ -1,0 +1,249 @@
+// coarse_gmres.cu -- the paper's own coarsest-grid solve (Sec. 5): the error equation
+// M_c e = b on the coarsest grid is solved by full (unrestarted) GMRES from e = 0 until the
+// relative residual reaches a tolerance (1e-11 in the paper), instead of by the precomputed
+// dense inverse the library uses by default.
+//
+// The coarsest grid holds at most a few thousand unknowns, too few to fill the GPU and too many
+// for one SM to orthogonalise quickly, so one thread-block cluster of CG_CS CTAs (distributed
+// shared memory, hardware cluster barriers) runs the whole iteration in one launch: each CTA
+// owns a contiguous slice of the grid (one node per thread), applies M on it, and contributes
+// partial inner products that every CTA then sums from the others' shared memory in rank
+// order, so all CTAs hold the same Hessenberg column, Givens rotations and stopping decision
+// and take every barrier together.  Classical Gram-Schmidt with a second pass on every step
+// (the unknown count is small, and the tolerance tight).  The basis lives in global memory
+// (L2-resident); values written during the launch by other CTAs are read through L2 only.
+#include "internal.cuh"
+
+#include <cooperative_groups.h>
+
+namespace helm {
+
+namespace {
+
+namespace cgr = cooperative_groups;
+
+constexpr int CG_NT = 512;
+constexpr int CG_NW = CG_NT / 32;
+constexpr int CG_MAXB = CG_MAX + 1;
+
+__device__ __forceinline__ z128 ld_l2(const z128* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return mkc<double>(v.x, v.y);
+}
+__device__ __forceinline__ void st_l2(z128* p, z128 v) {
+  __stcg(reinterpret_cast<double2*>(p), make_double2(v.re, v.im));
+}
+__device__ __forceinline__ z128 zdiv(z128 a, z128 b) {
+  const double d = b.re * b.re + b.im * b.im;
+  return mkc<double>((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
+}
+
+// (M v)_p on the coarsest grid: the 7-point operator with the level's k^2, Sommerfeld faces
+// taking the opposite neighbour and adding the face term to the diagonal, Dirichlet faces a
+// zero (the substitution of k_stencil).
+__device__ z128 coarse_apply(const Grid& g, const OpCoef<double>& c, const double* __restrict__ k2,
+                             const z128* v, int p) {
+  const int N1 = g.N1, N2 = g.N2, N3 = g.N3, S = N1 * N2;
+  const int i = p % N1, j = (p / N1) % N2, k = p / S;
+  const bool som = g.bc == 1;
+  const bool hxm = i > 0, hxp = i < N1 - 1, hym = j > 0, hyp = j < N2 - 1, hzm = k > 0, hzp = k < N3 - 1;
+  const int nf = som ? (!hxm) + (!hxp) + (!hym) + (!hyp) + (!hzm) + (!hzp) : 0;
+  const z128 z0 = mkc<double>(0.0, 0.0);
+  const z128 xm = hxm ? ld_l2(v + p - 1) : (som ? ld_l2(v + p + 1) : z0);
+  const z128 xp = hxp ? ld_l2(v + p + 1) : (som ? ld_l2(v + p - 1) : z0);
+  const z128 ym = hym ? ld_l2(v + p - N1) : (som ? ld_l2(v + p + N1) : z0);
+  const z128 yp = hyp ? ld_l2(v + p + N1) : (som ? ld_l2(v + p - N1) : z0);
+  const z128 zm = hzm ? ld_l2(v + p - S) : (som ? ld_l2(v + p + S) : z0);
+  const z128 zp = hzp ? ld_l2(v + p + S) : (som ? ld_l2(v + p - S) : z0);
+  const double kk = k2[p];
+  const z128 d = op_diag(c, kk, nf, nf ? face_k<double>(g, (size_t)p, kk) : 0.0);
+  return op_apply(d, c.real_shift && nf == 0, ld_l2(v + p), c.ih2, xm, xp, ym, yp, zm, zp);
+}
+
+template <typename TI, typename TO>
+__global__ void __cluster_dims__(CG_CS, 1, 1) __launch_bounds__(CG_NT)
+    k_coarse_gmres(Grid g, OpCoef<double> c, const double* __restrict__ k2, const cx<TI>* __restrict__ b,
+                   cx<TO>* __restrict__ e, z128* __restrict__ V, z128* __restrict__ H, int maxit, double tol,
+                   int* __restrict__ info, const int* __restrict__ active) {
+  if (active && *active == 0) return;  // read by every thread of every CTA: all return together
+  cgr::cluster_group cl = cgr::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int n = (int)g.npts();
+  const int chunk = (n + CG_CS - 1) / CG_CS;  // <= CG_NT (n <= CG_CS * CG_NT)
+  const int p0 = min(rank * chunk, n), p1 = min(p0 + chunk, n), len = p1 - p0;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int p = p0 + t;
+  const bool own = t < len;
+  __shared__ z128 part[2][CG_MAXB];  // this CTA's partial sums, read by every CTA of the cluster
+  __shared__ z128 sw[CG_NT];         // w on this CTA's nodes
+  __shared__ z128 hcol[CG_MAXB];     // the Hessenberg column being built (both passes)
+  __shared__ z128 hp[CG_MAXB];       // this pass's coefficients
+  __shared__ double scs[CG_MAX];
+  __shared__ z128 ssn[CG_MAX];
+  __shared__ z128 sg[CG_MAXB];
+  __shared__ z128 sy[CG_MAX];
+  __shared__ double sred[CG_NW];
+  __shared__ double sval;
+  __shared__ int sstop;
+
+  // sum over the cluster of one real value per thread: block sum into part[buf][0], barrier,
+  // then the CTAs' sums added in rank order (the same result in every CTA)
+  auto cluster_sum = [&](double x, int buf) -> double {
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sred[warp] = x;
+    __syncthreads();
+    if (t == 0) {
+      double s = 0.0;
+      for (int w = 0; w < CG_NW; ++w) s += sred[w];
+      part[buf][0] = mkc<double>(s, 0.0);
+    }
+    cl.sync();
+    if (t == 0) {
+      double s = 0.0;
+      for (int r = 0; r < CG_CS; ++r) s += cl.map_shared_rank(&part[buf][0], r)->re;
+      sval = s;
+    }
+    __syncthreads();
+    return sval;
+  };
+  // hp[i] = sum over the grid of conj(V_i) w, i <= j: warp w takes i = w, w + CG_NW, ...
+  auto dots = [&](int j, int buf) {
+    for (int i = warp; i <= j; i += CG_NW) {
+      double re = 0.0, im = 0.0;
+      const z128* Vi = V + (size_t)i * n + p0;
+      for (int q = lane; q < len; q += 32) cdot_acc(ld_l2(Vi + q), sw[q], re, im);
+      for (int o = 16; o; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      if (lane == 0) part[buf][i] = mkc<double>(re, im);
+    }
+    cl.sync();
+    for (int i = t; i <= j; i += CG_NT) {
+      double re = 0.0, im = 0.0;
+      for (int r = 0; r < CG_CS; ++r) {
+        const z128 v = cl.map_shared_rank(&part[buf][0], r)[i];
+        re += v.re;
+        im += v.im;
+      }
+      hp[i] = mkc<double>(re, im);
+    }
+    __syncthreads();
+  };
+
+  // beta = |b|, v_0 = b / beta
+  z128 bv = mkc<double>(0.0, 0.0);
+  if (own) bv = cvt<double>(b[p]);
+  const double beta = sqrt(cluster_sum(own ? bv.re * bv.re + bv.im * bv.im : 0.0, 0));
+  if (beta == 0.0 || !isfinite(beta)) {
+    if (own) e[p] = cvt<TO>(mkc<double>(0.0, 0.0));
+    if (rank == 0 && t == 0 && info) {
+      info[0] = 0;
+      info[1] = beta == 0.0;
+    }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
+    return;
+  }
+  if (own) st_l2(V + p, mkc<double>(bv.re / beta, bv.im / beta));
+  if (t == 0) sg[0] = mkc<double>(beta, 0.0);
+  int k = 0, conv = 0;
+  for (int j = 0; j < maxit; ++j) {
+    cl.sync();  // v_j complete in every CTA's slice; the reads of part[0] are done
+    if (own) sw[t] = coarse_apply(g, c, k2, V + (size_t)j * n, p);
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      dots(j, pass);
+      for (int i = t; i <= j; i += CG_NT) hcol[i] = pass == 0 ? hp[i] : cadd(hcol[i], hp[i]);
+      if (own) {
+        z128 w = sw[t];
+        for (int i = 0; i <= j; ++i) w = csub(w, cmul(hp[i], ld_l2(V + (size_t)i * n + p)));
+        sw[t] = w;
+      }
+      __syncthreads();
+    }
+    const z128 wv = own ? sw[t] : mkc<double>(0.0, 0.0);
+    const double hn = sqrt(cluster_sum(wv.re * wv.re + wv.im * wv.im, 0));
+    if (own && hn > 0.0) st_l2(V + (size_t)(j + 1) * n + p, mkc<double>(wv.re / hn, wv.im / hn));
+    if (t == 0) {
+      // previous rotations on the new column, then the rotation that zeroes h_{j+1,j}
+      hcol[j + 1] = mkc<double>(hn, 0.0);
+      for (int i = 0; i < j; ++i) {
+        const z128 a = hcol[i], bb = hcol[i + 1];
+        const double cs = scs[i];
+        const z128 sn = ssn[i];
+        const z128 sb = cmul(sn, bb);
+        const z128 ta = cmul(mkc<double>(-sn.re, sn.im), a);  // -conj(sn) a
+        hcol[i] = mkc<double>(cs * a.re + sb.re, cs * a.im + sb.im);
+        hcol[i + 1] = mkc<double>(ta.re + cs * bb.re, ta.im + cs * bb.im);
+      }
+      const z128 a = hcol[j], bb = hcol[j + 1];
+      const double na = hypot(a.re, a.im), nbb = hypot(bb.re, bb.im), tt = hypot(na, nbb);
+      double cs;
+      z128 sn;
+      if (na == 0.0) {
+        cs = 0.0;
+        sn = mkc<double>(1.0, 0.0);
+        hcol[j] = bb;
+      } else {
+        const z128 ph = mkc<double>(a.re / na, a.im / na);
+        cs = na / tt;
+        sn = cmul(ph, mkc<double>(bb.re / tt, -bb.im / tt));
+        hcol[j] = mkc<double>(ph.re * tt, ph.im * tt);
+      }
+      scs[j] = cs;
+      ssn[j] = sn;
+      const z128 gj = sg[j];
+      sg[j + 1] = cmul(mkc<double>(-sn.re, sn.im), gj);
+      sg[j] = mkc<double>(cs * gj.re, cs * gj.im);
+      if (rank == 0)
+        for (int i = 0; i <= j; ++i) st_l2(H + (size_t)j * CG_MAXB + i, hcol[i]);
+      const double est = hypot(sg[j + 1].re, sg[j + 1].im) / beta;
+      sstop = (est <= tol) ? 1 : (!(hn > 0.0) || !isfinite(est)) ? 2 : 0;
+    }
+    __syncthreads();
+    k = j + 1;
+    if (sstop) {
+      conv = sstop == 1;
+      break;
+    }
+  }
+  cl.sync();  // the columns written by rank 0 are visible; no shared memory is read after this
+  if (t == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      z128 acc = sg[i];
+      for (int q = i + 1; q < k; ++q) acc = csub(acc, cmul(ld_l2(H + (size_t)q * CG_MAXB + i), sy[q]));
+      sy[i] = zdiv(acc, ld_l2(H + (size_t)i * CG_MAXB + i));
+    }
+  }
+  __syncthreads();
+  if (own) {
+    z128 x = mkc<double>(0.0, 0.0);
+    for (int i = 0; i < k; ++i) x = cfma(sy[i], ld_l2(V + (size_t)i * n + p), x);
+    e[p] = cvt<TO>(x);
+  }
+  if (rank == 0 && t == 0 && info) {
+    info[0] = k;
+    info[1] = conv;
+  }
+}
+
+}  // namespace
+
+template <typename TI, typename TO>
+void launch_coarse_gmres(const Grid& g, double s_re, double s_im, const double* k2, const cx<TI>* b, cx<TO>* e,
+                         z128* V, z128* H, double tol, int* info, cudaStream_t st, const int* active) {
+  const int n = (int)g.npts();
+  const int maxit = n < CG_MAX ? n : CG_MAX;
+  k_coarse_gmres<TI, TO><<<CG_CS, CG_NT, 0, st>>>(g, coef_for<double>(g.h, s_re, s_im, 0.0), k2, b, e, V, H, maxit,
+                                                  tol, info, active);
+}
+template void launch_coarse_gmres<double, double>(const Grid&, double, double, const double*, const z128*, z128*,
+                                                  z128*, z128*, double, int*, cudaStream_t, const int*);
+template void launch_coarse_gmres<float, float>(const Grid&, double, double, const double*, const z64*, z64*, z128*,
+                                                z128*, double, int*, cudaStream_t, const int*);
+template void launch_coarse_gmres<double, float>(const Grid&, double, double, const double*, const z128*, z64*,
+                                                 z128*, z128*, double, int*, cudaStream_t, const int*);
+template void launch_coarse_gmres<float, double>(const Grid&, double, double, const double*, const z64*, z128*,
+                                                 z128*, z128*, double, int*, cudaStream_t, const int*);
+
+}  // namespace helm

@@ -263,6 +263,20 @@ struct OpCoef {
   int real_shift;  // s_im == 0 (the operator A): the diagonal is real away from the faces
 };
 
+// Coefficients of a level's operator in working precision R (host side), shift s = s_re + i s_im.
+template <typename R>
+inline OpCoef<R> coef_for(double h, double s_re, double s_im, double omega) {
+  OpCoef<R> c;
+  c.ih2 = (R)(1.0 / (h * h));
+  c.six_ih2 = (R)(6.0 / (h * h));
+  c.s_re = (R)s_re;
+  c.s_im = (R)s_im;
+  c.two_over_h = (R)(2.0 / h);
+  c.omega = (R)omega;
+  c.real_shift = s_im == 0.0;
+  return c;
+}
+
 // Diagonal of the operator at a node lying on `nf` Sommerfeld faces (kp = sqrt(k^2), used only
 // when nf > 0):
 // 6/h^2 - s k^2 - i (2 k / h) nf.  The face term comes from eliminating the ghost value

@@ -136,6 +136,9 @@ struct helm_ctx {
   Level L[MAX_LEVELS];
   int nc = 0;
   z128* Minv = nullptr;
+  // the paper's coarsest-grid GMRES (coarse_tol > 0): basis, Hessenberg columns, last report
+  z128 *cgV = nullptr, *cgH = nullptr;
+  int* cginfo = nullptr;
   // Krylov workspace
   int m = 0;
   size_t n0 = 0;
@@ -457,9 +460,22 @@ void down_full_launch(const VLevel<R>& F, const VLevel<R>& C, double sr, double 
 // the first relative level lf >= 1 whose sub-cycle (at least two levels, one right-hand side)
 // fits the shared-memory budget, with its vectors laid out in *cc and the byte count in
 // *bytes; L when none fits or the context runs without it.
+// The coarsest-grid solve e = M_c^{-1} b: the precomputed dense inverse, or with coarse_tol > 0
+// (one right-hand side) the paper's GMRES to that relative residual.
+template <typename TI, typename TO>
+void coarse_solve(helm_ctx* c, const cx<TI>* b, cx<TO>* e, cudaStream_t st, const int* active, int nb) {
+  if (c->p.coarse_tol > 0.0 && nb == 1) {
+    const Level& Lc = c->L[c->nlev - 1];
+    launch_coarse_gmres<TI, TO>(Lc.g, c->s_re, c->s_im, Lc.k2, b, e, c->cgV, c->cgH, c->p.coarse_tol, c->cginfo, st,
+                                active);
+  } else {
+    launch_coarse<TI, TO>(c->nc, c->Minv, b, e, st, active, nb);
+  }
+}
+
 template <typename R>
 int plan_coarse_cycle(helm_ctx* c, const VLevel<R>* lv, int L, CCycle<R>* cc, size_t* bytes) {
-  if (!c->p.fuse_coarse || lv[0].g.nb != 1 || !coarse_cycle_ready<R>()) return L;
+  if (!c->p.fuse_coarse || lv[0].g.nb != 1 || !coarse_cycle_ready<R>() || c->p.coarse_tol > 0.0) return L;
   for (int lf = 1; lf <= L - 2; ++lf) {
     if (L - lf > CC_MAX_LEVELS) continue;
     // layout in units of cx<R>: per level B, U (and T), then the FP64 omega/d copy, then the
@@ -514,7 +530,7 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
   const double nc = c->nc;
   if (L == 1) {
     KL(F_COARSE, nc * nc * 16 + nc * (ib + ob), 8 * nc * nc * nbv,
-       (launch_coarse<TI, TO>(c->nc, c->Minv, rin, zout, st, active, nbv)));
+       (coarse_solve<TI, TO>(c, rin, zout, st, active, nbv)));
     return;
   }
   // levels lf.. run as one single-CTA sub-cycle when they fit in shared memory
@@ -567,7 +583,7 @@ void run_vcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, const cx<TI>* ri
   } else {
     // coarsest: exact FP64 solve
     KL(F_COARSE, nc * nc * 16 + nc * 2 * cb, 8 * nc * nc * nbv,
-       (launch_coarse<R, R>(c->nc, c->Minv, lv[L - 1].B, lv[L - 1].E, st, active, nbv)));
+       (coarse_solve<R, R>(c, lv[L - 1].B, lv[L - 1].E, st, active, nbv)));
   }
   // up: prolongation + correction, post-smoothing
   for (int l = Ld - 2; l >= 0; --l) {
@@ -614,7 +630,7 @@ void vcycle_from(helm_ctx* c, const VLevel<R>* lv, int L, int l, cudaStream_t st
   const VLevel<R>& F = lv[l];
   const double nc = c->nc, cb = 2.0 * sizeof(R), kb = sizeof(R), db = F.dinv ? 16.0 : 0.0, kd = db ? 16.0 : kb;
   if (l == L - 1) {
-    KL(F_COARSE, nc * nc * 16 + nc * 2 * cb, 8 * nc * nc, (launch_coarse<R, R>(c->nc, c->Minv, F.B, F.E, st, active, F.g.nb)));
+    KL(F_COARSE, nc * nc * 16 + nc * 2 * cb, 8 * nc * nc, (coarse_solve<R, R>(c, F.B, F.E, st, active, F.g.nb)));
     return;
   }
   const VLevel<R>& C = lv[l + 1];
@@ -646,7 +662,7 @@ void fcycle_levels(helm_ctx* c, const VLevel<R>* lv, int L, int l, const cx<TI>*
   const double nc = c->nc, cb = 2.0 * sizeof(R), kb = sizeof(R), ib = 2.0 * sizeof(TI), ob = 2.0 * sizeof(TO);
   if (l == L - 1) {
     KL(F_COARSE, nc * nc * 16 + nc * (ib + ob), 8 * nc * nc,
-       (launch_coarse<TI, TO>(c->nc, c->Minv, rin, zout, st, active, lv[l].g.nb)));
+       (coarse_solve<TI, TO>(c, rin, zout, st, active, lv[l].g.nb)));
     return;
   }
   const VLevel<R>& F = lv[l];
@@ -1276,7 +1292,7 @@ void stage_impl(helm_ctx* c, int l, int stage, const cx<R>* b, const cx<R>* e, c
   const double sr = c->s_re, si = c->s_im, om = c->p.omega;
   Level& F = c->L[l];
   if (stage == 2) {
-    launch_coarse<R, R>(c->nc, c->Minv, b, out, st, nullptr);
+    coarse_solve<R, R>(c, b, out, st, nullptr, 1);
     return;
   }
   Level& C = c->L[l + 1];
@@ -1922,6 +1938,7 @@ void helm_default_params(helm_params* p) {
   p->fuse_up = -1;
   p->stall_window = 1000;
   p->reorth_keep = 0.1;
+  p->coarse_tol = 0.0;
 }
 
 const char* helm_last_error(const helm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
@@ -2087,6 +2104,12 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
     dfree(c, sing);
     if (hsing) return fail(c, HELM_ENUMERIC, "coarsest-grid operator is singular");
   }
+  if (P.coarse_tol > 0.0) {
+    if (c->nc > CG_CS * 512) return fail(c, HELM_EINVAL, "coarse_tol > 0 needs a coarsest grid of at most %d unknowns", CG_CS * 512);
+    TRY(dalloc(c, &c->cgV, (size_t)(CG_MAX + 1) * c->nc));
+    TRY(dalloc(c, &c->cgH, (size_t)CG_MAX * (CG_MAX + 1)));
+    TRY(dalloc(c, &c->cginfo, 2));
+  }
   // Krylov workspace
   const int m = P.restart;
   c->m = m;
@@ -2185,6 +2208,7 @@ helm_status helm_create(int n1, int n2, int n3, double h, const double* k2, helm
   if (P.fuse_up < -1 || P.fuse_up > 1) return fail(nullptr, HELM_EINVAL, "fuse_up must lie in -1..1");
   if (P.stall_window < 0) return fail(nullptr, HELM_EINVAL, "stall_window must be >= 0");
   if (!(P.reorth_keep >= 0.0 && P.reorth_keep < 1.0)) return fail(nullptr, HELM_EINVAL, "reorth_keep must lie in [0, 1)");
+  if (!(P.coarse_tol >= 0.0 && P.coarse_tol < 1.0)) return fail(nullptr, HELM_EINVAL, "coarse_tol must lie in [0, 1)");
   if (P.precision == HELM_PREC_MIXED && P.krylov == HELM_GMRES) P.krylov = HELM_FGMRES;
   helm_ctx* c = new (std::nothrow) helm_ctx();
   if (!c) return fail(nullptr, HELM_ENOMEM, "host allocation failed");

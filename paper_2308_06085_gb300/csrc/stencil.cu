@@ -1415,18 +1415,6 @@ dim3 grid_for(const Grid& g, int fam, int& zchunk, dim3& blk) {
   return dim3(bx, by, bz);
 }
 
-template <typename R>
-OpCoef<R> coef_for(double h, double s_re, double s_im, double omega) {
-  OpCoef<R> c;
-  c.ih2 = (R)(1.0 / (h * h));
-  c.six_ih2 = (R)(6.0 / (h * h));
-  c.s_re = (R)s_re;
-  c.s_im = (R)s_im;
-  c.two_over_h = (R)(2.0 / h);
-  c.omega = (R)omega;
-  c.real_shift = s_im == 0.0;
-  return c;
-}
 
 }  // namespace
 

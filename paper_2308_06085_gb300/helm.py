@@ -43,7 +43,7 @@ class Params(C.Structure):
                 ("reorth", C.c_int), ("cycle", C.c_int), ("idr_kappa", C.c_double),
                 ("graphs", C.c_int), ("autotune", C.c_int), ("side", C.c_int),
                 ("fuse_coarse", C.c_int), ("gs_sums", C.c_int), ("fuse_down", C.c_int), ("fuse_up", C.c_int),
-                ("stall_window", C.c_int), ("reorth_keep", C.c_double)]
+                ("stall_window", C.c_int), ("reorth_keep", C.c_double), ("coarse_tol", C.c_double)]
 
 
 class KernelStat(C.Structure):
@@ -195,7 +195,7 @@ class Solver:
     def __init__(self, n, h, k2, bc=SOMMERFELD, *, beta1=1.0, beta2=-0.5, omega=0.8, coarsest_n=4,
                  krylov="gmres", restart=30, tol=1e-6, max_iter=2000, precision="fp64", orth=None,
                  reorth=None, cycle="v", idr_s=4, idr_kappa=0.7, shadow=None, graphs=True, autotune=True, side="right", fuse_coarse=False, gs_sums=True, fuse_down=-1, fuse_up=-1, stall_window=1000,
-                 reorth_keep=0.1, device=None):
+                 reorth_keep=0.1, coarse_tol=0.0, device=None):
         n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(int(x) for x in n)
         self.n = (n1, n2, n3)
         self.h = float(h)
@@ -220,6 +220,7 @@ class Solver:
         p.fuse_up = int(fuse_up)
         p.stall_window = int(stall_window)
         p.reorth_keep = float(reorth_keep)
+        p.coarse_tol = float(coarse_tol)
         p.restart, p.tol, p.max_iter = restart, tol, max_iter
         p.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
         if orth is not None:

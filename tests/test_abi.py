@@ -45,7 +45,7 @@ def test_default_params_are_the_papers(libhelm):
     assert (p.beta1, p.beta2, p.omega, p.nu1, p.nu2) == (1.0, -0.5, 0.8, 1, 1)
     assert (p.restart, p.tol, p.krylov, p.precision) == (30, 1e-6, 0, 0)
     assert (p.graphs, p.autotune, p.side, p.fuse_coarse, p.gs_sums, p.fuse_down, p.fuse_up) == (1, 1, 0, 0, 1, -1, -1)
-    assert p.stall_window == 1000 and p.reorth_keep == 0.1
+    assert p.stall_window == 1000 and p.reorth_keep == 0.1 and p.coarse_tol == 0.0
 
 
 @pytest.mark.parametrize("args,msg", [
@@ -76,7 +76,8 @@ def test_bad_parameters_rejected(libhelm):
                             ("omega", 0.0, "omega"), ("tol", 0.0, "tol"), ("precision", 7, "precision"),
                             ("gs_sums", 2, "gs_sums"), ("side", 3, "side"), ("cycle", 2, "cycle"),
                             ("fuse_down", 4, "fuse_down"), ("fuse_up", 2, "fuse_up"),
-                            ("stall_window", -1, "stall_window"), ("reorth_keep", 1.0, "reorth_keep")]:
+                            ("stall_window", -1, "stall_window"), ("reorth_keep", 1.0, "reorth_keep"),
+                            ("coarse_tol", -1.0, "coarse_tol")]:
         p = helm.Params()
         libhelm.helm_default_params(C.byref(p))
         setattr(p, field, val)
