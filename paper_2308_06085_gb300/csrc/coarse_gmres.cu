@@ -9,8 +9,8 @@
 // owns a contiguous slice of the grid (one node per thread), applies M on it, and contributes
 // partial inner products that every CTA then sums from the others' shared memory in rank
 // order, so all CTAs hold the same Hessenberg column, Givens rotations and stopping decision
-// and take every barrier together.  Classical Gram-Schmidt with a second pass on every step
-// (the unknown count is small, and the tolerance tight).  The basis lives in global memory
+// and take every barrier together.  Classical Gram-Schmidt with the library's selective second
+// pass (the reorth_keep test).  The basis lives in global memory
 // (L2-resident); values written during the launch by other CTAs are read through L2 only.
 #include "internal.cuh"
 
@@ -64,7 +64,7 @@ template <typename TI, typename TO>
 __global__ void __cluster_dims__(CG_CS, 1, 1) __launch_bounds__(CG_NT)
     k_coarse_gmres(Grid g, OpCoef<double> c, const double* __restrict__ k2, const cx<TI>* __restrict__ b,
                    cx<TO>* __restrict__ e, z128* __restrict__ V, z128* __restrict__ H, int maxit, double tol,
-                   int* __restrict__ info, const int* __restrict__ active) {
+                   double keep, int* __restrict__ info, const int* __restrict__ active) {
   if (active && *active == 0) return;  // read by every thread of every CTA: all return together
   cgr::cluster_group cl = cgr::this_cluster();
   const int rank = (int)cl.block_rank();
@@ -84,7 +84,7 @@ __global__ void __cluster_dims__(CG_CS, 1, 1) __launch_bounds__(CG_NT)
   __shared__ z128 sy[CG_MAX];
   __shared__ double sred[CG_NW];
   __shared__ double sval;
-  __shared__ int sstop;
+  __shared__ int sstop, spass2;
 
   // sum over the cluster of one real value per thread: block sum into part[buf][0], barrier,
   // then the CTAs' sums added in rank order (the same result in every CTA)
@@ -106,12 +106,18 @@ __global__ void __cluster_dims__(CG_CS, 1, 1) __launch_bounds__(CG_NT)
     __syncthreads();
     return sval;
   };
-  // hp[i] = sum over the grid of conj(V_i) w, i <= j: warp w takes i = w, w + CG_NW, ...
-  auto dots = [&](int j, int buf) {
-    for (int i = warp; i <= j; i += CG_NW) {
+  // hp[i] = sum over the grid of conj(V_i) w, i <= j, and with `wn` hp[j + 1] = |w|^2: warp w
+  // takes i = w, w + CG_NW, ...
+  auto dots = [&](int j, int buf, int wn) {
+    for (int i = warp; i <= j + wn; i += CG_NW) {
       double re = 0.0, im = 0.0;
       const z128* Vi = V + (size_t)i * n + p0;
-      for (int q = lane; q < len; q += 32) cdot_acc(ld_l2(Vi + q), sw[q], re, im);
+      if (i > j) {
+        for (int q = lane; q < len; q += 32) re = fma(sw[q].re, sw[q].re, fma(sw[q].im, sw[q].im, re));
+      } else {
+#pragma unroll 4
+        for (int q = lane; q < len; q += 32) cdot_acc(ld_l2(Vi + q), sw[q], re, im);
+      }
       for (int o = 16; o; o >>= 1) {
         re += __shfl_xor_sync(0xffffffffu, re, o);
         im += __shfl_xor_sync(0xffffffffu, im, o);
@@ -119,7 +125,7 @@ __global__ void __cluster_dims__(CG_CS, 1, 1) __launch_bounds__(CG_NT)
       if (lane == 0) part[buf][i] = mkc<double>(re, im);
     }
     cl.sync();
-    for (int i = t; i <= j; i += CG_NT) {
+    for (int i = t; i <= j + wn; i += CG_NT) {
       double re = 0.0, im = 0.0;
       for (int r = 0; r < CG_CS; ++r) {
         const z128 v = cl.map_shared_rank(&part[buf][0], r)[i];
@@ -151,15 +157,25 @@ __global__ void __cluster_dims__(CG_CS, 1, 1) __launch_bounds__(CG_NT)
     cl.sync();  // v_j complete in every CTA's slice; the reads of part[0] are done
     if (own) sw[t] = coarse_apply(g, c, k2, V + (size_t)j * n, p);
     __syncthreads();
+    // classical Gram-Schmidt; the second pass only when the first kept less than `keep` of
+    // |w|^2 (the Daniel-Gragg-Kaufman-Stewart test, decided alike in every CTA)
     for (int pass = 0; pass < 2; ++pass) {
-      dots(j, pass);
+      dots(j, pass, pass == 0);
+      if (pass == 0 && t == 0) {
+        double h2 = 0.0;
+        for (int i = 0; i <= j; ++i) h2 += hp[i].re * hp[i].re + hp[i].im * hp[i].im;
+        const double w2 = hp[j + 1].re;
+        spass2 = !(w2 - h2 >= keep * w2);
+      }
       for (int i = t; i <= j; i += CG_NT) hcol[i] = pass == 0 ? hp[i] : cadd(hcol[i], hp[i]);
       if (own) {
         z128 w = sw[t];
+#pragma unroll 8
         for (int i = 0; i <= j; ++i) w = csub(w, cmul(hp[i], ld_l2(V + (size_t)i * n + p)));
         sw[t] = w;
       }
       __syncthreads();
+      if (!spass2) break;
     }
     const z128 wv = own ? sw[t] : mkc<double>(0.0, 0.0);
     const double hn = sqrt(cluster_sum(wv.re * wv.re + wv.im * wv.im, 0));
@@ -218,6 +234,7 @@ __global__ void __cluster_dims__(CG_CS, 1, 1) __launch_bounds__(CG_NT)
   __syncthreads();
   if (own) {
     z128 x = mkc<double>(0.0, 0.0);
+#pragma unroll 8
     for (int i = 0; i < k; ++i) x = cfma(sy[i], ld_l2(V + (size_t)i * n + p), x);
     e[p] = cvt<TO>(x);
   }
@@ -231,19 +248,19 @@ __global__ void __cluster_dims__(CG_CS, 1, 1) __launch_bounds__(CG_NT)
 
 template <typename TI, typename TO>
 void launch_coarse_gmres(const Grid& g, double s_re, double s_im, const double* k2, const cx<TI>* b, cx<TO>* e,
-                         z128* V, z128* H, double tol, int* info, cudaStream_t st, const int* active) {
+                         z128* V, z128* H, double tol, double keep, int* info, cudaStream_t st, const int* active) {
   const int n = (int)g.npts();
   const int maxit = n < CG_MAX ? n : CG_MAX;
   k_coarse_gmres<TI, TO><<<CG_CS, CG_NT, 0, st>>>(g, coef_for<double>(g.h, s_re, s_im, 0.0), k2, b, e, V, H, maxit,
-                                                  tol, info, active);
+                                                  tol, keep, info, active);
 }
 template void launch_coarse_gmres<double, double>(const Grid&, double, double, const double*, const z128*, z128*,
-                                                  z128*, z128*, double, int*, cudaStream_t, const int*);
+                                                  z128*, z128*, double, double, int*, cudaStream_t, const int*);
 template void launch_coarse_gmres<float, float>(const Grid&, double, double, const double*, const z64*, z64*, z128*,
-                                                z128*, double, int*, cudaStream_t, const int*);
+                                                z128*, double, double, int*, cudaStream_t, const int*);
 template void launch_coarse_gmres<double, float>(const Grid&, double, double, const double*, const z128*, z64*,
-                                                 z128*, z128*, double, int*, cudaStream_t, const int*);
+                                                 z128*, z128*, double, double, int*, cudaStream_t, const int*);
 template void launch_coarse_gmres<float, double>(const Grid&, double, double, const double*, const z64*, z128*,
-                                                 z128*, z128*, double, int*, cudaStream_t, const int*);
+                                                 z128*, z128*, double, double, int*, cudaStream_t, const int*);
 
 }  // namespace helm

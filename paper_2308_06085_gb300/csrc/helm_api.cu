@@ -466,8 +466,8 @@ template <typename TI, typename TO>
 void coarse_solve(helm_ctx* c, const cx<TI>* b, cx<TO>* e, cudaStream_t st, const int* active, int nb) {
   if (c->p.coarse_tol > 0.0 && nb == 1) {
     const Level& Lc = c->L[c->nlev - 1];
-    launch_coarse_gmres<TI, TO>(Lc.g, c->s_re, c->s_im, Lc.k2, b, e, c->cgV, c->cgH, c->p.coarse_tol, c->cginfo, st,
-                                active);
+    launch_coarse_gmres<TI, TO>(Lc.g, c->s_re, c->s_im, Lc.k2, b, e, c->cgV, c->cgH, c->p.coarse_tol,
+                                c->p.reorth_keep, c->cginfo, st, active);
   } else {
     launch_coarse<TI, TO>(c->nc, c->Minv, b, e, st, active, nb);
   }
