@@ -562,7 +562,7 @@ def run_ours(args):
 # ncu traffic records: a deterministic region of launches, then the counters written beside
 # the algorithmic bytes the library's profiler counted for the same launches
 # ------------------------------------------------------------------------------------------
-REGION_OUT = os.path.join(ROOT, "gpurun_out")
+REGION_OUT = os.path.join(ROOT, "_build", "ncu_regions")  # scratch, not tracked
 REGION_KERNELS = {  # ncu -k filter for each region
     "gs": "regex:k_mdot|k_gs_update",
     "vcycle64": "regex:k_smooth0|k_stencil|k_restrict|k_prolong|k_rr|k_up|k_down",
@@ -580,7 +580,7 @@ def ncu_region(torch, helm, inputs, kind):
       vcycle32 : one Arnoldi step of the mixed solve (its complex64 V-cycle; the FP32 kernels are
                  told apart from the FP64 outer ones by their template arguments).
     The library's profiler runs over the same launches; its per-family launch counts and
-    algorithmic bytes go to gpurun_out/ncu_region_<kind>.json for --write-traffic."""
+    algorithmic bytes go to _build/ncu_regions/ncu_region_<kind>.json for --write-traffic."""
     w = inputs.workload(HEADLINE, HEADLINE_N)
     if kind == "gs":
         s = helm.Solver(w["n"], w["h"], w["k2"], helm.SOMMERFELD, restart=8, max_iter=8, reorth="always",

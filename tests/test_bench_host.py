@@ -54,17 +54,17 @@ def test_write_traffic_from_an_ncu_csv(tmp_path, monkeypatch):
     """The finest level's down-sweep kernel is the first launch of its family in the region and
     its up-sweep kernel the last; each record holds DRAM bytes over the library's count."""
     (tmp_path / "profiles").mkdir()
-    (tmp_path / "gpurun_out").mkdir()
+    (tmp_path / "regions").mkdir()
     for f in bench.SOURCES["vcycle64"]:
         os.makedirs(tmp_path / os.path.dirname(f), exist_ok=True)
         (tmp_path / f).write_text("// source\n")
     region = {"region": "vcycle64", "workload": "w", "families": {
         "k_smooth0 (finest)": {"launches": 1, "bytes": 1.0e9}, "k_smooth0": {"launches": 1, "bytes": 1e8},
         "k_stencil(jacobi) (finest)": {"launches": 1, "bytes": 1.25e9}}}
-    (tmp_path / "gpurun_out" / "ncu_region_vcycle64.json").write_text(json.dumps(region))
+    (tmp_path / "regions" / "ncu_region_vcycle64.json").write_text(json.dumps(region))
     (tmp_path / "cap.csv").write_text(CSV)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "REGION_OUT", str(tmp_path / "gpurun_out"))
+    monkeypatch.setattr(bench, "REGION_OUT", str(tmp_path / "regions"))
     bench.write_traffic(str(tmp_path / "cap.csv"), "vcycle64")
     rec = json.loads((tmp_path / "profiles" / "ncu_traffic.json").read_text())["kernels"]
     assert rec["k_smooth0 (finest)"]["dram_bytes"] == pytest.approx(8e8)
