@@ -302,6 +302,13 @@ HELM_API helm_status helm_rhs_point(helm_ctx* ctx, int nsrc, const int* nodes, v
 HELM_API helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, helm_solve_info* info,
                        void* stream);
 
+/* helm_solve from the initial guess x = 0 (Sec. 3.2 starts GMRES from a given x_0; the
+ * paper's experiments start from zero).  x is output only: it is not read, and with host
+ * buffers only b is copied to the device before the solve.  Same arguments, waiting and
+ * return values as helm_solve. */
+HELM_API helm_status helm_solve_zero(helm_ctx* ctx, const void* b, void* x, helm_solve_info* info,
+                                     void* stream);
+
 /* Shadow space of IDR(s): s (1..8) device c128 grid vectors P_0 .. P_{s-1}, consecutive, one
  * grid vector each (the layout of helm_solve's b).  IDR(s) builds its residuals orthogonal to
  * span(P) step by step (Sec. 3.1); the paper draws P at random, and the caller passes those

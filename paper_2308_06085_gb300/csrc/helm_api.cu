@@ -1910,6 +1910,45 @@ helm_status solve_batched_core(helm_ctx* c, int nrhs, const z128* B, z128* X, he
 
 }  // namespace
 
+namespace {
+
+// helm_solve / helm_solve_zero: the solve through device or host buffers; with `zero` the
+// initial guess is 0 and x is output only (not read, so not copied to the device).
+helm_status solve_entry(helm_ctx* c, const void* b, void* x, helm_solve_info* info, void* stream, bool zero) {
+  if (!c) return HELM_EINVAL;
+  if (!b || !x || b == x) return fail(c, HELM_EINVAL, "b and x must be distinct non-NULL pointers");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+  if (bdev != xdev) return fail(c, HELM_EINVAL, "b and x must both be device or both be host pointers");
+  const size_t bytes = c->n0 * sizeof(z128);
+  const z128* bd = (const z128*)b;
+  z128* xd = (z128*)x;
+  if (!bdev) {
+    CU(cudaMemcpyAsync(c->bs, b, bytes, cudaMemcpyHostToDevice, st));
+    if (!zero) CU(cudaMemcpyAsync(c->xs, x, bytes, cudaMemcpyHostToDevice, st));
+    bd = c->bs;
+    xd = c->xs;
+  }
+  if (zero) CU(cudaMemsetAsync(xd, 0, bytes, st));
+  helm_solve_info tmp;
+  helm_solve_info* inf = info ? info : &tmp;
+  c->err.clear();
+  helm_status s = krylov_device(c, bd, xd, inf, st);
+  if (!bdev && (s == HELM_OK || s == HELM_ENOCONV || s == HELM_ENUMERIC)) {
+    CU(cudaMemcpyAsync(x, c->xs, bytes, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+  }
+  inf->status = (int)s;
+  inf->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (s == HELM_ENOCONV && c->err.empty())
+    fail(c, s, "max_iter (%d) reached at relative residual %.3e", c->p.max_iter, inf->rel_residual);
+  if (s == HELM_ENUMERIC) fail(c, s, "non-finite residual or Krylov breakdown");
+  return s;
+}
+
+}  // namespace
+
 extern "C" {
 
 void helm_default_params(helm_params* p) {
@@ -2557,35 +2596,11 @@ helm_status helm_set_shadow_space(helm_ctx* c, int s, const void* P, void* strea
 }
 
 helm_status helm_solve(helm_ctx* c, const void* b, void* x, helm_solve_info* info, void* stream) {
-  if (!c) return HELM_EINVAL;
-  if (!b || !x || b == x) return fail(c, HELM_EINVAL, "b and x must be distinct non-NULL pointers");
-  const auto t0 = std::chrono::steady_clock::now();
-  cudaStream_t st = (cudaStream_t)stream;
-  const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
-  if (bdev != xdev) return fail(c, HELM_EINVAL, "b and x must both be device or both be host pointers");
-  const size_t bytes = c->n0 * sizeof(z128);
-  const z128* bd = (const z128*)b;
-  z128* xd = (z128*)x;
-  if (!bdev) {
-    CU(cudaMemcpyAsync(c->bs, b, bytes, cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(c->xs, x, bytes, cudaMemcpyHostToDevice, st));
-    bd = c->bs;
-    xd = c->xs;
-  }
-  helm_solve_info tmp;
-  helm_solve_info* inf = info ? info : &tmp;
-  c->err.clear();
-  helm_status s = krylov_device(c, bd, xd, inf, st);
-  if (!bdev && (s == HELM_OK || s == HELM_ENOCONV || s == HELM_ENUMERIC)) {
-    CU(cudaMemcpyAsync(x, c->xs, bytes, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-  }
-  inf->status = (int)s;
-  inf->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  if (s == HELM_ENOCONV && c->err.empty())
-    fail(c, s, "max_iter (%d) reached at relative residual %.3e", c->p.max_iter, inf->rel_residual);
-  if (s == HELM_ENUMERIC) fail(c, s, "non-finite residual or Krylov breakdown");
-  return s;
+  return solve_entry(c, b, x, info, stream, false);
+}
+
+helm_status helm_solve_zero(helm_ctx* c, const void* b, void* x, helm_solve_info* info, void* stream) {
+  return solve_entry(c, b, x, info, stream, true);
 }
 
 }  // extern "C"

@@ -96,6 +96,7 @@ def lib():
     L.helm_vcycle_stage.argtypes = [vp, i, i, i, vp, vp, vp, vp]
     L.helm_rhs_point.argtypes = [vp, i, C.POINTER(i), vp, vp]
     L.helm_solve.argtypes = [vp, vp, vp, C.POINTER(SolveInfo), vp]
+    L.helm_solve_zero.argtypes = [vp, vp, vp, C.POINTER(SolveInfo), vp]
     L.helm_profile.argtypes = [vp, i]
     L.helm_profile_read.argtypes = [vp, C.POINTER(KernelStat), i, C.POINTER(i), C.POINTER(C.c_longlong)]
     L.helm_solve_batched.argtypes = [vp, i, vp, vp, C.POINTER(SolveInfo), vp]
@@ -115,7 +116,7 @@ def lib():
     L.helm_last_error.argtypes = [vp]
     L.helm_last_error.restype = C.c_char_p
     for f in ("helm_create", "helm_destroy", "helm_levels", "helm_level_dims", "helm_apply", "cslp_vcycle",
-              "helm_vcycle_stage", "helm_rhs_point", "helm_solve", "helm_profile", "helm_profile_read"):
+              "helm_vcycle_stage", "helm_rhs_point", "helm_solve", "helm_solve_zero", "helm_profile", "helm_profile_read"):
         getattr(L, f).restype = i
     _lib = L
     return L
@@ -453,20 +454,23 @@ class Solver:
             self._check(st)
         return loss.value, grad, info.as_dict()
 
-    def solve(self, b, x=None):
+    def solve(self, b, x=None, zero_guess=False):
         """Solve A x = b.  b (and x, the initial guess) are complex128 tensors on the GPU, or
-        both on the host (pinned or pageable), in which case the library stages the copies."""
+        both on the host (pinned or pageable), in which case the library stages the copies.
+        zero_guess: start from x = 0 (helm_solve_zero); x, when given, only receives the
+        solution."""
         host = b.device.type == "cpu"
         b = b.reshape(self.shape).contiguous()
         if b.dtype != torch.complex128:
             raise TypeError("helm_solve takes complex128 vectors")
         if x is None:
-            x = torch.zeros_like(b)
+            x = torch.empty_like(b) if zero_guess else torch.zeros_like(b)
         x = x.reshape(self.shape)
-        if (x.device.type == "cpu") != host or not x.is_contiguous():
-            raise TypeError("x must be a contiguous tensor on the same kind of device as b")
+        if (x.device.type == "cpu") != host or not x.is_contiguous() or x.dtype != torch.complex128:
+            raise TypeError("x must be a contiguous complex128 tensor on the same kind of device as b")
         info = SolveInfo()
-        st = lib().helm_solve(self._ctx, _ptr(b), _ptr(x), C.byref(info), _stream())
+        entry = lib().helm_solve_zero if zero_guess else lib().helm_solve
+        st = entry(self._ctx, _ptr(b), _ptr(x), C.byref(info), _stream())
         if st not in (OK, ENOCONV):
             self._check(st)
         out = info.as_dict()

@@ -210,6 +210,13 @@ def test_solve_host_buffers_and_warm_start(helm):
     # warm start from the solution: converged at entry, no Arnoldi step
     x2, info2 = s.solve(b, xd.clone())
     assert info2["iterations"] == 0 and info2["rel_residual"] <= 1e-6
+    # helm_solve_zero ignores what x holds on entry (device and pinned host buffers): the same
+    # solve as from a zero guess, bit for bit
+    junk = torch.full(s.shape, 7.0 + 3.0j, dtype=torch.complex128)
+    xz, infoz = s.solve(b, junk.clone().cuda(), zero_guess=True)
+    assert infoz["iterations"] == infod["iterations"] and torch.equal(xz, xd)
+    xzh, infozh = s.solve(bh, junk.clone().pin_memory(), zero_guess=True)
+    np.testing.assert_array_equal(xzh.numpy(), xd.cpu().numpy())
 
 
 def test_solve_edge_cases(helm):
