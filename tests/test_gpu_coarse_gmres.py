@@ -102,3 +102,26 @@ def test_table1_with_the_papers_coarse_solver(helm):
     rb = o.bicgstab(w["rhs"], tol=1e-6, max_iter=2000)
     assert abs(counts["bicgstab"] - rb["iters"]) <= 0.1 * rb["iters"], (counts, rb["iters"])
     assert 0.85 * 359 <= counts["bicgstab"] <= 1.1 * 407, counts
+
+
+@pytest.mark.parametrize("precision,krylov,cycle", [("mixed", "fgmres", "v"), ("fp64", "gmres", "f"),
+                                                    ("fp64", "idrs", "v")])
+def test_solves_with_the_coarse_gmres(helm, precision, krylov, cycle):
+    """Whole solves (captured in CUDA graphs, the complex64 cycle included) with the coarse GMRES:
+    they reach the true relative residual 1e-6 with the oracle's operator, in the iteration count
+    of the same solve with the dense coarsest inverse (within one for GMRES, 10% for IDR(s))."""
+    w = I.workload("wedge", 32)
+    counts = []
+    for tol in (TOL, 0.0):
+        s = helm.Solver(w["n"], w["h"], w["k2"], S, coarsest_n=8, krylov=krylov, precision=precision, cycle=cycle,
+                        coarse_tol=tol, max_iter=3000)
+        b = s.rhs_point(w["sources"])
+        x, info = s.solve(b)
+        s.close()
+        assert info["status"] == 0, info
+        bn = b.cpu().numpy()
+        ax = oracle.apply(x.cpu().numpy(), w["k2"], w["h"], S)
+        assert np.linalg.norm(bn - ax) <= 1.01e-6 * np.linalg.norm(bn)
+        counts.append(info["iterations"])
+    slack = 1 if krylov != "idrs" else max(2, 0.1 * counts[1])
+    assert abs(counts[0] - counts[1]) <= slack, counts
