@@ -309,6 +309,12 @@ HELM_API helm_status helm_solve(helm_ctx* ctx, const void* b, void* x, helm_solv
 HELM_API helm_status helm_solve_zero(helm_ctx* ctx, const void* b, void* x, helm_solve_info* info,
                                      void* stream);
 
+/* Report of the last coarsest-grid GMRES of a context created with coarse_tol > 0 (Sec. 5):
+ * *steps = GMRES steps it took, *converged = 1 when it met coarse_tol (0 when it stopped at
+ * 256 steps or on a breakdown).  Waits for the device.  HELM_EINVAL for a context that solves
+ * the coarsest grid with the dense inverse. */
+HELM_API helm_status helm_coarse_info(helm_ctx* ctx, int* steps, int* converged);
+
 /* Shadow space of IDR(s): s (1..8) device c128 grid vectors P_0 .. P_{s-1}, consecutive, one
  * grid vector each (the layout of helm_solve's b).  IDR(s) builds its residuals orthogonal to
  * span(P) step by step (Sec. 3.1); the paper draws P at random, and the caller passes those

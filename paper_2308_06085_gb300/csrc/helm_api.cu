@@ -2148,6 +2148,7 @@ static helm_status create_impl(helm_ctx* c, int n1, int n2, int n3, double h, co
     TRY(dalloc(c, &c->cgV, (size_t)(CG_MAX + 1) * c->nc));
     TRY(dalloc(c, &c->cgH, (size_t)CG_MAX * (CG_MAX + 1)));
     TRY(dalloc(c, &c->cginfo, 2));
+    CU(cudaMemsetAsync(c->cginfo, 0, 2 * sizeof(int), st));
   }
   // Krylov workspace
   const int m = P.restart;
@@ -2601,6 +2602,18 @@ helm_status helm_solve(helm_ctx* c, const void* b, void* x, helm_solve_info* inf
 
 helm_status helm_solve_zero(helm_ctx* c, const void* b, void* x, helm_solve_info* info, void* stream) {
   return solve_entry(c, b, x, info, stream, true);
+}
+
+helm_status helm_coarse_info(helm_ctx* c, int* steps, int* converged) {
+  if (!c || !steps || !converged) return HELM_EINVAL;
+  if (!c->cginfo) return fail(c, HELM_EINVAL, "the context solves the coarsest grid exactly (coarse_tol = 0)");
+  int h[2] = {0, 0};
+  // the last solve may have run on any stream: wait for the device, then read
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(h, c->cginfo, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(c, HELM_ECUDA, "helm_coarse_info: %s", cudaGetErrorString(cudaGetLastError()));
+  *steps = h[0];
+  *converged = h[1];
+  return HELM_OK;
 }
 
 }  // extern "C"

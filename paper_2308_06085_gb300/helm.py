@@ -97,6 +97,8 @@ def lib():
     L.helm_rhs_point.argtypes = [vp, i, C.POINTER(i), vp, vp]
     L.helm_solve.argtypes = [vp, vp, vp, C.POINTER(SolveInfo), vp]
     L.helm_solve_zero.argtypes = [vp, vp, vp, C.POINTER(SolveInfo), vp]
+    L.helm_coarse_info.argtypes = [vp, C.POINTER(i), C.POINTER(i)]
+    L.helm_coarse_info.restype = i
     L.helm_profile.argtypes = [vp, i]
     L.helm_profile_read.argtypes = [vp, C.POINTER(KernelStat), i, C.POINTER(i), C.POINTER(C.c_longlong)]
     L.helm_solve_batched.argtypes = [vp, i, vp, vp, C.POINTER(SolveInfo), vp]
@@ -310,6 +312,12 @@ class Solver:
         v = C.c_int(-1 if variant is None else int(variant))
         self._check(lib().helm_dot_variant(self._ctx, 0 if variant is None else 1, C.byref(v)))
         return v.value
+
+    def coarse_info(self):
+        """(steps, converged) of the last coarsest-grid GMRES (contexts with coarse_tol > 0)."""
+        steps, conv = C.c_int(), C.c_int()
+        self._check(lib().helm_coarse_info(self._ctx, C.byref(steps), C.byref(conv)))
+        return steps.value, bool(conv.value)
 
     def kernel_variants(self, level):
         """{'tiled', 'fused_down', 'down_full', 'up_full', 'rr'} in use on `level`: the

@@ -53,12 +53,16 @@ def test_single_level_is_the_coarse_solve(helm, n, bc):
     s = helm.Solver(n, h, k2, bc, coarsest_n=big, coarse_tol=TOL)
     assert s.nlevels == 1
     e = s.vcycle(dev(r)).cpu().numpy()
+    steps, converged = s.coarse_info()
+    assert converged and 0 < steps <= min(256, int(np.prod(shape))), (steps, converged)
     again = s.vcycle(dev(r)).cpu().numpy()
     s.close()
     assert np.array_equal(e, again)  # deterministic: every CTA sums the partials in rank order
     me = oracle.apply(e, k2, h, bc, (1.0, 0.5))  # M = -Lap - (1 + 0.5 i) k^2 (beta2 = -0.5)
     assert np.linalg.norm(r - me) <= 2 * TOL * np.linalg.norm(r)
     t = helm.Solver(n, h, k2, bc, coarsest_n=big)
+    with pytest.raises(helm.HelmError):
+        t.coarse_info()  # the dense inverse keeps no GMRES report
     exact = t.vcycle(dev(r)).cpu().numpy()
     t.close()
     assert rel(e, exact) <= 1e-7  # tol times the coarse operator's condition number, with room
