@@ -174,7 +174,8 @@ typedef struct {
                        rounding).  0 < tol < 1: the paper's own choice (Sec. 5), full GMRES on
                        the coarsest grid from a zero guess until its relative residual is
                        <= tol (the paper uses 1e-11), at most 256 steps, run by one
-                       thread-block cluster; one right-hand side at a time (the batched solver
+                       thread-block cluster of 16 CTAs (8 where the GPU cannot place 16); one
+                       right-hand side at a time (the batched solver
                        keeps the dense inverse).  Needs a coarsest grid of at most 4096 unknowns
                        and (257 x that count + 65792) x 16 bytes of device memory. */
 } helm_params;

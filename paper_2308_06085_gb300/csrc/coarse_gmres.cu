@@ -4,7 +4,8 @@
 // dense inverse the library uses by default.
 //
 // The coarsest grid holds at most a few thousand unknowns, too few to fill the GPU and too many
-// for one SM to orthogonalise quickly, so one thread-block cluster of CG_CS CTAs (distributed
+// for one SM to orthogonalise quickly, so one thread-block cluster of 16 CTAs where the GPU
+// can schedule that many (else CG_CS = 8, the portable size) (distributed
 // shared memory, hardware cluster barriers) runs the whole iteration in one launch: each CTA
 // owns a contiguous slice of the grid (one node per thread), applies M on it, and contributes
 // partial inner products that every CTA then sums from the others' shared memory in rank
@@ -61,15 +62,16 @@ __device__ z128 coarse_apply(const Grid& g, const OpCoef<double>& c, const doubl
 }
 
 template <typename TI, typename TO>
-__global__ void __cluster_dims__(CG_CS, 1, 1) __launch_bounds__(CG_NT)
+__global__ void __launch_bounds__(CG_NT)
     k_coarse_gmres(Grid g, OpCoef<double> c, const double* __restrict__ k2, const cx<TI>* __restrict__ b,
                    cx<TO>* __restrict__ e, z128* __restrict__ V, z128* __restrict__ H, int maxit, double tol,
                    double keep, int* __restrict__ info, const int* __restrict__ active) {
   if (active && *active == 0) return;  // read by every thread of every CTA: all return together
   cgr::cluster_group cl = cgr::this_cluster();
   const int rank = (int)cl.block_rank();
+  const int cs = (int)cl.num_blocks();  // the grid is one cluster
   const int n = (int)g.npts();
-  const int chunk = (n + CG_CS - 1) / CG_CS;  // <= CG_NT (n <= CG_CS * CG_NT)
+  const int chunk = (n + cs - 1) / cs;  // <= CG_NT (n <= CG_CS * CG_NT)
   const int p0 = min(rank * chunk, n), p1 = min(p0 + chunk, n), len = p1 - p0;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int p = p0 + t;
@@ -100,7 +102,7 @@ __global__ void __cluster_dims__(CG_CS, 1, 1) __launch_bounds__(CG_NT)
     cl.sync();
     if (t == 0) {
       double s = 0.0;
-      for (int r = 0; r < CG_CS; ++r) s += cl.map_shared_rank(&part[buf][0], r)->re;
+      for (int r = 0; r < cs; ++r) s += cl.map_shared_rank(&part[buf][0], r)->re;
       sval = s;
     }
     __syncthreads();
@@ -127,7 +129,7 @@ __global__ void __cluster_dims__(CG_CS, 1, 1) __launch_bounds__(CG_NT)
     cl.sync();
     for (int i = t; i <= j + wn; i += CG_NT) {
       double re = 0.0, im = 0.0;
-      for (int r = 0; r < CG_CS; ++r) {
+      for (int r = 0; r < cs; ++r) {
         const z128 v = cl.map_shared_rank(&part[buf][0], r)[i];
         re += v.re;
         im += v.im;
@@ -251,8 +253,38 @@ void launch_coarse_gmres(const Grid& g, double s_re, double s_im, const double* 
                          z128* V, z128* H, double tol, double keep, int* info, cudaStream_t st, const int* active) {
   const int n = (int)g.npts();
   const int maxit = n < CG_MAX ? n : CG_MAX;
-  k_coarse_gmres<TI, TO><<<CG_CS, CG_NT, 0, st>>>(g, coef_for<double>(g.h, s_re, s_im, 0.0), k2, b, e, V, H, maxit,
-                                                  tol, keep, info, active);
+  auto kern = k_coarse_gmres<TI, TO>;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(CG_NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  // the cluster size, chosen once: 16 CTAs (a non-portable size) when the GPU can place such a
+  // cluster, else the portable 8 (the first call comes from helm_create's set-up or a first
+  // cycle, before any graph capture)
+  static const int cs = [&] {
+    const bool clean = cudaPeekAtLastError() == cudaSuccess;
+    int ok = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+      cudaLaunchConfig_t q = cfg;
+      cudaLaunchAttribute qa = at[0];
+      qa.val.clusterDim.x = 16;
+      q.gridDim = dim3(16);
+      q.attrs = &qa;
+      if (cudaOccupancyMaxActiveClusters(&ok, kern, &q) != cudaSuccess) ok = 0;
+    }
+    if (clean) cudaGetLastError();  // a refused query leaves no error behind (an earlier one stays)
+    return ok >= 1 ? 16 : CG_CS;
+  }();
+  at[0].val.clusterDim.x = cs;
+  cfg.gridDim = dim3(cs);
+  cudaLaunchKernelEx(&cfg, kern, g, coef_for<double>(g.h, s_re, s_im, 0.0), k2, b, e, V, H, maxit, tol, keep, info,
+                     active);
 }
 template void launch_coarse_gmres<double, double>(const Grid&, double, double, const double*, const z128*, z128*,
                                                   z128*, z128*, double, double, int*, cudaStream_t, const int*);
