@@ -4,15 +4,15 @@
 // dense inverse the library uses by default.
 //
 // The coarsest grid holds at most a few thousand unknowns, too few to fill the GPU and too many
-// for one SM to orthogonalise quickly, so one thread-block cluster of 16 CTAs where the GPU
-// can schedule that many (else CG_CS = 8, the portable size) (distributed
-// shared memory, hardware cluster barriers) runs the whole iteration in one launch: each CTA
-// owns a contiguous slice of the grid (one node per thread), applies M on it, and contributes
-// partial inner products that every CTA then sums from the others' shared memory in rank
-// order, so all CTAs hold the same Hessenberg column, Givens rotations and stopping decision
-// and take every barrier together.  Classical Gram-Schmidt with the library's selective second
-// pass (the reorth_keep test).  The basis lives in global memory
-// (L2-resident); values written during the launch by other CTAs are read through L2 only.
+// for one SM to orthogonalise quickly, so one thread-block cluster (16 CTAs where the GPU can
+// place a cluster that large, else the portable 8; distributed shared memory, hardware cluster
+// barriers) runs the whole iteration in one launch: each CTA owns a contiguous slice of the
+// grid (one node per thread), applies M on it, and contributes partial inner products that
+// every CTA then sums from the others' shared memory in rank order, so all CTAs hold the same
+// Hessenberg column, Givens rotations and stopping decision and take every barrier together.
+// Classical Gram-Schmidt with the library's selective second pass (the reorth_keep test).  The
+// basis lives in global memory (L2-resident); values written during the launch by other CTAs
+// are read through L2 only.
 #include "internal.cuh"
 
 #include <cooperative_groups.h>

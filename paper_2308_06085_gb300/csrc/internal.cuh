@@ -31,10 +31,10 @@ void launch_restrict(const Grid& gf, const Grid& gc, const cx<R>* r, cx<R>* out,
 template <typename R>
 void launch_prolong_add(const Grid& gf, const Grid& gc, const cx<R>* u1, const cx<R>* e, cx<R>* out, cudaStream_t st,
                         const int* active);
-// e = Minv b for nb right-hand sides (node-major, right-hand side innermost)
 // The paper's coarsest-grid solve: full GMRES on M_c e = b from e = 0 to the relative
 // residual tol (at most CG_MAX steps; second Gram-Schmidt pass when the first kept less than
-// `keep` of |w|^2), by one cluster of CG_CS CTAs; V holds (CG_MAX + 1) grid
+// `keep` of |w|^2), by one cluster of 16 CTAs (CG_CS = 8 where the GPU cannot place 16); V
+// holds (CG_MAX + 1) grid
 // vectors and H CG_MAX columns of CG_MAX + 1, both device scratch of the context; info[0] =
 // steps taken, info[1] = 1 when tol was met.  The grid may hold at most CG_CS * 512 unknowns.
 constexpr int CG_CS = 8;
@@ -42,6 +42,7 @@ constexpr int CG_MAX = 256;
 template <typename TI, typename TO>
 void launch_coarse_gmres(const Grid& g, double s_re, double s_im, const double* k2, const cx<TI>* b, cx<TO>* e,
                          z128* V, z128* H, double tol, double keep, int* info, cudaStream_t st, const int* active);
+// e = Minv b for nb right-hand sides (node-major, right-hand side innermost)
 template <typename TI, typename TO>
 void launch_coarse(int nc, const z128* Minv, const cx<TI>* b, cx<TO>* e, cudaStream_t st, const int* active,
                    int nb = 1);
