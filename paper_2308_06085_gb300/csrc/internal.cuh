@@ -34,9 +34,9 @@ void launch_prolong_add(const Grid& gf, const Grid& gc, const cx<R>* u1, const c
 // The paper's coarsest-grid solve: full GMRES on M_c e = b from e = 0 to the relative
 // residual tol (at most CG_MAX steps; second Gram-Schmidt pass when the first kept less than
 // `keep` of |w|^2), by one cluster of 16 CTAs (CG_CS = 8 where the GPU cannot place 16); V
-// holds (CG_MAX + 1) grid
-// vectors and H CG_MAX columns of CG_MAX + 1, both device scratch of the context; info[0] =
-// steps taken, info[1] = 1 when tol was met.  The grid may hold at most CG_CS * 512 unknowns.
+// holds (CG_MAX + 1) grid vectors and H CG_MAX columns of CG_MAX + 1, both device scratch of
+// the context; info[0] = steps taken, info[1] = 1 when tol was met.  The grid may hold at most
+// CG_CS * 512 unknowns.
 constexpr int CG_CS = 8;
 constexpr int CG_MAX = 256;
 template <typename TI, typename TO>
